@@ -1,0 +1,387 @@
+"""Pins of the CPU oracle to facts outside itself (no GPU).
+
+Each test checks the binary128 oracle against exact rational arithmetic
+(``fractions.Fraction``), a closed form, an invariant of the factorization,
+or a library routine on a case where that routine is accurate enough, so
+that a dropped term, a wrong sign or index, or a transposed operand in the
+oracle fails at least one of them.
+"""
+from fractions import Fraction as F
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+U64 = 2.0 ** -53
+
+
+def fr(a):
+    return [[F(float(a[i, j])) for j in range(a.shape[1])] for i in range(a.shape[0])]
+
+
+def dd_fr(hi, lo, i, j):
+    return F(float(hi[i, j])) + F(float(lo[i, j]))
+
+
+def exact_gram(x, y):
+    xs, ys = fr(x), fr(y)
+    n = x.shape[0]
+    return [[sum((xs[r][i] * ys[r][j] for r in range(n)), F(0)) for j in range(y.shape[1])]
+            for i in range(x.shape[1])]
+
+
+def abs_gram(x, y):
+    return np.abs(x).T @ np.abs(y)
+
+
+def wide_range(g, n, k):
+    """Entries with random signs and exponents spread over 2^-30 .. 2^30."""
+    m = g.standard_normal((n, k))
+    e = g.integers(-30, 30, size=(n, k))
+    return np.asfortranarray(np.ldexp(m, e))
+
+
+# ------------------------------------------------------------------ Gram
+
+@pytest.mark.parametrize("n,kx,ky", [(1, 1, 1), (7, 2, 3), (33, 3, 2), (64, 4, 4)])
+def test_gram_matches_exact_rational_sum(n, kx, ky):
+    g = synth.rng(11 + n)
+    x = wide_range(g, n, kx)
+    y = wide_range(g, n, ky)
+    hi, lo = oracle.gram(x, y)
+    ex = exact_gram(x, y)
+    bound = abs_gram(x, y)
+    for i in range(kx):
+        for j in range(ky):
+            err = abs(dd_fr(hi, lo, i, j) - ex[i][j])
+            # n roundings in binary128 plus the split into hi + lo
+            tol = F((n + 1) * 2.0 ** -112) * F(float(bound[i, j])) + F(2.0 ** -105) * abs(ex[i][j])
+            assert err <= tol, (i, j, float(err), float(tol))
+            assert hi[i, j] == float(ex[i][j]) or abs(F(float(hi[i, j])) - ex[i][j]) <= F(U64) * abs(ex[i][j]) * 1.0001
+
+
+def test_gram_symmetric_default_and_transpose():
+    g = synth.rng(5)
+    x = wide_range(g, 40, 3)
+    y = wide_range(g, 40, 5)
+    hxy, _ = oracle.gram(x, y)
+    hyx, _ = oracle.gram(y, x)
+    assert np.array_equal(hxy, hyx.T)
+    hs, ls = oracle.gram(x)
+    hx, lx = oracle.gram(x, x)
+    assert np.array_equal(hs, hx) and np.array_equal(ls, lx)
+    assert np.array_equal(hs, hs.T)
+
+
+def test_gram_f32_matches_exact():
+    g = synth.rng(3)
+    x = g.standard_normal((50, 3)).astype(np.float32)
+    hi, lo = oracle.gram_f32(x)
+    ex = exact_gram(x.astype(np.float64), x.astype(np.float64))
+    for i in range(3):
+        for j in range(3):
+            # FP32 products are exact in 48 bits, so the binary128 sum of 50 of them is exact
+            assert dd_fr(hi, lo, i, j) == ex[i][j]
+
+
+def test_gram_cancellation_is_resolved():
+    # x = [1, 2^-100, -1], y = [1, 1, 1]: every partial sum is exact in binary128
+    # (1 + 2^-100 needs 101 bits), FP64 would return 0
+    x = np.array([[1.0], [2.0 ** -100], [-1.0]])
+    y = np.ones((3, 1))
+    hi, lo = oracle.gram(x, y)
+    assert hi[0, 0] == 2.0 ** -100 and lo[0, 0] == 0.0
+
+
+# ------------------------------------------------------------ projection
+
+def test_project_matches_exact_rational():
+    g = synth.rng(21)
+    n, kv, k = 24, 3, 2
+    v = g.standard_normal((n, kv))
+    y = g.standard_normal((n, k))
+    yt, (chi, clo), (mhi, mlo) = oracle.project(v, y)
+    vs, ys = fr(v), fr(y)
+    c = [[sum((vs[r][i] * ys[r][j] for r in range(n)), F(0)) for j in range(k)] for i in range(kv)]
+    for i in range(kv):
+        for j in range(k):
+            assert abs(dd_fr(chi, clo, i, j) - c[i][j]) <= F(2.0 ** -104) * (abs(c[i][j]) + 1)
+    for r in range(n):
+        for j in range(k):
+            ex = ys[r][j] - sum((vs[r][i] * c[i][j] for i in range(kv)), F(0))
+            # rounded once; the binary128 C perturbs the exact value far below one FP64 ulp
+            assert abs(F(float(yt[r, j])) - ex) <= F(0.5 * U64 * 2) * abs(ex) * F(1.000001) + F(2.0 ** -200)
+    ex_m = exact_gram(yt, yt)
+    for i in range(k):
+        for j in range(k):
+            assert abs(dd_fr(mhi, mlo, i, j) - ex_m[i][j]) <= F(2.0 ** -104) * (abs(ex_m[i][j]) + 1)
+
+
+def test_project_special_cases():
+    v = synth.orthonormal_basis(200, 4, 7)
+    a = synth.rng(8).standard_normal((4, 2))
+    # Y in span(V): the projection leaves a residual at the FP64 rounding level of Y
+    y_in = np.asfortranarray(v @ a)
+    yt, (chi, _), _ = oracle.project(v, y_in)
+    assert np.max(np.abs(yt)) < 1e-14 * np.max(np.abs(y_in))
+    np.testing.assert_allclose(chi, a, rtol=0, atol=1e-14)
+    # Y orthogonal to V (built from the complement): Y~ = Y and C ~ 0
+    full = synth.orthonormal_basis(200, 6, 7)
+    y_perp = np.asfortranarray(full[:, 4:6] * 3.0)
+    yt2, (c2, _), _ = oracle.project(full[:, :4], y_perp)
+    assert np.max(np.abs(c2)) < 1e-14
+    np.testing.assert_allclose(yt2, y_perp, rtol=0, atol=1e-14)
+
+
+# -------------------------------------------------------------- Cholesky
+
+def spd(k, kappa, seed):
+    x = synth.conditioned(4 * k + 8, k, kappa, seed)
+    return oracle.gram(x)
+
+
+def test_cholesky_diagonal_closed_form():
+    d = np.array([4.0, 2.0, 9.0, 1e-8])
+    m = np.diag(d)
+    r_hi, r_lo, info = oracle.cholesky(m)
+    assert info == 0
+    for i in range(4):
+        assert r_hi[i, i] == np.sqrt(d[i])  # IEEE sqrt is correctly rounded; so is hi
+        assert abs((F(float(r_hi[i, i])) + F(float(r_lo[i, i]))) ** 2 - F(float(d[i]))) <= F(2.0 ** -104) * F(float(d[i]))
+    assert np.count_nonzero(r_hi - np.diag(np.diag(r_hi))) == 0
+
+
+@pytest.mark.parametrize("k,kappa", [(2, 10.0), (5, 1e3), (8, 1e6)])
+def test_cholesky_reconstructs_m(k, kappa):
+    m_hi, m_lo = spd(k, kappa, 40 + k)
+    r_hi, r_lo, info = oracle.cholesky(m_hi, m_lo)
+    assert info == 0
+    assert np.all(np.diag(r_hi) > 0)
+    assert np.all(np.tril(r_hi, -1) == 0)
+    for i in range(k):
+        for j in range(i, k):
+            rtr = sum(((F(float(r_hi[l, i])) + F(float(r_lo[l, i]))) * (F(float(r_hi[l, j])) + F(float(r_lo[l, j])))
+                       for l in range(k)), F(0))
+            mij = dd_fr(m_hi, m_lo, i, j)
+            scale = F(float(np.sqrt(m_hi[i, i] * m_hi[j, j])))
+            assert abs(rtr - mij) <= F(2.0 ** -100) * scale
+
+
+def test_cholesky_agrees_with_lapack_when_well_conditioned():
+    m_hi, m_lo = spd(6, 1e2, 77)
+    r_hi, _, info = oracle.cholesky(m_hi, m_lo)
+    assert info == 0
+    lap = np.linalg.cholesky(m_hi + m_lo).T
+    np.testing.assert_allclose(r_hi, lap, rtol=1e-12, atol=1e-13 * np.max(np.abs(lap)))
+
+
+def test_cholesky_breakdown_reports_column():
+    assert oracle.cholesky(np.array([[1.0, 2.0], [2.0, 1.0]]))[2] == 2
+    assert oracle.cholesky(np.array([[0.0, 0.0], [0.0, 1.0]]))[2] == 1
+    assert oracle.cholesky(np.array([[-1.0]]))[2] == 1
+    # exactly singular rank-one matrix x x^T with x = [1, 2, 3]: pivot 2 is exactly zero
+    x = np.array([1.0, 2.0, 3.0])
+    assert oracle.cholesky(np.outer(x, x))[2] == 2
+
+
+def test_triinv_is_inverse():
+    m_hi, m_lo = spd(6, 1e4, 91)
+    r_hi, r_lo, _ = oracle.cholesky(m_hi, m_lo)
+    z_hi, z_lo = oracle.triinv(r_hi, r_lo)
+    assert np.all(np.tril(z_hi, -1) == 0)
+    k = 6
+    for i in range(k):
+        for j in range(k):
+            s = sum(((F(float(r_hi[i, l])) + F(float(r_lo[i, l]))) * (F(float(z_hi[l, j])) + F(float(z_lo[l, j])))
+                     for l in range(k)), F(0))
+            assert abs(s - (1 if i == j else 0)) <= F(2.0 ** -98) * F(1e4)
+    np.testing.assert_allclose(z_hi, np.linalg.inv(r_hi + r_lo), rtol=1e-10, atol=1e-12 * np.max(np.abs(z_hi)))
+
+
+# ---------------------------------------------------------------- Jacobi
+
+def test_jacobi_2x2_closed_form():
+    import mpmath as mp
+    mp.mp.prec = 200
+    a, b, c = 2.0, 0.75, -1.25
+    (lh, ll), u = oracle.jacobi(np.array([[a, b], [b, c]]))
+    lam = sorted(mp.mpf(h) + mp.mpf(l) for h, l in zip(lh, ll))
+    mid = (mp.mpf(a) + c) / 2
+    rad = mp.sqrt(((mp.mpf(a) - c) / 2) ** 2 + mp.mpf(b) ** 2)
+    assert abs(lam[0] - (mid - rad)) < mp.mpf(2) ** -104
+    assert abs(lam[1] - (mid + rad)) < mp.mpf(2) ** -104
+
+
+@pytest.mark.parametrize("k,kappa", [(3, 10.0), (8, 1e6), (16, 1e12)])
+def test_jacobi_invariants(k, kappa):
+    m_hi, m_lo = spd(k, kappa, 300 + k)
+    (lh, ll), u = oracle.jacobi(m_hi, m_lo)
+    # eigenvectors orthonormal to FP64 rounding (U is returned rounded to FP64)
+    assert np.max(np.abs(u.T @ u - np.eye(k))) < 10 * k * U64
+    # eigenvalues equal the squared singular values built into the generator
+    lam = np.sort(lh + ll)[::-1]
+    sig = synth.logspace_sigma(k, kappa)
+    ref = sig ** 2
+    assert np.max(np.abs(lam - ref) / ref) < 1e3 * U64 * kappa  # FP64 input X perturbs sigma_min by ~u*kappa
+    # library check where the library is accurate
+    np.testing.assert_allclose(np.sort(lh), np.linalg.eigvalsh(m_hi + m_lo), rtol=0,
+                               atol=50 * k * U64 * np.max(lh))
+
+
+def test_jacobi_diagonal_is_fixed_point():
+    d = np.array([3.0, 1.0, 2.0])
+    (lh, ll), u = oracle.jacobi(np.diag(d))
+    assert np.array_equal(lh, d) and np.array_equal(u, np.eye(3))
+
+
+# ------------------------------------------------------------- SVQB's Z
+
+@pytest.mark.parametrize("k,kappa", [(2, 1.0), (6, 1e3), (8, 1e8)])
+def test_svqb_z_is_inverse_square_root(k, kappa):
+    import mpmath as mp
+    mp.mp.prec = 240
+    m_hi, m_lo = spd(k, kappa, 500 + k)
+    z_hi, z_lo, rank = oracle.svqb_z(m_hi, m_lo)
+    assert rank == k
+    assert np.array_equal(z_hi, z_hi.T)
+    Z = mp.matrix(k, k)
+    M = mp.matrix(k, k)
+    for i in range(k):
+        for j in range(k):
+            Z[i, j] = mp.mpf(z_hi[i, j]) + mp.mpf(z_lo[i, j])
+            M[i, j] = mp.mpf(m_hi[i, j]) + mp.mpf(m_lo[i, j])
+    E = Z.T * M * Z - mp.eye(k)
+    # binary128 eigen-solve of M with condition kappa^2: error ~ k * kappa^2 * 2^-113
+    assert max(abs(E[i, j]) for i in range(k) for j in range(k)) < mp.mpf(2) ** -108 * k * max(kappa, 1e4) ** 2
+
+
+def test_svqb_z_identity_and_library():
+    z_hi, z_lo, rank = oracle.svqb_z(np.eye(4))
+    assert rank == 4 and np.array_equal(z_hi, np.eye(4)) and not np.any(z_lo)
+    import scipy.linalg as sl
+    m_hi, m_lo = spd(5, 30.0, 61)
+    z_hi, _, _ = oracle.svqb_z(m_hi, m_lo)
+    ref = np.linalg.inv(np.real(sl.sqrtm(m_hi + m_lo)))
+    np.testing.assert_allclose(z_hi, ref, rtol=1e-11, atol=1e-12 * np.max(np.abs(ref)))
+
+
+def test_svqb_z_rank_cut():
+    z_hi, _, rank = oracle.svqb_z(np.diag([1.0, 1e-20, 4.0]), tol=1e-10)
+    assert rank == 2
+    np.testing.assert_array_equal(z_hi, np.diag([1.0, 0.0, 0.5]))
+
+
+# ------------------------------------------------------- CholQR / SVQB
+
+@pytest.mark.parametrize("kappa", [1.0, 1e4, 1e8, 1e12])
+def test_cholqr_invariants(kappa):
+    n, k = 300, 6
+    x = synth.conditioned(n, k, kappa, 900)
+    q, (r_hi, r_lo), info = oracle.cholqr(x, passes=1)
+    assert info == 0
+    two, fro, mx = oracle.orth_err(q)
+    # binary128 CholQR loses orthogonality like kappa^2 * u_128 (u_128 = 2^-113);
+    # on top of that Q is rounded once to FP64
+    assert two < 4 * k * U64 + kappa ** 2 * 2.0 ** -111
+    if kappa >= 1e12:
+        assert two > kappa ** 2 * 2.0 ** -120  # the kappa^2 law of the quad arithmetic is visible
+    assert oracle.fact_err(x, q, r_hi, r_lo) < 4 * U64 * np.sqrt(k)
+    assert np.all(np.diag(r_hi) > 0) and np.all(np.tril(r_hi, -1) == 0)
+    sv = np.linalg.svd(r_hi + r_lo, compute_uv=False)
+    sig = synth.logspace_sigma(k, kappa)
+    assert np.max(np.abs(sv - sig)) < 1e2 * U64 * np.sqrt(n)
+
+
+def test_cholqr_k1_is_normalization():
+    g = synth.rng(1)
+    x = g.standard_normal((37, 1))
+    q, (r_hi, r_lo), info = oracle.cholqr(x)
+    ss = sum((F(float(v)) ** 2 for v in x[:, 0]), F(0))
+    r = F(float(r_hi[0, 0])) + F(float(r_lo[0, 0]))
+    assert abs(r * r - ss) <= F(2.0 ** -104) * ss
+    for i in range(37):
+        ex = F(float(x[i, 0])) / r
+        assert abs(F(float(q[i, 0])) - ex) <= F(U64) * abs(ex) * F(1.0000001)
+
+
+def test_cholqr_orthonormal_and_orthogonal_inputs():
+    u = synth.orthonormal_basis(100, 5, 3)
+    q, (r_hi, _), info = oracle.cholqr(u)
+    assert info == 0
+    np.testing.assert_allclose(r_hi, np.eye(5), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(q, u, rtol=0, atol=4 * U64)
+    s = np.array([1.0, 1e3, 1e-3, 7.0, 0.5])
+    q2, (r2, _), _ = oracle.cholqr(np.asfortranarray(u * s))
+    np.testing.assert_allclose(np.diag(r2), s, rtol=1e-14)
+    off = r2 - np.diag(np.diag(r2))
+    assert np.max(np.abs(off)) < 1e-14 * np.max(s)
+
+
+def test_cholqr_two_passes_and_given_gram():
+    x = synth.conditioned(200, 4, 1e6, 17)
+    q1, (r1h, r1l), _ = oracle.cholqr(x, passes=1)
+    q2, (r2h, r2l), _ = oracle.cholqr(x, passes=2)
+    assert oracle.fact_err(x, q2, r2h, r2l) < 8 * U64
+    assert oracle.orth_err(q2)[0] < 8 * U64
+    m = oracle.gram(x)
+    q3, (r3h, _), _ = oracle.cholqr(x, passes=1, m=m)
+    assert np.array_equal(q3, q1) and np.array_equal(r3h, r1h)
+
+
+def test_cholqr_breakdown_leaves_x():
+    x = np.asfortranarray(np.ones((10, 2)))  # exactly rank one
+    q, _, info = oracle.cholqr(x)
+    assert info == 2
+    assert np.array_equal(q, x)
+
+
+@pytest.mark.parametrize("kappa", [1.0, 1e6, 1e10])
+def test_svqb_invariants(kappa):
+    x = synth.conditioned(250, 5, kappa, 4242)
+    q, (z_hi, z_lo), rank = oracle.svqb(x)
+    assert rank == 5
+    assert oracle.orth_err(q)[0] < 20 * U64 + kappa ** 2 * 2.0 ** -111  # same kappa^2 u_128 law
+    assert np.array_equal(z_hi, z_hi.T)
+    # X Z = Q (the update is the only step after Z)
+    np.testing.assert_allclose(x @ (z_hi + z_lo), q, rtol=0, atol=1e-12 * kappa * np.max(np.abs(q)))
+
+
+def test_svqb_orthogonal_columns_give_diagonal_z():
+    u = synth.orthonormal_basis(80, 3, 9)
+    s = np.array([2.0, 0.25, 8.0])
+    q, (z_hi, _), rank = oracle.svqb(np.asfortranarray(u * s))
+    np.testing.assert_allclose(z_hi, np.diag(1 / s), rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(q, u, rtol=0, atol=8 * U64)
+
+
+# --------------------------------------------------------------- measures
+
+def test_orth_err_closed_forms():
+    q = np.array([[1.0], [2.0 ** -20]])  # Q^T Q - I = 2^-40
+    two, fro, mx = oracle.orth_err(q)
+    assert two == 2.0 ** -40 and fro == 2.0 ** -40 and mx == 2.0 ** -40
+    d1, d2 = 2.0 ** -10, -(2.0 ** -12)
+    q2 = np.diag([1 + d1, 1 + d2])
+    e1, e2 = 2 * d1 + d1 * d1, 2 * d2 + d2 * d2
+    two, fro, mx = oracle.orth_err(q2)
+    assert two == max(abs(e1), abs(e2))
+    assert abs(fro - np.hypot(e1, e2)) <= U64 * fro
+    # a rotation-like off-diagonal perturbation: E = [[0, e],[e, 0]] has 2-norm |e|
+    c = 2.0 ** -15
+    q3 = np.array([[1.0, c], [0.0, 1.0]])  # Q^T Q = [[1, c], [c, 1 + c^2]]
+    two, fro, mx = oracle.orth_err(q3)
+    lam = abs(c * c / 2) + np.sqrt((c * c / 2) ** 2 + c * c)
+    assert abs(two - lam) <= 4 * U64 * lam
+
+
+def test_cross_err_and_fact_err_closed_forms():
+    w = np.zeros((4, 1)); w[0, 0] = 1.0
+    q = np.array([[0.25, -3.0], [1.0, 0.0], [0.0, 4.0], [0.0, 0.0]])
+    assert oracle.cross_err(w, q) == np.hypot(0.25, 3.0)
+    x = np.array([[3.0], [4.0]])
+    qq = np.array([[0.375], [0.5]])  # exact binary fractions: Q R = X for R = 8
+    assert oracle.fact_err(x, qq, np.array([[8.0]])) == 0.0
+    # R = 8.5: X - Q R = [-0.1875, -0.25], norm 0.3125 = ||X|| / 16
+    assert oracle.fact_err(x, qq, np.array([[8.5]])) == 0.0625
