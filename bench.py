@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the block-orthogonalization hot path on one GB300 (or N replicas).
+
+Workload (one "step" = one pass of the whole path over one block):
+  V: 4,000,000 x 64 FP64 orthonormal basis, Y: 4,000,000 x 16 FP64 with
+  singular values log-spaced 1 .. 1e-10 (seeded, synthetic; see synth.py).
+  step = eo_project (C = V^T Y, Y~ = Y - V C with M = Y~^T Y~ fused, DD)
+       + eo_cholqr  (DD, first pass from the fused M, automatic second pass).
+The inputs (2.6 GB per step) are larger than L2 (129 MB), so no flush is
+needed between steps.
+
+Prints ONE JSON line.  `value` is algorithmic HBM bytes / device time (GB/s)
+over all ranks; `e2e` is the same metric through the C-ABI with the inputs in
+pinned host memory and the host<->device copies inside the timed region.
+`--impl reference` times the binary128 CPU oracle on a bounded row sample of
+the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gram/CholQR HBM GB/s and blocks/s at ||Q^TQ-I||<=1e-14, DD vs plain FP64; p50/p99"
+WORKLOAD = "projection plus orthogonalization: V 4,000,000x64 orthonormal FP64, Y 4,000,000x16 FP64 (sigma 1..1e-10); V^T Y, Y - V(V^T Y), DD-Gram CholQR"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["eo", "reference"], default="eo")
+    ap.add_argument("--n", type=int, default=4_000_000)
+    ap.add_argument("--kv", type=int, default=64)
+    ap.add_argument("--k", type=int, default=16)
+    ap.add_argument("--kappa", type=float, default=1e10)
+    ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU-oracle sample (0 = auto)")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def step_bytes(n, kv, k, two_passes):
+    """Algorithmic HBM bytes of one step: what the method must read and write.
+
+    V^T Y reads V and Y; the fused pass reads V and Y and writes Y~; the first
+    CholQR update reads and writes Y~; a second pass reads Q for its Gram
+    matrix and reads and writes it in its update."""
+    b = 8 * n * (kv + k) + 8 * n * (kv + 2 * k) + 16 * n * k
+    if two_passes:
+        b += 8 * n * k + 16 * n * k
+    return b
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def cpu_sample(v, y, rows, passes=2):
+    """Time the oracle's projection + CholQR on the first `rows` rows."""
+    import oracle
+    vs = np.asfortranarray(v[:rows])
+    ys = np.asfortranarray(y[:rows])
+    t0 = time.perf_counter()
+    yt, _, m = oracle.project(vs, ys)
+    oracle.cholqr(yt, passes=passes, m=m)
+    dt = time.perf_counter() - t0
+    return dt, step_bytes(rows, v.shape[1], y.shape[1], passes == 2)
+
+
+def cpu_baseline(v, y, rows):
+    import oracle
+    if rows <= 0:  # calibrate to ~10-20 s of work
+        rows = min(v.shape[0], 4096)
+        dt, _ = cpu_sample(v, y, rows)
+        target = 12.0
+        rows = int(min(v.shape[0], max(4096, rows * target / max(dt, 1e-3))))
+    dt, nbytes = cpu_sample(v, y, rows)
+    return {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"first {rows} rows of the same V and Y, binary128 projection + 2-pass CholQR, {dt:.1f} s"}
+
+
+# -------------------------------------------------------------- clocks
+
+class Clocks:
+    def __init__(self, path, index):
+        self.path = path
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [s.strip() for s in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------- GPU arm
+
+def run_eo(a):
+    import torch
+    import torch.distributed as dist
+    import paper_1806_01036_gb300 as eo
+    import synth
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    n, kv, k = a.n, a.kv, a.k
+    v_np, y_np = synth.project_block(seed=synth.SEED_BASE + 1 + 1000 * rank, n=n, kv=kv, k=k, kappa=a.kappa)
+
+    def to_dev(x):
+        return torch.from_numpy(np.ascontiguousarray(x.T)).to(dev).t()
+
+    V, Y = to_dev(v_np), to_dev(y_np)
+    Yt = torch.empty((k, n), dtype=torch.float64, device=dev).t()
+    ctx = eo.Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        _, _, m = eo.project(ctx, V, Y, Yout=Yt, prec=eo.DD)
+        return eo.cholqr(ctx, Yt, passes=0, prec=eo.DD, M=m)
+
+    for _ in range(max(3, a.warmup)):
+        rh, rl, info = step()
+    torch.cuda.synchronize()
+    info0 = int(info.item())
+    rd = torch.diagonal(rh).abs()
+    two_passes = bool((rd.max() / rd.min()).item() > 1e7)
+    # orthogonality of the result, measured with the library's own DD Gram
+    gh, gl = eo.gram(ctx, Yt, prec=eo.DD)
+    orth = float(torch.linalg.matrix_norm(gh - torch.eye(k, dtype=torch.float64, device=dev) + gl, ord=2).item())
+    cross = eo.gram(ctx, V, Yt, prec=eo.DD)
+    cross_err = float(torch.linalg.matrix_norm(cross[0] + cross[1], ord=2).item())
+
+    nbytes = step_bytes(n, kv, k, two_passes)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = ctx.launches()
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/eo_clocks_{os.getpid()}.csv", local)
+    with clk:
+        t_all0 = torch.cuda.Event(enable_timing=True)
+        t_all1 = torch.cuda.Event(enable_timing=True)
+        t_all0.record(stream)
+        for i in range(a.steps):
+            ev[i][0].record(stream)
+            _, _, m = eo.project(ctx, V, Y, Yout=Yt, prec=eo.DD)
+            ev[i][1].record(stream)
+            eo.cholqr(ctx, Yt, passes=0, prec=eo.DD, M=m)
+            ev[i][2].record(stream)
+        t_all1.record(stream)
+        torch.cuda.synchronize()
+    launches = ctx.launches() - l0
+    if ws > 1:
+        dist.barrier()
+    total_ms = t_all0.elapsed_time(t_all1)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    per = [e[0].elapsed_time(e[2]) for e in ev]
+    proj_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    chol_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    ms = total_ms / a.steps
+    value = ws * nbytes / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant launch sequence (the projection call)
+    peak, peak_kind = peak_hbm()
+    proj_bytes = 8 * n * (kv + k) + 8 * n * (kv + 2 * k)
+    achieved = proj_bytes / (proj_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "eo_project (V^T Y Gram + fused projection/Gram pass)",
+            "peak_source": peak_kind, "launch_ms": proj_ms, "cholqr_ms": chol_ms}
+
+    # plain FP64 comparator on the same input (two passes; breaks down at this kappa)
+    Yp = torch.empty_like(Yt.t()).t()
+    comp = {}
+    try:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, mp = eo.project(ctx, V, Y, Yout=Yp, prec=eo.FP64)
+        _, _, infop = eo.cholqr(ctx, Yp, passes=2, prec=eo.FP64, M=mp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tms = e0.elapsed_time(e1)
+        comp = {"prec": "fp64", "ms_per_step": tms, "value": step_bytes(n, kv, k, True) / (tms * 1e-3) / 1e9,
+                "cholesky_info": int(infop.item())}
+    except Exception as ex:  # pragma: no cover - reporting only
+        comp = {"error": str(ex)}
+    del Yp
+
+    # end to end through the C-ABI with pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        Vh = torch.from_numpy(np.ascontiguousarray(v_np.T)).pin_memory()
+        Yh = torch.from_numpy(np.ascontiguousarray(y_np.T)).pin_memory()
+        Qh = torch.empty((k, n), dtype=torch.float64).pin_memory()
+        Rh = torch.empty((k, k), dtype=torch.float64).pin_memory()
+        Vd = torch.empty((kv, n), dtype=torch.float64, device=dev)
+        Yd = torch.empty((k, n), dtype=torch.float64, device=dev)
+        Qd = torch.empty((k, n), dtype=torch.float64, device=dev)
+
+        def e2e_step():
+            Vd.copy_(Vh, non_blocking=True)
+            Yd.copy_(Yh, non_blocking=True)
+            _, _, m = eo.project(ctx, Vd.t(), Yd.t(), Yout=Qd.t(), prec=eo.DD)
+            r, _, _ = eo.cholqr(ctx, Qd.t(), passes=0, prec=eo.DD, M=m)
+            Qh.copy_(Qd, non_blocking=True)
+            Rh.copy_(r.t(), non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ke = max(1, min(a.steps, 5))
+        s0.record(stream)
+        for _ in range(ke):
+            e2e_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ems = s0.elapsed_time(s1) / ke
+        if ws > 1:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": ws * nbytes / (ems * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ems,
+               "h2d_bytes_per_step": 8 * n * (kv + k), "d2h_bytes_per_step": 8 * n * k + 8 * k * k}
+
+    cpu = None
+    if rank == 0 and not a.no_cpu:
+        cpu = cpu_baseline(v_np, y_np, a.cpu_rows)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded; V Haar-orthonormal, Y = U diag(sigma) W^T, sigma 1..1e-10)",
+        "config": {"workload": WORKLOAD, "n": n, "kv": kv, "k": k, "kappa": a.kappa, "prec": "dd",
+                   "passes": 2 if two_passes else 1, "parallelism": f"replicas x{ws}",
+                   "l2": "inputs (2.6 GB/step) larger than L2; no flush"},
+        "blocks_per_s": ws * 1000.0 / ms, "p50_ms": float(np.percentile(per, 50)),
+        "p99_ms": float(np.percentile(per, 99)),
+        "orth_err": orth, "cross_err": cross_err, "cholesky_info": info0,
+        "bytes_per_step": nbytes, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "clocks": clk.summary(), "gpu_launches": launches, "fp64_comparator": comp,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------- reference arm
+
+def run_reference(a):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import synth
+    rows = a.cpu_rows if a.cpu_rows > 0 else 20_000
+    n, kv, k = a.n, a.kv, a.k
+    v_np = synth.orthonormal_basis(rows, kv, synth.SEED_BASE + 1)
+    y_np = synth.conditioned(rows, k, a.kappa, synth.SEED_BASE + 1 + 1000)
+    for _ in range(a.warmup):
+        cpu_sample(v_np, y_np, rows)
+    times = []
+    nbytes = 0
+    for _ in range(a.steps):
+        dt, nbytes = cpu_sample(v_np, y_np, rows)
+        times.append(dt)
+    ms = 1000 * statistics.mean(times)
+    value = nbytes / (ms * 1e-3) / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f128", "data": "synthetic (seeded, same recipe)",
+           "config": {"workload": WORKLOAD, "n": n, "kv": kv, "k": k, "kappa": a.kappa, "sample_rows": rows},
+           "cpu_baseline": {"value": value, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
+                            "sample": f"{rows} rows per step of the same workload recipe"},
+           "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_eo(a)
+
+
+if __name__ == "__main__":
+    main()

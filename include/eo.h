@@ -1,0 +1,146 @@
+/*
+ * eo.h — block orthogonalization on one GPU (NVIDIA GB300, sm_103a).
+ *
+ * The operations are those of the two-phase orthogonalization of
+ * arXiv:1806.01036, Sec. 4.2 ("Using higher precision for robust and fast
+ * orthogonalization"): given a block X (n-by-k) and an orthonormal basis W
+ * (n-by-kv; called V here), phase I forms Y~ = (I - V V^T) X, phase II builds
+ * the Gram matrix M = Y~^T Y~, finds Z with Z^T M Z = I (Cholesky: Z = R^{-1};
+ * SVQB: Z from M = U Lambda U^T) and returns Y = Y~ Z.  Each call runs in one
+ * of three precisions (eo_prec): plain FP64, FP64 data with double-double
+ * ("DD") accumulation as in the paper's DD kernels, or FP32 data with FP64
+ * accumulation.
+ *
+ * Conventions shared by every call
+ *  - Matrices are column-major with a leading dimension (ld*) >= rows.  Large
+ *    matrices (n rows) are DEVICE pointers; they are borrowed, never freed.
+ *  - Small matrices (k-by-k, kv-by-k) passed in or out are DEVICE pointers.
+ *    A double-double value is the unevaluated sum hi + lo of two FP64 arrays
+ *    with the same layout; every *_lo pointer may be NULL when the low part is
+ *    not wanted (in FP64 and F32 modes the low parts are written as zero).
+ *  - Calls are asynchronous on the context's stream (eo_set_stream) and may
+ *    be captured in a CUDA graph once a first call of the same shape has run
+ *    outside capture (the first call may grow the context's scratch memory).
+ *  - The return value reports argument and CUDA errors only.  Numerical
+ *    outcomes (Cholesky breakdown, SVQB rank) are written to device memory so
+ *    that no call synchronizes with the host.
+ *  - Sizes: 1 <= k, kv <= 64; n >= 0.  A context is not thread-safe; use one
+ *    per host thread.
+ *  - Ownership: the context owns its scratch memory (grown on demand, freed by
+ *    eo_destroy); the caller owns every pointer it passes.
+ */
+#ifndef EO_H
+#define EO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EO_KMAX 64
+
+#if defined(__GNUC__)
+#define EO_API __attribute__((visibility("default")))
+#else
+#define EO_API
+#endif
+
+/* Arithmetic of a call (Sec. 4.2: FP64 vs DD kernels; the FP32-input mode
+ * is the building block of the single-precision iterations of Sec. 4.1). */
+typedef enum {
+  EO_FP64 = 0, /* FP64 data, FP64 accumulation                                   */
+  EO_DD = 1,   /* FP64 data, double-double accumulation, results rounded once     */
+  EO_F32 = 2   /* FP32 data (float*), FP64 accumulation of the exact products     */
+} eo_prec;
+
+typedef enum {
+  EO_OK = 0,
+  EO_EINVAL = 1,      /* bad argument (size, leading dimension, NULL pointer, mode) */
+  EO_ENOMEM = 2,      /* scratch allocation failed                                   */
+  EO_ECUDA = 3,       /* a CUDA call or kernel launch failed (see eo_last_error)     */
+  EO_ETIMEOUT = 4,    /* a bounded device-side wait expired                          */
+  EO_EUNSUPPORTED = 5 /* valid but not implemented combination                       */
+} eo_status;
+
+typedef struct eo_ctx eo_ctx;
+
+/* Create a context on CUDA device `device` (made current for the call).
+ * The context starts on the legacy default stream. */
+EO_API eo_status eo_create(eo_ctx** ctx, int device);
+EO_API eo_status eo_destroy(eo_ctx* ctx);
+/* Borrow a cudaStream_t for all later calls (NULL = default stream). */
+EO_API eo_status eo_set_stream(eo_ctx* ctx, void* cuda_stream);
+/* Text of the last error on this context ("" if none).  Owned by the context. */
+EO_API const char* eo_last_error(const eo_ctx* ctx);
+EO_API int eo_version(void);
+/* Number of kernels this context has launched so far (diagnostics). */
+EO_API uint64_t eo_kernel_launches(const eo_ctx* ctx);
+
+/*
+ * Gram product G = X^T Y (kx-by-ky), the matrix-matrix product that carries
+ * "the bulk of computation" of phase II (Sec. 4.2, M = Y~^T Y~) and, with
+ * Y = X and X = W, the W^T X of phase I.
+ *   X: n-by-kx, Y: n-by-ky (Y == NULL: Y = X and ky must equal kx; G is then
+ *   symmetric and both triangles are written).  FP64 data, or float data in
+ *   EO_F32 mode.  G_hi (required) / G_lo: kx-by-ky with leading dimension ldg.
+ * EO_DD: every G_ij is the double-double rounding of the sum of the exact
+ * products (error far below 2^-100 |X|^T|Y| for these sizes); results do not
+ * depend on the launch configuration.
+ */
+EO_API eo_status eo_gram(eo_ctx* ctx, int64_t n, int kx, const void* X, int64_t ldx, int ky, const void* Y, int64_t ldy,
+                  double* G_hi, double* G_lo, int ldg, eo_prec prec);
+
+/*
+ * Phase I projection against an orthonormal basis V (Sec. 4.2:
+ * Y~ = (I - W W^T) X), with the phase-II Gram matrix of the result fused into
+ * the same pass over the data (the paper's "kernel fusion").
+ *   V: n-by-kv, Y: n-by-k (FP64).  C = V^T Y is written to C_hi/C_lo (kv-by-k,
+ *   ldc; C_hi may be NULL).  Yout (n-by-k, ldyo) receives Y - V C, rounded
+ *   once to FP64; Yout may equal Y (in place) but must not otherwise overlap
+ *   it.  If M_hi != NULL, M = Yout^T Yout of the rounded result (k-by-k, ldm)
+ *   is accumulated in the same pass.
+ * EO_F32 is not supported (EO_EUNSUPPORTED).
+ */
+EO_API eo_status eo_project(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y,
+                     int64_t ldy, double* Yout, int64_t ldyo, double* C_hi, double* C_lo, int ldc, double* M_hi,
+                     double* M_lo, int ldm, eo_prec prec);
+
+/*
+ * Cholesky QR (Sec. 4.2: M = R^T R, Z = R^{-1}, Y = Y~ Z): X <- Q in place.
+ *   X: n-by-k (FP64, or float in EO_F32 mode), ldx.
+ *   M_hi/M_lo: optional Gram matrix of X for the first pass (as produced by
+ *   eo_project's fused pass); NULL = compute it.
+ *   R_hi/R_lo: optional k-by-k outputs (ldr): upper-triangular R with positive
+ *   diagonal and X_in = Q R (R is the product of the passes' factors).
+ *   passes: 1 or 2, or 0 = automatic (a second pass runs, on the device, when
+ *   the first factor's diagonal ratio max R_ii / min R_ii exceeds 1e4 in
+ *   EO_FP64/EO_F32 or 1e7 in EO_DD).
+ *   info_dev: optional device int: 0 on success, j >= 1 if the j-th pivot of a
+ *   pass was not positive (X then keeps the last completed pass), -1 if M had a
+ *   NaN or Inf.
+ */
+EO_API eo_status eo_cholqr(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, const double* M_hi, const double* M_lo,
+                    int ldm, double* R_hi, double* R_lo, int ldr, int passes, eo_prec prec, int* info_dev);
+
+/*
+ * SVQB (Sec. 4.2: M = U Lambda U^T, Y = Y~ Z): X <- X Z in place with the
+ * symmetric Z = U Lambda^{-1/2} U^T = M^{-1/2}, the solution of
+ * min ||Z - I||_F subject to Z^T M Z = I (the Procrustes argument of the same
+ * section).  Eigenvalues at or below tol * lambda_max are treated as zero
+ * (Z uses the pseudo-inverse square root, and the result spans the numerical
+ * range of X); tol < 0 selects k * 2^-52 (FP64, F32) or k * 2^-104 (DD).
+ *   M_hi/M_lo: optional Gram matrix for the first pass (NULL = compute).
+ *   Z_hi/Z_lo: optional k-by-k output (ldz), the product of the passes' Z.
+ *   passes: 1 or 2 (0 = automatic as in eo_cholqr, from lambda_max/lambda_min).
+ *   rank_dev: optional device int, the number of eigenvalues kept in the
+ *   last pass, or -1 if M had a NaN or Inf.
+ */
+EO_API eo_status eo_svqb(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, const double* M_hi, const double* M_lo,
+                  int ldm, double* Z_hi, double* Z_lo, int ldz, double tol, int passes, eo_prec prec, int* rank_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EO_H */

@@ -1,0 +1,199 @@
+"""Python binding of libeo (include/eo.h): block orthogonalization on one GPU.
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+Matrices are torch tensors on the GPU in column-major layout, i.e. an n-by-k
+matrix is a tensor of shape (n, k) with stride (1, ld), ld >= n (for example
+``t.t()`` of a contiguous (k, n) tensor, or :func:`colmajor`).  Small k-by-k
+results are returned as FP64 tensors (hi, lo) on the same device.
+
+The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_1806_01036_gb300.build``); importing this module on a
+machine without it raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+FP64, DD, F32 = 0, 1, 2
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
+KMAX = 64
+
+_lib = None
+_p, _i64, _int, _dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+
+
+class EoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"eo status {status}: {msg}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libeo.so (ctypes.CDLL) with argument types declared."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError(f"libeo.so is not built ({path}); run __graft_entry__.build()")
+        L = C.CDLL(path)
+        L.eo_version.restype = _int
+        L.eo_kernel_launches.argtypes = [_p]
+        L.eo_kernel_launches.restype = C.c_uint64
+        L.eo_create.argtypes = [C.POINTER(_p), _int]
+        L.eo_destroy.argtypes = [_p]
+        L.eo_set_stream.argtypes = [_p, _p]
+        L.eo_last_error.argtypes = [_p]
+        L.eo_last_error.restype = C.c_char_p
+        L.eo_gram.argtypes = [_p, _i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int, _int]
+        L.eo_project.argtypes = [_p, _i64, _int, _p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _p, _p, _int, _int]
+        L.eo_cholqr.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _int, _int, _p]
+        L.eo_svqb.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _dbl, _int, _int, _p]
+        for f in ("eo_create", "eo_destroy", "eo_set_stream", "eo_gram", "eo_project", "eo_cholqr", "eo_svqb"):
+            getattr(L, f).restype = _int
+        _lib = L
+    return _lib
+
+
+def colmajor(t):
+    """Column-major copy (shape unchanged) of a 2-D tensor."""
+    return t.t().contiguous().t()
+
+
+def _mat(t, name, dtype=None):
+    import torch
+    if t.dim() == 1:
+        t = t.reshape(-1, 1)
+    if t.dim() != 2 or not t.is_cuda:
+        raise ValueError(f"{name} must be a 2-D CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+    if t.shape[0] > 1 and t.stride(0) != 1:
+        raise ValueError(f"{name} must be column-major (stride(0) == 1); use colmajor()")
+    ld = t.stride(1) if t.shape[1] > 1 else max(1, t.shape[0])
+    return t, int(t.shape[0]), int(t.shape[1]), int(max(ld, t.shape[0], 1))
+
+
+def _small(k1, k2, device):
+    import torch
+    hi = torch.zeros((k2, k1), dtype=torch.float64, device=device).t()
+    lo = torch.zeros((k2, k1), dtype=torch.float64, device=device).t()
+    return hi, lo
+
+
+class Context:
+    """An eo_ctx bound to one device; calls run on torch's current stream."""
+
+    def __init__(self, device: int = 0):
+        h = _p()
+        st = lib().eo_create(C.byref(h), int(device))
+        if st != OK:
+            raise EoError(st, "eo_create failed")
+        self.h = h
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().eo_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        lib().eo_set_stream(self.h, C.c_void_p(s.cuda_stream))
+
+    def launches(self) -> int:
+        """Kernels this context has launched (eo_kernel_launches)."""
+        return int(lib().eo_kernel_launches(self.h))
+
+    def check(self, st: int):
+        if st != OK:
+            raise EoError(st, lib().eo_last_error(self.h).decode())
+
+
+def _dtype(prec):
+    import torch
+    return torch.float32 if prec == F32 else torch.float64
+
+
+def gram(ctx: Context, X, Y=None, prec: int = DD, out=None):
+    """(G_hi, G_lo) with G = X^T Y (Y = X when None)."""
+    X, n, kx, ldx = _mat(X, "X", _dtype(prec))
+    if Y is not None:
+        Y, ny, ky, ldy = _mat(Y, "Y", _dtype(prec))
+        if ny != n:
+            raise ValueError("X and Y must have the same number of rows")
+    else:
+        ky, ldy = kx, ldx
+    hi, lo = out if out is not None else _small(kx, ky, X.device)
+    ctx.set_stream()
+    ctx.check(lib().eo_gram(ctx.h, n, kx, X.data_ptr(), ldx, ky, None if Y is None else Y.data_ptr(), ldy,
+                            hi.data_ptr(), None if lo is None else lo.data_ptr(), hi.stride(1) if kx > 0 else 1, prec))
+    return hi, lo
+
+
+def project(ctx: Context, V, Y, Yout=None, prec: int = DD, want_m: bool = True):
+    """(Yout, (C_hi, C_lo), (M_hi, M_lo) or None): Yout = Y - V (V^T Y), M = Yout^T Yout."""
+    import torch
+    V, n, kv, ldv = _mat(V, "V", torch.float64)
+    Y, ny, k, ldy = _mat(Y, "Y", torch.float64)
+    if ny != n:
+        raise ValueError("V and Y must have the same number of rows")
+    if Yout is None:
+        Yout = colmajor(torch.empty((n, k), dtype=torch.float64, device=Y.device))
+    Yout, _, _, ldyo = _mat(Yout, "Yout", torch.float64)
+    ch, cl = _small(kv, k, V.device)
+    mh, ml = _small(k, k, V.device) if want_m else (None, None)
+    ctx.set_stream()
+    ctx.check(lib().eo_project(ctx.h, n, kv, V.data_ptr(), ldv, k, Y.data_ptr(), ldy, Yout.data_ptr(), ldyo,
+                               ch.data_ptr(), cl.data_ptr(), ch.stride(1), None if mh is None else mh.data_ptr(),
+                               None if ml is None else ml.data_ptr(), k, prec))
+    return Yout, (ch, cl), ((mh, ml) if want_m else None)
+
+
+def cholqr(ctx: Context, X, passes: int = 1, prec: int = DD, M=None, info=None):
+    """In place X <- Q.  Returns (R_hi, R_lo, info) with info a device int32 tensor."""
+    import torch
+    X, n, k, ldx = _mat(X, "X", _dtype(prec))
+    rh, rl = _small(k, k, X.device)
+    if info is None:
+        info = torch.zeros(1, dtype=torch.int32, device=X.device)
+    mh, ml, ldm = None, None, k
+    if M is not None:
+        mh, ml = M
+        ldm = mh.stride(1)
+    ctx.set_stream()
+    ctx.check(lib().eo_cholqr(ctx.h, n, k, X.data_ptr(), ldx, None if mh is None else mh.data_ptr(),
+                              None if ml is None else ml.data_ptr(), ldm, rh.data_ptr(), rl.data_ptr(), rh.stride(1),
+                              int(passes), prec, info.data_ptr()))
+    return rh, rl, info
+
+
+def svqb(ctx: Context, X, passes: int = 1, prec: int = DD, tol: float = -1.0, M=None, rank=None):
+    """In place X <- X Z.  Returns (Z_hi, Z_lo, rank) with rank a device int32 tensor."""
+    import torch
+    X, n, k, ldx = _mat(X, "X", _dtype(prec))
+    zh, zl = _small(k, k, X.device)
+    if rank is None:
+        rank = torch.zeros(1, dtype=torch.int32, device=X.device)
+    mh, ml, ldm = None, None, k
+    if M is not None:
+        mh, ml = M
+        ldm = mh.stride(1)
+    ctx.set_stream()
+    ctx.check(lib().eo_svqb(ctx.h, n, k, X.data_ptr(), ldx, None if mh is None else mh.data_ptr(),
+                            None if ml is None else ml.data_ptr(), ldm, zh.data_ptr(), zl.data_ptr(), zh.stride(1),
+                            float(tol), int(passes), prec, rank.data_ptr()))
+    return zh, zl, rank

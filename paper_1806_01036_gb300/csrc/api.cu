@@ -1,0 +1,287 @@
+// api.cu — the C-ABI of include/eo.h: context, argument checks, scratch
+// memory, and the launch sequences of eo_gram / eo_project / eo_cholqr /
+// eo_svqb (arXiv:1806.01036, Sec. 4.2: phase I projection, phase II Gram,
+// factorization of the Gram matrix and the final multiplication Y~ Z).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+
+struct eo_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  uint64_t launches = 0;
+  std::string err;
+};
+
+namespace eo {
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr uint64_t kGramLaunches = 2;  // partial sums + fixed-order reduction
+constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Scratch layout: [DevStatus][SmallWs][C hi/lo (KMAX x KMAX)][partials ...]
+constexpr size_t kOffStatus = 0;
+constexpr size_t kOffWs = align_up(sizeof(DevStatus));
+constexpr size_t kOffC = kOffWs + align_up(sizeof(SmallWs));
+constexpr size_t kOffParts = kOffC + align_up(2 * sizeof(double) * KMAX * KMAX);
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+eo_status fail(eo_ctx* c, eo_status s, const char* fmt, const char* a = "", long long b = 0) {
+  if (c) {
+    char buf[512];
+    snprintf(buf, sizeof buf, fmt, a, b);
+    c->err = buf;
+  }
+  return s;
+}
+
+eo_status cuda_fail(eo_ctx* c, const char* where, cudaError_t e) {
+  if (c) c->err = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
+  return EO_ECUDA;
+}
+
+eo_status ensure_scratch(eo_ctx* c, size_t parts_bytes) {
+  const size_t need = kOffParts + align_up(std::max<size_t>(parts_bytes, kAlign));
+  if (need <= c->scratch_bytes) return EO_OK;
+  if (c->scratch) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, "scratch resize (sync)", e);
+    cudaFree(c->scratch);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+  }
+  const size_t grown = need + need / 4;
+  cudaError_t e = cudaMalloc(&c->scratch, grown);
+  if (e != cudaSuccess) {
+    c->scratch = nullptr;
+    cudaGetLastError();
+    return fail(c, EO_ENOMEM, "cannot allocate %s%lld bytes of scratch", "", (long long)grown);
+  }
+  c->scratch_bytes = grown;
+  return EO_OK;
+}
+
+DevStatus* status_of(eo_ctx* c) { return reinterpret_cast<DevStatus*>(static_cast<char*>(c->scratch) + kOffStatus); }
+SmallWs* ws_of(eo_ctx* c) { return reinterpret_cast<SmallWs*>(static_cast<char*>(c->scratch) + kOffWs); }
+double* c_hi_of(eo_ctx* c) { return reinterpret_cast<double*>(static_cast<char*>(c->scratch) + kOffC); }
+double* c_lo_of(eo_ctx* c) { return c_hi_of(c) + KMAX * KMAX; }
+void* parts_of(eo_ctx* c) { return static_cast<char*>(c->scratch) + kOffParts; }
+
+__global__ void copy_small_kernel(int rows, int cols, const double* sh, const double* sl, int lds, double* dh,
+                                  double* dl, int ldd) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < rows * cols; t += gridDim.x * blockDim.x) {
+    const int i = t % rows, j = t / rows;
+    if (dh) dh[(size_t)j * ldd + i] = sh[(size_t)j * lds + i];
+    if (dl) dl[(size_t)j * ldd + i] = sl[(size_t)j * lds + i];
+  }
+}
+
+bool valid_prec(int p) { return p == EO_FP64 || p == EO_DD || p == EO_F32; }
+
+#define EO_CHECK(cond, code, ...) \
+  do {                            \
+    if (!(cond)) return fail(ctx, code, __VA_ARGS__); \
+  } while (0)
+
+#define EO_CUDA(expr, where)                          \
+  do {                                                \
+    cudaError_t e_ = (expr);                          \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, where, e_); \
+  } while (0)
+
+}  // namespace
+}  // namespace eo
+
+namespace eo {
+namespace {
+
+template <bool CHOL>
+eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, int64_t ldx, const double* M_hi,
+                      const double* M_lo, int ldm, double* O_hi, double* O_lo, int ldo, double tol, int passes,
+                      eo_prec prec, int* out_dev) {
+  if (!ctx) return EO_EINVAL;
+  ctx->err.clear();
+  EO_CHECK(valid_prec(prec), EO_EINVAL, "%s: bad precision mode %lld", name, (long long)prec);
+  EO_CHECK(n >= 0 && k >= 1 && k <= KMAX, EO_EINVAL, "%s: bad sizes (n=%lld)", name, (long long)n);
+  EO_CHECK(X != nullptr, EO_EINVAL, "%s: null X", name);
+  EO_CHECK(ldx >= std::max<int64_t>(1, n), EO_EINVAL, "%s: ldx too small%lld", name, (long long)ldx);
+  EO_CHECK(!M_hi || ldm >= k, EO_EINVAL, "%s: ldm too small%lld", name, (long long)ldm);
+  EO_CHECK(!(O_hi || O_lo) || ldo >= k, EO_EINVAL, "%s: output leading dimension too small%lld", name, (long long)ldo);
+  EO_CHECK(passes >= 0 && passes <= 2, EO_EINVAL, "%s: passes must be 0, 1 or 2 (%lld)", name, (long long)passes);
+  DeviceGuard g(ctx->device);
+  EO_CHECK(g.ok, EO_ECUDA, "%s: cannot select device", name);
+  eo_status s = ensure_scratch(ctx, gram_scratch_bytes(n, k, k, true));
+  if (s != EO_OK) return s;
+  DevStatus* st = status_of(ctx);
+  SmallWs* ws = ws_of(ctx);
+  const Mode mode = (Mode)prec;
+  const Mode small_mode = mode == MODE_DD ? MODE_DD : MODE_FP64;
+  EO_CUDA(launch_status_init(st, k, ctx->stream), name);
+  ctx->launches += 1;
+  const int npass = passes == 1 ? 1 : 2;
+  for (int p = 0; p < npass; ++p) {
+    const double* mh = ws->Mh;
+    const double* ml = ws->Ml;
+    int ld = KMAX;
+    if (p == 0 && M_hi) {
+      mh = M_hi;
+      ml = M_lo;
+      ld = ldm;
+    } else {
+      EO_CUDA(launch_gram(mode, n, k, X, ldx, k, X, ldx, true, parts_of(ctx), ws->Mh, ws->Ml, KMAX, &st->gate[2 * p],
+                          ctx->stream),
+              name);
+      ctx->launches += kGramLaunches;
+    }
+    if (CHOL)
+      EO_CUDA(launch_chol_small(small_mode, k, mh, ml, ld, ws, O_hi, O_lo, ldo, st, p, passes, out_dev, ctx->stream),
+              name);
+    else
+      EO_CUDA(launch_svqb_small(small_mode, k, mh, ml, ld, ws, O_hi, O_lo, ldo, tol, st, p, passes, out_dev,
+                                ctx->stream),
+              name);
+    EO_CUDA(launch_update(mode, n, k, X, ldx, ws->Zh, ws->Zl, CHOL, &st->gate[2 * p + 1], ctx->stream), name);
+    ctx->launches += 2;  // factorization + update
+  }
+  return EO_OK;
+}
+
+}  // namespace
+}  // namespace eo
+
+using namespace eo;
+
+extern "C" {
+
+int eo_version(void) { return 1; }
+
+eo_status eo_create(eo_ctx** out, int device) {
+  if (!out) return EO_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return EO_ECUDA;
+  }
+  eo_ctx* c = new eo_ctx();
+  c->device = device;
+  *out = c;
+  return EO_OK;
+}
+
+eo_status eo_destroy(eo_ctx* ctx) {
+  if (!ctx) return EO_EINVAL;
+  {
+    DeviceGuard g(ctx->device);
+    if (ctx->scratch) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(ctx->scratch);
+    }
+  }
+  delete ctx;
+  return EO_OK;
+}
+
+eo_status eo_set_stream(eo_ctx* ctx, void* stream) {
+  if (!ctx) return EO_EINVAL;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return EO_OK;
+}
+
+const char* eo_last_error(const eo_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+uint64_t eo_kernel_launches(const eo_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+eo_status eo_gram(eo_ctx* ctx, int64_t n, int kx, const void* X, int64_t ldx, int ky, const void* Y, int64_t ldy,
+                  double* G_hi, double* G_lo, int ldg, eo_prec prec) {
+  if (!ctx) return EO_EINVAL;
+  ctx->err.clear();
+  const bool sym = Y == nullptr;
+  if (sym) {
+    ky = kx;
+    ldy = ldx;
+  }
+  EO_CHECK(valid_prec(prec), EO_EINVAL, "eo_gram: bad precision mode%s %lld", "", (long long)prec);
+  EO_CHECK(n >= 0 && kx >= 1 && kx <= KMAX && ky >= 1 && ky <= KMAX, EO_EINVAL, "eo_gram: bad sizes%s (n=%lld)", "",
+           (long long)n);
+  EO_CHECK(X != nullptr && G_hi != nullptr, EO_EINVAL, "eo_gram: null pointer%s", "");
+  EO_CHECK(ldx >= std::max<int64_t>(1, n) && ldy >= std::max<int64_t>(1, n) && ldg >= kx, EO_EINVAL,
+           "eo_gram: leading dimension too small%s", "");
+  DeviceGuard g(ctx->device);
+  EO_CHECK(g.ok, EO_ECUDA, "eo_gram: cannot select device%s", "");
+  eo_status s = ensure_scratch(ctx, gram_scratch_bytes(n, kx, ky, sym));
+  if (s != EO_OK) return s;
+  EO_CUDA(launch_gram((Mode)prec, n, kx, X, ldx, ky, sym ? X : Y, ldy, sym, parts_of(ctx), G_hi, G_lo, ldg, nullptr,
+                      ctx->stream),
+          "eo_gram");
+  ctx->launches += kGramLaunches;
+  return EO_OK;
+}
+
+eo_status eo_project(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y,
+                     int64_t ldy, double* Yout, int64_t ldyo, double* C_hi, double* C_lo, int ldc, double* M_hi,
+                     double* M_lo, int ldm, eo_prec prec) {
+  if (!ctx) return EO_EINVAL;
+  ctx->err.clear();
+  EO_CHECK(valid_prec(prec), EO_EINVAL, "eo_project: bad precision mode%s %lld", "", (long long)prec);
+  EO_CHECK(prec != EO_F32, EO_EUNSUPPORTED, "eo_project: FP32 inputs are not supported%s", "");
+  EO_CHECK(n >= 0 && kv >= 1 && kv <= KMAX && k >= 1 && k <= KMAX, EO_EINVAL, "eo_project: bad sizes%s", "");
+  EO_CHECK(V && Y && Yout, EO_EINVAL, "eo_project: null pointer%s", "");
+  const int64_t mn = std::max<int64_t>(1, n);
+  EO_CHECK(ldv >= mn && ldy >= mn && ldyo >= mn, EO_EINVAL, "eo_project: leading dimension too small%s", "");
+  EO_CHECK(!C_hi || ldc >= kv, EO_EINVAL, "eo_project: ldc too small%s", "");
+  EO_CHECK(!M_hi || ldm >= k, EO_EINVAL, "eo_project: ldm too small%s", "");
+  DeviceGuard g(ctx->device);
+  EO_CHECK(g.ok, EO_ECUDA, "eo_project: cannot select device%s", "");
+  const size_t need = std::max(gram_scratch_bytes(n, kv, k, false), project_scratch_bytes(n, kv, k));
+  eo_status s = ensure_scratch(ctx, need);
+  if (s != EO_OK) return s;
+  double* ch = c_hi_of(ctx);
+  double* cl = c_lo_of(ctx);
+  const Mode mode = (Mode)prec;
+  EO_CUDA(launch_gram(mode, n, kv, V, ldv, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, nullptr, ctx->stream),
+          "eo_project (V^T Y)");
+  ctx->launches += kGramLaunches;
+  if (C_hi || C_lo) {
+    copy_small_kernel<<<4, 256, 0, ctx->stream>>>(kv, k, ch, cl, KMAX, C_hi, C_lo, ldc);
+    EO_CUDA(cudaGetLastError(), "eo_project (copy C)");
+    ctx->launches += 1;
+  }
+  EO_CUDA(launch_project_fused(mode, n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, mode == MODE_DD ? cl : nullptr, KMAX,
+                               parts_of(ctx), M_hi, M_lo, ldm, ctx->stream),
+          "eo_project (fused pass)");
+  ctx->launches += M_hi ? 2 : 1;
+  return EO_OK;
+}
+
+
+eo_status eo_cholqr(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, const double* M_hi, const double* M_lo,
+                    int ldm, double* R_hi, double* R_lo, int ldr, int passes, eo_prec prec, int* info_dev) {
+  return orth_common<true>(ctx, "eo_cholqr", n, k, X, ldx, M_hi, M_lo, ldm, R_hi, R_lo, ldr, 0.0, passes, prec,
+                           info_dev);
+}
+
+eo_status eo_svqb(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, const double* M_hi, const double* M_lo,
+                  int ldm, double* Z_hi, double* Z_lo, int ldz, double tol, int passes, eo_prec prec, int* rank_dev) {
+  return orth_common<false>(ctx, "eo_svqb", n, k, X, ldx, M_hi, M_lo, ldm, Z_hi, Z_lo, ldz, tol, passes, prec,
+                            rank_dev);
+}
+
+}  // extern "C"

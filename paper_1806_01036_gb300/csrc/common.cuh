@@ -1,0 +1,73 @@
+// common.cuh — declarations shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dd.cuh"
+#include "eo.h"
+
+namespace eo {
+
+enum Mode : int { MODE_FP64 = EO_FP64, MODE_DD = EO_DD, MODE_F32 = EO_F32 };
+
+constexpr int KMAX = EO_KMAX;
+
+// Device-resident status of one call.  gate[2p] enables the Gram and the
+// small factorization of pass p, gate[2p+1] the streaming update of pass p;
+// the factorization of pass p sets the gates of what follows, so a call never
+// returns to the host between passes.
+struct DevStatus {
+  int info;
+  int rank;
+  int gate[8];
+  int pad[6];
+};
+
+// Device workspace for the k-by-k matrices of one call (FP64 hi/lo arrays,
+// column-major with leading dimension KMAX).
+struct SmallWs {
+  double Mh[KMAX * KMAX], Ml[KMAX * KMAX];  // Gram matrix of the current pass
+  double Zh[KMAX * KMAX], Zl[KMAX * KMAX];  // transform of the current pass
+  double Th[KMAX * KMAX], Tl[KMAX * KMAX];  // accumulated R (CholQR) or Z (SVQB)
+};
+
+// ----------------------------------------------------------- Gram kernels
+// Number of per-CTA partial results the Gram launch will produce and the
+// scratch it needs (bytes) for a kx-by-ky Gram over n rows.
+int gram_num_parts(int64_t n, int kx, int ky, bool sym);
+size_t gram_scratch_bytes(int64_t n, int kx, int ky, bool sym);
+
+// G = X^T Y (Y == X when sym).  X, Y are double* (or float* in MODE_F32).
+// The kx-by-ky result goes to (G_hi, G_lo, ldg); G_lo may be null.
+// gate: optional device flag; the kernels do nothing when *gate == 0.
+cudaError_t launch_gram(Mode mode, int64_t n, int kx, const void* X, int64_t ldx, int ky, const void* Y,
+                        int64_t ldy, bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
+                        cudaStream_t st);
+
+// --------------------------------------------------- projection kernels
+size_t project_scratch_bytes(int64_t n, int kv, int k);
+// Yout = Y - V C with C = (C_hi + C_lo) (kv-by-k, ldc), and, if M_hi is not
+// null, M = Yout^T Yout accumulated in the same pass.
+cudaError_t launch_project_fused(Mode mode, int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y,
+                                 int64_t ldy, double* Yout, int64_t ldyo, const double* C_hi, const double* C_lo,
+                                 int ldc, void* scratch, double* M_hi, double* M_lo, int ldm, cudaStream_t st);
+
+// ------------------------------------------------------- update kernels
+// X <- X Z for Z = (Zh + Zl) (k-by-k, ld KMAX); tri: Z upper triangular.
+cudaError_t launch_update(Mode mode, int64_t n, int k, void* X, int64_t ldx, const double* Zh, const double* Zl,
+                          bool tri, const int* gate, cudaStream_t st);
+
+// ------------------------------------------------ small k-by-k kernels
+cudaError_t launch_status_init(DevStatus* s, int k, cudaStream_t st);
+// One CholQR factorization step of pass `pass` (0 or 1): M -> R, Z = R^{-1},
+// T <- R T.  passes: 1, 2 or 0 (automatic).
+cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
+                              double* R_hi, double* R_lo, int ldr, DevStatus* s, int pass, int passes,
+                              int* info_user, cudaStream_t st);
+cudaError_t launch_svqb_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
+                              double* Z_hi, double* Z_lo, int ldz, double tol, DevStatus* s, int pass, int passes,
+                              int* rank_user, cudaStream_t st);
+
+}  // namespace eo

@@ -1,0 +1,391 @@
+// small.cu — the k-by-k steps of phase II, one CTA each
+// (arXiv:1806.01036, Sec. 4.2: "operations on small n_b x n_b matrices are
+// cost negligible, even in extended precision").
+//
+//   chol_small:  M = R^T R (right-looking Cholesky, R upper with positive
+//                diagonal), Z = R^{-1} (column-parallel back substitution),
+//                T <- R T (R of all passes), and the gates of what follows.
+//   svqb_small:  M = U Lambda U^T by cyclic Jacobi in the parallel
+//                (round-robin) ordering, Z = U Lambda^{+1/2} U^T = M^{-1/2}
+//                (Frobenius-nearest to I among Z with Z^T M Z = I, by the
+//                Procrustes argument of the same section), T <- T Z.
+// In EO_DD the arithmetic is DD throughout (divisions and square roots by
+// Newton-Raphson, dd.cuh); otherwise it is FP64.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace eo {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int MODE>
+struct Ar {
+  static __device__ __forceinline__ dd add(dd a, dd b) { return dd{__dadd_rn(a.hi, b.hi), 0.0}; }
+  static __device__ __forceinline__ dd sub(dd a, dd b) { return dd{__dsub_rn(a.hi, b.hi), 0.0}; }
+  static __device__ __forceinline__ dd mul(dd a, dd b) { return dd{__dmul_rn(a.hi, b.hi), 0.0}; }
+  static __device__ __forceinline__ dd div(dd a, dd b) { return dd{__ddiv_rn(a.hi, b.hi), 0.0}; }
+  static __device__ __forceinline__ dd sqrt(dd a) { return dd{__dsqrt_rn(a.hi), 0.0}; }
+  static __device__ __forceinline__ dd fma(dd a, dd b, dd c) { return dd{__fma_rn(a.hi, b.hi, c.hi), 0.0}; }
+};
+
+template <>
+struct Ar<MODE_DD> {
+  static __device__ __forceinline__ dd add(dd a, dd b) { return dd_add(a, b); }
+  static __device__ __forceinline__ dd sub(dd a, dd b) { return dd_sub(a, b); }
+  static __device__ __forceinline__ dd mul(dd a, dd b) { return dd_mul(a, b); }
+  static __device__ __forceinline__ dd div(dd a, dd b) { return dd_div(a, b); }
+  static __device__ __forceinline__ dd sqrt(dd a) { return dd_sqrt(a); }
+  static __device__ __forceinline__ dd fma(dd a, dd b, dd c) { return dd_add(dd_mul(a, b), c); }
+};
+
+__device__ __forceinline__ double dabs(double x) { return x < 0 ? -x : x; }
+
+__global__ void status_init_kernel(DevStatus* s, int k) {
+  if (threadIdx.x == 0) {
+    s->info = 0;
+    s->rank = k;
+    for (int i = 0; i < 8; ++i) s->gate[i] = 0;
+    s->gate[0] = 1;
+  }
+}
+
+__device__ void finish_gates(DevStatus* s, int pass, int run_update, int want_next) {
+  s->gate[2 * pass + 1] = run_update;
+  if (pass + 1 < 4) s->gate[2 * pass + 2] = want_next;
+}
+
+// ------------------------------------------------------------ Cholesky
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) chol_small_kernel(int k, const double* Mh, const double* Ml, int ldm,
+                                                              SmallWs* ws, double* Rh_u, double* Rl_u, int ldr,
+                                                              DevStatus* st, int pass, int passes, double thr,
+                                                              int* info_user) {
+  using A_ = Ar<MODE>;
+  if (st->gate[2 * pass] == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  dd* A = reinterpret_cast<dd*>(smem_raw);  // A(i,j) = A[j*k+i]; R overwrites the upper triangle
+  dd* Z = A + k * k;
+  __shared__ int flag;
+  __shared__ dd inv;
+  const int tid = threadIdx.x;
+  if (tid == 0) flag = 0;
+  __syncthreads();
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    const int a = min(i, j), b = max(i, j);
+    dd v = dd{Mh[(size_t)b * ldm + a], Ml ? Ml[(size_t)b * ldm + a] : 0.0};
+    if (MODE != MODE_DD) v.lo = 0.0;
+    if (!dd_finite(v)) atomicExch(&flag, -1);
+    A[t] = v;
+  }
+  __syncthreads();
+  if (flag == 0) {
+    for (int j = 0; j < k; ++j) {
+      if (tid == 0) {
+        dd d = A[j * k + j];
+        if (!(d.hi > 0.0)) {
+          flag = j + 1;
+        } else {
+          dd r = A_::sqrt(d);
+          A[j * k + j] = r;
+          inv = A_::div(dd{1.0, 0.0}, r);
+        }
+      }
+      __syncthreads();
+      if (flag) break;
+      for (int l = j + 1 + tid; l < k; l += kThreads) A[l * k + j] = A_::mul(A[l * k + j], inv);
+      __syncthreads();
+      const int m = k - j - 1;
+      for (int t = tid; t < m * m; t += kThreads) {
+        const int a = j + 1 + t % m, b = j + 1 + t / m;
+        if (a <= b) A[b * k + a] = A_::sub(A[b * k + a], A_::mul(A[a * k + j], A[b * k + j]));
+      }
+      __syncthreads();
+    }
+  }
+  if (flag != 0) {
+    if (tid == 0) {
+      st->info = flag;
+      finish_gates(st, pass, 0, 0);
+      if (info_user) *info_user = flag;
+    }
+    return;
+  }
+  // Z = R^{-1}: diagonal first, then rows i = k-2 .. 0, all columns j > i at once.
+  for (int t = tid; t < k * k; t += kThreads) Z[t] = dd{0.0, 0.0};
+  __syncthreads();
+  for (int i = tid; i < k; i += kThreads) Z[i * k + i] = A_::div(dd{1.0, 0.0}, A[i * k + i]);
+  __syncthreads();
+  for (int i = k - 2; i >= 0; --i) {
+    for (int j = i + 1 + tid; j < k; j += kThreads) {
+      dd s = dd{0.0, 0.0};
+      for (int l = i + 1; l <= j; ++l) s = A_::fma(A[l * k + i], Z[j * k + l], s);
+      Z[j * k + i] = A_::mul(dd_neg(s), Z[i * k + i]);
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    ws->Zh[j * KMAX + i] = Z[t].hi;
+    ws->Zl[j * KMAX + i] = Z[t].lo;
+  }
+  __syncthreads();
+  // T <- R T (upper triangular product); T = R on the first pass.
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    dd v = dd{0.0, 0.0};
+    if (i <= j) {
+      if (pass == 0) {
+        v = A[j * k + i];
+      } else {
+        for (int l = i; l <= j; ++l)
+          v = A_::fma(A[l * k + i], dd{ws->Th[j * KMAX + l], ws->Tl[j * KMAX + l]}, v);
+      }
+    }
+    Z[t] = v;  // Z's copy is already in global memory
+  }
+  __syncthreads();
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    ws->Th[j * KMAX + i] = Z[t].hi;
+    ws->Tl[j * KMAX + i] = Z[t].lo;
+    if (Rh_u) Rh_u[(size_t)j * ldr + i] = Z[t].hi;
+    if (Rl_u) Rl_u[(size_t)j * ldr + i] = Z[t].lo;
+  }
+  if (tid == 0) {
+    double dmax = 0.0, dmin = 1e308;
+    for (int i = 0; i < k; ++i) {
+      dmax = fmax(dmax, A[i * k + i].hi);
+      dmin = fmin(dmin, A[i * k + i].hi);
+    }
+    int next = 0;
+    if (pass == 0) next = passes == 2 ? 1 : (passes == 0 ? (dmax > thr * dmin) : 0);
+    finish_gates(st, pass, 1, next);
+    if (info_user) *info_user = st->info;
+  }
+}
+
+// --------------------------------------------------------------- SVQB
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) svqb_small_kernel(int k, const double* Mh, const double* Ml, int ldm,
+                                                              SmallWs* ws, double* Zh_u, double* Zl_u, int ldz,
+                                                              double tol, DevStatus* st, int pass, int passes,
+                                                              double thr, double eps, int* rank_user) {
+  using A_ = Ar<MODE>;
+  if (st->gate[2 * pass] == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  dd* A = reinterpret_cast<dd*>(smem_raw);  // k*k
+  dd* U = A + k * k;                         // k*k
+  dd* cs = U + k * k;                        // 2 * (k/2 + 1): c, s per pair
+  int* pr = reinterpret_cast<int*>(cs + 2 * (k / 2 + 1));  // 2 * (k/2 + 1): p, q per pair
+  __shared__ int flag, rot_count;
+  const int tid = threadIdx.x;
+  const int kk = k + (k & 1);  // even number of players; index k is a dummy
+  const int npairs = kk / 2;
+  if (tid == 0) flag = 0;
+  __syncthreads();
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    const int a = min(i, j), b = max(i, j);
+    dd v = dd{Mh[(size_t)b * ldm + a], Ml ? Ml[(size_t)b * ldm + a] : 0.0};
+    if (MODE != MODE_DD) v.lo = 0.0;
+    if (!dd_finite(v)) atomicExch(&flag, -1);
+    A[t] = v;
+    U[t] = dd{i == j ? 1.0 : 0.0, 0.0};
+  }
+  __syncthreads();
+  if (flag != 0) {
+    if (tid == 0) {
+      st->rank = -1;
+      finish_gates(st, pass, 0, 0);
+      if (rank_user) *rank_user = -1;
+    }
+    return;
+  }
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) rot_count = 0;
+    __syncthreads();
+    for (int step = 0; step < kk - 1; ++step) {
+      // round-robin pairing: player 0 fixed, the others rotate by `step`
+      for (int p = tid; p < npairs; p += kThreads) {
+        auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (kk - 1); };
+        int a = player(p), b = player(kk - 1 - p);
+        int lo = min(a, b), hi = max(a, b);
+        dd c = dd{1.0, 0.0}, s = dd{0.0, 0.0};
+        if (hi < k) {
+          const dd apq = A[hi * k + lo];
+          const dd app = A[lo * k + lo], aqq = A[hi * k + hi];
+          const double scale = sqrt(dabs(app.hi) * dabs(aqq.hi));
+          if (dabs(apq.hi) > eps * scale && apq.hi != 0.0) {
+            const dd theta = A_::div(A_::sub(aqq, app), A_::add(apq, apq));
+            const dd th2 = A_::add(A_::mul(theta, theta), dd{1.0, 0.0});
+            dd t = A_::div(dd{1.0, 0.0}, A_::add(dd{dabs(theta.hi), theta.hi < 0 ? -theta.lo : theta.lo},
+                                                  A_::sqrt(th2)));
+            if (theta.hi < 0) t = dd_neg(t);
+            c = A_::div(dd{1.0, 0.0}, A_::sqrt(A_::add(A_::mul(t, t), dd{1.0, 0.0})));
+            s = A_::mul(t, c);
+            atomicAdd(&rot_count, 1);
+          }
+        }
+        cs[2 * p] = c;
+        cs[2 * p + 1] = s;
+        pr[2 * p] = lo;
+        pr[2 * p + 1] = hi;
+      }
+      __syncthreads();
+      // rows p, q of A: A <- J^T A
+      for (int t = tid; t < npairs * k; t += kThreads) {
+        const int p = t % npairs, m = t / npairs;
+        const int a = pr[2 * p], b = pr[2 * p + 1];
+        if (b >= k) continue;
+        const dd c = cs[2 * p], s = cs[2 * p + 1];
+        const dd x = A[m * k + a], y = A[m * k + b];
+        A[m * k + a] = A_::sub(A_::mul(c, x), A_::mul(s, y));
+        A[m * k + b] = A_::add(A_::mul(s, x), A_::mul(c, y));
+      }
+      __syncthreads();
+      // columns p, q of A and of U: A <- A J, U <- U J
+      for (int t = tid; t < npairs * k; t += kThreads) {
+        const int p = t % npairs, m = t / npairs;
+        const int a = pr[2 * p], b = pr[2 * p + 1];
+        if (b >= k) continue;
+        const dd c = cs[2 * p], s = cs[2 * p + 1];
+        dd x = A[a * k + m], y = A[b * k + m];
+        A[a * k + m] = A_::sub(A_::mul(c, x), A_::mul(s, y));
+        A[b * k + m] = A_::add(A_::mul(s, x), A_::mul(c, y));
+        x = U[a * k + m];
+        y = U[b * k + m];
+        U[a * k + m] = A_::sub(A_::mul(c, x), A_::mul(s, y));
+        U[b * k + m] = A_::add(A_::mul(s, x), A_::mul(c, y));
+      }
+      __syncthreads();
+      for (int p = tid; p < npairs; p += kThreads) {
+        const int a = pr[2 * p], b = pr[2 * p + 1];
+        if (b < k && !(cs[2 * p + 1].hi == 0.0 && cs[2 * p + 1].lo == 0.0)) {
+          A[b * k + a] = dd{0.0, 0.0};
+          A[a * k + b] = dd{0.0, 0.0};
+        }
+      }
+      __syncthreads();
+    }
+    if (rot_count == 0) break;
+    __syncthreads();
+  }
+  // w_l = lambda_l^{-1/2} for kept eigenvalues; Z = U diag(w) U^T into A's storage.
+  __shared__ double lmax_s, lmin_s;
+  __shared__ int rank_s;
+  dd* w = cs;  // reuse: k entries needed, cs has 2*(k/2+1) >= k
+  if (tid == 0) {
+    double lmax = 0.0;
+    for (int i = 0; i < k; ++i) lmax = fmax(lmax, A[i * k + i].hi);
+    int rank = 0;
+    double lmin = lmax;
+    for (int i = 0; i < k; ++i) {
+      const dd l = A[i * k + i];
+      if (lmax > 0.0 && l.hi > tol * lmax) {
+        w[i] = A_::div(dd{1.0, 0.0}, A_::sqrt(l));
+        ++rank;
+        lmin = fmin(lmin, l.hi);
+      } else {
+        w[i] = dd{0.0, 0.0};
+      }
+    }
+    lmax_s = lmax;
+    lmin_s = lmin;
+    rank_s = rank;
+  }
+  __syncthreads();
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    dd v = dd{0.0, 0.0};
+    for (int l = 0; l < k; ++l) v = A_::fma(A_::mul(U[l * k + i], w[l]), U[l * k + j], v);
+    A[t] = v;
+  }
+  __syncthreads();
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    ws->Zh[j * KMAX + i] = A[t].hi;
+    ws->Zl[j * KMAX + i] = A[t].lo;
+  }
+  __syncthreads();
+  // T <- T Z (full product); T = Z on the first pass.  U's storage is free now.
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    dd v = dd{0.0, 0.0};
+    if (pass == 0) {
+      v = A[t];
+    } else {
+      for (int l = 0; l < k; ++l) v = A_::fma(dd{ws->Th[l * KMAX + i], ws->Tl[l * KMAX + i]}, A[j * k + l], v);
+    }
+    U[t] = v;
+  }
+  __syncthreads();
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    ws->Th[j * KMAX + i] = U[t].hi;
+    ws->Tl[j * KMAX + i] = U[t].lo;
+    if (Zh_u) Zh_u[(size_t)j * ldz + i] = U[t].hi;
+    if (Zl_u) Zl_u[(size_t)j * ldz + i] = U[t].lo;
+  }
+  if (tid == 0) {
+    st->rank = rank_s;
+    int next = 0;
+    if (pass == 0) next = passes == 2 ? 1 : (passes == 0 ? (lmax_s > thr * thr * lmin_s) : 0);
+    finish_gates(st, pass, 1, next);
+    if (rank_user) *rank_user = rank_s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_status_init(DevStatus* s, int k, cudaStream_t st) {
+  status_init_kernel<<<1, 32, 0, st>>>(s, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
+                              double* R_hi, double* R_lo, int ldr, DevStatus* s, int pass, int passes, int* info_user,
+                              cudaStream_t st) {
+  const size_t smem = 2 * (size_t)k * k * sizeof(dd);
+  cudaError_t e;
+  if (mode == MODE_DD) {
+    e = cudaFuncSetAttribute(chol_small_kernel<MODE_DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    chol_small_kernel<MODE_DD><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, R_hi, R_lo, ldr, s, pass, passes, 1e7,
+                                                         info_user);
+  } else {
+    e = cudaFuncSetAttribute(chol_small_kernel<MODE_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    chol_small_kernel<MODE_FP64><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, R_hi, R_lo, ldr, s, pass, passes, 1e4,
+                                                           info_user);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_svqb_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
+                              double* Z_hi, double* Z_lo, int ldz, double tol, DevStatus* s, int pass, int passes,
+                              int* rank_user, cudaStream_t st) {
+  const size_t smem = 2 * (size_t)k * k * sizeof(dd) + 2 * (size_t)(k / 2 + 1) * sizeof(dd) +
+                      2 * (size_t)(k / 2 + 1) * sizeof(int);
+  cudaError_t e;
+  if (mode == MODE_DD) {
+    if (tol < 0) tol = k * 0x1p-104;
+    e = cudaFuncSetAttribute(svqb_small_kernel<MODE_DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    svqb_small_kernel<MODE_DD><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, Z_hi, Z_lo, ldz, tol, s, pass, passes,
+                                                         1e7, 0x1p-106, rank_user);
+  } else {
+    if (tol < 0) tol = k * 0x1p-52;
+    e = cudaFuncSetAttribute(svqb_small_kernel<MODE_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    svqb_small_kernel<MODE_FP64><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, Z_hi, Z_lo, ldz, tol, s, pass, passes,
+                                                           1e4, 0x1p-53, rank_user);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace eo

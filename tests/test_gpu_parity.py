@@ -1,0 +1,342 @@
+"""GPU parity: the CUDA library (through its C-ABI binding) against the
+binary128 oracle on the same seeded inputs.
+
+Tolerances (u = 2^-53, u2 = 2^-104; |A| is the entry-wise absolute value):
+  * Gram, DD mode:    |G - G*| <= u2 |G*| + (n + 64) 2^-105 (|X|^T |Y|)
+      Every product is formed exactly (TwoProd); each thread's Dot2 chain
+      and the fixed reduction tree add at most a few u^2 per partial sum, so a
+      bound linear in n holds (tighter than Dot2's gamma_n^2).
+  * Gram, FP64/F32:   |G - G*| <= gamma_n |X|^T |Y|, gamma_n = n u / (1 - n u)
+      (the textbook dot-product bound; F32 products are exact in FP64).
+  * CholQR/SVQB, DD:  both sides factor a Gram matrix that is accurate to
+      eps_M = (n + 64) 2^-104 relative; a perturbation of relative size eps of
+      M moves R (and Q) by at most ~kappa^2 eps, so
+      |Q - Q*| <= 4 u + 8 kappa^2 (eps_M + k u2) and the same, times ||R||, for R.
+      The orthogonality gate of the method itself (||Q^T Q - I||_2 <= 1e-14 up
+      to kappa(X) = 1e8 in one DD pass) is checked with the oracle's
+      binary128 measure.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+U2 = 2.0 ** -104
+
+
+def torch_mod():
+    import torch
+    return torch
+
+
+def dev(a, dtype=None):
+    """numpy column-major -> CUDA tensor with the same column-major layout."""
+    torch = torch_mod()
+    a = np.asfortranarray(a if dtype is None else a.astype(dtype))
+    t = torch.from_numpy(np.ascontiguousarray(a.T)).cuda()
+    return t.t()
+
+
+def host(t):
+    return np.asfortranarray(t.detach().cpu().numpy())
+
+
+def dd_err(hi, lo, ref_hi, ref_lo):
+    """|(hi + lo) - (ref_hi + ref_lo)| entry-wise, evaluated without cancellation loss."""
+    return np.abs((hi - ref_hi) + (lo - ref_lo))
+
+
+def gamma(n):
+    return n * U / (1 - n * U)
+
+
+# ------------------------------------------------------------------ Gram
+
+@pytest.mark.parametrize("n,kx,ky", [(1, 1, 1), (33, 3, 3), (1000, 8, 8), (4099, 13, 5), (100_003, 16, 16),
+                                     (20_000, 64, 64), (20_001, 64, 16)])
+def test_gram_dd_matches_oracle(eo, ctx, n, kx, ky):
+    x = synth.gaussian(n, kx, 100 + kx)
+    y = x if kx == ky and n % 2 else synth.gaussian(n, ky, 200 + ky)
+    sym = y is x
+    gh, gl = eo.gram(ctx, dev(x), None if sym else dev(y), prec=eo.DD)
+    rh, rl = oracle.gram(x, None if sym else y)
+    err = dd_err(host(gh), host(gl), rh, rl)
+    tol = U2 * np.abs(rh) + (n + 64) * 2.0 ** -105 * (np.abs(x).T @ np.abs(y))
+    assert np.all(err <= tol), float(np.max(err / tol))
+    # the high part is the FP64 rounding of the exact sum (up to the last bit)
+    assert np.all(np.abs(host(gh) - rh) <= 2 * U * np.abs(rh) + tol)
+    if sym:
+        assert np.array_equal(host(gh), host(gh).T)
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+@pytest.mark.parametrize("n,k", [(777, 5), (50_000, 16)])
+def test_gram_fp64_and_f32_within_textbook_bound(eo, ctx, prec, n, k):
+    x = synth.conditioned(n, k, 1e3, 300 + k)
+    if prec == eo.F32:
+        x32 = x.astype(np.float32)
+        gh, gl = eo.gram(ctx, dev(x32), prec=prec)
+        rh, rl = oracle.gram_f32(x32)
+        ax = np.abs(x32.astype(np.float64))
+    else:
+        gh, gl = eo.gram(ctx, dev(x), prec=prec)
+        rh, rl = oracle.gram(x)
+        ax = np.abs(x)
+    err = np.abs(host(gh) - (rh + rl))
+    assert np.all(err <= gamma(n) * (ax.T @ ax) + U * np.abs(rh))
+    assert not np.any(host(gl))
+
+
+def test_gram_ld_padding_is_not_read(eo, ctx):
+    n, k, ld = 1001, 4, 1040
+    x = synth.gaussian(n, k, 5)
+    buf = synth.with_ld(x, ld, fill=np.nan)
+    torch = torch_mod()
+    t = torch.from_numpy(np.ascontiguousarray(buf.T)).cuda().t()[:n, :]
+    assert t.stride(1) == ld
+    gh, gl = eo.gram(ctx, t, prec=eo.DD)
+    rh, rl = oracle.gram(x)
+    assert np.all(np.isfinite(host(gh)))
+    assert np.all(dd_err(host(gh), host(gl), rh, rl) <= U2 * np.abs(rh) + (n + 64) * 2.0 ** -105 * (np.abs(x).T @ np.abs(x)))
+
+
+def test_gram_empty_rows_give_zero(eo, ctx):
+    torch = torch_mod()
+    x = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    x = x.t().contiguous().t()
+    hi = torch.full((3, 3), 7.0, dtype=torch.float64, device="cuda").t()
+    lo = torch.full((3, 3), 7.0, dtype=torch.float64, device="cuda").t()
+    gh, gl = eo.gram(ctx, x, prec=eo.DD, out=(hi, lo))
+    assert not torch.any(gh) and not torch.any(gl)
+
+
+def test_gram_is_deterministic(eo, ctx):
+    x = synth.gaussian(300_001, 8, 9)
+    d = dev(x)
+    a = eo.gram(ctx, d, prec=eo.DD)
+    b = eo.gram(ctx, d, prec=eo.DD)
+    assert np.array_equal(host(a[0]), host(b[0])) and np.array_equal(host(a[1]), host(b[1]))
+
+
+# ------------------------------------------------------------ projection
+
+@pytest.mark.parametrize("n,kv,k", [(1, 1, 1), (5000, 10, 4), (20_003, 64, 16), (30_000, 40, 2)])
+def test_project_dd_matches_oracle(eo, ctx, n, kv, k):
+    v = synth.orthonormal_basis(n, kv, 31) if n >= kv else synth.gaussian(n, kv, 31)
+    y = synth.conditioned(n, k, 1e6, 32) if n >= k else synth.gaussian(n, k, 32)
+    yt_d, (ch, cl), (mh, ml) = eo.project(ctx, dev(v), dev(y), prec=eo.DD)
+    yt_o, (ch_o, cl_o), _ = oracle.project(v, y)
+    bound_c = U2 * np.abs(ch_o) + (n + 64) * 2.0 ** -105 * (np.abs(v).T @ np.abs(y))
+    assert np.all(dd_err(host(ch), host(cl), ch_o, cl_o) <= bound_c)
+    yt = host(yt_d)
+    tol_y = 2 * U * np.abs(yt_o) + 2.0 ** -100 * (np.abs(y) + np.abs(v) @ np.abs(ch_o)) + np.abs(v) @ bound_c
+    assert np.all(np.abs(yt - yt_o) <= tol_y)
+    # M is the Gram matrix of the rounded result the kernel wrote
+    m_o = oracle.gram(yt)
+    assert np.all(dd_err(host(mh), host(ml), *m_o) <= U2 * np.abs(m_o[0]) + (n + 64) * 2.0 ** -105 * (np.abs(yt).T @ np.abs(yt)))
+
+
+def test_project_in_place_and_fp64(eo, ctx):
+    n, kv, k = 12_345, 12, 3
+    v = synth.orthonormal_basis(n, kv, 41)
+    y = synth.gaussian(n, k, 42)
+    d = dev(y)
+    yt_d, _, (mh, _) = eo.project(ctx, dev(v), d, Yout=d, prec=eo.FP64)
+    assert yt_d.data_ptr() == d.data_ptr()
+    yt_o, (ch_o, _), _ = oracle.project(v, y)
+    yt = host(yt_d)
+    c_bound = gamma(n) * (np.abs(v).T @ np.abs(y))
+    tol = gamma(kv + 2) * (np.abs(y) + np.abs(v) @ (np.abs(ch_o) + c_bound)) + np.abs(v) @ c_bound
+    assert np.all(np.abs(yt - yt_o) <= tol)
+    assert oracle.cross_err(v, yt) < 1e-13 * np.linalg.norm(y, 2)
+
+
+# --------------------------------------------------------------- CholQR
+
+def cholqr_tol(n, k, kappa):
+    eps_m = (n + 64) * U2
+    return 4 * U + 8 * kappa ** 2 * (eps_m + k * U2)
+
+
+@pytest.mark.parametrize("n,k,kappa", [(20_000, 8, 1e2), (20_000, 8, 1e6), (20_001, 16, 1e8), (5_000, 4, 1e8),
+                                       (4_097, 1, 1.0), (3000, 33, 1e4)])
+def test_cholqr_dd_one_pass(eo, ctx, n, k, kappa):
+    x = synth.conditioned(n, k, kappa, 500 + k)
+    d = dev(x)
+    rh, rl, info = eo.cholqr(ctx, d, passes=1, prec=eo.DD)
+    assert int(info.item()) == 0
+    q = host(d)
+    q_o, (rh_o, rl_o), info_o = oracle.cholqr(x, passes=1)
+    assert info_o == 0
+    tol = cholqr_tol(n, k, kappa)
+    assert np.max(np.abs(q - q_o)) <= tol
+    r = host(rh) + host(rl)
+    assert np.max(np.abs(r - (rh_o + rl_o))) <= tol * np.max(np.abs(rh_o))
+    assert np.all(np.tril(host(rh), -1) == 0) and np.all(np.diag(host(rh)) > 0)
+    # the method's own accuracy claim: one DD pass is orthogonal to 1e-14 up to kappa = 1e8
+    assert oracle.orth_err(q)[0] <= 1e-14
+    assert oracle.fact_err(x, q, host(rh), host(rl)) <= 1e-15 * np.sqrt(k) + 8 * U
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6])
+def test_cholqr_fp64_loses_orthogonality_like_kappa_squared(eo, ctx, kappa):
+    n, k = 20_000, 8
+    x = synth.conditioned(n, k, kappa, 600)
+    dp, dd_ = dev(x), dev(x)
+    _, _, info_p = eo.cholqr(ctx, dp, prec=eo.FP64)
+    _, _, info_d = eo.cholqr(ctx, dd_, prec=eo.DD)
+    assert int(info_p.item()) == 0 and int(info_d.item()) == 0
+    e_plain = oracle.orth_err(host(dp))[0]
+    e_dd = oracle.orth_err(host(dd_))[0]
+    assert e_plain <= 10 * n * kappa ** 2 * U  # kappa^2 u law with the Gram's gamma_n
+    assert e_dd <= 1e-14
+    if kappa >= 1e6:
+        assert e_plain >= 1e3 * e_dd  # DD wins by orders of magnitude once kappa^2 u dominates
+
+
+def test_cholqr_fp64_parity_well_conditioned(eo, ctx):
+    n, k, kappa = 20_000, 6, 10.0
+    x = synth.conditioned(n, k, kappa, 601)
+    d = dev(x)
+    rh, _, info = eo.cholqr(ctx, d, prec=eo.FP64)
+    q_o, (rh_o, _), _ = oracle.cholqr(x)
+    tol = 8 * kappa ** 2 * (gamma(n) + gamma(k + 1))
+    assert np.max(np.abs(host(d) - q_o)) <= tol
+    assert np.max(np.abs(host(rh) - rh_o)) <= tol * np.max(np.abs(rh_o))
+
+
+@pytest.mark.parametrize("kappa", [1e10, 1e12])
+def test_cholqr_dd_two_passes_and_auto(eo, ctx, kappa):
+    n, k = 20_000, 8
+    x = synth.conditioned(n, k, kappa, 700)
+    d2, da = dev(x), dev(x)
+    rh, rl, info = eo.cholqr(ctx, d2, passes=2, prec=eo.DD)
+    assert int(info.item()) == 0
+    q = host(d2)
+    assert oracle.orth_err(q)[0] <= 1e-14
+    assert oracle.fact_err(x, q, host(rh), host(rl)) <= 1e-14
+    eo.cholqr(ctx, da, passes=0, prec=eo.DD)  # automatic: a second pass runs here
+    assert np.array_equal(host(da), q)
+
+
+def test_cholqr_auto_single_pass_when_well_conditioned(eo, ctx):
+    x = synth.conditioned(10_000, 8, 1e3, 701)
+    d1, da = dev(x), dev(x)
+    eo.cholqr(ctx, d1, passes=1, prec=eo.DD)
+    eo.cholqr(ctx, da, passes=0, prec=eo.DD)
+    assert np.array_equal(host(d1), host(da))
+
+
+def test_cholqr_special_inputs(eo, ctx):
+    # orthonormal input: R = I, Q = X
+    u = synth.orthonormal_basis(9000, 6, 3)
+    d = dev(u)
+    rh, rl, _ = eo.cholqr(ctx, d, prec=eo.DD)
+    assert np.max(np.abs(host(rh) + host(rl) - np.eye(6))) <= 1e-15
+    assert np.max(np.abs(host(d) - u)) <= 4 * U
+    # orthogonal, unnormalized columns: R diagonal
+    s = np.array([1.0, 1e3, 1e-3, 7.0, 0.5, 2.0])
+    d = dev(np.asfortranarray(u * s))
+    rh, _, _ = eo.cholqr(ctx, d, prec=eo.DD)
+    np.testing.assert_allclose(np.diag(host(rh)), s, rtol=1e-14)
+
+
+def test_cholqr_breakdown_and_nan(eo, ctx):
+    x = synth.gaussian(1000, 3, 4)
+    x[:, 1] = 0.0  # the second pivot is exactly zero
+    d = dev(x)
+    _, _, info = eo.cholqr(ctx, d, prec=eo.DD)
+    assert int(info.item()) == 2
+    assert np.array_equal(host(d), x)  # X is left as it was
+    y = synth.gaussian(1000, 3, 5)
+    y[10, 2] = np.nan
+    d = dev(y)
+    _, _, info = eo.cholqr(ctx, d, prec=eo.DD)
+    assert int(info.item()) == -1
+
+
+def test_cholqr_with_gram_from_project(eo, ctx):
+    n, kv, k = 40_000, 16, 4
+    v = synth.orthonormal_basis(n, kv, 71)
+    y = synth.conditioned(n, k, 1e5, 72)
+    yt, _, m = eo.project(ctx, dev(v), dev(y), prec=eo.DD)
+    a = yt.clone().t().contiguous().t()
+    eo.cholqr(ctx, yt, prec=eo.DD, M=m)
+    eo.cholqr(ctx, a, prec=eo.DD)
+    assert np.max(np.abs(host(yt) - host(a))) <= cholqr_tol(n, k, 1e5)
+    q = host(yt)
+    assert oracle.orth_err(q)[0] <= 1e-14
+    assert oracle.cross_err(v, q) <= 1e-14
+
+
+def test_cholqr_f32(eo, ctx):
+    n, k = 30_000, 8
+    x = synth.conditioned(n, k, 1e2, 80).astype(np.float32)
+    d = dev(x)
+    rh, _, info = eo.cholqr(ctx, d, prec=eo.F32)
+    assert int(info.item()) == 0
+    q = host(d).astype(np.float64)
+    assert oracle.orth_err(q)[0] <= 1e-5  # FP32 storage of Q: u32 = 6e-8 per entry
+    q_o, (rh_o, _), _ = oracle.cholqr(x.astype(np.float64))
+    np.testing.assert_allclose(host(rh), rh_o, rtol=0, atol=1e-12 * np.max(np.abs(rh_o)))
+
+
+# ----------------------------------------------------------------- SVQB
+
+@pytest.mark.parametrize("n,k,kappa", [(20_000, 8, 1e2), (20_000, 8, 1e6), (10_001, 16, 1e7), (777, 3, 1.0)])
+def test_svqb_dd_matches_oracle(eo, ctx, n, k, kappa):
+    x = synth.conditioned(n, k, kappa, 800 + k)
+    d = dev(x)
+    zh, zl, rank = eo.svqb(ctx, d, prec=eo.DD)
+    assert int(rank.item()) == k
+    q_o, (zh_o, zl_o), _ = oracle.svqb(x)
+    tol = cholqr_tol(n, k, kappa)
+    assert np.max(np.abs(host(d) - q_o)) <= tol
+    z = host(zh) + host(zl)
+    assert np.max(np.abs(z - (zh_o + zl_o))) <= tol * np.max(np.abs(zh_o))
+    assert np.array_equal(host(zh), host(zh).T)
+    assert oracle.orth_err(host(d))[0] <= 1e-14
+
+
+def test_svqb_rank_deficient(eo, ctx):
+    x = synth.gaussian(5000, 4, 90)
+    x[:, 2] = 0.0
+    d = dev(x)
+    _, _, rank = eo.svqb(ctx, d, prec=eo.DD)
+    assert int(rank.item()) == 3
+    q = host(d)
+    # Q spans the range of X: Q^T Q is the orthogonal projector onto it
+    p = q.T @ q
+    assert np.max(np.abs(p @ p - p)) < 1e-13
+    assert abs(np.trace(p) - 3.0) < 1e-13
+
+
+def test_svqb_orthonormal_input_is_fixed(eo, ctx):
+    u = synth.orthonormal_basis(4000, 5, 91)
+    d = dev(u)
+    zh, zl, _ = eo.svqb(ctx, d, prec=eo.DD)
+    assert np.max(np.abs(host(zh) + host(zl) - np.eye(5))) <= 1e-15
+    assert np.max(np.abs(host(d) - u)) <= 8 * U
+
+
+# ------------------------------------------------------------ arguments
+
+def test_invalid_arguments_are_rejected(eo, ctx):
+    torch = torch_mod()
+    x = dev(synth.gaussian(100, 3, 1))
+    L = eo.lib()
+    h = ctx.h
+    g = torch.zeros((3, 3), dtype=torch.float64, device="cuda")
+    assert L.eo_gram(h, 100, 0, x.data_ptr(), 100, 0, None, 100, g.data_ptr(), None, 3, 1) == eo.EINVAL
+    assert L.eo_gram(h, 100, 65, x.data_ptr(), 100, 65, None, 100, g.data_ptr(), None, 65, 1) == eo.EINVAL
+    assert L.eo_gram(h, 100, 3, x.data_ptr(), 99, 3, None, 99, g.data_ptr(), None, 3, 1) == eo.EINVAL
+    assert L.eo_gram(h, 100, 3, None, 100, 3, None, 100, g.data_ptr(), None, 3, 1) == eo.EINVAL
+    assert L.eo_gram(h, 100, 3, x.data_ptr(), 100, 3, None, 100, g.data_ptr(), None, 3, 7) == eo.EINVAL
+    assert b"precision" in L.eo_last_error(h)
+    assert L.eo_cholqr(h, 100, 3, x.data_ptr(), 100, None, None, 3, None, None, 3, 3, 1, None) == eo.EINVAL
+    assert L.eo_project(h, 100, 3, x.data_ptr(), 100, 3, x.data_ptr(), 100, x.data_ptr(), 100, None, None, 3,
+                        None, None, 3, eo.F32) == eo.EUNSUPPORTED
