@@ -249,6 +249,20 @@ def run_eo(a):
                 "cholesky_info": int(infop.item())}
     except Exception as ex:  # pragma: no cover - reporting only
         comp = {"error": str(ex)}
+    # the paper's FP64-pipe compensated kernels (TwoProd + TwoSum) on the same input
+    eft = {}
+    try:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, me = eo.project(ctx, V, Y, Yout=Yp, prec=eo.DD_EFT)
+        _, _, infoe = eo.cholqr(ctx, Yp, passes=0, prec=eo.DD_EFT, M=me)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tms = e0.elapsed_time(e1)
+        eft = {"prec": "dd_eft", "ms_per_step": tms, "value": nbytes / (tms * 1e-3) / 1e9,
+               "cholesky_info": int(infoe.item())}
+    except Exception as ex:  # pragma: no cover - reporting only
+        eft = {"error": str(ex)}
     del Yp
 
     # end to end through the C-ABI with pinned host buffers
@@ -303,7 +317,7 @@ def run_eo(a):
         "p99_ms": float(np.percentile(per, 99)),
         "orth_err": orth, "cross_err": cross_err, "cholesky_info": info0,
         "bytes_per_step": nbytes, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-        "clocks": clk.summary(), "gpu_launches": launches, "fp64_comparator": comp,
+        "clocks": clk.summary(), "gpu_launches": launches, "fp64_comparator": comp, "dd_eft_comparator": eft,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -49,10 +49,22 @@ extern "C" {
 /* Arithmetic of a call (Sec. 4.2: FP64 vs DD kernels; the FP32-input mode
  * is the building block of the single-precision iterations of Sec. 4.1). */
 typedef enum {
-  EO_FP64 = 0, /* FP64 data, FP64 accumulation                                   */
-  EO_DD = 1,   /* FP64 data, double-double accumulation, results rounded once     */
-  EO_F32 = 2   /* FP32 data (float*), FP64 accumulation of the exact products     */
+  EO_FP64 = 0,   /* FP64 data, FP64 accumulation                                  */
+  EO_DD = 1,     /* FP64 data, compensated accumulation (>= double-double accuracy),
+                    results rounded once; the sums are formed exactly in integer
+                    fixed point (see below)                                        */
+  EO_F32 = 2,    /* FP32 data (float*), FP64 accumulation of the exact products    */
+  EO_DD_EFT = 3  /* as EO_DD, but the sums use the paper's FP64 error-free
+                    transformations (TwoProd + TwoSum) on the FP64 pipe           */
 } eo_prec;
+
+/* EO_DD accuracy: each group of values summed against another (a column of a
+ * block of rows, a row of V or X, a column of C or Z) is aligned to its
+ * largest exponent and held as a 104-bit integer; products of 26-bit limbs
+ * are summed exactly and the ten most significant limb products are kept, so
+ * each product carries an error below 2^-101 max|x| max|y|, and every result
+ * is rounded once.  Integer sums are associative: results do not depend on
+ * the order of the partial sums. */
 
 typedef enum {
   EO_OK = 0,

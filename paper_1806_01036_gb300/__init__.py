@@ -17,7 +17,7 @@ import os
 
 from . import build as _build
 
-FP64, DD, F32 = 0, 1, 2
+FP64, DD, F32, DD_EFT = 0, 1, 2, 3
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
 KMAX = 64
 

@@ -93,7 +93,10 @@ __global__ void copy_small_kernel(int rows, int cols, const double* sh, const do
   }
 }
 
-bool valid_prec(int p) { return p == EO_FP64 || p == EO_DD || p == EO_F32; }
+bool valid_prec(int p) { return p == EO_FP64 || p == EO_DD || p == EO_F32 || p == EO_DD_EFT; }
+
+// Mode of the FP64-pipe kernels for a precision (EO_DD_EFT runs them in DD).
+Mode pipe_mode(eo_prec p) { return p == EO_DD_EFT ? MODE_DD : (Mode)p; }
 
 #define EO_CHECK(cond, code, ...) \
   do {                            \
@@ -120,18 +123,19 @@ eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, 
   ctx->err.clear();
   EO_CHECK(valid_prec(prec), EO_EINVAL, "%s: bad precision mode %lld", name, (long long)prec);
   EO_CHECK(n >= 0 && k >= 1 && k <= KMAX, EO_EINVAL, "%s: bad sizes (n=%lld)", name, (long long)n);
-  EO_CHECK(X != nullptr, EO_EINVAL, "%s: null X", name);
+  EO_CHECK(X != nullptr || n == 0, EO_EINVAL, "%s: null X", name);
   EO_CHECK(ldx >= std::max<int64_t>(1, n), EO_EINVAL, "%s: ldx too small%lld", name, (long long)ldx);
   EO_CHECK(!M_hi || ldm >= k, EO_EINVAL, "%s: ldm too small%lld", name, (long long)ldm);
   EO_CHECK(!(O_hi || O_lo) || ldo >= k, EO_EINVAL, "%s: output leading dimension too small%lld", name, (long long)ldo);
   EO_CHECK(passes >= 0 && passes <= 2, EO_EINVAL, "%s: passes must be 0, 1 or 2 (%lld)", name, (long long)passes);
   DeviceGuard g(ctx->device);
   EO_CHECK(g.ok, EO_ECUDA, "%s: cannot select device", name);
-  eo_status s = ensure_scratch(ctx, gram_scratch_bytes(n, k, k, true));
+  const bool fx = prec == EO_DD;
+  eo_status s = ensure_scratch(ctx, fx ? fx_gram_scratch_bytes(n, k, k, true) : gram_scratch_bytes(n, k, k, true));
   if (s != EO_OK) return s;
   DevStatus* st = status_of(ctx);
   SmallWs* ws = ws_of(ctx);
-  const Mode mode = (Mode)prec;
+  const Mode mode = pipe_mode(prec);
   const Mode small_mode = mode == MODE_DD ? MODE_DD : MODE_FP64;
   EO_CUDA(launch_status_init(st, k, ctx->stream), name);
   ctx->launches += 1;
@@ -144,6 +148,11 @@ eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, 
       mh = M_hi;
       ml = M_lo;
       ld = ldm;
+    } else if (fx) {
+      EO_CUDA(launch_fx_gram(n, k, static_cast<const double*>(X), ldx, k, static_cast<const double*>(X), ldx, true,
+                             parts_of(ctx), ws->Mh, ws->Ml, KMAX, &st->gate[2 * p], ctx->stream),
+              name);
+      ctx->launches += kGramLaunches;
     } else {
       EO_CUDA(launch_gram(mode, n, k, X, ldx, k, X, ldx, true, parts_of(ctx), ws->Mh, ws->Ml, KMAX, &st->gate[2 * p],
                           ctx->stream),
@@ -157,7 +166,12 @@ eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, 
       EO_CUDA(launch_svqb_small(small_mode, k, mh, ml, ld, ws, O_hi, O_lo, ldo, tol, st, p, passes, out_dev,
                                 ctx->stream),
               name);
-    EO_CUDA(launch_update(mode, n, k, X, ldx, ws->Zh, ws->Zl, CHOL, &st->gate[2 * p + 1], ctx->stream), name);
+    if (fx)
+      EO_CUDA(launch_fx_update(n, k, static_cast<double*>(X), ldx, ws->Zh, ws->Zl, CHOL, &st->gate[2 * p + 1],
+                               ctx->stream),
+              name);
+    else
+      EO_CUDA(launch_update(mode, n, k, X, ldx, ws->Zh, ws->Zl, CHOL, &st->gate[2 * p + 1], ctx->stream), name);
     ctx->launches += 2;  // factorization + update
   }
   return EO_OK;
@@ -221,16 +235,24 @@ eo_status eo_gram(eo_ctx* ctx, int64_t n, int kx, const void* X, int64_t ldx, in
   EO_CHECK(valid_prec(prec), EO_EINVAL, "eo_gram: bad precision mode%s %lld", "", (long long)prec);
   EO_CHECK(n >= 0 && kx >= 1 && kx <= KMAX && ky >= 1 && ky <= KMAX, EO_EINVAL, "eo_gram: bad sizes%s (n=%lld)", "",
            (long long)n);
-  EO_CHECK(X != nullptr && G_hi != nullptr, EO_EINVAL, "eo_gram: null pointer%s", "");
+  EO_CHECK((X != nullptr || n == 0) && G_hi != nullptr, EO_EINVAL, "eo_gram: null pointer%s", "");
   EO_CHECK(ldx >= std::max<int64_t>(1, n) && ldy >= std::max<int64_t>(1, n) && ldg >= kx, EO_EINVAL,
            "eo_gram: leading dimension too small%s", "");
   DeviceGuard g(ctx->device);
   EO_CHECK(g.ok, EO_ECUDA, "eo_gram: cannot select device%s", "");
-  eo_status s = ensure_scratch(ctx, gram_scratch_bytes(n, kx, ky, sym));
-  if (s != EO_OK) return s;
-  EO_CUDA(launch_gram((Mode)prec, n, kx, X, ldx, ky, sym ? X : Y, ldy, sym, parts_of(ctx), G_hi, G_lo, ldg, nullptr,
-                      ctx->stream),
-          "eo_gram");
+  if (prec == EO_DD) {
+    eo_status s = ensure_scratch(ctx, fx_gram_scratch_bytes(n, kx, ky, sym));
+    if (s != EO_OK) return s;
+    EO_CUDA(launch_fx_gram(n, kx, static_cast<const double*>(X), ldx, ky, static_cast<const double*>(sym ? X : Y),
+                           ldy, sym, parts_of(ctx), G_hi, G_lo, ldg, nullptr, ctx->stream),
+            "eo_gram");
+  } else {
+    eo_status s = ensure_scratch(ctx, gram_scratch_bytes(n, kx, ky, sym));
+    if (s != EO_OK) return s;
+    EO_CUDA(launch_gram(pipe_mode(prec), n, kx, X, ldx, ky, sym ? X : Y, ldy, sym, parts_of(ctx), G_hi, G_lo, ldg,
+                        nullptr, ctx->stream),
+            "eo_gram");
+  }
   ctx->launches += kGramLaunches;
   return EO_OK;
 }
@@ -243,31 +265,48 @@ eo_status eo_project(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ld
   EO_CHECK(valid_prec(prec), EO_EINVAL, "eo_project: bad precision mode%s %lld", "", (long long)prec);
   EO_CHECK(prec != EO_F32, EO_EUNSUPPORTED, "eo_project: FP32 inputs are not supported%s", "");
   EO_CHECK(n >= 0 && kv >= 1 && kv <= KMAX && k >= 1 && k <= KMAX, EO_EINVAL, "eo_project: bad sizes%s", "");
-  EO_CHECK(V && Y && Yout, EO_EINVAL, "eo_project: null pointer%s", "");
+  EO_CHECK((V && Y && Yout) || n == 0, EO_EINVAL, "eo_project: null pointer%s", "");
   const int64_t mn = std::max<int64_t>(1, n);
   EO_CHECK(ldv >= mn && ldy >= mn && ldyo >= mn, EO_EINVAL, "eo_project: leading dimension too small%s", "");
   EO_CHECK(!C_hi || ldc >= kv, EO_EINVAL, "eo_project: ldc too small%s", "");
   EO_CHECK(!M_hi || ldm >= k, EO_EINVAL, "eo_project: ldm too small%s", "");
   DeviceGuard g(ctx->device);
   EO_CHECK(g.ok, EO_ECUDA, "eo_project: cannot select device%s", "");
-  const size_t need = std::max(gram_scratch_bytes(n, kv, k, false), project_scratch_bytes(n, kv, k));
+  const bool fx = prec == EO_DD;
+  const size_t need = fx ? std::max(fx_gram_scratch_bytes(n, kv, k, false), fx_gram_scratch_bytes(n, k, k, true))
+                         : std::max(gram_scratch_bytes(n, kv, k, false), project_scratch_bytes(n, kv, k));
   eo_status s = ensure_scratch(ctx, need);
   if (s != EO_OK) return s;
   double* ch = c_hi_of(ctx);
   double* cl = c_lo_of(ctx);
-  const Mode mode = (Mode)prec;
-  EO_CUDA(launch_gram(mode, n, kv, V, ldv, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, nullptr, ctx->stream),
-          "eo_project (V^T Y)");
+  const Mode mode = pipe_mode(prec);
+  if (fx)
+    EO_CUDA(launch_fx_gram(n, kv, V, ldv, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, nullptr, ctx->stream),
+            "eo_project (V^T Y)");
+  else
+    EO_CUDA(launch_gram(mode, n, kv, V, ldv, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, nullptr, ctx->stream),
+            "eo_project (V^T Y)");
   ctx->launches += kGramLaunches;
   if (C_hi || C_lo) {
     copy_small_kernel<<<4, 256, 0, ctx->stream>>>(kv, k, ch, cl, KMAX, C_hi, C_lo, ldc);
     EO_CUDA(cudaGetLastError(), "eo_project (copy C)");
     ctx->launches += 1;
   }
-  EO_CUDA(launch_project_fused(mode, n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, mode == MODE_DD ? cl : nullptr, KMAX,
-                               parts_of(ctx), M_hi, M_lo, ldm, ctx->stream),
-          "eo_project (fused pass)");
-  ctx->launches += M_hi ? 2 : 1;
+  if (fx) {
+    EO_CUDA(launch_fx_project(n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, cl, KMAX, ctx->stream), "eo_project");
+    ctx->launches += 1;
+    if (M_hi) {
+      EO_CUDA(launch_fx_gram(n, k, Yout, ldyo, k, Yout, ldyo, true, parts_of(ctx), M_hi, M_lo, ldm, nullptr,
+                             ctx->stream),
+              "eo_project (Gram)");
+      ctx->launches += kGramLaunches;
+    }
+  } else {
+    EO_CUDA(launch_project_fused(mode, n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, mode == MODE_DD ? cl : nullptr, KMAX,
+                                 parts_of(ctx), M_hi, M_lo, ldm, ctx->stream),
+            "eo_project (fused pass)");
+    ctx->launches += M_hi ? 2 : 1;
+  }
   return EO_OK;
 }
 

@@ -10,6 +10,9 @@
 
 namespace eo {
 
+// Arithmetic of the FP64-pipe kernels (gram.cu, project.cu, update.cu,
+// small.cu).  EO_DD_EFT runs them with MODE_DD; EO_DD uses the integer
+// fixed-point kernels (fxgram.cu, fxrow.cu) for every sum over n rows.
 enum Mode : int { MODE_FP64 = EO_FP64, MODE_DD = EO_DD, MODE_F32 = EO_F32 };
 
 constexpr int KMAX = EO_KMAX;
@@ -58,6 +61,19 @@ cudaError_t launch_project_fused(Mode mode, int64_t n, int kv, const double* V, 
 // X <- X Z for Z = (Zh + Zl) (k-by-k, ld KMAX); tri: Z upper triangular.
 cudaError_t launch_update(Mode mode, int64_t n, int k, void* X, int64_t ldx, const double* Zh, const double* Zl,
                           bool tri, const int* gate, cudaStream_t st);
+
+// ------------------------------------- exact fixed-point (EO_DD) kernels
+size_t fx_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym);
+cudaError_t launch_fx_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
+                           bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
+                           cudaStream_t st);
+// X <- X Z in place (Z: k-by-k double-double, leading dimension KMAX).
+cudaError_t launch_fx_update(int64_t n, int k, double* X, int64_t ldx, const double* Zh, const double* Zl, bool tri,
+                             const int* gate, cudaStream_t st);
+// Yout = Y - V C (C: kv-by-k double-double with leading dimension ldc).
+cudaError_t launch_fx_project(int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y, int64_t ldy,
+                              double* Yout, int64_t ldyo, const double* C_hi, const double* C_lo, int ldc,
+                              cudaStream_t st);
 
 // ------------------------------------------------ small k-by-k kernels
 cudaError_t launch_status_init(DevStatus* s, int k, cudaStream_t st);

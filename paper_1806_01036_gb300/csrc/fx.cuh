@@ -1,0 +1,272 @@
+// fx.cuh — exact fixed-point accumulation of FP64 products on the integer pipe.
+//
+// The compensated ("DD") mode of arXiv:1806.01036, Sec. 4.2 needs sums of
+// FP64 products accurate to about 2^-104 relative.  GB300 runs FP64 at about
+// 2 FMA/clk/SM, but 32x32->64-bit integer multiply-adds (IMAD.WIDE) at about
+// 64/clk/SM, so the sums are formed here in integer arithmetic, exactly,
+// instead of with FP64 error-free transformations:
+//
+//  * A group of doubles that is summed over (a column of a row panel, a row
+//    of V, a column of Z) shares one alignment exponent A = the largest
+//    biased exponent in the group.  Each member x becomes the integer
+//      X = floor(|x| * 2^(1178 - A)) < 2^104   (x ~= sign(x) * X * 2^(A - 1178)),
+//    which is exact for every member within 51 binades of the largest, and
+//    is split into four signed 26-bit limbs L_0..L_3 (L_0 most significant).
+//  * A product x*y is sum_{a,b} L_a(x) L_b(y) 2^(26(6-a-b)) * 2^(Ax+Ay-2356).
+//    The ten limb products with a + b <= 3 are accumulated per diagonal
+//    d = a + b into 64-bit integers (each product < 2^52: exact for up to
+//    448 rows per accumulator); the dropped pairs contribute less than
+//    6 * 2^-104 of max|x| * max|y| per product.
+//  * Diagonal accumulators are combined into a 128-bit integer W in units of
+//    2^(Ax+Ay-2252) and rounded to FP64, or to a double-double, with
+//    round-to-nearest-even done in integer arithmetic.
+//
+// Integer sums are exact and associative, so every reduction built on this
+// is independent of the order of its partial sums.
+#pragma once
+
+#include <cstdint>
+
+namespace eo {
+namespace fx {
+
+constexpr int kLimbBits = 26;
+constexpr long long kLimbMask = (1ll << kLimbBits) - 1;
+constexpr int kRowsPerDrain = 384;  // rows a diagonal accumulator may absorb (< 448)
+constexpr int kScaleOffset = 2252;  // W * 2^(Ax + Ay - 2252)
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+struct Limbs {
+  int v[4];
+};
+
+// Biased exponent used for alignment: 1..2046 for finite nonzero values (1 for
+// subnormals), 0 for zero, 2047 for Inf/NaN.
+__device__ __forceinline__ int align_exp(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int be = (hi >> 20) & 0x7ff;
+  if (be == 0) return ((hi & 0xfffffu) | lo) ? 1 : 0;
+  return be;
+}
+
+// Limbs of floor(|x| 2^(1178 - A)) with the sign of x; requires A >= align_exp(x).
+__device__ __forceinline__ Limbs to_limbs(double x, int A) {
+  const unsigned hi = (unsigned)__double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  int be = (hi >> 20) & 0x7ff;
+  unsigned mh = hi & 0xfffffu;
+  if (be) mh |= 0x100000u; else be = 1;
+  const unsigned long long m = ((unsigned long long)mh << 32) | lo;  // < 2^53
+  const int t = 51 - (A - be);  // X = m * 2^t
+  Limbs L;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int p = 78 - kLimbBits * a - t;  // limb a = bits [p, p+26) of m
+    unsigned long long b;
+    if (p >= 64) b = 0;
+    else if (p >= 0) b = m >> p;
+    else if (p > -64) b = m << (-p);
+    else b = 0;
+    L.v[a] = (int)(b & kLimbMask);
+  }
+  if (hi >> 31) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) L.v[a] = -L.v[a];
+  }
+  if (m == 0) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) L.v[a] = 0;
+  }
+  return L;
+}
+
+// Limbs of a double-double h + l (|l| <= ulp(h)/2) aligned to A >= align_exp(h):
+// floor(|h + l| 2^(1178 - A)), computed exactly in 128-bit integers.
+__device__ __forceinline__ Limbs to_limbs_dd(double h, double l, int A) {
+  auto fixed = [A](double x) -> i128 {  // signed, truncated toward zero
+    const unsigned hi = (unsigned)__double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    int be = (hi >> 20) & 0x7ff;
+    unsigned mh = hi & 0xfffffu;
+    if (be) mh |= 0x100000u; else be = 1;
+    const unsigned long long m = ((unsigned long long)mh << 32) | lo;
+    const int t = 51 - (A - be);
+    u128 X;
+    if (t >= 0) X = (u128)m << t;       // t <= 51 + (be_l - be_h) <= 51
+    else if (t > -64) X = (u128)(m >> (-t));
+    else X = 0;
+    return (hi >> 31) ? -(i128)X : (i128)X;
+  };
+  i128 X = fixed(h) + fixed(l);
+  const bool neg = X < 0;
+  u128 U = neg ? (u128)(-X) : (u128)X;
+  Limbs L;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int p = 78 - kLimbBits * a;
+    int v = (int)((U >> p) & (u128)kLimbMask);
+    L.v[a] = neg ? -v : v;
+  }
+  return L;
+}
+
+// acc[d] += sum_{a+b=d} x_a y_b for d = 0..3 (ten IMAD.WIDE).
+__device__ __forceinline__ void mac(long long acc[4], const Limbs& x, const Limbs& y) {
+  acc[0] += (long long)x.v[0] * y.v[0];
+  acc[1] += (long long)x.v[0] * y.v[1];
+  acc[1] += (long long)x.v[1] * y.v[0];
+  acc[2] += (long long)x.v[0] * y.v[2];
+  acc[2] += (long long)x.v[1] * y.v[1];
+  acc[2] += (long long)x.v[2] * y.v[0];
+  acc[3] += (long long)x.v[0] * y.v[3];
+  acc[3] += (long long)x.v[1] * y.v[2];
+  acc[3] += (long long)x.v[2] * y.v[1];
+  acc[3] += (long long)x.v[3] * y.v[0];
+}
+
+__device__ __forceinline__ void mac4(long long acc[4], const int4& x, const int4& y) {
+  Limbs a{{x.x, x.y, x.z, x.w}}, b{{y.x, y.y, y.z, y.w}};
+  mac(acc, a, b);
+}
+
+// W in units of 2^(Ax+Ay-2252): acc0 2^52 + acc1 2^26 + acc2 + floor(acc3 2^-26).
+__device__ __forceinline__ i128 acc_to_w(const long long acc[4]) {
+  return ((i128)acc[0] << 52) + ((i128)acc[1] << 26) + (i128)acc[2] + (i128)(acc[3] >> 26);
+}
+
+__device__ __forceinline__ void acc_shift(long long acc[4], int sh) {
+  if (sh <= 0) return;
+#pragma unroll
+  for (int d = 0; d < 4; ++d) acc[d] = sh >= 63 ? 0 : (acc[d] >> sh);
+}
+
+__device__ __forceinline__ i128 w_shift(i128 w, int sh) {
+  if (sh <= 0) return w;
+  return sh >= 127 ? (i128)0 : (w >> sh);
+}
+
+__device__ __forceinline__ int clz128(u128 u) {
+  const unsigned long long h = (unsigned long long)(u >> 64);
+  return h ? __clzll((long long)h) : 64 + __clzll((long long)(unsigned long long)u);
+}
+
+// Double with magnitude m * 2^e2 (2^52 <= m < 2^53, or m == 0) and the given sign.
+__device__ __forceinline__ double make_double(bool neg, unsigned long long m, int e2) {
+  if (m == 0) return neg ? -0.0 : 0.0;
+  const int be = e2 + 52 + 1023;
+  if (be >= 1 && be <= 2046) {
+    const unsigned long long bits =
+        ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
+  }
+  if (be > 2046) return neg ? -__longlong_as_double(0x7ff0000000000000ll) : __longlong_as_double(0x7ff0000000000000ll);
+  const double v = ldexp((double)m, e2);  // subnormal range: rare
+  return neg ? -v : v;
+}
+
+// Round |u| * 2^S to 53 bits (nearest, ties to even).  Returns the rounded
+// mantissa m (2^52 <= m < 2^53) and its exponent e2 (value = m * 2^e2), and the
+// rounded value as an integer in units of 2^S when it fits (for remainders).
+struct Rounded {
+  unsigned long long m;
+  int e2;
+  u128 as_units;  // m * 2^(e2 - S), exact
+  bool fits;
+};
+
+__device__ __forceinline__ Rounded round53(u128 u, int S) {
+  Rounded r;
+  const int p = 127 - clz128(u);
+  if (p <= 52) {
+    r.m = (unsigned long long)u << (52 - p);
+    r.e2 = S + p - 52;
+    r.as_units = u;
+    r.fits = true;
+    return r;
+  }
+  int sh = p - 52;
+  unsigned long long m = (unsigned long long)(u >> sh);
+  const u128 rem = u & (((u128)1 << sh) - 1);
+  const u128 half = (u128)1 << (sh - 1);
+  if (rem > half || (rem == half && (m & 1))) ++m;
+  u128 units = (u128)m << sh;  // m may be 2^53 here; the shift keeps it exact
+  r.fits = sh + 53 < 127;
+  if (m >> 53) {
+    m >>= 1;
+    ++sh;
+  }
+  r.m = m;
+  r.e2 = S + sh;
+  r.as_units = units;
+  return r;
+}
+
+// Nearest double to w * 2^S.
+__device__ __forceinline__ double w_to_double(i128 w, int S) {
+  if (w == 0) return 0.0;
+  const bool neg = w < 0;
+  const u128 u = neg ? (u128)(-w) : (u128)w;
+  const Rounded r = round53(u, S);
+  return make_double(neg, r.m, r.e2);
+}
+
+// Double-double (hi, lo) nearest to w * 2^S: hi = RN(w 2^S), lo = RN(w 2^S - hi).
+__device__ __forceinline__ void w_to_dd(i128 w, int S, double& hi, double& lo) {
+  if (w == 0) {
+    hi = 0.0;
+    lo = 0.0;
+    return;
+  }
+  const bool neg = w < 0;
+  const u128 u = neg ? (u128)(-w) : (u128)w;
+  const Rounded r = round53(u, S);
+  hi = make_double(neg, r.m, r.e2);
+  const i128 rem = (i128)u - (i128)r.as_units;  // |rem| <= half an ulp of hi, exact
+  lo = w_to_double(neg ? -rem : rem, S);
+}
+
+// 256-bit signed accumulator for sums of 128-bit terms.
+struct Acc256 {
+  u128 lo;
+  i128 hi;
+  __device__ __forceinline__ void zero() {
+    lo = 0;
+    hi = 0;
+  }
+  __device__ __forceinline__ void add(i128 v) {
+    const u128 nl = lo + (u128)v;
+    hi += (v < 0 ? (i128)-1 : (i128)0) + (nl < lo ? (i128)1 : (i128)0);
+    lo = nl;
+  }
+  __device__ __forceinline__ void add(const Acc256& o) {
+    const u128 nl = lo + o.lo;
+    hi += o.hi + (nl < lo ? (i128)1 : (i128)0);
+    lo = nl;
+  }
+  // Reduce to a 128-bit value and an extra scale shift (truncating if needed).
+  __device__ __forceinline__ i128 narrow(int& extra) const {
+    const i128 top = (i128)lo >> 127;  // sign extension of lo as signed
+    if (hi == top && (((i128)lo < 0) == (hi < 0))) {
+      extra = 0;
+      return (i128)lo;
+    }
+    // find how many bits the 256-bit value needs and shift right to fit in 126
+    const bool neg = hi < 0;
+    u128 mh = (u128)hi, ml = lo;
+    if (neg) {  // magnitude of the two's complement 256-bit value
+      ml = ~ml + 1;
+      mh = ~mh + (ml == 0 ? 1 : 0);
+    }
+    const int bits = 128 + (128 - clz128(mh));
+    const int sh = bits - 126;
+    const u128 mag = (ml >> sh) | (mh << (128 - sh));
+    extra = sh;
+    return neg ? -(i128)mag : (i128)mag;
+  }
+};
+
+}  // namespace fx
+}  // namespace eo

@@ -1,0 +1,200 @@
+// fxrow.cu — row-wise products of the compensated mode with exact
+// fixed-point accumulation (fx.cuh):
+//   fx_update:   Y = Y~ Z, the final multiplication of phase II
+//                (arXiv:1806.01036, Sec. 4.2; Z = R^{-1} upper triangular for
+//                CholQR, the symmetric M^{-1/2} for SVQB);
+//   fx_project:  Y~ = Y - V C, the phase I projection with C = V^T Y.
+// Z (or C) is a double-double k-by-k (kv-by-k) matrix; each of its columns
+// is aligned to its largest exponent once per CTA.  Each row of the streamed
+// matrix (Y~ or V) is aligned to its own largest exponent.  A thread owns one
+// row and four output columns; it forms the four sums of exact limb products
+// and rounds each once to FP64 (for the projection, after subtracting the
+// sum from y exactly in integer arithmetic).
+#include <algorithm>
+
+#include "common.cuh"
+#include "fx.cuh"
+
+namespace eo {
+namespace {
+
+using namespace fx;
+
+constexpr int kThreads = 256;
+constexpr int JG = 4;  // output columns per thread
+
+// Limbs of the columns of a double-double matrix B (rows x cols, leading
+// dimension ldb, hi/lo arrays), each column aligned to its largest exponent:
+// Bl[j * rows + i], Eb[j].
+__device__ void load_small_limbs(int rows, int cols, const double* Bh, const double* Bl_, int ldb, int4* Bl, int* Eb) {
+  for (int j = threadIdx.x; j < cols; j += blockDim.x) {
+    int e = 0;
+    for (int i = 0; i < rows; ++i) e = max(e, align_exp(Bh[(size_t)j * ldb + i]));
+    Eb[j] = e + 1;  // one binade of headroom: |h + l| may round up past the largest h
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < rows * cols; t += blockDim.x) {
+    const int i = t % rows, j = t / rows;
+    const double h = Bh[(size_t)j * ldb + i];
+    const double l = Bl_ ? Bl_[(size_t)j * ldb + i] : 0.0;
+    const Limbs L = to_limbs_dd(h, l, Eb[j]);
+    Bl[(size_t)j * rows + i] = make_int4(L.v[0], L.v[1], L.v[2], L.v[3]);
+  }
+  __syncthreads();
+}
+
+// y - w 2^S, rounded to nearest.
+__device__ __forceinline__ double sub_round(double y, i128 w, int S) {
+  if (w == 0) return y;
+  const unsigned hi = (unsigned)__double2hiint(y);
+  const unsigned lo = (unsigned)__double2loint(y);
+  int be = (hi >> 20) & 0x7ff;
+  unsigned mh = hi & 0xfffffu;
+  if (be) mh |= 0x100000u; else be = 1;
+  const unsigned long long m = ((unsigned long long)mh << 32) | lo;
+  if (m == 0) return -w_to_double(w, S);
+  const int ey = be - 1075;  // y = +-m 2^ey
+  int d = ey - S;
+  int T = S;
+  i128 ym;
+  if (d > 72) {  // y dominates: coarsen the grid to 2^(ey - 72)
+    const int sh = d - 72;
+    w = w_shift(w, sh);
+    T = S + sh;
+    ym = (i128)m << 72;
+  } else if (d >= 0) {
+    ym = (i128)m << d;
+  } else {
+    ym = -d >= 64 ? (i128)0 : (i128)(m >> (-d));  // bits of y below the product grid
+  }
+  if (hi >> 31) ym = -ym;
+  return w_to_double(ym - w, T);
+}
+
+// Rows of a panel: P rows, with limbs of the streamed matrix (cols columns)
+// aligned per row.  Shared layout: Sl[c * P + r] (int4), Er[r].
+template <int MODE_UPDATE>
+__global__ void __launch_bounds__(kThreads, 2)
+    fx_rowprod_kernel(int64_t n, int kin, const double* A, int64_t lda, int kout, const double* Bh, const double* Bl,
+                      int ldb, int tri, const double* Yin, int64_t ldyin, double* Out, int64_t ldo, int P,
+                      const int* gate) {
+  if (gate && *gate == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int4* Blimb = reinterpret_cast<int4*>(smem_raw);                 // kout * kin
+  int4* Sl = Blimb + (size_t)kout * kin;                              // kin * P
+  double* pan = reinterpret_cast<double*>(Sl + (size_t)kin * P);      // kin * P
+  int* Eb = reinterpret_cast<int*>(pan + (size_t)kin * P);            // kout
+  int* Er = Eb + kout;                                                // P
+  load_small_limbs(kin, kout, Bh, Bl, ldb, Blimb, Eb);
+
+  const int ngroups = (kout + JG - 1) / JG;
+  const int tid = threadIdx.x;
+  const int my_r = tid % P, my_g = tid / P;  // P * ngroups <= blockDim
+  const bool active = my_g < ngroups;
+  const int j0 = my_g * JG;
+  const int parts = kThreads / P;  // threads per row in the exponent scan
+  const int64_t stride = (int64_t)gridDim.x * P;
+
+  for (int64_t pr = (int64_t)blockIdx.x * P; pr < n; pr += stride) {
+    const int rows = (int)min((int64_t)P, n - pr);
+    if (tid < P) Er[tid] = 0;
+    // the panel, coalesced along rows (every load precedes every store: in place is safe)
+    for (int e = tid; e < kin * P; e += kThreads) {
+      const int c = e / P, r = e % P;
+      pan[e] = r < rows ? A[(size_t)c * lda + pr + r] : 0.0;
+    }
+    __syncthreads();
+    if (my_g < parts) {  // row exponents: `parts` threads per row, strided over columns
+      int m = 0;
+      for (int c = my_g; c < kin; c += parts) m = max(m, align_exp(pan[(size_t)c * P + my_r]));
+      atomicMax(&Er[my_r], m);
+    }
+    __syncthreads();
+    for (int e = tid; e < kin * P; e += kThreads) {
+      const int r = e % P;
+      const Limbs L = to_limbs(pan[e], max(Er[r], 1));
+      Sl[e] = make_int4(L.v[0], L.v[1], L.v[2], L.v[3]);
+    }
+    __syncthreads();
+    if (active && my_r < rows) {
+      long long acc[JG][4];
+#pragma unroll
+      for (int q = 0; q < JG; ++q)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) acc[q][d] = 0;
+      const int iend = tri ? min(kin, j0 + JG) : kin;  // Z is upper triangular for CholQR
+      for (int i = 0; i < iend; ++i) {
+        const int4 a = Sl[(size_t)i * P + my_r];
+#pragma unroll
+        for (int q = 0; q < JG; ++q) {
+          const int j = min(j0 + q, kout - 1);
+          mac4(acc[q], a, Blimb[(size_t)j * kin + i]);
+        }
+      }
+      const int64_t r = pr + my_r;
+#pragma unroll
+      for (int q = 0; q < JG; ++q) {
+        const int j = j0 + q;
+        if (j < kout) {
+          const i128 w = acc_to_w(acc[q]);
+          const int S = max(Er[my_r], 1) + Eb[j] - kScaleOffset;
+          double out;
+          if (MODE_UPDATE)
+            out = w_to_double(w, S);
+          else
+            out = sub_round(Yin[(size_t)j * ldyin + r], w, S);
+          Out[(size_t)j * ldo + r] = out;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int rows_per_panel(int kout) {
+  const int ngroups = (kout + JG - 1) / JG;
+  int P = kThreads / ngroups;
+  return std::max(16, P);
+}
+
+size_t smem_bytes(int kin, int kout, int P) {
+  return sizeof(int4) * ((size_t)kout * kin + (size_t)kin * P) + sizeof(double) * (size_t)kin * P +
+         sizeof(int) * (kout + P);
+}
+
+cudaError_t launch_rowprod(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout, const double* Bh,
+                           const double* Bl, int ldb, bool tri, const double* Yin, int64_t ldyin, double* Out,
+                           int64_t ldo, const int* gate, cudaStream_t st) {
+  const int P = rows_per_panel(kout);
+  const size_t smem = smem_bytes(kin, kout, P);
+  const int64_t panels = (n + P - 1) / P;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(panels, 152 * 2));
+  cudaError_t e;
+  if (update) {
+    e = cudaFuncSetAttribute(fx_rowprod_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fx_rowprod_kernel<1><<<blocks, kThreads, smem, st>>>(n, kin, A, lda, kout, Bh, Bl, ldb, tri ? 1 : 0, nullptr, 0,
+                                                         Out, ldo, P, gate);
+  } else {
+    e = cudaFuncSetAttribute(fx_rowprod_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fx_rowprod_kernel<0><<<blocks, kThreads, smem, st>>>(n, kin, A, lda, kout, Bh, Bl, ldb, 0, Yin, ldyin, Out, ldo,
+                                                         P, gate);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fx_update(int64_t n, int k, double* X, int64_t ldx, const double* Zh, const double* Zl, bool tri,
+                             const int* gate, cudaStream_t st) {
+  return launch_rowprod(true, n, k, X, ldx, k, Zh, Zl, KMAX, tri, nullptr, 0, X, ldx, gate, st);
+}
+
+cudaError_t launch_fx_project(int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y, int64_t ldy,
+                              double* Yout, int64_t ldyo, const double* C_hi, const double* C_lo, int ldc,
+                              cudaStream_t st) {
+  return launch_rowprod(false, n, kv, V, ldv, k, C_hi, C_lo, ldc, false, Y, ldy, Yout, ldyo, nullptr, st);
+}
+
+}  // namespace eo

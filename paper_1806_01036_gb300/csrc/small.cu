@@ -299,11 +299,18 @@ __global__ void __launch_bounds__(kThreads) svqb_small_kernel(int k, const doubl
     rank_s = rank;
   }
   __syncthreads();
+  // one triangle, mirrored, so that Z is exactly symmetric
   for (int t = tid; t < k * k; t += kThreads) {
     const int i = t % k, j = t / k;
+    if (i > j) continue;
     dd v = dd{0.0, 0.0};
     for (int l = 0; l < k; ++l) v = A_::fma(A_::mul(U[l * k + i], w[l]), U[l * k + j], v);
     A[t] = v;
+  }
+  __syncthreads();
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    if (i > j) A[t] = A[i * k + j];
   }
   __syncthreads();
   for (int t = tid; t < k * k; t += kThreads) {
