@@ -54,6 +54,7 @@ eo_status fail(eo_ctx* c, eo_status s, const char* fmt, const char* a = "", long
 
 eo_status cuda_fail(eo_ctx* c, const char* where, cudaError_t e) {
   if (c) c->err = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
+  cudaGetLastError();  // a failed attribute call or launch must not surface in the next call
   return EO_ECUDA;
 }
 

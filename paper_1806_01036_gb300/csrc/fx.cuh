@@ -9,31 +9,75 @@
 //  * A group of doubles that is summed over (a column of a row panel, a row
 //    of V, a column of Z) shares one alignment exponent A = the largest
 //    biased exponent in the group.  Each member x becomes the integer
-//      X = floor(|x| * 2^(1178 - A)) < 2^104   (x ~= sign(x) * X * 2^(A - 1178)),
+//      X = floor(|x| * 2^(1126 - A)) < 2^104   (x ~= sign(x) * X * 2^(A - 1126)),
 //    which is exact for every member within 51 binades of the largest, and
 //    is split into four signed 26-bit limbs L_0..L_3 (L_0 most significant).
-//  * A product x*y is sum_{a,b} L_a(x) L_b(y) 2^(26(6-a-b)) * 2^(Ax+Ay-2356).
+//    (A is a biased exponent: |x| < 2^(A - 1022), so X < 2^104.)
+//  * A product x*y is sum_{a,b} L_a(x) L_b(y) 2^(26(6-a-b)) * 2^(Ax+Ay-2252).
 //    The ten limb products with a + b <= 3 are accumulated per diagonal
 //    d = a + b into 64-bit integers (each product < 2^52: exact for up to
 //    448 rows per accumulator); the dropped pairs contribute less than
 //    6 * 2^-104 of max|x| * max|y| per product.
 //  * Diagonal accumulators are combined into a 128-bit integer W in units of
-//    2^(Ax+Ay-2252) and rounded to FP64, or to a double-double, with
+//    2^(Ax+Ay-2148) and rounded to FP64, or to a double-double, with
 //    round-to-nearest-even done in integer arithmetic.
 //
 // Integer sums are exact and associative, so every reduction built on this
 // is independent of the order of its partial sums.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
+#include <cstring>
+
+#ifdef __CUDACC__
+#define FX_HD __host__ __device__ __forceinline__
+#else
+#define FX_HD inline
+#endif
 
 namespace eo {
 namespace fx {
 
+FX_HD unsigned hi32(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned)__double2hiint(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, 8);
+  return (unsigned)(b >> 32);
+#endif
+}
+FX_HD unsigned lo32(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned)__double2loint(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, 8);
+  return (unsigned)b;
+#endif
+}
+FX_HD double from_bits(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double x;
+  memcpy(&x, &b, 8);
+  return x;
+#endif
+}
+FX_HD int clz64(unsigned long long v) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)v);
+#else
+  return v ? __builtin_clzll(v) : 64;
+#endif
+}
+
 constexpr int kLimbBits = 26;
 constexpr long long kLimbMask = (1ll << kLimbBits) - 1;
 constexpr int kRowsPerDrain = 384;  // rows a diagonal accumulator may absorb (< 448)
-constexpr int kScaleOffset = 2252;  // W * 2^(Ax + Ay - 2252)
+constexpr int kScaleOffset = 2148;  // value = W * 2^(Ax + Ay - 2148)
 
 typedef __int128 i128;
 typedef unsigned __int128 u128;
@@ -44,18 +88,18 @@ struct Limbs {
 
 // Biased exponent used for alignment: 1..2046 for finite nonzero values (1 for
 // subnormals), 0 for zero, 2047 for Inf/NaN.
-__device__ __forceinline__ int align_exp(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x);
-  const unsigned lo = (unsigned)__double2loint(x);
+FX_HD int align_exp(double x) {
+  const unsigned hi = hi32(x);
+  const unsigned lo = lo32(x);
   const int be = (hi >> 20) & 0x7ff;
   if (be == 0) return ((hi & 0xfffffu) | lo) ? 1 : 0;
   return be;
 }
 
-// Limbs of floor(|x| 2^(1178 - A)) with the sign of x; requires A >= align_exp(x).
-__device__ __forceinline__ Limbs to_limbs(double x, int A) {
-  const unsigned hi = (unsigned)__double2hiint(x);
-  const unsigned lo = (unsigned)__double2loint(x);
+// Limbs of floor(|x| 2^(1126 - A)) with the sign of x; requires A >= align_exp(x).
+FX_HD Limbs to_limbs(double x, int A) {
+  const unsigned hi = hi32(x);
+  const unsigned lo = lo32(x);
   int be = (hi >> 20) & 0x7ff;
   unsigned mh = hi & 0xfffffu;
   if (be) mh |= 0x100000u; else be = 1;
@@ -83,12 +127,12 @@ __device__ __forceinline__ Limbs to_limbs(double x, int A) {
   return L;
 }
 
-// Limbs of a double-double h + l (|l| <= ulp(h)/2) aligned to A >= align_exp(h):
-// floor(|h + l| 2^(1178 - A)), computed exactly in 128-bit integers.
-__device__ __forceinline__ Limbs to_limbs_dd(double h, double l, int A) {
+// Limbs of a double-double h + l (|l| <= ulp(h)/2) aligned to A > align_exp(h):
+// floor(|h + l| 2^(1126 - A)), computed exactly in 128-bit integers.
+FX_HD Limbs to_limbs_dd(double h, double l, int A) {
   auto fixed = [A](double x) -> i128 {  // signed, truncated toward zero
-    const unsigned hi = (unsigned)__double2hiint(x);
-    const unsigned lo = (unsigned)__double2loint(x);
+    const unsigned hi = hi32(x);
+    const unsigned lo = lo32(x);
     int be = (hi >> 20) & 0x7ff;
     unsigned mh = hi & 0xfffffu;
     if (be) mh |= 0x100000u; else be = 1;
@@ -114,7 +158,7 @@ __device__ __forceinline__ Limbs to_limbs_dd(double h, double l, int A) {
 }
 
 // acc[d] += sum_{a+b=d} x_a y_b for d = 0..3 (ten IMAD.WIDE).
-__device__ __forceinline__ void mac(long long acc[4], const Limbs& x, const Limbs& y) {
+FX_HD void mac(long long acc[4], const Limbs& x, const Limbs& y) {
   acc[0] += (long long)x.v[0] * y.v[0];
   acc[1] += (long long)x.v[0] * y.v[1];
   acc[1] += (long long)x.v[1] * y.v[0];
@@ -127,42 +171,42 @@ __device__ __forceinline__ void mac(long long acc[4], const Limbs& x, const Limb
   acc[3] += (long long)x.v[3] * y.v[0];
 }
 
-__device__ __forceinline__ void mac4(long long acc[4], const int4& x, const int4& y) {
+FX_HD void mac4(long long acc[4], const int4& x, const int4& y) {
   Limbs a{{x.x, x.y, x.z, x.w}}, b{{y.x, y.y, y.z, y.w}};
   mac(acc, a, b);
 }
 
-// W in units of 2^(Ax+Ay-2252): acc0 2^52 + acc1 2^26 + acc2 + floor(acc3 2^-26).
-__device__ __forceinline__ i128 acc_to_w(const long long acc[4]) {
+// W in units of 2^(Ax+Ay-2148): acc0 2^52 + acc1 2^26 + acc2 + floor(acc3 2^-26).
+FX_HD i128 acc_to_w(const long long acc[4]) {
   return ((i128)acc[0] << 52) + ((i128)acc[1] << 26) + (i128)acc[2] + (i128)(acc[3] >> 26);
 }
 
-__device__ __forceinline__ void acc_shift(long long acc[4], int sh) {
+FX_HD void acc_shift(long long acc[4], int sh) {
   if (sh <= 0) return;
 #pragma unroll
   for (int d = 0; d < 4; ++d) acc[d] = sh >= 63 ? 0 : (acc[d] >> sh);
 }
 
-__device__ __forceinline__ i128 w_shift(i128 w, int sh) {
+FX_HD i128 w_shift(i128 w, int sh) {
   if (sh <= 0) return w;
   return sh >= 127 ? (i128)0 : (w >> sh);
 }
 
-__device__ __forceinline__ int clz128(u128 u) {
+FX_HD int clz128(u128 u) {
   const unsigned long long h = (unsigned long long)(u >> 64);
-  return h ? __clzll((long long)h) : 64 + __clzll((long long)(unsigned long long)u);
+  return h ? clz64(h) : 64 + clz64((unsigned long long)u);
 }
 
 // Double with magnitude m * 2^e2 (2^52 <= m < 2^53, or m == 0) and the given sign.
-__device__ __forceinline__ double make_double(bool neg, unsigned long long m, int e2) {
+FX_HD double make_double(bool neg, unsigned long long m, int e2) {
   if (m == 0) return neg ? -0.0 : 0.0;
   const int be = e2 + 52 + 1023;
   if (be >= 1 && be <= 2046) {
     const unsigned long long bits =
         ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1));
-    return __longlong_as_double((long long)bits);
+    return from_bits(bits);
   }
-  if (be > 2046) return neg ? -__longlong_as_double(0x7ff0000000000000ll) : __longlong_as_double(0x7ff0000000000000ll);
+  if (be > 2046) return from_bits(((unsigned long long)neg << 63) | 0x7ff0000000000000ull);
   const double v = ldexp((double)m, e2);  // subnormal range: rare
   return neg ? -v : v;
 }
@@ -177,7 +221,7 @@ struct Rounded {
   bool fits;
 };
 
-__device__ __forceinline__ Rounded round53(u128 u, int S) {
+FX_HD Rounded round53(u128 u, int S) {
   Rounded r;
   const int p = 127 - clz128(u);
   if (p <= 52) {
@@ -205,7 +249,7 @@ __device__ __forceinline__ Rounded round53(u128 u, int S) {
 }
 
 // Nearest double to w * 2^S.
-__device__ __forceinline__ double w_to_double(i128 w, int S) {
+FX_HD double w_to_double(i128 w, int S) {
   if (w == 0) return 0.0;
   const bool neg = w < 0;
   const u128 u = neg ? (u128)(-w) : (u128)w;
@@ -214,7 +258,7 @@ __device__ __forceinline__ double w_to_double(i128 w, int S) {
 }
 
 // Double-double (hi, lo) nearest to w * 2^S: hi = RN(w 2^S), lo = RN(w 2^S - hi).
-__device__ __forceinline__ void w_to_dd(i128 w, int S, double& hi, double& lo) {
+FX_HD void w_to_dd(i128 w, int S, double& hi, double& lo) {
   if (w == 0) {
     hi = 0.0;
     lo = 0.0;
@@ -228,26 +272,63 @@ __device__ __forceinline__ void w_to_dd(i128 w, int S, double& hi, double& lo) {
   lo = w_to_double(neg ? -rem : rem, S);
 }
 
+// y - w 2^S, rounded to nearest.
+FX_HD double sub_round(double y, i128 w, int S) {
+  if (w == 0) return y;
+  const unsigned hi = hi32(y);
+  const unsigned lo = lo32(y);
+  int be = (hi >> 20) & 0x7ff;
+  unsigned mh = hi & 0xfffffu;
+  if (be) mh |= 0x100000u; else be = 1;
+  const unsigned long long m = ((unsigned long long)mh << 32) | lo;
+  if (m == 0) return -w_to_double(w, S);
+  const int ey = be - 1075;  // y = +-m 2^ey
+  int d = ey - S;
+  int T = S;
+  i128 ym;
+  if (d > 72) {  // y dominates: coarsen the grid to 2^(ey - 72)
+    const int sh = d - 72;
+    w = w_shift(w, sh);
+    T = S + sh;
+    ym = (i128)m << 72;
+  } else if (d >= 0) {
+    ym = (i128)m << d;
+  } else {
+    // y has bits below the product's grid: move w onto y's grid when it fits,
+    // otherwise (|w| too large to shift) drop y's bits below 2^S
+    const u128 aw = w < 0 ? (u128)(-w) : (u128)w;
+    if (clz128(aw) > 1 - d) {
+      w <<= -d;
+      T = S + d;
+      ym = (i128)m;
+    } else {
+      ym = -d >= 64 ? (i128)0 : (i128)(m >> (-d));
+    }
+  }
+  if (hi >> 31) ym = -ym;
+  return w_to_double(ym - w, T);
+}
+
 // 256-bit signed accumulator for sums of 128-bit terms.
 struct Acc256 {
   u128 lo;
   i128 hi;
-  __device__ __forceinline__ void zero() {
+  FX_HD void zero() {
     lo = 0;
     hi = 0;
   }
-  __device__ __forceinline__ void add(i128 v) {
+  FX_HD void add(i128 v) {
     const u128 nl = lo + (u128)v;
     hi += (v < 0 ? (i128)-1 : (i128)0) + (nl < lo ? (i128)1 : (i128)0);
     lo = nl;
   }
-  __device__ __forceinline__ void add(const Acc256& o) {
+  FX_HD void add(const Acc256& o) {
     const u128 nl = lo + o.lo;
     hi += o.hi + (nl < lo ? (i128)1 : (i128)0);
     lo = nl;
   }
   // Reduce to a 128-bit value and an extra scale shift (truncating if needed).
-  __device__ __forceinline__ i128 narrow(int& extra) const {
+  FX_HD i128 narrow(int& extra) const {
     const i128 top = (i128)lo >> 127;  // sign extension of lo as signed
     if (hi == top && (((i128)lo < 0) == (hi < 0))) {
       extra = 0;

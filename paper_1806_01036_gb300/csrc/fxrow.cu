@@ -43,34 +43,6 @@ __device__ void load_small_limbs(int rows, int cols, const double* Bh, const dou
   __syncthreads();
 }
 
-// y - w 2^S, rounded to nearest.
-__device__ __forceinline__ double sub_round(double y, i128 w, int S) {
-  if (w == 0) return y;
-  const unsigned hi = (unsigned)__double2hiint(y);
-  const unsigned lo = (unsigned)__double2loint(y);
-  int be = (hi >> 20) & 0x7ff;
-  unsigned mh = hi & 0xfffffu;
-  if (be) mh |= 0x100000u; else be = 1;
-  const unsigned long long m = ((unsigned long long)mh << 32) | lo;
-  if (m == 0) return -w_to_double(w, S);
-  const int ey = be - 1075;  // y = +-m 2^ey
-  int d = ey - S;
-  int T = S;
-  i128 ym;
-  if (d > 72) {  // y dominates: coarsen the grid to 2^(ey - 72)
-    const int sh = d - 72;
-    w = w_shift(w, sh);
-    T = S + sh;
-    ym = (i128)m << 72;
-  } else if (d >= 0) {
-    ym = (i128)m << d;
-  } else {
-    ym = -d >= 64 ? (i128)0 : (i128)(m >> (-d));  // bits of y below the product grid
-  }
-  if (hi >> 31) ym = -ym;
-  return w_to_double(ym - w, T);
-}
-
 // Rows of a panel: P rows, with limbs of the streamed matrix (cols columns)
 // aligned per row.  Shared layout: Sl[c * P + r] (int4), Er[r].
 template <int MODE_UPDATE>
@@ -151,10 +123,17 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
-int rows_per_panel(int kout) {
+constexpr size_t kSmemBudget = 200 * 1024;
+
+int rows_per_panel(int kin, int kout) {
   const int ngroups = (kout + JG - 1) / JG;
-  int P = kThreads / ngroups;
-  return std::max(16, P);
+  int P = std::max(16, kThreads / ngroups);
+  // shared memory: B's limbs, the panel's limbs and values, exponents
+  const size_t fixed = sizeof(int4) * (size_t)kout * kin + sizeof(int) * kout;
+  const size_t per_row = (sizeof(int4) + sizeof(double)) * (size_t)kin + sizeof(int);
+  const int cap = (int)((kSmemBudget - fixed) / per_row);
+  if (P > cap) P = std::max(16, cap / 16 * 16);
+  return P;
 }
 
 size_t smem_bytes(int kin, int kout, int P) {
@@ -165,7 +144,7 @@ size_t smem_bytes(int kin, int kout, int P) {
 cudaError_t launch_rowprod(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout, const double* Bh,
                            const double* Bl, int ldb, bool tri, const double* Yin, int64_t ldyin, double* Out,
                            int64_t ldo, const int* gate, cudaStream_t st) {
-  const int P = rows_per_panel(kout);
+  const int P = rows_per_panel(kin, kout);
   const size_t smem = smem_bytes(kin, kout, P);
   const int64_t panels = (n + P - 1) / P;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(panels, 152 * 2));
