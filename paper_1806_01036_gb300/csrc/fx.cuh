@@ -181,10 +181,18 @@ FX_HD i128 acc_to_w(const long long acc[4]) {
   return ((i128)acc[0] << 52) + ((i128)acc[1] << 26) + (i128)acc[2] + (i128)(acc[3] >> 26);
 }
 
+// Divide the accumulated value by 2^sh (floor), as when the alignment
+// exponent of one of its factors grows by sh.  The diagonals carry different
+// weights, so the value is combined first and redistributed exactly:
+// W' = floor(W 2^-sh) = acc0' 2^52 + acc2' with 0 <= acc2' < 2^52.
 FX_HD void acc_shift(long long acc[4], int sh) {
   if (sh <= 0) return;
-#pragma unroll
-  for (int d = 0; d < 4; ++d) acc[d] = sh >= 63 ? 0 : (acc[d] >> sh);
+  i128 w = ((i128)acc[0] << 52) + ((i128)acc[1] << 26) + (i128)acc[2] + (i128)(acc[3] >> 26);
+  w = sh >= 127 ? (w < 0 ? (i128)-1 : (i128)0) : (w >> sh);
+  acc[0] = (long long)(w >> 52);
+  acc[1] = 0;
+  acc[2] = (long long)(w & (((i128)1 << 52) - 1));
+  acc[3] = 0;
 }
 
 FX_HD i128 w_shift(i128 w, int sh) {

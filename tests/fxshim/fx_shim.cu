@@ -30,6 +30,17 @@ void fxs_dot(int n, const double* x, const double* y, int Ax, int Ay, double* hi
   w_to_dd(acc_to_w(acc), Ax + Ay - kScaleOffset, *hi, *lo);
 }
 
+// The dot product of fxs_dot, but the alignment of y grows from Ay0 to Ay1
+// after the first n0 terms (the accumulator is rescaled, as in the Gram kernel).
+void fxs_dot_rescaled(int n, int n0, const double* x, const double* y, int Ax, int Ay0, int Ay1, double* hi,
+                      double* lo) {
+  long long acc[4] = {0, 0, 0, 0};
+  for (int i = 0; i < n0; ++i) mac(acc, to_limbs(x[i], Ax), to_limbs(y[i], Ay0));
+  acc_shift(acc, Ay1 - Ay0);
+  for (int i = n0; i < n; ++i) mac(acc, to_limbs(x[i], Ax), to_limbs(y[i], Ay1));
+  w_to_dd(acc_to_w(acc), Ax + Ay1 - kScaleOffset, *hi, *lo);
+}
+
 static i128 mk(long long lo, long long hi) { return (i128)(((u128)(unsigned long long)hi << 64) | (unsigned long long)lo); }
 
 void fxs_w_to_dd(long long wlo, long long whi, int S, double* hi, double* lo) { w_to_dd(mk(wlo, whi), S, *hi, *lo); }

@@ -30,6 +30,7 @@ def fx(tmp_path_factory):
     L.fxs_to_limbs.argtypes = [d, i, p]
     L.fxs_to_limbs_dd.argtypes = [d, d, i, p]
     L.fxs_dot.argtypes = [i, p, p, i, i, p, p]
+    L.fxs_dot_rescaled.argtypes = [i, i, p, p, i, i, i, p, p]
     L.fxs_w_to_dd.argtypes = [ll, ll, i, p, p]
     L.fxs_w_to_double.argtypes = [ll, ll, i]
     L.fxs_w_to_double.restype = d
@@ -120,6 +121,25 @@ def test_dot_matches_exact_sum(fx, n):
     bound = n * 8 * F(2) ** -104 * F(float(np.max(np.abs(x)))) * F(float(np.max(np.abs(y)))) * 4
     assert abs(F(hi.value) + F(lo.value) - exact) <= bound + F(2) ** -104 * abs(exact)
     assert hi.value == rn(exact) or abs(F(hi.value) - exact) <= F(2) ** -52 * abs(exact)
+
+
+@pytest.mark.parametrize("grow", [1, 3, 30])
+def test_dot_with_growing_alignment(fx, grow):
+    # as in the Gram kernel: later rows raise a column's alignment exponent and the
+    # accumulator is divided by 2^grow; the result keeps the full accuracy
+    g = np.random.default_rng(40 + grow)
+    n, n0 = 300, 120
+    x = g.standard_normal(n)
+    y = g.standard_normal(n)
+    y[n0:] *= 2.0 ** grow
+    Ax = max(fx.fxs_align_exp(float(v)) for v in x)
+    Ay0 = max(fx.fxs_align_exp(float(v)) for v in y[:n0])
+    Ay1 = max(fx.fxs_align_exp(float(v)) for v in y)
+    hi, lo = C.c_double(), C.c_double()
+    fx.fxs_dot_rescaled(n, n0, x.ctypes.data, y.ctypes.data, Ax, Ay0, Ay1, C.byref(hi), C.byref(lo))
+    exact = sum((F(float(a)) * F(float(b)) for a, b in zip(x, y)), F(0))
+    bound = n * 32 * F(2) ** -104 * F(float(np.max(np.abs(x)))) * F(float(np.max(np.abs(y))))
+    assert abs(F(hi.value) + F(lo.value) - exact) <= bound
 
 
 def test_w_to_dd_rounds_to_nearest(fx):
