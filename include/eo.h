@@ -151,6 +151,31 @@ EO_API eo_status eo_cholqr(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, 
 EO_API eo_status eo_svqb(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, const double* M_hi, const double* M_lo,
                   int ldm, double* Z_hi, double* Z_lo, int ldz, double tol, int passes, eo_prec prec, int* rank_dev);
 
+/*
+ * Allocation-free compensated Gram product (no counterpart in the paper).
+ *
+ * eo_gram_dd_noalloc computes the same G = X^T Y as eo_gram(..., EO_DD) for
+ * callers that cannot allocate device memory when they need it: a component
+ * whose GPU memory is wholly owned by another allocator, or a latency-critical
+ * loop that must not call cudaMalloc/cudaFree (which may synchronize the
+ * device).  It needs no context and allocates nothing: its scratch is a
+ * fixed array of EO_NOALLOC_SCRATCH_BYTES inside the library, held on every
+ * GPU that loads the library until the process exits.
+ *   X, Y, G_hi, G_lo, lds: as in eo_gram (Y == NULL: Y = X); FP64 data.
+ *   kx, ky must not exceed EO_NOALLOC_KMAX; larger sizes return EO_EINVAL.
+ *   cuda_stream: the cudaStream_t to run on (NULL = default stream); the
+ *   current CUDA device is used.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the one array, so calls whose work overlaps on the GPU
+ * (different streams, or other host threads) race and give wrong results;
+ * serialize them.  Returns EO_OK, EO_EINVAL or EO_ECUDA.
+ */
+#define EO_NOALLOC_KMAX 16
+#define EO_NOALLOC_SCRATCH_BYTES (152u * EO_NOALLOC_KMAX * EO_NOALLOC_KMAX * 32u)
+EO_API eo_status eo_gram_dd_noalloc(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y,
+                                    int64_t ldy, double* G_hi, double* G_lo, int ldg, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

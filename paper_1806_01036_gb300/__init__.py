@@ -55,7 +55,9 @@ def lib():
         L.eo_project.argtypes = [_p, _i64, _int, _p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _p, _p, _int, _int]
         L.eo_cholqr.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _int, _int, _p]
         L.eo_svqb.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _dbl, _int, _int, _p]
-        for f in ("eo_create", "eo_destroy", "eo_set_stream", "eo_gram", "eo_project", "eo_cholqr", "eo_svqb"):
+        L.eo_gram_dd_noalloc.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int, _p]
+        for f in ("eo_create", "eo_destroy", "eo_set_stream", "eo_gram", "eo_project", "eo_cholqr", "eo_svqb",
+                  "eo_gram_dd_noalloc"):
             getattr(L, f).restype = _int
         _lib = L
     return _lib
@@ -197,3 +199,27 @@ def svqb(ctx: Context, X, passes: int = 1, prec: int = DD, tol: float = -1.0, M=
                             None if ml is None else ml.data_ptr(), ldm, zh.data_ptr(), zl.data_ptr(), zh.stride(1),
                             float(tol), int(passes), prec, rank.data_ptr()))
     return zh, zl, rank
+
+
+NOALLOC_KMAX = 16
+
+
+def gram_dd_noalloc(X, Y=None, out=None):
+    """(G_hi, G_lo) = X^T Y in EO_DD through eo_gram_dd_noalloc (no context,
+    no device allocation inside the library; kx, ky <= 16).  Runs on torch's
+    current stream and device."""
+    import torch
+    X, n, kx, ldx = _mat(X, "X", torch.float64)
+    if Y is not None:
+        Y, ny, ky, ldy = _mat(Y, "Y", torch.float64)
+        if ny != n:
+            raise ValueError("X and Y must have the same number of rows")
+    else:
+        ky, ldy = kx, ldx
+    hi, lo = out if out is not None else _small(kx, ky, X.device)
+    st = lib().eo_gram_dd_noalloc(n, kx, X.data_ptr(), ldx, ky, None if Y is None else Y.data_ptr(), ldy,
+                                  hi.data_ptr(), None if lo is None else lo.data_ptr(), hi.stride(1),
+                                  C.c_void_p(torch.cuda.current_stream(X.device).cuda_stream))
+    if st != OK:
+        raise EoError(st, "eo_gram_dd_noalloc failed")
+    return hi, lo
