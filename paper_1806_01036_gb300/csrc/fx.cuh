@@ -97,6 +97,8 @@ FX_HD int align_exp(double x) {
 }
 
 // Limbs of floor(|x| 2^(1126 - A)) with the sign of x; requires A >= align_exp(x).
+// X = m 2^t (t = 51 - (A - be) <= 51) is formed as a 128-bit integer and the
+// limbs are cut from it with funnel shifts.
 FX_HD Limbs to_limbs(double x, int A) {
   const unsigned hi = hi32(x);
   const unsigned lo = lo32(x);
@@ -104,25 +106,20 @@ FX_HD Limbs to_limbs(double x, int A) {
   unsigned mh = hi & 0xfffffu;
   if (be) mh |= 0x100000u; else be = 1;
   const unsigned long long m = ((unsigned long long)mh << 32) | lo;  // < 2^53
-  const int t = 51 - (A - be);  // X = m * 2^t
+  const int t = 51 - (A - be);
+  u128 X;
+  if (t >= 0) X = (u128)m << t;
+  else if (t > -64) X = (u128)(m >> (-t));
+  else X = 0;
+  const unsigned long long x0 = (unsigned long long)X, x1 = (unsigned long long)(X >> 64);
   Limbs L;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int p = 78 - kLimbBits * a - t;  // limb a = bits [p, p+26) of m
-    unsigned long long b;
-    if (p >= 64) b = 0;
-    else if (p >= 0) b = m >> p;
-    else if (p > -64) b = m << (-p);
-    else b = 0;
-    L.v[a] = (int)(b & kLimbMask);
-  }
+  L.v[3] = (int)(x0 & kLimbMask);
+  L.v[2] = (int)((x0 >> 26) & kLimbMask);
+  L.v[1] = (int)(((x0 >> 52) | (x1 << 12)) & kLimbMask);
+  L.v[0] = (int)((x1 >> 14) & kLimbMask);
   if (hi >> 31) {
 #pragma unroll
     for (int a = 0; a < 4; ++a) L.v[a] = -L.v[a];
-  }
-  if (m == 0) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a) L.v[a] = 0;
   }
   return L;
 }
@@ -157,23 +154,41 @@ FX_HD Limbs to_limbs_dd(double h, double l, int A) {
   return L;
 }
 
-// acc[d] += sum_{a+b=d} x_a y_b for d = 0..3 (ten IMAD.WIDE).
-FX_HD void mac(long long acc[4], const Limbs& x, const Limbs& y) {
-  acc[0] += (long long)x.v[0] * y.v[0];
-  acc[1] += (long long)x.v[0] * y.v[1];
-  acc[1] += (long long)x.v[1] * y.v[0];
-  acc[2] += (long long)x.v[0] * y.v[2];
-  acc[2] += (long long)x.v[1] * y.v[1];
-  acc[2] += (long long)x.v[2] * y.v[0];
-  acc[3] += (long long)x.v[0] * y.v[3];
-  acc[3] += (long long)x.v[1] * y.v[2];
-  acc[3] += (long long)x.v[2] * y.v[1];
-  acc[3] += (long long)x.v[3] * y.v[0];
+// acc += a * b with a 32x32 -> 64-bit signed multiply-add (one IMAD.WIDE).
+FX_HD void madw(long long& acc, int a, int b) {
+#ifdef __CUDA_ARCH__
+  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+#else
+  acc += (long long)a * b;
+#endif
 }
 
+// acc[d] += sum_{a+b=d} x_a y_b for d = 0..3 (ten IMAD.WIDE).
+FX_HD void mac(long long acc[4], const Limbs& x, const Limbs& y) {
+  madw(acc[0], x.v[0], y.v[0]);
+  madw(acc[1], x.v[0], y.v[1]);
+  madw(acc[1], x.v[1], y.v[0]);
+  madw(acc[2], x.v[0], y.v[2]);
+  madw(acc[2], x.v[1], y.v[1]);
+  madw(acc[2], x.v[2], y.v[0]);
+  madw(acc[3], x.v[0], y.v[3]);
+  madw(acc[3], x.v[1], y.v[2]);
+  madw(acc[3], x.v[2], y.v[1]);
+  madw(acc[3], x.v[3], y.v[0]);
+}
+
+// mac() on limbs held in int4 (x = L0, y = L1, z = L2, w = L3).
 FX_HD void mac4(long long acc[4], const int4& x, const int4& y) {
-  Limbs a{{x.x, x.y, x.z, x.w}}, b{{y.x, y.y, y.z, y.w}};
-  mac(acc, a, b);
+  madw(acc[0], x.x, y.x);
+  madw(acc[1], x.x, y.y);
+  madw(acc[1], x.y, y.x);
+  madw(acc[2], x.x, y.z);
+  madw(acc[2], x.y, y.y);
+  madw(acc[2], x.z, y.x);
+  madw(acc[3], x.x, y.w);
+  madw(acc[3], x.y, y.z);
+  madw(acc[3], x.z, y.y);
+  madw(acc[3], x.w, y.x);
 }
 
 // W in units of 2^(Ax+Ay-2148): acc0 2^52 + acc1 2^26 + acc2 + floor(acc3 2^-26).

@@ -54,8 +54,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int4* Blimb = reinterpret_cast<int4*>(smem_raw);                 // kout * kin
   int4* Sl = Blimb + (size_t)kout * kin;                              // kin * P
-  double* pan = reinterpret_cast<double*>(Sl + (size_t)kin * P);      // kin * P
-  int* Eb = reinterpret_cast<int*>(pan + (size_t)kin * P);            // kout
+  int* Eb = reinterpret_cast<int*>(Sl + (size_t)kin * P);             // kout
   int* Er = Eb + kout;                                                // P
   load_small_limbs(kin, kout, Bh, Bl, ldb, Blimb, Eb);
 
@@ -70,21 +69,19 @@ __global__ void __launch_bounds__(kThreads, 2)
   for (int64_t pr = (int64_t)blockIdx.x * P; pr < n; pr += stride) {
     const int rows = (int)min((int64_t)P, n - pr);
     if (tid < P) Er[tid] = 0;
-    // the panel, coalesced along rows (every load precedes every store: in place is safe)
-    for (int e = tid; e < kin * P; e += kThreads) {
-      const int c = e / P, r = e % P;
-      pan[e] = r < rows ? A[(size_t)c * lda + pr + r] : 0.0;
-    }
     __syncthreads();
-    if (my_g < parts) {  // row exponents: `parts` threads per row, strided over columns
+    // row exponents: `parts` threads per row, strided over columns (loads
+    // coalesced along rows; every load of the panel precedes every store of it,
+    // so the update may run in place)
+    if (my_g < parts && my_r < rows) {
       int m = 0;
-      for (int c = my_g; c < kin; c += parts) m = max(m, align_exp(pan[(size_t)c * P + my_r]));
+      for (int c = my_g; c < kin; c += parts) m = max(m, align_exp(A[(size_t)c * lda + pr + my_r]));
       atomicMax(&Er[my_r], m);
     }
     __syncthreads();
-    for (int e = tid; e < kin * P; e += kThreads) {
-      const int r = e % P;
-      const Limbs L = to_limbs(pan[e], max(Er[r], 1));
+    for (int e = tid; e < kin * P; e += kThreads) {  // second read of the panel: from L1/L2
+      const int c = e / P, r = e % P;
+      const Limbs L = r < rows ? to_limbs(A[(size_t)c * lda + pr + r], max(Er[r], 1)) : Limbs{{0, 0, 0, 0}};
       Sl[e] = make_int4(L.v[0], L.v[1], L.v[2], L.v[3]);
     }
     __syncthreads();
@@ -123,22 +120,21 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
-constexpr size_t kSmemBudget = 200 * 1024;
+constexpr size_t kSmemBudget = 110 * 1024;  // two CTAs per SM
 
 int rows_per_panel(int kin, int kout) {
   const int ngroups = (kout + JG - 1) / JG;
   int P = std::max(16, kThreads / ngroups);
   // shared memory: B's limbs, the panel's limbs and values, exponents
   const size_t fixed = sizeof(int4) * (size_t)kout * kin + sizeof(int) * kout;
-  const size_t per_row = (sizeof(int4) + sizeof(double)) * (size_t)kin + sizeof(int);
+  const size_t per_row = sizeof(int4) * (size_t)kin + sizeof(int);
   const int cap = (int)((kSmemBudget - fixed) / per_row);
   if (P > cap) P = std::max(16, cap / 16 * 16);
   return P;
 }
 
 size_t smem_bytes(int kin, int kout, int P) {
-  return sizeof(int4) * ((size_t)kout * kin + (size_t)kin * P) + sizeof(double) * (size_t)kin * P +
-         sizeof(int) * (kout + P);
+  return sizeof(int4) * ((size_t)kout * kin + (size_t)kin * P) + sizeof(int) * (kout + P);
 }
 
 cudaError_t launch_rowprod(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout, const double* Bh,
