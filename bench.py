@@ -4,8 +4,9 @@
 Workload (one "step" = one pass of the whole path over one block):
   V: 4,000,000 x 64 FP64 orthonormal basis, Y: 4,000,000 x 16 FP64 with
   singular values log-spaced 1 .. 1e-10 (seeded, synthetic; see synth.py).
-  step = eo_project (C = V^T Y, Y~ = Y - V C with M = Y~^T Y~ fused, DD)
-       + eo_cholqr  (DD, first pass from the fused M, automatic second pass).
+  step = eo_gram          (C = V^T Y, compensated)
+       + eo_project_apply (Y~ = Y - V C and M = Y~^T Y~, compensated)
+       + eo_cholqr        (compensated, first pass from M, automatic second pass).
 The inputs (2.6 GB per step) are larger than L2 (129 MB), so no flush is
 needed between steps.
 
@@ -48,6 +49,29 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
+
+
+def max_over_ranks(x, device):
+    """Largest value of x over all ranks (x itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world_size, bytes_per_rank, max_ms):
+    """Whole-job GB/s: every rank processed bytes_per_rank in at most max_ms."""
+    return world_size * bytes_per_rank / (max_ms * 1e-3) / 1e9
+
+
+def alu_peak_tflops(sm_mhz=2070.0, sms=152):
+    """Peak of the compensated (EO_DD) engine in algorithmic TFLOP/s: 64
+    integer multiply-add lanes per SM per clock, ten 32x32->64-bit limb
+    products per exact multiply-add, two flops per multiply-add."""
+    return 64 * sms * sm_mhz * 1e6 / 10 * 2 / 1e12
 
 
 def step_bytes(n, kv, k, two_passes):
@@ -175,9 +199,11 @@ def run_eo(a):
     ctx = eo.Context(local)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        _, _, m = eo.project(ctx, V, Y, Yout=Yt, prec=eo.DD)
-        return eo.cholqr(ctx, Yt, passes=0, prec=eo.DD, M=m)
+    def step(prec=eo.DD, out=None, passes=0):
+        out = Yt if out is None else out
+        c = eo.gram(ctx, V, Y, prec=prec)
+        _, m = eo.project_apply(ctx, V, Y, c, Yout=out, prec=prec)
+        return eo.cholqr(ctx, out, passes=passes, prec=prec, M=m)
 
     for _ in range(max(3, a.warmup)):
         rh, rl, info = step()
@@ -187,13 +213,13 @@ def run_eo(a):
     two_passes = bool((rd.max() / rd.min()).item() > 1e7)
     # orthogonality of the result, measured with the library's own DD Gram
     gh, gl = eo.gram(ctx, Yt, prec=eo.DD)
-    orth = float(torch.linalg.matrix_norm(gh - torch.eye(k, dtype=torch.float64, device=dev) + gl, ord=2).item())
+    e = (gh.cpu().numpy() - np.eye(k)) + gl.cpu().numpy()  # k-by-k: its 2-norm on the host
+    orth = float(np.linalg.norm(e, 2))
     cross = eo.gram(ctx, V, Yt, prec=eo.DD)
-    cross_err = float(torch.linalg.matrix_norm(cross[0] + cross[1], ord=2).item())
+    cross_err = float(np.linalg.norm(cross[0].cpu().numpy() + cross[1].cpu().numpy(), 2))
 
     nbytes = step_bytes(n, kv, k, two_passes)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(a.steps)]
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -206,33 +232,38 @@ def run_eo(a):
         t_all0.record(stream)
         for i in range(a.steps):
             ev[i][0].record(stream)
-            _, _, m = eo.project(ctx, V, Y, Yout=Yt, prec=eo.DD)
+            c = eo.gram(ctx, V, Y, prec=eo.DD)
             ev[i][1].record(stream)
-            eo.cholqr(ctx, Yt, passes=0, prec=eo.DD, M=m)
+            _, m = eo.project_apply(ctx, V, Y, c, Yout=Yt, prec=eo.DD)
             ev[i][2].record(stream)
+            eo.cholqr(ctx, Yt, passes=0, prec=eo.DD, M=m)
+            ev[i][3].record(stream)
         t_all1.record(stream)
         torch.cuda.synchronize()
     launches = ctx.launches() - l0
     if ws > 1:
         dist.barrier()
-    total_ms = t_all0.elapsed_time(t_all1)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    per = [e[0].elapsed_time(e[2]) for e in ev]
-    proj_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
-    chol_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    total_ms = max_over_ranks(t_all0.elapsed_time(t_all1), dev)
+    per = [e[0].elapsed_time(e[3]) for e in ev]
+    gram_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    apply_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    chol_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
     ms = total_ms / a.steps
-    value = ws * nbytes / (ms * 1e-3) / 1e9
+    value = weak_scaling_value(ws, nbytes, ms)
 
-    # roofline of the dominant launch sequence (the projection call)
-    peak, peak_kind = peak_hbm()
-    proj_bytes = 8 * n * (kv + k) + 8 * n * (kv + 2 * k)
-    achieved = proj_bytes / (proj_ms * 1e-3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "eo_project (V^T Y Gram + fused projection/Gram pass)",
-            "peak_source": peak_kind, "launch_ms": proj_ms, "cholqr_ms": chol_ms}
+    # roofline of the dominant kernel: the compensated Gram V^T Y (fx_gram_partial
+    # + its fixed-order reduction), bound by the integer multiply-add pipe
+    hbm_peak, peak_kind = peak_hbm()
+    gram_flops = 2.0 * n * kv * k
+    achieved = gram_flops / (gram_ms * 1e-3) / 1e12
+    peak = alu_peak_tflops()
+    gram_bytes = 8 * n * (kv + k)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "fx_gram_partial_kernel (compensated V^T Y, 4e6 x 64 x 16)",
+            "peak_source": "derived: 64 IMAD lanes/clk/SM x 152 SMs x 2070 MHz / 10 limb products x 2 flops",
+            "launch_ms": gram_ms, "hbm_achieved_gbs": gram_bytes / (gram_ms * 1e-3) / 1e9,
+            "hbm_frac": gram_bytes / (gram_ms * 1e-3) / 1e9 / hbm_peak, "hbm_peak_gbs": hbm_peak,
+            "hbm_peak_source": peak_kind, "apply_ms": apply_ms, "cholqr_ms": chol_ms}
 
     # plain FP64 comparator on the same input (two passes; breaks down at this kappa)
     Yp = torch.empty_like(Yt.t()).t()
@@ -240,8 +271,7 @@ def run_eo(a):
     try:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, _, mp = eo.project(ctx, V, Y, Yout=Yp, prec=eo.FP64)
-        _, _, infop = eo.cholqr(ctx, Yp, passes=2, prec=eo.FP64, M=mp)
+        _, _, infop = step(prec=eo.FP64, out=Yp, passes=2)
         e1.record(stream)
         torch.cuda.synchronize()
         tms = e0.elapsed_time(e1)
@@ -254,8 +284,7 @@ def run_eo(a):
     try:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        _, _, me = eo.project(ctx, V, Y, Yout=Yp, prec=eo.DD_EFT)
-        _, _, infoe = eo.cholqr(ctx, Yp, passes=0, prec=eo.DD_EFT, M=me)
+        _, _, infoe = step(prec=eo.DD_EFT, out=Yp, passes=0)
         e1.record(stream)
         torch.cuda.synchronize()
         tms = e0.elapsed_time(e1)
@@ -279,7 +308,8 @@ def run_eo(a):
         def e2e_step():
             Vd.copy_(Vh, non_blocking=True)
             Yd.copy_(Yh, non_blocking=True)
-            _, _, m = eo.project(ctx, Vd.t(), Yd.t(), Yout=Qd.t(), prec=eo.DD)
+            c = eo.gram(ctx, Vd.t(), Yd.t(), prec=eo.DD)
+            _, m = eo.project_apply(ctx, Vd.t(), Yd.t(), c, Yout=Qd.t(), prec=eo.DD)
             r, _, _ = eo.cholqr(ctx, Qd.t(), passes=0, prec=eo.DD, M=m)
             Qh.copy_(Qd, non_blocking=True)
             Rh.copy_(r.t(), non_blocking=True)
@@ -294,12 +324,8 @@ def run_eo(a):
             e2e_step()
         s1.record(stream)
         torch.cuda.synchronize()
-        ems = s0.elapsed_time(s1) / ke
-        if ws > 1:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": ws * nbytes / (ems * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ems,
+        ems = max_over_ranks(s0.elapsed_time(s1) / ke, dev)
+        e2e = {"value": weak_scaling_value(ws, nbytes, ems), "unit": "GB/s", "ms_per_step": ems,
                "h2d_bytes_per_step": 8 * n * (kv + k), "d2h_bytes_per_step": 8 * n * k + 8 * k * k}
 
     cpu = None

@@ -119,6 +119,17 @@ EO_API eo_status eo_project(eo_ctx* ctx, int64_t n, int kv, const double* V, int
                      double* M_lo, int ldm, eo_prec prec);
 
 /*
+ * The second half of phase I for a given C (Sec. 4.2: Y~ = X - W (W^T X)):
+ * Yout = Y - V C with C = C_hi + C_lo (kv-by-k, ldc; C_lo may be NULL), and,
+ * if M_hi != NULL, M = Yout^T Yout of the rounded result.  eo_project is
+ * eo_gram(V, Y) followed by this call; calling the two separately lets a
+ * caller reuse or inspect C.  Layout, aliasing and modes as in eo_project.
+ */
+EO_API eo_status eo_project_apply(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ldv, int k,
+                                  const double* Y, int64_t ldy, double* Yout, int64_t ldyo, const double* C_hi,
+                                  const double* C_lo, int ldc, double* M_hi, double* M_lo, int ldm, eo_prec prec);
+
+/*
  * Cholesky QR (Sec. 4.2: M = R^T R, Z = R^{-1}, Y = Y~ Z): X <- Q in place.
  *   X: n-by-k (FP64, or float in EO_F32 mode), ldx.
  *   M_hi/M_lo: optional Gram matrix of X for the first pass (as produced by

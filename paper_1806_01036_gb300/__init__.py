@@ -53,11 +53,13 @@ def lib():
         L.eo_last_error.restype = C.c_char_p
         L.eo_gram.argtypes = [_p, _i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int, _int]
         L.eo_project.argtypes = [_p, _i64, _int, _p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _p, _p, _int, _int]
+        L.eo_project_apply.argtypes = [_p, _i64, _int, _p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _p, _p, _int,
+                                       _int]
         L.eo_cholqr.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _int, _int, _p]
         L.eo_svqb.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _dbl, _int, _int, _p]
         L.eo_gram_dd_noalloc.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int, _p]
-        for f in ("eo_create", "eo_destroy", "eo_set_stream", "eo_gram", "eo_project", "eo_cholqr", "eo_svqb",
-                  "eo_gram_dd_noalloc"):
+        for f in ("eo_create", "eo_destroy", "eo_set_stream", "eo_gram", "eo_project", "eo_project_apply",
+                  "eo_cholqr", "eo_svqb", "eo_gram_dd_noalloc"):
             getattr(L, f).restype = _int
         _lib = L
     return _lib
@@ -163,6 +165,26 @@ def project(ctx: Context, V, Y, Yout=None, prec: int = DD, want_m: bool = True):
                                ch.data_ptr(), cl.data_ptr(), ch.stride(1), None if mh is None else mh.data_ptr(),
                                None if ml is None else ml.data_ptr(), k, prec))
     return Yout, (ch, cl), ((mh, ml) if want_m else None)
+
+
+def project_apply(ctx: Context, V, Y, C, Yout=None, prec: int = DD, want_m: bool = True):
+    """(Yout, (M_hi, M_lo) or None): Yout = Y - V C for C = (C_hi, C_lo), M = Yout^T Yout."""
+    import torch
+    V, n, kv, ldv = _mat(V, "V", torch.float64)
+    Y, ny, k, ldy = _mat(Y, "Y", torch.float64)
+    if ny != n:
+        raise ValueError("V and Y must have the same number of rows")
+    ch, cl = C
+    if Yout is None:
+        Yout = colmajor(torch.empty((n, k), dtype=torch.float64, device=Y.device))
+    Yout, _, _, ldyo = _mat(Yout, "Yout", torch.float64)
+    mh, ml = _small(k, k, V.device) if want_m else (None, None)
+    ctx.set_stream()
+    ctx.check(lib().eo_project_apply(ctx.h, n, kv, V.data_ptr(), ldv, k, Y.data_ptr(), ldy, Yout.data_ptr(), ldyo,
+                                     ch.data_ptr(), None if cl is None else cl.data_ptr(), ch.stride(1),
+                                     None if mh is None else mh.data_ptr(), None if ml is None else ml.data_ptr(),
+                                     k, prec))
+    return Yout, ((mh, ml) if want_m else None)
 
 
 def cholqr(ctx: Context, X, passes: int = 1, prec: int = DD, M=None, info=None):

@@ -116,6 +116,33 @@ Mode pipe_mode(eo_prec p) { return p == EO_DD_EFT ? MODE_DD : (Mode)p; }
 namespace eo {
 namespace {
 
+// Y - V C (and optionally M = Yout^T Yout) for a C already in device memory.
+eo_status apply_projection(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y,
+                           int64_t ldy, double* Yout, int64_t ldyo, const double* ch, const double* cl, int ldc,
+                           double* M_hi, double* M_lo, int ldm, eo_prec prec) {
+  if (prec == EO_DD) {
+    EO_CUDA(launch_fx_project(n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, cl, ldc, ctx->stream), "eo_project");
+    ctx->launches += 1;
+    if (M_hi) {
+      EO_CUDA(launch_fx_gram(n, k, Yout, ldyo, k, Yout, ldyo, true, parts_of(ctx), M_hi, M_lo, ldm, nullptr,
+                             ctx->stream),
+              "eo_project (Gram)");
+      ctx->launches += kGramLaunches;
+    }
+  } else {
+    const Mode mode = pipe_mode(prec);
+    EO_CUDA(launch_project_fused(mode, n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, mode == MODE_DD ? cl : nullptr, ldc,
+                                 parts_of(ctx), M_hi, M_lo, ldm, ctx->stream),
+            "eo_project (fused pass)");
+    ctx->launches += M_hi ? 2 : 1;
+  }
+  return EO_OK;
+}
+
+size_t apply_scratch(int64_t n, int kv, int k, eo_prec prec) {
+  return prec == EO_DD ? fx_gram_scratch_bytes(n, k, k, true) : project_scratch_bytes(n, kv, k);
+}
+
 template <bool CHOL>
 eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, int64_t ldx, const double* M_hi,
                       const double* M_lo, int ldm, double* O_hi, double* O_lo, int ldo, double tol, int passes,
@@ -293,22 +320,28 @@ eo_status eo_project(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ld
     EO_CUDA(cudaGetLastError(), "eo_project (copy C)");
     ctx->launches += 1;
   }
-  if (fx) {
-    EO_CUDA(launch_fx_project(n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, cl, KMAX, ctx->stream), "eo_project");
-    ctx->launches += 1;
-    if (M_hi) {
-      EO_CUDA(launch_fx_gram(n, k, Yout, ldyo, k, Yout, ldyo, true, parts_of(ctx), M_hi, M_lo, ldm, nullptr,
-                             ctx->stream),
-              "eo_project (Gram)");
-      ctx->launches += kGramLaunches;
-    }
-  } else {
-    EO_CUDA(launch_project_fused(mode, n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, mode == MODE_DD ? cl : nullptr, KMAX,
-                                 parts_of(ctx), M_hi, M_lo, ldm, ctx->stream),
-            "eo_project (fused pass)");
-    ctx->launches += M_hi ? 2 : 1;
-  }
-  return EO_OK;
+  return apply_projection(ctx, n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, cl, KMAX, M_hi, M_lo, ldm, prec);
+}
+
+eo_status eo_project_apply(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y,
+                           int64_t ldy, double* Yout, int64_t ldyo, const double* C_hi, const double* C_lo, int ldc,
+                           double* M_hi, double* M_lo, int ldm, eo_prec prec) {
+  if (!ctx) return EO_EINVAL;
+  ctx->err.clear();
+  EO_CHECK(valid_prec(prec), EO_EINVAL, "eo_project_apply: bad precision mode%s %lld", "", (long long)prec);
+  EO_CHECK(prec != EO_F32, EO_EUNSUPPORTED, "eo_project_apply: FP32 inputs are not supported%s", "");
+  EO_CHECK(n >= 0 && kv >= 1 && kv <= KMAX && k >= 1 && k <= KMAX, EO_EINVAL, "eo_project_apply: bad sizes%s", "");
+  EO_CHECK((V && Y && Yout) || n == 0, EO_EINVAL, "eo_project_apply: null pointer%s", "");
+  EO_CHECK(C_hi != nullptr, EO_EINVAL, "eo_project_apply: C_hi is required%s", "");
+  const int64_t mn = std::max<int64_t>(1, n);
+  EO_CHECK(ldv >= mn && ldy >= mn && ldyo >= mn, EO_EINVAL, "eo_project_apply: leading dimension too small%s", "");
+  EO_CHECK(ldc >= kv, EO_EINVAL, "eo_project_apply: ldc too small%s", "");
+  EO_CHECK(!M_hi || ldm >= k, EO_EINVAL, "eo_project_apply: ldm too small%s", "");
+  DeviceGuard g(ctx->device);
+  EO_CHECK(g.ok, EO_ECUDA, "eo_project_apply: cannot select device%s", "");
+  eo_status s = ensure_scratch(ctx, apply_scratch(n, kv, k, prec));
+  if (s != EO_OK) return s;
+  return apply_projection(ctx, n, kv, V, ldv, k, Y, ldy, Yout, ldyo, C_hi, C_lo, ldc, M_hi, M_lo, ldm, prec);
 }
 
 

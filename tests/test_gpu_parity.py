@@ -198,6 +198,20 @@ def test_project_dd_matches_oracle(eo, ctx, engine, n, kv, k):
     assert np.all(dd_err(host(mh), host(ml), *m_o) <= dd_gram_tol(yt, yt, m_o[0], engine))
 
 
+@pytest.mark.parametrize("engine", [1, 0])
+def test_project_apply_equals_project(eo, ctx, engine):
+    n, kv, k = 33_333, 24, 6
+    v = synth.orthonormal_basis(n, kv, 51)
+    y = synth.conditioned(n, k, 1e4, 52)
+    V, Y = dev(v), dev(y)
+    yt1, c1, m1 = eo.project(ctx, V, Y, prec=engine)
+    c = eo.gram(ctx, V, Y, prec=engine)
+    yt2, m2 = eo.project_apply(ctx, V, Y, c, prec=engine)
+    assert np.array_equal(host(c1[0]), host(c[0])) and np.array_equal(host(c1[1]), host(c[1]))
+    assert np.array_equal(host(yt1), host(yt2))
+    assert np.array_equal(host(m1[0]), host(m2[0])) and np.array_equal(host(m1[1]), host(m2[1]))
+
+
 def test_project_in_place_and_fp64(eo, ctx):
     n, kv, k = 12_345, 12, 3
     v = synth.orthonormal_basis(n, kv, 41)
