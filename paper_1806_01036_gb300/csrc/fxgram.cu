@@ -53,7 +53,8 @@ struct GramPlan {
   int ntiles;        // needed tiles
   int groups;        // CTAs per row chunk
   int tiles_per_group;
-  int P;             // rows per panel
+  int P;             // rows per panel (a power of two, >= 32)
+  int lgP;           // log2(P)
   int max_slots;     // columns held per CTA (bound)
 };
 
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                            const double* __restrict__ Y, int64_t ldy, GramPlan plan, int64_t rows_per_chunk,
                            FxPart* __restrict__ parts, const int* gate) {
   if (gate && *gate == 0) return;
-  const int P = plan.P;
+  const int P = plan.P, lgP = plan.lgP;
   const int sym = plan.sym;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // layout: limbs [slots][P] int4 | panel 2 x [slots][P] double | Wt [max(tiles,16)][8] i128 | ints
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const bool active = my_t < T;
   int ti = 0, tj = 0;
   if (active) nth_tile(t0 + my_t, plan.nti, plan.ntj, sym, ti, tj);
-  const int rot = Rl < 8 ? (my_t * Rl) % P : 0;  // spreads the tiles of a warp over the banks
+  const int rot = Rl < 8 ? (my_t * Rl) & (P - 1) : 0;  // spreads the tiles of a warp over the banks
 
   int xs[TI], ys[TJ];
 #pragma unroll
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int rows = (int)min((int64_t)P, r1 - pr);
     double* dst0 = pan + (size_t)buf * S * P;
     for (int e = tid; e < nslots * P; e += kThreads) {
-      const int c = e / P, r = e % P;
+      const int c = e >> lgP, r = e & (P - 1);
       double* dst = dst0 + e;
       if (r < rows) {
         const double* src;
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int ae = align_exp(cur[e]);
       if (ae == 2047) flag = 1;
       const int m = __reduce_max_sync(0xffffffffu, ae);  // a warp's 32 values share one column (P % 32 == 0)
-      if (lane == 0) atomicMax(&pmax[e / P], m);
+      if (lane == 0) atomicMax(&pmax[e >> lgP], m);
     }
     __syncthreads();
     for (int c = tid; c < nslots; c += kThreads) {
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     }
     for (int e = tid; e < nslots * P; e += kThreads) {
-      const Limbs L = to_limbs(cur[e], max(Erun[e / P], 1));
+      const Limbs L = to_limbs(cur[e], max(Erun[e >> lgP], 1));
       limb[e] = make_int4(L.v[0], L.v[1], L.v[2], L.v[3]);
     }
     __syncthreads();
@@ -417,6 +418,7 @@ GramPlan make_plan(int kx, int ky, bool sym) {
   int P = 128;
   while (P > 32 && fixed + (size_t)worst * P * (sizeof(int4) + 2 * sizeof(double)) > kSmemBudget) P /= 2;
   p.P = P;
+  p.lgP = P == 128 ? 7 : (P == 64 ? 6 : 5);
   return p;
 }
 

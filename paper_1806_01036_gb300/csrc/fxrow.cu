@@ -49,7 +49,7 @@ template <int MODE_UPDATE>
 __global__ void __launch_bounds__(kThreads, 2)
     fx_rowprod_kernel(int64_t n, int kin, const double* A, int64_t lda, int kout, const double* Bh, const double* Bl,
                       int ldb, int tri, const double* Yin, int64_t ldyin, double* Out, int64_t ldo, int P,
-                      const int* gate) {
+                      int lgP, const int* gate) {
   if (gate && *gate == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int4* Blimb = reinterpret_cast<int4*>(smem_raw);                 // kout * kin
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
   const int ngroups = (kout + JG - 1) / JG;
   const int tid = threadIdx.x;
-  const int my_r = tid % P, my_g = tid / P;  // P * ngroups <= blockDim
+  const int my_r = tid & (P - 1), my_g = tid >> lgP;  // P * ngroups <= blockDim
   const bool active = my_g < ngroups;
   const int j0 = my_g * JG;
   const int parts = kThreads / P;  // threads per row in the exponent scan
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     __syncthreads();
     for (int e = tid; e < kin * P; e += kThreads) {  // second read of the panel: from L1/L2
-      const int c = e / P, r = e % P;
+      const int c = e >> lgP, r = e & (P - 1);
       const Limbs L = r < rows ? to_limbs(A[(size_t)c * lda + pr + r], max(Er[r], 1)) : Limbs{{0, 0, 0, 0}};
       Sl[e] = make_int4(L.v[0], L.v[1], L.v[2], L.v[3]);
     }
@@ -124,12 +124,13 @@ constexpr size_t kSmemBudget = 110 * 1024;  // two CTAs per SM
 
 int rows_per_panel(int kin, int kout) {
   const int ngroups = (kout + JG - 1) / JG;
-  int P = std::max(16, kThreads / ngroups);
+  int P = 16;  // a power of two with P * ngroups <= kThreads
+  while (P * 2 * ngroups <= kThreads) P *= 2;
   // shared memory: B's limbs, the panel's limbs and values, exponents
   const size_t fixed = sizeof(int4) * (size_t)kout * kin + sizeof(int) * kout;
   const size_t per_row = sizeof(int4) * (size_t)kin + sizeof(int);
   const int cap = (int)((kSmemBudget - fixed) / per_row);
-  if (P > cap) P = std::max(16, cap / 16 * 16);
+  while (P > 16 && P > cap) P /= 2;
   return P;
 }
 
@@ -141,6 +142,8 @@ cudaError_t launch_rowprod(bool update, int64_t n, int kin, const double* A, int
                            const double* Bl, int ldb, bool tri, const double* Yin, int64_t ldyin, double* Out,
                            int64_t ldo, const int* gate, cudaStream_t st) {
   const int P = rows_per_panel(kin, kout);
+  int lgP = 0;
+  while ((1 << lgP) < P) ++lgP;
   const size_t smem = smem_bytes(kin, kout, P);
   const int64_t panels = (n + P - 1) / P;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(panels, 152 * 2));
@@ -149,12 +152,12 @@ cudaError_t launch_rowprod(bool update, int64_t n, int kin, const double* A, int
     e = cudaFuncSetAttribute(fx_rowprod_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fx_rowprod_kernel<1><<<blocks, kThreads, smem, st>>>(n, kin, A, lda, kout, Bh, Bl, ldb, tri ? 1 : 0, nullptr, 0,
-                                                         Out, ldo, P, gate);
+                                                         Out, ldo, P, lgP, gate);
   } else {
     e = cudaFuncSetAttribute(fx_rowprod_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fx_rowprod_kernel<0><<<blocks, kThreads, smem, st>>>(n, kin, A, lda, kout, Bh, Bl, ldb, 0, Yin, ldyin, Out, ldo,
-                                                         P, gate);
+                                                         P, lgP, gate);
   }
   return cudaGetLastError();
 }
