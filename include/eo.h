@@ -163,6 +163,27 @@ EO_API eo_status eo_svqb(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, co
                   int ldm, double* Z_hi, double* Z_lo, int ldz, double tol, int passes, eo_prec prec, int* rank_dev);
 
 /*
+ * Iterated two-phase orthogonalization (Sec. 4.2: "a robust algorithm is
+ * obtained by iterating this process, alternating between the two phases and
+ * using a rank-revealing technique in phase II"; the runtime figure iterates
+ * "until convergence at epsilon = 1e-10").  Each iteration runs phase I
+ * (C = V^T Y, Y <- Y - V C) and measures max |C_ij| and max |M - I|_ij with
+ * M = Y^T Y of the projected block; when both are <= eps the iteration stops
+ * there, otherwise phase II applies SVQB (Z = M^{-1/2} with eigenvalue cut tol,
+ * as in eo_svqb) and the next iteration follows.  Y (n-by-k, FP64) is updated
+ * in place; V (n-by-kv) must be orthonormal.  All max_iter iterations
+ * (1..16) are enqueued at once and skipped on the device after convergence.
+ *   iters_dev: optional device int, the number of SVQB updates applied before
+ *   convergence was seen, or -max_iter if it was not seen.
+ *   rank_dev: optional device int, the rank of the last SVQB applied (k when
+ *   none was needed).
+ * EO_F32 is not supported.
+ */
+EO_API eo_status eo_orthogonalize(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ldv, int k, double* Y,
+                                  int64_t ldy, double eps, int max_iter, double tol, eo_prec prec, int* iters_dev,
+                                  int* rank_dev);
+
+/*
  * Allocation-free compensated Gram product (no counterpart in the paper).
  *
  * eo_gram_dd_noalloc computes the same G = X^T Y as eo_gram(..., EO_DD) for

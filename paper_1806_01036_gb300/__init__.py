@@ -55,11 +55,12 @@ def lib():
         L.eo_project.argtypes = [_p, _i64, _int, _p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _p, _p, _int, _int]
         L.eo_project_apply.argtypes = [_p, _i64, _int, _p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _p, _p, _int,
                                        _int]
+        L.eo_orthogonalize.argtypes = [_p, _i64, _int, _p, _i64, _int, _p, _i64, _dbl, _int, _dbl, _int, _p, _p]
         L.eo_cholqr.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _int, _int, _p]
         L.eo_svqb.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _dbl, _int, _int, _p]
         L.eo_gram_dd_noalloc.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int, _p]
         for f in ("eo_create", "eo_destroy", "eo_set_stream", "eo_gram", "eo_project", "eo_project_apply",
-                  "eo_cholqr", "eo_svqb", "eo_gram_dd_noalloc"):
+                  "eo_cholqr", "eo_svqb", "eo_orthogonalize", "eo_gram_dd_noalloc"):
             getattr(L, f).restype = _int
         _lib = L
     return _lib
@@ -221,6 +222,22 @@ def svqb(ctx: Context, X, passes: int = 1, prec: int = DD, tol: float = -1.0, M=
                             None if ml is None else ml.data_ptr(), ldm, zh.data_ptr(), zl.data_ptr(), zh.stride(1),
                             float(tol), int(passes), prec, rank.data_ptr()))
     return zh, zl, rank
+
+
+def orthogonalize(ctx: Context, V, Y, eps: float = 1e-10, max_iter: int = 8, prec: int = DD, tol: float = -1.0):
+    """Iterated two-phase orthogonalization of Y (in place) against V and
+    among its columns.  Returns (iters, rank) as device int32 tensors."""
+    import torch
+    V, n, kv, ldv = _mat(V, "V", torch.float64)
+    Y, ny, k, ldy = _mat(Y, "Y", torch.float64)
+    if ny != n:
+        raise ValueError("V and Y must have the same number of rows")
+    iters = torch.zeros(1, dtype=torch.int32, device=Y.device)
+    rank = torch.zeros(1, dtype=torch.int32, device=Y.device)
+    ctx.set_stream()
+    ctx.check(lib().eo_orthogonalize(ctx.h, n, kv, V.data_ptr(), ldv, k, Y.data_ptr(), ldy, float(eps),
+                                     int(max_iter), float(tol), prec, iters.data_ptr(), rank.data_ptr()))
+    return iters, rank
 
 
 NOALLOC_KMAX = 16

@@ -119,12 +119,12 @@ namespace {
 // Y - V C (and optionally M = Yout^T Yout) for a C already in device memory.
 eo_status apply_projection(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y,
                            int64_t ldy, double* Yout, int64_t ldyo, const double* ch, const double* cl, int ldc,
-                           double* M_hi, double* M_lo, int ldm, eo_prec prec) {
+                           double* M_hi, double* M_lo, int ldm, eo_prec prec, const int* gate = nullptr) {
   if (prec == EO_DD) {
-    EO_CUDA(launch_fx_project(n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, cl, ldc, ctx->stream), "eo_project");
+    EO_CUDA(launch_fx_project(n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, cl, ldc, gate, ctx->stream), "eo_project");
     ctx->launches += 1;
     if (M_hi) {
-      EO_CUDA(launch_fx_gram(n, k, Yout, ldyo, k, Yout, ldyo, true, parts_of(ctx), M_hi, M_lo, ldm, nullptr,
+      EO_CUDA(launch_fx_gram(n, k, Yout, ldyo, k, Yout, ldyo, true, parts_of(ctx), M_hi, M_lo, ldm, gate,
                              ctx->stream),
               "eo_project (Gram)");
       ctx->launches += kGramLaunches;
@@ -132,7 +132,7 @@ eo_status apply_projection(eo_ctx* ctx, int64_t n, int kv, const double* V, int6
   } else {
     const Mode mode = pipe_mode(prec);
     EO_CUDA(launch_project_fused(mode, n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, mode == MODE_DD ? cl : nullptr, ldc,
-                                 parts_of(ctx), M_hi, M_lo, ldm, ctx->stream),
+                                 parts_of(ctx), M_hi, M_lo, ldm, gate, ctx->stream),
             "eo_project (fused pass)");
     ctx->launches += M_hi ? 2 : 1;
   }
@@ -187,11 +187,13 @@ eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, 
               name);
       ctx->launches += kGramLaunches;
     }
+    const SmallGates gates{&st->gate[2 * p], &st->gate[2 * p + 1], p + 1 < npass ? &st->gate[2 * p + 2] : nullptr};
     if (CHOL)
-      EO_CUDA(launch_chol_small(small_mode, k, mh, ml, ld, ws, O_hi, O_lo, ldo, st, p, passes, out_dev, ctx->stream),
+      EO_CUDA(launch_chol_small(small_mode, k, mh, ml, ld, ws, O_hi, O_lo, ldo, st, gates, p, passes, out_dev,
+                                ctx->stream),
               name);
     else
-      EO_CUDA(launch_svqb_small(small_mode, k, mh, ml, ld, ws, O_hi, O_lo, ldo, tol, st, p, passes, out_dev,
+      EO_CUDA(launch_svqb_small(small_mode, k, mh, ml, ld, ws, O_hi, O_lo, ldo, tol, st, gates, p, passes, out_dev,
                                 ctx->stream),
               name);
     if (fx)
@@ -355,6 +357,68 @@ eo_status eo_svqb(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, const dou
                   int ldm, double* Z_hi, double* Z_lo, int ldz, double tol, int passes, eo_prec prec, int* rank_dev) {
   return orth_common<false>(ctx, "eo_svqb", n, k, X, ldx, M_hi, M_lo, ldm, Z_hi, Z_lo, ldz, tol, passes, prec,
                             rank_dev);
+}
+
+eo_status eo_orthogonalize(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ldv, int k, double* Y,
+                           int64_t ldy, double eps, int max_iter, double tol, eo_prec prec, int* iters_dev,
+                           int* rank_dev) {
+  if (!ctx) return EO_EINVAL;
+  ctx->err.clear();
+  EO_CHECK(valid_prec(prec), EO_EINVAL, "eo_orthogonalize: bad precision mode%s %lld", "", (long long)prec);
+  EO_CHECK(prec != EO_F32, EO_EUNSUPPORTED, "eo_orthogonalize: FP32 inputs are not supported%s", "");
+  EO_CHECK(n >= 0 && kv >= 1 && kv <= KMAX && k >= 1 && k <= KMAX, EO_EINVAL, "eo_orthogonalize: bad sizes%s", "");
+  EO_CHECK((V && Y) || n == 0, EO_EINVAL, "eo_orthogonalize: null pointer%s", "");
+  const int64_t mn = std::max<int64_t>(1, n);
+  EO_CHECK(ldv >= mn && ldy >= mn, EO_EINVAL, "eo_orthogonalize: leading dimension too small%s", "");
+  EO_CHECK(max_iter >= 1 && max_iter <= kMaxIter, EO_EINVAL, "eo_orthogonalize: max_iter must be in [1, %lld]", "",
+           (long long)kMaxIter);
+  EO_CHECK(eps >= 0.0, EO_EINVAL, "eo_orthogonalize: eps must be >= 0%s", "");
+  DeviceGuard g(ctx->device);
+  EO_CHECK(g.ok, EO_ECUDA, "eo_orthogonalize: cannot select device%s", "");
+  const bool fx = prec == EO_DD;
+  const size_t need = fx ? std::max(fx_gram_scratch_bytes(n, kv, k, false), fx_gram_scratch_bytes(n, k, k, true))
+                         : std::max(gram_scratch_bytes(n, kv, k, false), project_scratch_bytes(n, kv, k));
+  eo_status s = ensure_scratch(ctx, need);
+  if (s != EO_OK) return s;
+  DevStatus* st = status_of(ctx);
+  SmallWs* ws = ws_of(ctx);
+  double* ch = c_hi_of(ctx);
+  double* cl = c_lo_of(ctx);
+  const Mode small_mode = pipe_mode(prec) == MODE_DD ? MODE_DD : MODE_FP64;
+  EO_CUDA(launch_status_init(st, k, ctx->stream), "eo_orthogonalize");
+  ctx->launches += 1;
+  for (int it = 0; it < max_iter; ++it) {
+    const int* run = &st->gate[kItRun + it];
+    // phase I: C = V^T Y, Y <- Y - V C (in place), M = Y^T Y
+    if (fx)
+      EO_CUDA(launch_fx_gram(n, kv, V, ldv, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, run, ctx->stream),
+              "eo_orthogonalize (V^T Y)");
+    else
+      EO_CUDA(launch_gram(pipe_mode(prec), n, kv, V, ldv, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, run,
+                          ctx->stream),
+              "eo_orthogonalize (V^T Y)");
+    ctx->launches += kGramLaunches;
+    s = apply_projection(ctx, n, kv, V, ldv, k, Y, ldy, Y, ldy, ch, cl, KMAX, ws->Mh, ws->Ml, KMAX, prec, run);
+    if (s != EO_OK) return s;
+    // converged when both V^T Y and Y^T Y - I are below eps: stop here
+    EO_CUDA(launch_converge(run, ch, cl, KMAX, kv, k, ws->Mh, ws->Ml, KMAX, eps, st, it, max_iter, iters_dev,
+                            rank_dev, ctx->stream),
+            "eo_orthogonalize (test)");
+    // phase II: SVQB of the projected block
+    const SmallGates gates{&st->gate[kItSvqb + it], &st->gate[kItUpd + it], nullptr};
+    EO_CUDA(launch_svqb_small(small_mode, k, ws->Mh, ws->Ml, KMAX, ws, nullptr, nullptr, KMAX, tol, st, gates, 0, 1,
+                              rank_dev, ctx->stream),
+            "eo_orthogonalize (SVQB)");
+    if (fx)
+      EO_CUDA(launch_fx_update(n, k, Y, ldy, ws->Zh, ws->Zl, false, &st->gate[kItUpd + it], ctx->stream),
+              "eo_orthogonalize (update)");
+    else
+      EO_CUDA(launch_update(pipe_mode(prec), n, k, Y, ldy, ws->Zh, ws->Zl, false, &st->gate[kItUpd + it],
+                            ctx->stream),
+              "eo_orthogonalize (update)");
+    ctx->launches += 3;
+  }
+  return EO_OK;
 }
 
 }  // extern "C"

@@ -24,9 +24,16 @@ constexpr int KMAX = EO_KMAX;
 struct DevStatus {
   int info;
   int rank;
-  int gate[8];
-  int pad[6];
+  int iters;
+  int pad;
+  int gate[64];
 };
+
+// Gate layout of eo_orthogonalize (iteration i < kMaxIter): the projection,
+// Gram and convergence test of iteration i run when gate[kItRun + i] != 0,
+// its SVQB when gate[kItSvqb + i] != 0, its update when gate[kItUpd + i] != 0.
+constexpr int kMaxIter = 16;
+constexpr int kItRun = 0, kItSvqb = 16, kItUpd = 32;
 
 // Device workspace for the k-by-k matrices of one call (FP64 hi/lo arrays,
 // column-major with leading dimension KMAX).
@@ -55,7 +62,8 @@ size_t project_scratch_bytes(int64_t n, int kv, int k);
 // null, M = Yout^T Yout accumulated in the same pass.
 cudaError_t launch_project_fused(Mode mode, int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y,
                                  int64_t ldy, double* Yout, int64_t ldyo, const double* C_hi, const double* C_lo,
-                                 int ldc, void* scratch, double* M_hi, double* M_lo, int ldm, cudaStream_t st);
+                                 int ldc, void* scratch, double* M_hi, double* M_lo, int ldm, const int* gate,
+                                 cudaStream_t st);
 
 // ------------------------------------------------------- update kernels
 // X <- X Z for Z = (Zh + Zl) (k-by-k, ld KMAX); tri: Z upper triangular.
@@ -73,17 +81,34 @@ cudaError_t launch_fx_update(int64_t n, int k, double* X, int64_t ldx, const dou
 // Yout = Y - V C (C: kv-by-k double-double with leading dimension ldc).
 cudaError_t launch_fx_project(int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y, int64_t ldy,
                               double* Yout, int64_t ldyo, const double* C_hi, const double* C_lo, int ldc,
-                              cudaStream_t st);
+                              const int* gate, cudaStream_t st);
 
 // ------------------------------------------------ small k-by-k kernels
+// Gates of one small factorization: it runs when *run != 0 and sets *upd
+// (run the update that follows) and, if next is not null, *next (run the
+// next pass).
+struct SmallGates {
+  const int* run;
+  int* upd;
+  int* next;
+};
+
 cudaError_t launch_status_init(DevStatus* s, int k, cudaStream_t st);
 // One CholQR factorization step of pass `pass` (0 or 1): M -> R, Z = R^{-1},
 // T <- R T.  passes: 1, 2 or 0 (automatic).
 cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
-                              double* R_hi, double* R_lo, int ldr, DevStatus* s, int pass, int passes,
+                              double* R_hi, double* R_lo, int ldr, DevStatus* s, SmallGates g, int pass, int passes,
                               int* info_user, cudaStream_t st);
 cudaError_t launch_svqb_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
-                              double* Z_hi, double* Z_lo, int ldz, double tol, DevStatus* s, int pass, int passes,
-                              int* rank_user, cudaStream_t st);
+                              double* Z_hi, double* Z_lo, int ldz, double tol, DevStatus* s, SmallGates g, int pass,
+                              int passes, int* rank_user, cudaStream_t st);
+// Convergence test of iteration `iter` of eo_orthogonalize: converged when
+// max |C_ij| <= eps and max |M_ij - delta_ij| <= eps (C kv-by-k, M k-by-k,
+// hi + lo).  Sets the SVQB/update gates of this iteration and the run gate of
+// the next one, and the iteration count (negative when max_iter iterations
+// did not converge).
+cudaError_t launch_converge(const int* run, const double* Ch, const double* Cl, int ldc, int kv, int k,
+                            const double* Mh, const double* Ml, int ldm, double eps, DevStatus* s, int iter,
+                            int max_iter, int* iters_user, int* rank_user, cudaStream_t st);
 
 }  // namespace eo

@@ -171,8 +171,8 @@ cudaError_t launch_fx_update(int64_t n, int k, double* X, int64_t ldx, const dou
 
 cudaError_t launch_fx_project(int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y, int64_t ldy,
                               double* Yout, int64_t ldyo, const double* C_hi, const double* C_lo, int ldc,
-                              cudaStream_t st) {
-  return launch_rowprod(false, n, kv, V, ldv, k, C_hi, C_lo, ldc, false, Y, ldy, Yout, ldyo, nullptr, st);
+                              const int* gate, cudaStream_t st) {
+  return launch_rowprod(false, n, kv, V, ldv, k, C_hi, C_lo, ldc, false, Y, ldy, Yout, ldyo, gate, st);
 }
 
 }  // namespace eo

@@ -42,7 +42,9 @@ __global__ void __launch_bounds__(kThreads) project_fused_kernel(int64_t n, int 
                                                                  int64_t ldy, double* Yout, int64_t ldyo,
                                                                  const double* __restrict__ C_hi,
                                                                  const double* __restrict__ C_lo, int ldc, int P,
-                                                                 int want_m, dd* __restrict__ parts) {
+                                                                 int want_m, dd* __restrict__ parts,
+                                                                 const int* gate) {
+  if (gate && *gate == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dd* Cs = reinterpret_cast<dd*>(smem_raw);
   double* panel = reinterpret_cast<double*>(Cs + (size_t)kv * k);
@@ -170,7 +172,8 @@ __global__ void __launch_bounds__(kThreads) project_fused_kernel(int64_t n, int 
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) sym_reduce_kernel(int k, int nparts, const dd* __restrict__ parts,
-                                                              double* G_hi, double* G_lo, int ldg) {
+                                                              double* G_hi, double* G_lo, int ldg, const int* gate) {
+  if (gate && *gate == 0) return;
   const int warp = (blockIdx.x * kThreads + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int E = k * k;
   if (warp >= E) return;
@@ -211,7 +214,8 @@ size_t project_scratch_bytes(int64_t n, int kv, int k) {
 
 cudaError_t launch_project_fused(Mode mode, int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y,
                                  int64_t ldy, double* Yout, int64_t ldyo, const double* C_hi, const double* C_lo,
-                                 int ldc, void* scratch, double* M_hi, double* M_lo, int ldm, cudaStream_t st) {
+                                 int ldc, void* scratch, double* M_hi, double* M_lo, int ldm, const int* gate,
+                                 cudaStream_t st) {
   const int P = panel_rows(k);
   const int np = project_parts(n, k);
   const size_t smem = (size_t)kv * k * sizeof(dd) + (size_t)P * k * sizeof(double);
@@ -222,14 +226,14 @@ cudaError_t launch_project_fused(Mode mode, int64_t n, int kv, const double* V, 
     e = cudaFuncSetAttribute(project_fused_kernel<MODE_DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     project_fused_kernel<MODE_DD><<<np, kThreads, smem, st>>>(n, kv, V, ldv, k, Y, ldy, Yout, ldyo, C_hi, C_lo, ldc, P,
-                                                              want_m, parts);
-    if (want_m) sym_reduce_kernel<MODE_DD><<<(k * k * 32 + kThreads - 1) / kThreads, kThreads, 0, st>>>(k, np, parts, M_hi, M_lo, ldm);
+                                                              want_m, parts, gate);
+    if (want_m) sym_reduce_kernel<MODE_DD><<<(k * k * 32 + kThreads - 1) / kThreads, kThreads, 0, st>>>(k, np, parts, M_hi, M_lo, ldm, gate);
   } else {
     e = cudaFuncSetAttribute(project_fused_kernel<MODE_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     project_fused_kernel<MODE_FP64><<<np, kThreads, smem, st>>>(n, kv, V, ldv, k, Y, ldy, Yout, ldyo, C_hi, C_lo, ldc,
-                                                                P, want_m, parts);
-    if (want_m) sym_reduce_kernel<MODE_FP64><<<(k * k * 32 + kThreads - 1) / kThreads, kThreads, 0, st>>>(k, np, parts, M_hi, M_lo, ldm);
+                                                                P, want_m, parts, gate);
+    if (want_m) sym_reduce_kernel<MODE_FP64><<<(k * k * 32 + kThreads - 1) / kThreads, kThreads, 0, st>>>(k, np, parts, M_hi, M_lo, ldm, gate);
   }
   return cudaGetLastError();
 }

@@ -43,17 +43,17 @@ struct Ar<MODE_DD> {
 __device__ __forceinline__ double dabs(double x) { return x < 0 ? -x : x; }
 
 __global__ void status_init_kernel(DevStatus* s, int k) {
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) s->gate[i] = i == 0;
   if (threadIdx.x == 0) {
     s->info = 0;
     s->rank = k;
-    for (int i = 0; i < 8; ++i) s->gate[i] = 0;
-    s->gate[0] = 1;
+    s->iters = 0;
   }
 }
 
-__device__ void finish_gates(DevStatus* s, int pass, int run_update, int want_next) {
-  s->gate[2 * pass + 1] = run_update;
-  if (pass + 1 < 4) s->gate[2 * pass + 2] = want_next;
+__device__ void finish_gates(const SmallGates& g, int run_update, int want_next) {
+  *g.upd = run_update;
+  if (g.next) *g.next = want_next;
 }
 
 // ------------------------------------------------------------ Cholesky
@@ -61,10 +61,10 @@ __device__ void finish_gates(DevStatus* s, int pass, int run_update, int want_ne
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) chol_small_kernel(int k, const double* Mh, const double* Ml, int ldm,
                                                               SmallWs* ws, double* Rh_u, double* Rl_u, int ldr,
-                                                              DevStatus* st, int pass, int passes, double thr,
-                                                              int* info_user) {
+                                                              DevStatus* st, SmallGates g, int pass, int passes,
+                                                              double thr, int* info_user) {
   using A_ = Ar<MODE>;
-  if (st->gate[2 * pass] == 0) return;
+  if (*g.run == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dd* A = reinterpret_cast<dd*>(smem_raw);  // A(i,j) = A[j*k+i]; R overwrites the upper triangle
   dd* Z = A + k * k;
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) chol_small_kernel(int k, const doubl
   if (flag != 0) {
     if (tid == 0) {
       st->info = flag;
-      finish_gates(st, pass, 0, 0);
+      finish_gates(g, 0, 0);
       if (info_user) *info_user = flag;
     }
     return;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) chol_small_kernel(int k, const doubl
     }
     int next = 0;
     if (pass == 0) next = passes == 2 ? 1 : (passes == 0 ? (dmax > thr * dmin) : 0);
-    finish_gates(st, pass, 1, next);
+    finish_gates(g, 1, next);
     if (info_user) *info_user = st->info;
   }
 }
@@ -173,10 +173,10 @@ __global__ void __launch_bounds__(kThreads) chol_small_kernel(int k, const doubl
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) svqb_small_kernel(int k, const double* Mh, const double* Ml, int ldm,
                                                               SmallWs* ws, double* Zh_u, double* Zl_u, int ldz,
-                                                              double tol, DevStatus* st, int pass, int passes,
-                                                              double thr, double eps, int* rank_user) {
+                                                              double tol, DevStatus* st, SmallGates g, int pass,
+                                                              int passes, double thr, double eps, int* rank_user) {
   using A_ = Ar<MODE>;
-  if (st->gate[2 * pass] == 0) return;
+  if (*g.run == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dd* A = reinterpret_cast<dd*>(smem_raw);  // k*k
   dd* U = A + k * k;                         // k*k
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) svqb_small_kernel(int k, const doubl
   if (flag != 0) {
     if (tid == 0) {
       st->rank = -1;
-      finish_gates(st, pass, 0, 0);
+      finish_gates(g, 0, 0);
       if (rank_user) *rank_user = -1;
     }
     return;
@@ -342,12 +342,57 @@ __global__ void __launch_bounds__(kThreads) svqb_small_kernel(int k, const doubl
     st->rank = rank_s;
     int next = 0;
     if (pass == 0) next = passes == 2 ? 1 : (passes == 0 ? (lmax_s > thr * thr * lmin_s) : 0);
-    finish_gates(st, pass, 1, next);
+    finish_gates(g, 1, next);
     if (rank_user) *rank_user = rank_s;
   }
 }
 
+// ------------------------------------------------------ convergence test
+
+__global__ void __launch_bounds__(kThreads) converge_kernel(const int* run, const double* Ch, const double* Cl, int ldc,
+                                                            int kv, int k, const double* Mh, const double* Ml,
+                                                            int ldm, double eps, DevStatus* st, int iter,
+                                                            int max_iter, int* iters_user, int* rank_user) {
+  if (*run == 0) return;
+  __shared__ double red[kThreads];
+  double m = 0.0;
+  for (int t = threadIdx.x; t < kv * k; t += kThreads) {
+    const int i = t % kv, j = t / kv;
+    const double c = Ch[(size_t)j * ldc + i] + (Cl ? Cl[(size_t)j * ldc + i] : 0.0);
+    m = fmax(m, dabs(c));
+  }
+  for (int t = threadIdx.x; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    // (M_hi - delta) + M_lo: the subtraction of 1 is exact near 1
+    const double e = (Mh[(size_t)j * ldm + i] - (i == j ? 1.0 : 0.0)) + (Ml ? Ml[(size_t)j * ldm + i] : 0.0);
+    m = fmax(m, isnan(e) ? 1e300 : dabs(e));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = kThreads / 2; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const bool conv = red[0] <= eps;
+    st->gate[kItSvqb + iter] = conv ? 0 : 1;
+    if (iter + 1 < max_iter) st->gate[kItRun + iter + 1] = conv ? 0 : 1;
+    if (conv) st->iters = iter;  // updates applied before convergence was seen
+    else if (iter + 1 == max_iter) st->iters = -max_iter;
+    if (iters_user && (conv || iter + 1 == max_iter)) *iters_user = st->iters;
+    if (rank_user && conv) *rank_user = st->rank;  // k when no SVQB was needed
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_converge(const int* run, const double* Ch, const double* Cl, int ldc, int kv, int k,
+                            const double* Mh, const double* Ml, int ldm, double eps, DevStatus* s, int iter,
+                            int max_iter, int* iters_user, int* rank_user, cudaStream_t st) {
+  converge_kernel<<<1, kThreads, 0, st>>>(run, Ch, Cl, ldc, kv, k, Mh, Ml, ldm, eps, s, iter, max_iter, iters_user,
+                                          rank_user);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_status_init(DevStatus* s, int k, cudaStream_t st) {
   status_init_kernel<<<1, 32, 0, st>>>(s, k);
@@ -355,27 +400,27 @@ cudaError_t launch_status_init(DevStatus* s, int k, cudaStream_t st) {
 }
 
 cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
-                              double* R_hi, double* R_lo, int ldr, DevStatus* s, int pass, int passes, int* info_user,
-                              cudaStream_t st) {
+                              double* R_hi, double* R_lo, int ldr, DevStatus* s, SmallGates g, int pass, int passes,
+                              int* info_user, cudaStream_t st) {
   const size_t smem = 2 * (size_t)k * k * sizeof(dd);
   cudaError_t e;
   if (mode == MODE_DD) {
     e = cudaFuncSetAttribute(chol_small_kernel<MODE_DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    chol_small_kernel<MODE_DD><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, R_hi, R_lo, ldr, s, pass, passes, 1e7,
-                                                         info_user);
+    chol_small_kernel<MODE_DD><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, R_hi, R_lo, ldr, s, g, pass, passes,
+                                                         1e7, info_user);
   } else {
     e = cudaFuncSetAttribute(chol_small_kernel<MODE_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    chol_small_kernel<MODE_FP64><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, R_hi, R_lo, ldr, s, pass, passes, 1e4,
-                                                           info_user);
+    chol_small_kernel<MODE_FP64><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, R_hi, R_lo, ldr, s, g, pass, passes,
+                                                           1e4, info_user);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_svqb_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
-                              double* Z_hi, double* Z_lo, int ldz, double tol, DevStatus* s, int pass, int passes,
-                              int* rank_user, cudaStream_t st) {
+                              double* Z_hi, double* Z_lo, int ldz, double tol, DevStatus* s, SmallGates g, int pass,
+                              int passes, int* rank_user, cudaStream_t st) {
   const size_t smem = 2 * (size_t)k * k * sizeof(dd) + 2 * (size_t)(k / 2 + 1) * sizeof(dd) +
                       2 * (size_t)(k / 2 + 1) * sizeof(int);
   cudaError_t e;
@@ -383,14 +428,14 @@ cudaError_t launch_svqb_small(Mode mode, int k, const double* Mh, const double* 
     if (tol < 0) tol = k * 0x1p-104;
     e = cudaFuncSetAttribute(svqb_small_kernel<MODE_DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    svqb_small_kernel<MODE_DD><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, Z_hi, Z_lo, ldz, tol, s, pass, passes,
-                                                         1e7, 0x1p-106, rank_user);
+    svqb_small_kernel<MODE_DD><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, Z_hi, Z_lo, ldz, tol, s, g, pass,
+                                                         passes, 1e7, 0x1p-106, rank_user);
   } else {
     if (tol < 0) tol = k * 0x1p-52;
     e = cudaFuncSetAttribute(svqb_small_kernel<MODE_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    svqb_small_kernel<MODE_FP64><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, Z_hi, Z_lo, ldz, tol, s, pass, passes,
-                                                           1e4, 0x1p-53, rank_user);
+    svqb_small_kernel<MODE_FP64><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, Z_hi, Z_lo, ldz, tol, s, g, pass,
+                                                           passes, 1e4, 0x1p-53, rank_user);
   }
   return cudaGetLastError();
 }

@@ -57,6 +57,27 @@ def gaussian(n: int, k: int, seed: int) -> np.ndarray:
     return np.asfortranarray(rng(seed).standard_normal((n, k)))
 
 
+def hadamard_basis(n: int, k: int, seed: int) -> np.ndarray:
+    """n-by-k basis that is orthonormal exactly in FP64.
+
+    Columns of the Sylvester-Hadamard matrix (entries (-1)^popcount(i & j)),
+    scaled by 1/sqrt(n), which is a power of two when n is a power of 4; the
+    rows are permuted and sign-flipped at random (seeded), which keeps every
+    entry exact and the columns exactly orthonormal."""
+    if n & (n - 1) or (n.bit_length() - 1) % 2:
+        raise ValueError("n must be a power of 4")
+    if k > n:
+        raise ValueError("k must not exceed n")
+    g = rng(seed)
+    cols = g.choice(n, size=k, replace=False)
+    i = np.arange(n)[:, None]
+    pc = np.vectorize(lambda v: bin(int(v)).count("1") & 1)(i & cols[None, :])
+    h = np.where(pc == 1, -1.0, 1.0) / np.sqrt(float(n))
+    perm = g.permutation(n)
+    signs = np.where(g.random(n) < 0.5, -1.0, 1.0)
+    return np.asfortranarray(h[perm] * signs[:, None])
+
+
 def orthonormal_basis(n: int, k: int, seed: int) -> np.ndarray:
     """Orthonormal n-by-k basis V (Householder QR of a seeded Gaussian)."""
     return haar(rng(seed), n, k)

@@ -385,3 +385,12 @@ def test_cross_err_and_fact_err_closed_forms():
     assert oracle.fact_err(x, qq, np.array([[8.0]])) == 0.0
     # R = 8.5: X - Q R = [-0.1875, -0.25], norm 0.3125 = ||X|| / 16
     assert oracle.fact_err(x, qq, np.array([[8.5]])) == 0.0625
+
+
+def test_hadamard_basis_is_exactly_orthonormal():
+    w = synth.hadamard_basis(64, 10, 3)
+    g = w.T @ w  # every product is +-1/64 and every partial sum is exact in FP64
+    assert np.array_equal(g, np.eye(10))
+    assert set(np.unique(np.abs(w))) == {0.125}
+    hi, lo = oracle.gram(w)
+    assert np.array_equal(hi, np.eye(10)) and not np.any(lo)
