@@ -4,6 +4,7 @@
 // factorization of the Gram matrix and the final multiplication Y~ Z).
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -96,6 +97,29 @@ __global__ void copy_small_kernel(int rows, int cols, const double* sh, const do
 
 bool valid_prec(int p) { return p == EO_FP64 || p == EO_DD || p == EO_F32 || p == EO_DD_EFT; }
 
+// Engine of a compensated Gram product: the tensor-core digits (tcgram.cu)
+// when the 16x8 output tiles are well filled, the integer limbs (fxgram.cu)
+// otherwise.  EO_DD_GRAM_ENGINE=int|tc overrides the choice (both engines
+// give results within the same bound).
+bool use_tc_gram(int kx, int ky) {
+  const char* e = getenv("EO_DD_GRAM_ENGINE");
+  if (e && e[0] == 't') return true;
+  if (e && e[0] == 'i') return false;
+  return kx >= 16 && ky >= 8 && kx * ky > 256;  // 16x16 and smaller: the integer engine is faster
+}
+
+size_t dd_gram_scratch(int64_t n, int kx, int ky, bool sym) {
+  return std::max(fx_gram_scratch_bytes(n, kx, ky, sym), tc_gram_scratch_bytes(n, kx, ky, sym));
+}
+
+cudaError_t launch_dd_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
+                           bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
+                           cudaStream_t st) {
+  if (use_tc_gram(kx, sym ? kx : ky))
+    return launch_tc_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st);
+  return launch_fx_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st);
+}
+
 // Mode of the FP64-pipe kernels for a precision (EO_DD_EFT runs them in DD).
 Mode pipe_mode(eo_prec p) { return p == EO_DD_EFT ? MODE_DD : (Mode)p; }
 
@@ -124,7 +148,7 @@ eo_status apply_projection(eo_ctx* ctx, int64_t n, int kv, const double* V, int6
     EO_CUDA(launch_fx_project(n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, cl, ldc, gate, ctx->stream), "eo_project");
     ctx->launches += 1;
     if (M_hi) {
-      EO_CUDA(launch_fx_gram(n, k, Yout, ldyo, k, Yout, ldyo, true, parts_of(ctx), M_hi, M_lo, ldm, gate,
+      EO_CUDA(launch_dd_gram(n, k, Yout, ldyo, k, Yout, ldyo, true, parts_of(ctx), M_hi, M_lo, ldm, gate,
                              ctx->stream),
               "eo_project (Gram)");
       ctx->launches += kGramLaunches;
@@ -140,7 +164,7 @@ eo_status apply_projection(eo_ctx* ctx, int64_t n, int kv, const double* V, int6
 }
 
 size_t apply_scratch(int64_t n, int kv, int k, eo_prec prec) {
-  return prec == EO_DD ? fx_gram_scratch_bytes(n, k, k, true) : project_scratch_bytes(n, kv, k);
+  return prec == EO_DD ? dd_gram_scratch(n, k, k, true) : project_scratch_bytes(n, kv, k);
 }
 
 template <bool CHOL>
@@ -159,7 +183,7 @@ eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, 
   DeviceGuard g(ctx->device);
   EO_CHECK(g.ok, EO_ECUDA, "%s: cannot select device", name);
   const bool fx = prec == EO_DD;
-  eo_status s = ensure_scratch(ctx, fx ? fx_gram_scratch_bytes(n, k, k, true) : gram_scratch_bytes(n, k, k, true));
+  eo_status s = ensure_scratch(ctx, fx ? dd_gram_scratch(n, k, k, true) : gram_scratch_bytes(n, k, k, true));
   if (s != EO_OK) return s;
   DevStatus* st = status_of(ctx);
   SmallWs* ws = ws_of(ctx);
@@ -177,7 +201,7 @@ eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, 
       ml = M_lo;
       ld = ldm;
     } else if (fx) {
-      EO_CUDA(launch_fx_gram(n, k, static_cast<const double*>(X), ldx, k, static_cast<const double*>(X), ldx, true,
+      EO_CUDA(launch_dd_gram(n, k, static_cast<const double*>(X), ldx, k, static_cast<const double*>(X), ldx, true,
                              parts_of(ctx), ws->Mh, ws->Ml, KMAX, &st->gate[2 * p], ctx->stream),
               name);
       ctx->launches += kGramLaunches;
@@ -271,9 +295,9 @@ eo_status eo_gram(eo_ctx* ctx, int64_t n, int kx, const void* X, int64_t ldx, in
   DeviceGuard g(ctx->device);
   EO_CHECK(g.ok, EO_ECUDA, "eo_gram: cannot select device%s", "");
   if (prec == EO_DD) {
-    eo_status s = ensure_scratch(ctx, fx_gram_scratch_bytes(n, kx, ky, sym));
+    eo_status s = ensure_scratch(ctx, dd_gram_scratch(n, kx, ky, sym));
     if (s != EO_OK) return s;
-    EO_CUDA(launch_fx_gram(n, kx, static_cast<const double*>(X), ldx, ky, static_cast<const double*>(sym ? X : Y),
+    EO_CUDA(launch_dd_gram(n, kx, static_cast<const double*>(X), ldx, ky, static_cast<const double*>(sym ? X : Y),
                            ldy, sym, parts_of(ctx), G_hi, G_lo, ldg, nullptr, ctx->stream),
             "eo_gram");
   } else {
@@ -303,7 +327,7 @@ eo_status eo_project(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ld
   DeviceGuard g(ctx->device);
   EO_CHECK(g.ok, EO_ECUDA, "eo_project: cannot select device%s", "");
   const bool fx = prec == EO_DD;
-  const size_t need = fx ? std::max(fx_gram_scratch_bytes(n, kv, k, false), fx_gram_scratch_bytes(n, k, k, true))
+  const size_t need = fx ? std::max(dd_gram_scratch(n, kv, k, false), dd_gram_scratch(n, k, k, true))
                          : std::max(gram_scratch_bytes(n, kv, k, false), project_scratch_bytes(n, kv, k));
   eo_status s = ensure_scratch(ctx, need);
   if (s != EO_OK) return s;
@@ -311,7 +335,7 @@ eo_status eo_project(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ld
   double* cl = c_lo_of(ctx);
   const Mode mode = pipe_mode(prec);
   if (fx)
-    EO_CUDA(launch_fx_gram(n, kv, V, ldv, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, nullptr, ctx->stream),
+    EO_CUDA(launch_dd_gram(n, kv, V, ldv, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, nullptr, ctx->stream),
             "eo_project (V^T Y)");
   else
     EO_CUDA(launch_gram(mode, n, kv, V, ldv, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, nullptr, ctx->stream),
@@ -376,7 +400,7 @@ eo_status eo_orthogonalize(eo_ctx* ctx, int64_t n, int kv, const double* V, int6
   DeviceGuard g(ctx->device);
   EO_CHECK(g.ok, EO_ECUDA, "eo_orthogonalize: cannot select device%s", "");
   const bool fx = prec == EO_DD;
-  const size_t need = fx ? std::max(fx_gram_scratch_bytes(n, kv, k, false), fx_gram_scratch_bytes(n, k, k, true))
+  const size_t need = fx ? std::max(dd_gram_scratch(n, kv, k, false), dd_gram_scratch(n, k, k, true))
                          : std::max(gram_scratch_bytes(n, kv, k, false), project_scratch_bytes(n, kv, k));
   eo_status s = ensure_scratch(ctx, need);
   if (s != EO_OK) return s;
@@ -391,7 +415,7 @@ eo_status eo_orthogonalize(eo_ctx* ctx, int64_t n, int kv, const double* V, int6
     const int* run = &st->gate[kItRun + it];
     // phase I: C = V^T Y, Y <- Y - V C (in place), M = Y^T Y
     if (fx)
-      EO_CUDA(launch_fx_gram(n, kv, V, ldv, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, run, ctx->stream),
+      EO_CUDA(launch_dd_gram(n, kv, V, ldv, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, run, ctx->stream),
               "eo_orthogonalize (V^T Y)");
     else
       EO_CUDA(launch_gram(pipe_mode(prec), n, kv, V, ldv, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, run,

@@ -71,6 +71,22 @@ cudaError_t launch_update(Mode mode, int64_t n, int k, void* X, int64_t ldx, con
                           bool tri, const int* gate, cudaStream_t st);
 
 // ------------------------------------- exact fixed-point (EO_DD) kernels
+// Partial Gram entry of one row chunk: an exact integer w (128 bits) with
+// value w * 2^s, and a flag for non-finite inputs.
+struct __align__(16) FxPart {
+  long long wl, wh;
+  int s, flag;
+  long long pad;
+};
+// Sum the row-chunk partials of every entry exactly and round once:
+// G_hi/G_lo (kx-by-ky, ldg; the upper triangle mirrored when sym).
+cudaError_t launch_fx_reduce(int kx, int ky, bool sym, int nchunks, const FxPart* parts, double* G_hi, double* G_lo,
+                             int ldg, const int* gate, cudaStream_t st);
+// The same product on the tensor cores (tcgram.cu); same partial format.
+size_t tc_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym);
+cudaError_t launch_tc_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
+                           bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
+                           cudaStream_t st);
 size_t fx_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym);
 cudaError_t launch_fx_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
                            bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,

@@ -40,11 +40,6 @@ constexpr int TI = 2, TJ = 4;       // tile: TI columns of X by TJ columns of Y
 constexpr int kMaxTiles = 128;      // tiles per CTA (8 per warp)
 constexpr size_t kSmemBudget = 200 * 1024;
 
-struct __align__(16) FxPart {
-  long long wl, wh;
-  int s, flag;
-  long long pad;
-};
 
 // Launch geometry shared by host and device.
 struct GramPlan {
@@ -434,6 +429,14 @@ int num_chunks(int64_t n, const GramPlan& p) {
 }
 
 }  // namespace
+
+cudaError_t launch_fx_reduce(int kx, int ky, bool sym, int nchunks, const FxPart* parts, double* G_hi, double* G_lo,
+                             int ldg, const int* gate, cudaStream_t st) {
+  const int E = kx * ky;
+  fx_gram_reduce_kernel<<<(E * 32 + kRedThreads - 1) / kRedThreads, kRedThreads, 0, st>>>(
+      kx, ky, sym ? 1 : 0, nchunks, parts, G_hi, G_lo, ldg, gate);
+  return cudaGetLastError();
+}
 
 size_t fx_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym) {
   if (sym) ky = kx;

@@ -104,6 +104,40 @@ def test_gram_fp64_and_f32_within_textbook_bound(eo, ctx, prec, n, k):
     assert not np.any(host(gl))
 
 
+@pytest.mark.parametrize("engine", ["int", "tc"])
+@pytest.mark.parametrize("n,kx,ky,sym", [(1, 1, 1, True), (33, 3, 3, True), (1000, 8, 8, False), (4099, 13, 5, False),
+                                         (100_003, 16, 16, True), (20_000, 64, 64, True), (20_001, 64, 16, False),
+                                         (70_001, 2, 7, False), (50_000, 40, 24, False), (30_017, 33, 33, True),
+                                         (131, 17, 9, False)])
+def test_gram_dd_both_engines(eo, ctx, monkeypatch, engine, n, kx, ky, sym):
+    """The integer-limb and the tensor-core-digit engines of EO_DD against the oracle."""
+    monkeypatch.setenv("EO_DD_GRAM_ENGINE", engine)
+    x = synth.gaussian(n, kx, 400 + kx)
+    y = x if sym else synth.gaussian(n, ky, 500 + ky)
+    gh, gl = eo.gram(ctx, dev(x), None if sym else dev(y), prec=eo.DD)
+    rh, rl = oracle.gram(x, None if sym else y)
+    err = dd_err(host(gh), host(gl), rh, rl)
+    tol = dd_gram_tol(x, y, rh, 1)
+    assert np.all(err <= tol), float(np.max(err / tol))
+    if sym:
+        assert np.array_equal(host(gh), host(gh).T)
+
+
+@pytest.mark.parametrize("engine", ["int", "tc"])
+def test_gram_dd_engines_rescale_and_range(eo, ctx, monkeypatch, engine):
+    monkeypatch.setenv("EO_DD_GRAM_ENGINE", engine)
+    n = 200_000
+    x = synth.gaussian(n, 16, 18) * np.logspace(-30, 3, n)[:, None]
+    y = synth.gaussian(n, 8, 19) * np.logspace(3, -30, n)[:, None]
+    g = synth.rng(23)
+    z = np.asfortranarray(np.ldexp(g.standard_normal((n, 16)), g.integers(-80, 20, size=(n, 16))))
+    for a, b in ((x, None), (x, y), (z, None)):
+        gh, gl = eo.gram(ctx, dev(a), None if b is None else dev(b), prec=eo.DD)
+        rh, rl = oracle.gram(a, b)
+        bb = a if b is None else b
+        assert np.all(dd_err(host(gh), host(gl), rh, rl) <= dd_gram_tol(a, bb, rh, 1))
+
+
 def test_gram_dd_integer_inputs_are_exact(eo, ctx):
     # small integers sit exactly on the fixed-point grid: every product and sum is exact
     g = synth.rng(17)
