@@ -97,26 +97,27 @@ __global__ void copy_small_kernel(int rows, int cols, const double* sh, const do
 
 bool valid_prec(int p) { return p == EO_FP64 || p == EO_DD || p == EO_F32 || p == EO_DD_EFT; }
 
-// Engine of a compensated Gram product: the tensor-core digits (tcgram.cu)
-// when the 16x8 output tiles are well filled, the integer limbs (fxgram.cu)
-// otherwise.  EO_DD_GRAM_ENGINE=int|tc overrides the choice (both engines
+// Engine of a compensated Gram product: the tcgen05 digit engine
+// (umma_gram.cu) once one side has 16 columns or more (its 128-lane tensor-
+// memory tiles are then reasonably filled), the integer limbs (fxgram.cu)
+// otherwise.  EO_DD_GRAM_ENGINE=int|umma overrides the choice (both engines
 // give results within the same bound).
-bool use_tc_gram(int kx, int ky) {
+bool use_umma_gram(int kx, int ky) {
   const char* e = getenv("EO_DD_GRAM_ENGINE");
-  if (e && e[0] == 't') return true;
+  if (e && e[0] == 'u') return true;
   if (e && e[0] == 'i') return false;
-  return kx >= 16 && ky >= 8 && kx * ky > 256;  // 16x16 and smaller: the integer engine is faster
+  return std::max(kx, ky) >= 16;
 }
 
 size_t dd_gram_scratch(int64_t n, int kx, int ky, bool sym) {
-  return std::max(fx_gram_scratch_bytes(n, kx, ky, sym), tc_gram_scratch_bytes(n, kx, ky, sym));
+  return std::max(fx_gram_scratch_bytes(n, kx, ky, sym), umma_gram_scratch_bytes(n, kx, ky, sym));
 }
 
 cudaError_t launch_dd_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
                            bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
                            cudaStream_t st) {
-  if (use_tc_gram(kx, sym ? kx : ky))
-    return launch_tc_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st);
+  if (use_umma_gram(kx, sym ? kx : ky))
+    return launch_umma_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st);
   return launch_fx_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st);
 }
 

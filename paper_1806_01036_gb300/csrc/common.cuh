@@ -82,11 +82,11 @@ struct __align__(16) FxPart {
 // G_hi/G_lo (kx-by-ky, ldg; the upper triangle mirrored when sym).
 cudaError_t launch_fx_reduce(int kx, int ky, bool sym, int nchunks, const FxPart* parts, double* G_hi, double* G_lo,
                              int ldg, const int* gate, cudaStream_t st);
-// The same product on the tensor cores (tcgram.cu); same partial format.
-size_t tc_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym);
-cudaError_t launch_tc_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
-                           bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
-                           cudaStream_t st);
+// The same product on the tcgen05 tensor cores (umma_gram.cu); same partial format.
+size_t umma_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym);
+cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
+                             bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
+                             cudaStream_t st);
 size_t fx_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym);
 cudaError_t launch_fx_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
                            bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,

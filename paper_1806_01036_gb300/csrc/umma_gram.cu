@@ -1,0 +1,741 @@
+// umma_gram.cu — compensated Gram products G = X^T Y on the 5th-generation
+// tensor cores (tcgen05.mma, accumulators in tensor memory).
+//
+// arXiv:1806.01036, Sec. 4.2: M = Y~^T Y~ and W^T X summed over n rows with
+// increased precision.  The sums are exact, as in fx.cuh; the digit products
+// run on the tensor cores:
+//
+//  * each value x of a column is aligned to the column's running exponent A
+//    and held as X = floor(|x| 2^(1127 - A)) < 2^105, cut into 15 digits of
+//    7 bits, X = sum_s D_s 2^(98 - 7s);
+//  * a digit is the FP16 number +-D_s 2^-24 (bit pattern: the digit with the
+//    value's sign; an FP16 subnormal), so every product of two digits is
+//    exact on the grid 2^-48 and sums of fewer than 2^24 grid units are exact
+//    in the FP32 accumulators;
+//  * digit slabs sit in shared memory in the canonical K-major layout (8x16-
+//    byte core matrices; the K dimension is the row index of X and Y).  One
+//    MMA multiplies J consecutive X slabs (M = 128 = J x kxp TMEM lanes) by
+//    the Y slabs t = 0 .. T-1 (N = T x kyp) and writes at TMEM column offset
+//    J q kyp, so the product of slabs s = Jq + j and t lands in column block
+//    c = Jq + t of lane block j: column block c of lane block j collects the
+//    digit diagonal d = c + j, and the 120 digit pairs with d <= 14 take
+//    15 / J + 1 MMAs per 16 rows;
+//  * every R rows (R such that no accumulator can reach 2^24 units) the
+//    accumulators are read back (tcgen05.ld), converted to integers and added
+//    to 32-bit running sums per (lane, column); these are folded into a
+//    128-bit total W in the units of the integer engine (value =
+//    W 2^(Ax + Ay - 2148)) every 8192 rows, before an alignment exponent
+//    grows, and at the end.  The row-chunk partials go through the same
+//    exact, order-free reduction (fx_gram_reduce).
+//
+// The dropped digit pairs (d >= 15) weigh less than 2^-101 max|x| max|y| per
+// row, as in the integer engine.  Pipeline per CTA (one per SM): cp.async
+// staging of panel p+1, conversion of panel p into one of two digit buffers
+// while the tensor cores run panel p-1, one elected thread issuing the MMAs
+// and committing them to an mbarrier per buffer.  Every wait is bounded; a
+// wait that runs out marks the partials non-finite, so the result is NaN.
+#include <algorithm>
+
+#include "common.cuh"
+#include "fx.cuh"
+
+namespace eo {
+namespace {
+
+using namespace fx;
+
+constexpr int kConvWarps = 16;                // staging, conversion and drains
+constexpr int kConvThreads = 32 * kConvWarps;
+constexpr int kThreads = kConvThreads + 32;  // plus one MMA-issuing warp
+constexpr int NS = 15;        // digits per value
+constexpr int kLanes = 128;   // MMA M = TMEM lanes
+constexpr int kMaxItems = 3;  // items (two rows of one column) per thread and panel
+constexpr int kOffsetDigits = 2148;
+constexpr int kFoldRows = 8192;  // rows between folds of the 32-bit running sums
+constexpr size_t kSmemCap = 225 * 1024;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
+
+struct UPlan {
+  int kxp, kyp, J, nq;  // X tile width (J = 128 / kxp lane blocks), Y tile width, MMAs per k-step
+  int ntx, nty;         // tiles over X and Y columns
+  int shared;           // X and Y are one matrix held once (symmetric, kx <= 16)
+  int P;                // rows per panel (multiple of 16)
+  int drain_panels;     // panels accumulated in TMEM between drains
+  int fold_drains;      // drains between folds of the running sums
+  int nslots;           // staged columns per CTA
+  unsigned dig_bytes;   // one digit buffer (A part, then B part unless shared)
+  unsigned a_bytes;     // A part of a digit buffer
+  unsigned stage_bytes; // one staging buffer
+};
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of the given parity to complete.  Gives up (false) once
+// *abort is set or after kWaitNs, and then sets *abort so that every other
+// wait of the CTA gives up at once.
+__device__ __noinline__ bool mbar_wait(unsigned bar, unsigned parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort || gtimer() - t0 > kWaitNs) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+// The same, but only the time limit ends it (waits for MMAs already issued).
+__device__ __noinline__ bool mbar_wait_final(unsigned bar, unsigned parity, volatile int* abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (gtimer() - t0 > kWaitNs) {
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Barrier 1 among the converter warps only.
+__device__ __forceinline__ void bar_conv() { asm volatile("bar.sync 1, %0;" ::"n"(kConvThreads) : "memory"); }
+__device__ __forceinline__ bool bar_conv_or(bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((unsigned)v), "n"(kConvThreads)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(unsigned dst, unsigned ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: no swizzle, K-major canonical layout;
+// lbo = bytes between core matrices adjacent in K, sbo = in M/N.
+__device__ __forceinline__ unsigned long long sdesc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((addr >> 4) & 0x3fffu) | ((unsigned long long)((lbo >> 4) & 0x3fffu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: FP16 A and B (K-major), FP32 D.
+__host__ __device__ constexpr unsigned idesc_f16(int M, int N) {
+  return (1u << 4) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                        unsigned accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(unsigned bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+// Three column groups of NY consecutive TMEM columns (this warp's 32 lanes),
+// loaded and waited for in one step.
+template <int NY>
+__device__ __forceinline__ void tmem_ld3(unsigned a0, unsigned a1, unsigned a2, unsigned (&v)[3][NY]) {
+  if constexpr (NY == 4) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%12];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%13];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%14];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[0][2]), "=r"(v[0][3]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[1][2]),
+          "=r"(v[1][3]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(v[2][2]), "=r"(v[2][3])
+        : "r"(a0), "r"(a1), "r"(a2)
+        : "memory");
+  } else {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%6];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2,%3}, [%7];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4,%5}, [%8];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[2][0]), "=r"(v[2][1])
+        : "r"(a0), "r"(a1), "r"(a2)
+        : "memory");
+  }
+}
+
+// Six groups: three of the accumulators and three of the running sums.
+template <int NY>
+__device__ __forceinline__ void tmem_ld3x2(unsigned a0, unsigned a1, unsigned a2, unsigned b0, unsigned b1,
+                                           unsigned b2, unsigned (&v)[3][NY], unsigned (&w)[3][NY]) {
+  if constexpr (NY == 4) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%24];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%25];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%26];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12,%13,%14,%15}, [%27];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16,%17,%18,%19}, [%28];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%20,%21,%22,%23}, [%29];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[0][2]), "=r"(v[0][3]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[1][2]),
+          "=r"(v[1][3]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(v[2][2]), "=r"(v[2][3]), "=r"(w[0][0]), "=r"(w[0][1]),
+          "=r"(w[0][2]), "=r"(w[0][3]), "=r"(w[1][0]), "=r"(w[1][1]), "=r"(w[1][2]), "=r"(w[1][3]), "=r"(w[2][0]),
+          "=r"(w[2][1]), "=r"(w[2][2]), "=r"(w[2][3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(b0), "r"(b1), "r"(b2)
+        : "memory");
+  } else {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%12];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2,%3}, [%13];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4,%5}, [%14];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6,%7}, [%15];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8,%9}, [%16];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10,%11}, [%17];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(w[0][0]),
+          "=r"(w[0][1]), "=r"(w[1][0]), "=r"(w[1][1]), "=r"(w[2][0]), "=r"(w[2][1])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(b0), "r"(b1), "r"(b2)
+        : "memory");
+  }
+}
+template <int NY>
+__device__ __forceinline__ void tmem_st3(unsigned a0, unsigned a1, unsigned a2, const unsigned (&v)[3][NY]) {
+  if constexpr (NY == 4) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%3,%4,%5,%6};\n"
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%1], {%7,%8,%9,%10};\n"
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%2], {%11,%12,%13,%14};\n" ::"r"(a0),
+        "r"(a1), "r"(a2), "r"(v[0][0]), "r"(v[0][1]), "r"(v[0][2]), "r"(v[0][3]), "r"(v[1][0]), "r"(v[1][1]),
+        "r"(v[1][2]), "r"(v[1][3]), "r"(v[2][0]), "r"(v[2][1]), "r"(v[2][2]), "r"(v[2][3])
+        : "memory");
+  } else {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%3,%4};\n"
+        "tcgen05.st.sync.aligned.32x32b.x2.b32 [%1], {%5,%6};\n"
+        "tcgen05.st.sync.aligned.32x32b.x2.b32 [%2], {%7,%8};\n" ::"r"(a0),
+        "r"(a1), "r"(a2), "r"(v[0][0]), "r"(v[0][1]), "r"(v[1][0]), "r"(v[1][1]), "r"(v[2][0]), "r"(v[2][1])
+        : "memory");
+  }
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async8(unsigned dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// ------------------------------------------------------------ digits
+// X = floor(|x| 2^(1127 - A)) < 2^105 as four 32-bit words (w[0] least
+// significant); A >= align_exp(x).  X = m 2^t with m the 53-bit significand.
+__device__ __forceinline__ void xwords(double x, int A, unsigned (&w)[4]) {
+  const unsigned hi = hi32(x), lo = lo32(x);
+  const int e = (hi >> 20) & 0x7ff;
+  const unsigned mh = (hi & 0xfffffu) | (e ? 0x100000u : 0u);
+  const int t = 52 - A + max(e, 1);
+  if (t >= 0) {
+    const int bo = t & 31;
+    const unsigned s0 = lo << bo, s1 = __funnelshift_l(lo, mh, bo), s2 = __funnelshift_l(mh, 0u, bo);
+    const bool up = t >= 32;
+    w[0] = up ? 0u : s0;
+    w[1] = up ? s0 : s1;
+    w[2] = up ? s1 : s2;
+    w[3] = up ? s2 : 0u;
+  } else {  // more than 52 binades below the column's largest value
+    const int r = -t;
+    const unsigned long long m = ((unsigned long long)mh << 32) | lo;
+    const unsigned long long v = r < 64 ? m >> r : 0ull;
+    w[0] = (unsigned)v;
+    w[1] = (unsigned)(v >> 32);
+    w[2] = 0u;
+    w[3] = 0u;
+  }
+}
+
+// Bits [q, q + 7) of X in the low bits of the result (higher bits: junk).
+template <int S>
+__device__ __forceinline__ unsigned digit_field(const unsigned (&w)[4]) {
+  constexpr int q = 98 - 7 * S, wi = q >> 5, bo = q & 31;
+  if constexpr (bo + 7 <= 32) return w[wi] >> bo;
+  else return __funnelshift_r(w[wi], w[wi + 1], bo);
+}
+
+// The 15 digit words of two consecutive rows (low half: row r, high half:
+// row r + 1; each +-D 2^-24 as FP16) into their slabs, slab s at dst + s * stride.
+template <int S>
+__device__ __forceinline__ void store_digits(unsigned char* dst, unsigned stride, const unsigned (&a)[4],
+                                             const unsigned (&b)[4], unsigned signs) {
+  if constexpr (S < NS) {
+    const unsigned w = (__byte_perm(digit_field<S>(a), digit_field<S>(b), 0x5410) & 0x007f007fu) | signs;
+    *reinterpret_cast<unsigned*>(dst + S * stride) = w;
+    store_digits<S + 1>(dst, stride, a, b, signs);
+  }
+}
+
+// ------------------------------------------------------------ kernel
+// Warps 0..15 stage, scan, convert and drain (named barrier 1); warp 16
+// issues the MMAs: per panel p it waits for ready[p & 1] (512 arrivals: the
+// digits of p are in buffer p & 1 and TMEM is drained if due), issues the
+// MMAs and commits them to full[p & 1], which the converters wait on before
+// they reuse the buffer (panel p + 2) or read TMEM.
+template <int KYP>
+__global__ void __launch_bounds__(kThreads, 1)
+    umma_gram_partial_kernel(int64_t n, int kx, const double* __restrict__ X, int64_t ldx, int ky,
+                             const double* __restrict__ Y, int64_t ldy, UPlan pl, int64_t rows_per_chunk,
+                             int aligned16, FxPart* __restrict__ parts, const int* gate) {
+  if (gate && *gate == 0) return;
+  constexpr int NY = KYP / 4;  // Y columns of one converter thread in a drain
+  const int kxp = pl.kxp, P = pl.P, nslots = pl.nslots;
+  const int tx = blockIdx.x / pl.nty, ty = blockIdx.x % pl.nty;
+  const int x0 = tx * kxp, y0 = ty * KYP;  // first X / Y column of the tile
+  const unsigned SBO = (unsigned)P * 16;   // bytes per 8-row group of a slab (P / 8 core matrices)
+
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* dig = smem;                                                   // 2 digit buffers
+  double* stage = reinterpret_cast<double*>(smem + 2 * (size_t)pl.dig_bytes);  // 2 staging buffers
+  int* Erun = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(stage) + 2 * (size_t)pl.stage_bytes);
+  int* pmax = Erun + nslots;  // two panels' column maxima
+  __shared__ __align__(8) unsigned long long full_bar[2], ready_bar[2];
+  __shared__ unsigned tmem_base;
+  __shared__ int flag, bad, fresh_flag[2];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int SP = P + 2;  // staging stride per column (doubles): conflict-free 16-byte reads
+
+  // ---- set-up: TMEM (accumulators in columns 0..255, running sums in 256..511),
+  // barriers, zero slabs, exponents
+  if (warp == 0) tmem_alloc(smem_u32(&tmem_base), 512);
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&full_bar[b]), 1);
+      mbar_init(smem_u32(&ready_bar[b]), kConvThreads);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    flag = 0;
+    bad = 0;
+  }
+  for (int c = tid; c < 3 * nslots; c += kThreads) Erun[c] = 0;  // Erun and both pmax
+  {  // slab 15 of every operand stays zero
+    const unsigned za = (unsigned)kxp / 8u * SBO, zb = (unsigned)KYP / 8u * SBO;  // bytes of one slab
+    for (int b = 0; b < 2; ++b) {
+      unsigned* pa = reinterpret_cast<unsigned*>(dig + (size_t)b * pl.dig_bytes + 15u * za);
+      for (unsigned e = tid; e < za / 4; e += kThreads) pa[e] = 0u;
+      if (!pl.shared) {
+        unsigned* pb = reinterpret_cast<unsigned*>(dig + (size_t)b * pl.dig_bytes + pl.a_bytes + 15u * zb);
+        for (unsigned e = tid; e < zb / 4; e += kThreads) pb[e] = 0u;
+      }
+    }
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned taddr = tmem_base;
+
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+  const int64_t r1 = min(n, r0 + rows_per_chunk);
+  const int npan = r0 < r1 ? (int)((r1 - r0 + P - 1) / P) : 0;
+  const unsigned dig_s = smem_u32(dig);
+  const unsigned fb0 = smem_u32(&full_bar[0]), rb0 = smem_u32(&ready_bar[0]);
+
+  // the partial sums of this thread's lane: lane block jl (digit phase), X column xl
+  const int Lq = (warp & 3) * 32, L = Lq + lane;
+  const int jl = L >> (31 - __clz(kxp)), xl = L & (kxp - 1);
+  const int yq = (warp >> 2) * NY;  // first of this thread's NY Y columns
+  i128 W[NY];
+#pragma unroll
+  for (int y = 0; y < NY; ++y) W[y] = 0;
+
+  if (warp == kConvWarps) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      int p = 0;
+      for (; p < npan; ++p) {
+        const int db = p & 1;
+        if (!mbar_wait(rb0 + 8u * db, (unsigned)(p >> 1) & 1u, &bad)) break;
+        tc_fence_after();
+        const bool fresh = fresh_flag[db] != 0;
+        const unsigned abase = dig_s + (unsigned)db * pl.dig_bytes;
+        const unsigned bbase = pl.shared ? abase : abase + pl.a_bytes;
+        for (int ks = 0; ks < P / 16; ++ks) {
+          for (int q = 0; q < pl.nq; ++q) {
+            const int T = NS - pl.J * q;
+            const int Tp = KYP == 16 ? T : (T + 1) & ~1;  // N a multiple of 16
+            const unsigned long long ad =
+                sdesc(abase + (unsigned)(pl.J * q * kxp / 8) * SBO + (unsigned)ks * 256u, 128u, SBO);
+            const unsigned long long bd = sdesc(bbase + (unsigned)ks * 256u, 128u, SBO);
+            mma_f16(taddr + (unsigned)(KYP * pl.J * q), ad, bd, idesc_f16(kLanes, KYP * Tp),
+                    (fresh && ks == 0 && q == 0) ? 0u : 1u);
+          }
+        }
+        mma_commit(fb0 + 8u * db);
+      }
+      // the last committed MMAs finish before TMEM and shared memory are released
+      if (p > 0) mbar_wait_final(fb0 + 8u * ((p - 1) & 1), (unsigned)((p - 1) >> 1) & 1u, &bad);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- converters: staging, exponents, digits, drains
+    const unsigned tacc = taddr + ((unsigned)Lq << 16) + (unsigned)yq;
+    const unsigned tsum = tacc + 256u;
+    {
+      unsigned z[3][NY];
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+#pragma unroll
+        for (int y = 0; y < NY; ++y) z[u][y] = 0u;
+#pragma unroll
+      for (int c0 = 0; c0 < NS; c0 += 3)
+        tmem_st3<NY>(tsum + c0 * KYP, tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, z);
+      tmem_wait_st();
+    }
+
+    auto issue = [&](int p) {
+      const int64_t pr = r0 + (int64_t)p * P;
+      const int rows = (int)min((int64_t)P, r1 - pr);
+      const unsigned sdst = smem_u32(stage) + (unsigned)(p & 1) * pl.stage_bytes;
+      const int lgh = __ffs(P) - 2;  // log2(P / 2)
+      for (int e = tid; e < nslots << lgh; e += kConvThreads) {
+        const int c = e >> lgh, r = (e & ((1 << lgh) - 1)) * 2;
+        const bool isx = pl.shared || c < kxp;
+        const int col = isx ? x0 + c : y0 + (c - kxp);
+        const bool valid = col < (isx ? kx : ky);
+        const double* src = valid ? (isx ? X + (size_t)col * ldx : Y + (size_t)col * ldy) + pr : X;
+        const int have = valid ? max(0, min(2, rows - r)) : 0;
+        const unsigned dst = sdst + (unsigned)(c * SP + r) * 8u;
+        if (aligned16) {
+          cp_async16(dst, have ? src + r : src, (unsigned)have * 8u);
+        } else {
+          cp_async8(dst, have >= 1 ? src + r : src, have >= 1 ? 8u : 0u);
+          cp_async8(dst + 8, have >= 2 ? src + r + 1 : src, have >= 2 ? 8u : 0u);
+        }
+      }
+      cp_async_commit();
+    };
+
+    auto drain = [&]() {  // TMEM accumulators -> TMEM running sums (column block c of lane block jl: diagonal c + jl)
+#pragma unroll
+      for (int c0 = 0; c0 < NS; c0 += 3) {
+        unsigned v[3][NY], sm[3][NY];
+        tmem_ld3x2<NY>(tacc + c0 * KYP, tacc + (c0 + 1) * KYP, tacc + (c0 + 2) * KYP, tsum + c0 * KYP,
+                       tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, v, sm);
+        // (column blocks with c + jl > 14 collect no kept diagonal: the fold skips them)
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+          for (int y = 0; y < NY; ++y) sm[u][y] += (unsigned)__float2int_rn(__uint_as_float(v[u][y]) * 0x1p48f);
+        tmem_st3<NY>(tsum + c0 * KYP, tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, sm);
+      }
+      tmem_wait_st();
+    };
+    auto fold = [&]() {  // running sums -> W (units 2^(Ax + Ay - 2148)), sums back to zero
+      i128 h[NY];
+#pragma unroll
+      for (int y = 0; y < NY; ++y) h[y] = 0;
+#pragma unroll
+      for (int c0 = 0; c0 < NS; c0 += 3) {
+        unsigned sm[3][NY];
+        tmem_ld3<NY>(tsum + c0 * KYP, tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, sm);
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+          for (int y = 0; y < NY; ++y)
+            if (c0 + u + jl <= 14) h[y] = (h[y] << 7) + (i128)(int)sm[u][y];
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+          for (int y = 0; y < NY; ++y) sm[u][y] = 0u;
+        tmem_st3<NY>(tsum + c0 * KYP, tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, sm);
+      }
+      tmem_wait_st();
+#pragma unroll
+      for (int y = 0; y < NY; ++y) W[y] += h[y] >> 8;
+    };
+
+    // This thread's items (two rows of one column) of every panel: i = tid +
+    // k * 512.  Within a warp, lanes l, l ^ 8, l ^ 16, l ^ 24 share a column,
+    // and the 32 digit words a warp stores per slab fill 128 contiguous
+    // bytes.  it_s: column << 16 | staging offset; it_d: digit offset | B operand << 31.
+    const int half = P >> 1, ncg = nslots >> 3;
+    const int nitems = nslots * half;
+    unsigned it_s[kMaxItems], it_d[kMaxItems];
+#pragma unroll
+    for (int k = 0; k < kMaxItems; ++k) {
+      const int i = tid + k * kConvThreads;
+      const int cl = i & 7, rl = (i >> 3) & 3, rest = i >> 5;
+      const int c = (rest % ncg) * 8 + cl, rh = rest / ncg, r = (rh * 4 + rl) * 2;
+      const bool isb = !pl.shared && c >= kxp;
+      const int lc = isb ? c - kxp : c;
+      it_s[k] = ((unsigned)c << 16) | (unsigned)(c * SP + r);
+      it_d[k] = ((isb ? pl.a_bytes : 0u) + (unsigned)(lc >> 3) * SBO + (unsigned)rh * 128u +
+                 (unsigned)(lc & 7) * 16u + (unsigned)rl * 4u) |
+                ((unsigned)isb << 31);
+    }
+    const unsigned stride_a = (unsigned)kxp / 8u * SBO, stride_b = (unsigned)KYP / 8u * SBO;
+    const bool scan_lead = (lane & 24) == 0;  // one lane of the four that share a column
+
+    int undrained = 0, drains = 0;
+    bool fresh = true;
+    if (npan > 0) issue(0);
+    for (int p = 0; p < npan; ++p) {
+      const int db = p & 1;
+      const double* st = reinterpret_cast<const double*>(reinterpret_cast<const unsigned char*>(stage) +
+                                                          (size_t)db * pl.stage_bytes);
+      int* pm = pmax + db * nslots;  // this panel's column maxima
+      cp_async_wait0();
+      bar_conv();  // panel p staged; panel p-1's conversion has read the other staging buffer
+      if (p > 0 && tid < nslots) {  // fold panel p-1's maxima into the running exponents
+        int* pq = pmax + ((p - 1) & 1) * nslots;
+        Erun[tid] = max(Erun[tid], pq[tid]);
+        pq[tid] = 0;
+      }
+      if (p + 1 < npan) issue(p + 1);
+
+      // largest exponent of each column in the panel: max of |x| bit patterns
+#pragma unroll
+      for (int k = 0; k < kMaxItems; ++k) {
+        if (tid + k * kConvThreads < nitems) {
+          const double2 v = *reinterpret_cast<const double2*>(st + (it_s[k] & 0xffffu));
+          const unsigned ka = (hi32(v.x) & 0x7fffffffu) | min(lo32(v.x), 1u);
+          const unsigned kb = (hi32(v.y) & 0x7fffffffu) | min(lo32(v.y), 1u);
+          unsigned m = max(ka, kb);
+          m = max(m, __shfl_xor_sync(0xffffffffu, m, 8));
+          m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
+          if (scan_lead && m) {
+            int e = (int)(m >> 20);
+            if (e == 0) e = 1;  // subnormal
+            if (e == 2047) flag = 1;
+            atomicMax(&pm[it_s[k] >> 16], e);
+          }
+        }
+      }
+      bar_conv();
+      const bool grew_local = tid < nslots && Erun[tid] != 0 && pm[tid] > Erun[tid];
+
+      // the digit buffer db is free once the MMAs of panel p-2 are done
+      if (p >= 2) mbar_wait(fb0 + 8u * db, (unsigned)((p - 2) >> 1) & 1u, &bad);
+
+      // digits of panel p
+      unsigned char* dbuf = dig + (size_t)db * pl.dig_bytes;
+#pragma unroll
+      for (int k = 0; k < kMaxItems; ++k) {
+        if (tid + k * kConvThreads < nitems) {
+          const int c = (int)(it_s[k] >> 16);
+          const double2 v = *reinterpret_cast<const double2*>(st + (it_s[k] & 0xffffu));
+          const int A = max(max(Erun[c], pm[c]), 1);
+          unsigned wa[4], wb[4];
+          xwords(v.x, A, wa);
+          xwords(v.y, A, wb);
+          const unsigned signs = ((hi32(v.x) >> 31) << 15) | (hi32(v.y) & 0x80000000u);
+          store_digits<0>(dbuf + (it_d[k] & 0x7fffffffu), (it_d[k] >> 31) ? stride_b : stride_a, wa, wb, signs);
+        }
+      }
+      fence_proxy_async();
+      const bool grew = bar_conv_or(grew_local);
+
+      if ((grew || undrained >= pl.drain_panels) && undrained > 0) {
+        // all MMAs so far (the last commit is panel p-1's) are done before TMEM is read
+        mbar_wait(fb0 + 8u * ((p - 1) & 1), (unsigned)((p - 1) >> 1) & 1u, &bad);
+        tc_fence_after();
+        drain();
+        ++drains;
+        if (grew || drains == pl.fold_drains) {
+          fold();
+          drains = 0;
+        }
+        if (grew) {  // totals onto the new grid: divide by 2^(growth of both columns' exponents)
+          const int ysb = pl.shared ? 0 : kxp;
+#pragma unroll
+          for (int y = 0; y < NY; ++y) {
+            const int cx = xl, cy = ysb + yq + y;
+            const int dx = Erun[cx] ? max(Erun[cx], pm[cx]) - Erun[cx] : 0;
+            const int dy = Erun[cy] ? max(Erun[cy], pm[cy]) - Erun[cy] : 0;
+            W[y] = w_shift(W[y], dx + dy);
+          }
+        }
+        tc_fence_before();
+        undrained = 0;
+        fresh = true;
+      }
+      if (tid == 0) fresh_flag[db] = fresh ? 1 : 0;
+      mbar_arrive(rb0 + 8u * db);  // digits of p ready (and TMEM drained if it was due)
+      fresh = false;
+      ++undrained;
+    }
+
+    // last drain and fold
+    if (npan > 0) {
+      mbar_wait(fb0 + 8u * ((npan - 1) & 1), (unsigned)((npan - 1) >> 1) & 1u, &bad);
+      tc_fence_after();
+      drain();
+      fold();
+      tc_fence_before();
+    }
+    bar_conv();
+    if (npan > 0 && tid < nslots) Erun[tid] = max(Erun[tid], pmax[((npan - 1) & 1) * nslots + tid]);
+  }
+
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(taddr, 512);
+  }
+
+  // sum the lane blocks (digit phase j) of every output and write the partials
+  i128* red = reinterpret_cast<i128*>(dig);  // 128 lanes x KYP entries (the MMAs are done)
+  if (warp < kConvWarps) {
+#pragma unroll
+    for (int y = 0; y < NY; ++y) red[L * KYP + yq + y] = W[y];
+  }
+  __syncthreads();
+  const int J = pl.J;
+  for (int e = tid; e < kxp * KYP; e += kThreads) {
+    const int xo = e / KYP, yo = e % KYP;
+    const int i = x0 + xo, j = y0 + yo;
+    if (i >= kx || j >= ky) continue;
+    i128 w = 0;
+    for (int b = 0; b < J; ++b) w += red[(b * kxp + xo) * KYP + yo];
+    const int cy = pl.shared ? yo : kxp + yo;
+    FxPart o;
+    o.wl = (long long)(unsigned long long)(u128)w;
+    o.wh = (long long)(w >> 64);
+    o.s = max(Erun[xo], 1) + max(Erun[cy], 1) - kOffsetDigits;
+    o.flag = flag | bad;
+    o.pad = 0;
+    parts[(size_t)blockIdx.y * ((size_t)kx * ky) + (size_t)j * kx + i] = o;
+  }
+}
+
+// ------------------------------------------------------------ host side
+int pow2_at_least(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+UPlan make_plan(int kx, int ky, bool sym) {
+  UPlan p{};
+  if (sym && kx <= 16) {
+    p.shared = 1;
+    p.kxp = 16;
+    p.kyp = 16;
+  } else {
+    p.kxp = std::min(128, std::max(16, pow2_at_least(kx)));
+    p.kyp = ky <= 8 ? 8 : 16;
+  }
+  p.J = kLanes / p.kxp;
+  p.nq = 14 / p.J + 1;
+  p.ntx = (kx + p.kxp - 1) / p.kxp;
+  p.nty = p.shared ? 1 : (ky + p.kyp - 1) / p.kyp;
+  p.nslots = p.shared ? p.kxp : p.kxp + p.kyp;
+  // rows an accumulator may absorb: digit pairs per entry and row <= 14 / J + 1, each < 2^14
+  const int pairs = 14 / p.J + 1;
+  const int rows_cap = (int)((1u << 24) / ((unsigned)pairs * 127u * 127u));
+  int best = 16;
+  for (int P = 16; P <= 128; P *= 2) {
+    if (P > rows_cap || (size_t)p.nslots * P / 2 > (size_t)kMaxItems * kConvThreads) break;
+    const size_t dig = (size_t)32 * P * (p.shared ? p.kxp : p.kxp + p.kyp);
+    const size_t stg = (size_t)p.nslots * (P + 2) * 8;
+    const size_t red = (size_t)kLanes * p.kyp * 16;
+    if (std::max(2 * dig, red) + 2 * stg + 12 * (size_t)p.nslots > kSmemCap) break;
+    best = P;
+  }
+  p.P = best;
+  p.drain_panels = std::max(1, rows_cap / p.P);
+  // a drain adds at most drain rows x pairs x 127^2 to a 32-bit running sum
+  const long long per_drain = (long long)p.drain_panels * p.P * pairs * 127 * 127;
+  p.fold_drains = (int)std::max(1ll, std::min<long long>(kFoldRows / (p.drain_panels * p.P),
+                                                          ((1ll << 31) - 1) / per_drain));
+  p.a_bytes = (unsigned)(32 * p.P * p.kxp);
+  p.dig_bytes = (unsigned)(32 * p.P * (p.shared ? p.kxp : p.kxp + p.kyp));
+  p.stage_bytes = (unsigned)(p.nslots * (p.P + 2) * 8);
+  return p;
+}
+
+size_t plan_smem(const UPlan& p) {
+  const size_t red = (size_t)kLanes * p.kyp * 16;
+  return std::max(2 * (size_t)p.dig_bytes, red) + 2 * (size_t)p.stage_bytes + 3 * sizeof(int) * p.nslots;
+}
+
+int num_chunks(int64_t n, const UPlan& p) {
+  const int tiles = p.ntx * p.nty;
+  const int64_t by_rows = (n + p.P - 1) / p.P;
+  const int64_t want = std::max<int64_t>(1, (152 + tiles - 1) / tiles);  // one CTA per SM
+  const int64_t need = (n + (1ll << 22) - 1) >> 22;                     // <= 2^22 rows per chunk
+  return (int)std::max<int64_t>(1, std::min(by_rows, std::max(want, need)));
+}
+
+template <int KYP>
+cudaError_t launch_kernel(const UPlan& plan, int chunks, int64_t n, int kx, const double* X, int64_t ldx, int ky,
+                          const double* Y, int64_t ldy, int64_t rpc, int aligned16, FxPart* parts, const int* gate,
+                          cudaStream_t st) {
+  const size_t smem = plan_smem(plan);
+  cudaError_t e =
+      cudaFuncSetAttribute(umma_gram_partial_kernel<KYP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(plan.ntx * plan.nty, chunks);
+  umma_gram_partial_kernel<KYP>
+      <<<grid, kThreads, smem, st>>>(n, kx, X, ldx, ky, Y, ldy, plan, rpc, aligned16, parts, gate);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t umma_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym) {
+  if (sym) ky = kx;
+  return (size_t)num_chunks(n, make_plan(kx, ky, sym)) * (size_t)kx * ky * sizeof(FxPart);
+}
+
+cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
+                             bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
+                             cudaStream_t st) {
+  if (sym) {
+    Y = X;
+    ldy = ldx;
+    ky = kx;
+  }
+  const UPlan plan = make_plan(kx, ky, sym);
+  const int chunks = num_chunks(n, plan);
+  int64_t rpc = (n + chunks - 1) / chunks;
+  rpc = std::max<int64_t>(plan.P, (rpc + plan.P - 1) / plan.P * plan.P);
+  const int aligned16 = ((uintptr_t)X % 16 == 0) && ((uintptr_t)Y % 16 == 0) && ldx % 2 == 0 && ldy % 2 == 0;
+  FxPart* parts = static_cast<FxPart*>(scratch);
+  cudaError_t e = plan.kyp == 16
+                      ? launch_kernel<16>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, aligned16, parts, gate, st)
+                      : launch_kernel<8>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, aligned16, parts, gate, st);
+  if (e != cudaSuccess) return e;
+  return launch_fx_reduce(kx, ky, sym, chunks, parts, G_hi, G_lo, ldg, gate, st);
+}
+
+}  // namespace eo

@@ -104,13 +104,13 @@ def test_gram_fp64_and_f32_within_textbook_bound(eo, ctx, prec, n, k):
     assert not np.any(host(gl))
 
 
-@pytest.mark.parametrize("engine", ["int", "tc"])
+@pytest.mark.parametrize("engine", ["int", "umma"])
 @pytest.mark.parametrize("n,kx,ky,sym", [(1, 1, 1, True), (33, 3, 3, True), (1000, 8, 8, False), (4099, 13, 5, False),
                                          (100_003, 16, 16, True), (20_000, 64, 64, True), (20_001, 64, 16, False),
                                          (70_001, 2, 7, False), (50_000, 40, 24, False), (30_017, 33, 33, True),
-                                         (131, 17, 9, False)])
+                                         (131, 17, 9, False), (9_000, 64, 12, False), (5_003, 48, 16, False)])
 def test_gram_dd_both_engines(eo, ctx, monkeypatch, engine, n, kx, ky, sym):
-    """The integer-limb and the tensor-core-digit engines of EO_DD against the oracle."""
+    """The integer-limb and the tcgen05 digit engines of EO_DD against the oracle."""
     monkeypatch.setenv("EO_DD_GRAM_ENGINE", engine)
     x = synth.gaussian(n, kx, 400 + kx)
     y = x if sym else synth.gaussian(n, ky, 500 + ky)
@@ -123,7 +123,7 @@ def test_gram_dd_both_engines(eo, ctx, monkeypatch, engine, n, kx, ky, sym):
         assert np.array_equal(host(gh), host(gh).T)
 
 
-@pytest.mark.parametrize("engine", ["int", "tc"])
+@pytest.mark.parametrize("engine", ["int", "umma"])
 def test_gram_dd_engines_rescale_and_range(eo, ctx, monkeypatch, engine):
     monkeypatch.setenv("EO_DD_GRAM_ENGINE", engine)
     n = 200_000
@@ -136,6 +136,45 @@ def test_gram_dd_engines_rescale_and_range(eo, ctx, monkeypatch, engine):
         rh, rl = oracle.gram(a, b)
         bb = a if b is None else b
         assert np.all(dd_err(host(gh), host(gl), rh, rl) <= dd_gram_tol(a, bb, rh, 1))
+
+
+@pytest.mark.parametrize("engine", ["int", "umma"])
+@pytest.mark.parametrize("kx,ky,sym", [(64, 16, False), (16, 16, True), (64, 40, False), (20, 8, False)])
+def test_gram_dd_engines_largest_digits(eo, ctx, monkeypatch, engine, kx, ky, sym):
+    """Every mantissa bit set and one exponent per column: all leading digits
+    take their largest value, so every per-diagonal sum reaches its bound."""
+    monkeypatch.setenv("EO_DD_GRAM_ENGINE", engine)
+    n = 70_001
+    top = 2.0 - 2.0 ** -52
+    g = synth.rng(31)
+    x = np.asfortranarray(np.full((n, kx), top) * np.ldexp(1.0, g.integers(-3, 4, size=kx))[None, :])
+    y = x if sym else np.asfortranarray(np.full((n, ky), -top) * np.ldexp(1.0, g.integers(-3, 4, size=ky))[None, :])
+    y[::7, :] *= -1.0
+    gh, gl = eo.gram(ctx, dev(x), None if sym else dev(y), prec=eo.DD)
+    rh, rl = oracle.gram(x, None if sym else y)
+    assert np.all(dd_err(host(gh), host(gl), rh, rl) <= dd_gram_tol(x, y, rh, 1))
+
+
+@pytest.mark.parametrize("engine", ["int", "umma"])
+def test_gram_dd_engines_odd_leading_dimension(eo, ctx, monkeypatch, engine):
+    """Leading dimensions and base addresses that are only 8-byte aligned."""
+    monkeypatch.setenv("EO_DD_GRAM_ENGINE", engine)
+    torch = torch_mod()
+    n, kx, ky = 3001, 24, 16
+    x = synth.gaussian(n, kx, 41)
+    y = synth.gaussian(n, ky, 42)
+    ts = []
+    for a, ld in ((x, 3003), (y, 3005)):
+        buf = synth.with_ld(a, ld + 1, fill=np.nan)
+        t = torch.from_numpy(np.ascontiguousarray(buf.T)).cuda().reshape(-1)
+        # a view starting one element into the buffer, leading dimension ld (odd)
+        v = t[1:1 + ld * a.shape[1]].reshape(a.shape[1], ld).t()[:n, :]
+        v.copy_(torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t())
+        assert v.stride(1) == ld and v.data_ptr() % 16 == 8
+        ts.append(v)
+    gh, gl = eo.gram(ctx, ts[0], ts[1], prec=eo.DD)
+    rh, rl = oracle.gram(x, y)
+    assert np.all(dd_err(host(gh), host(gl), rh, rl) <= dd_gram_tol(x, y, rh, 1))
 
 
 def test_gram_dd_integer_inputs_are_exact(eo, ctx):
