@@ -29,12 +29,19 @@
 //    exact, order-free reduction (fx_gram_reduce).
 //
 // The dropped digit pairs (d >= 15) weigh less than 2^-101 max|x| max|y| per
-// row, as in the integer engine.  Pipeline per CTA (one per SM): cp.async
-// staging of panel p+1, conversion of panel p into one of two digit buffers
-// while the tensor cores run panel p-1, one elected thread issuing the MMAs
-// and committing them to an mbarrier per buffer.  Every wait is bounded; a
-// wait that runs out marks the partials non-finite, so the result is NaN.
+// row, as in the integer engine.  Pipeline per CTA (one per SM): TMA loads
+// of the FP64 panels (128-byte swizzle, two panels ahead), conversion of
+// panel p into one of two digit buffers while the tensor cores run panel
+// p-1, one warp issuing the MMAs and committing them to an mbarrier per
+// buffer.  Every wait is bounded; a wait that runs out marks the partials
+// non-finite, so the result is NaN.  Inputs that TMA cannot address (a base
+// address not 16-byte aligned or an odd leading dimension) go to the integer
+// engine.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "fx.cuh"
@@ -65,7 +72,7 @@ struct UPlan {
   int nslots;           // staged columns per CTA
   unsigned dig_bytes;   // one digit buffer (A part, then B part unless shared)
   unsigned a_bytes;     // A part of a digit buffer
-  unsigned stage_bytes; // one staging buffer
+  unsigned stage_bytes; // one staging buffer: P / 16 TMA boxes of X (16 rows x kxp), then of Y
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -226,6 +233,57 @@ __device__ __forceinline__ void tmem_ld3x2(unsigned a0, unsigned a1, unsigned a2
         : "memory");
   }
 }
+// The same loads without the wait; tmem_wait_ld_regs completes them (it names
+// the destination registers so that no use can move above the wait).
+template <int NY>
+__device__ __forceinline__ void tmem_ld3x2_nowait(unsigned a0, unsigned a1, unsigned a2, unsigned b0, unsigned b1,
+                                                  unsigned b2, unsigned (&v)[3][NY], unsigned (&w)[3][NY]) {
+  if constexpr (NY == 4) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%24];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%25];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%26];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12,%13,%14,%15}, [%27];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16,%17,%18,%19}, [%28];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%20,%21,%22,%23}, [%29];\n"
+        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[0][2]), "=r"(v[0][3]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[1][2]),
+          "=r"(v[1][3]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(v[2][2]), "=r"(v[2][3]), "=r"(w[0][0]), "=r"(w[0][1]),
+          "=r"(w[0][2]), "=r"(w[0][3]), "=r"(w[1][0]), "=r"(w[1][1]), "=r"(w[1][2]), "=r"(w[1][3]), "=r"(w[2][0]),
+          "=r"(w[2][1]), "=r"(w[2][2]), "=r"(w[2][3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(b0), "r"(b1), "r"(b2)
+        : "memory");
+  } else {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%12];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2,%3}, [%13];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4,%5}, [%14];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6,%7}, [%15];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8,%9}, [%16];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10,%11}, [%17];\n"
+        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(w[0][0]),
+          "=r"(w[0][1]), "=r"(w[1][0]), "=r"(w[1][1]), "=r"(w[2][0]), "=r"(w[2][1])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(b0), "r"(b1), "r"(b2)
+        : "memory");
+  }
+}
+template <int NY>
+__device__ __forceinline__ void tmem_wait_ld_regs(unsigned (&v)[3][NY], unsigned (&w)[3][NY]) {
+  if constexpr (NY == 4) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0][0]), "+r"(v[0][1]), "+r"(v[0][2]), "+r"(v[0][3]), "+r"(v[1][0]), "+r"(v[1][1]),
+                   "+r"(v[1][2]), "+r"(v[1][3]), "+r"(v[2][0]), "+r"(v[2][1]), "+r"(v[2][2]), "+r"(v[2][3]),
+                   "+r"(w[0][0]), "+r"(w[0][1]), "+r"(w[0][2]), "+r"(w[0][3]), "+r"(w[1][0]), "+r"(w[1][1]),
+                   "+r"(w[1][2]), "+r"(w[1][3]), "+r"(w[2][0]), "+r"(w[2][1]), "+r"(w[2][2]), "+r"(w[2][3])
+                 :
+                 : "memory");
+  } else {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0][0]), "+r"(v[0][1]), "+r"(v[1][0]), "+r"(v[1][1]), "+r"(v[2][0]), "+r"(v[2][1]),
+                   "+r"(w[0][0]), "+r"(w[0][1]), "+r"(w[1][0]), "+r"(w[1][1]), "+r"(w[2][0]), "+r"(w[2][1])
+                 :
+                 : "memory");
+  }
+}
 template <int NY>
 __device__ __forceinline__ void tmem_st3(unsigned a0, unsigned a1, unsigned a2, const unsigned (&v)[3][NY]) {
   if constexpr (NY == 4) {
@@ -247,14 +305,17 @@ __device__ __forceinline__ void tmem_st3(unsigned a0, unsigned a1, unsigned a2, 
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void cp_async16(unsigned dst, const void* src, unsigned src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void cp_async8(unsigned dst, const void* src, unsigned src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+// 2-D TMA tile load (box of the tensor map at coordinates (x, y) = (row, column)).
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ------------------------------------------------------------ digits
 // X = floor(|x| 2^(1127 - A)) < 2^105 as four 32-bit words (w[0] least
@@ -313,7 +374,8 @@ template <int KYP>
 __global__ void __launch_bounds__(kThreads, 1)
     umma_gram_partial_kernel(int64_t n, int kx, const double* __restrict__ X, int64_t ldx, int ky,
                              const double* __restrict__ Y, int64_t ldy, UPlan pl, int64_t rows_per_chunk,
-                             int aligned16, FxPart* __restrict__ parts, const int* gate) {
+                             const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
+                             FxPart* __restrict__ parts, const int* gate) {
   if (gate && *gate == 0) return;
   constexpr int NY = KYP / 4;  // Y columns of one converter thread in a drain
   const int kxp = pl.kxp, P = pl.P, nslots = pl.nslots;
@@ -321,17 +383,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int x0 = tx * kxp, y0 = ty * KYP;  // first X / Y column of the tile
   const unsigned SBO = (unsigned)P * 16;   // bytes per 8-row group of a slab (P / 8 core matrices)
 
-  extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* dig = smem;                                                   // 2 digit buffers
-  double* stage = reinterpret_cast<double*>(smem + 2 * (size_t)pl.dig_bytes);  // 2 staging buffers
-  int* Erun = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(stage) + 2 * (size_t)pl.stage_bytes);
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned base (the 128-byte swizzle of the TMA boxes is anchored there)
+  unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* stage = smem;                                 // 2 staging buffers (TMA boxes)
+  unsigned char* dig = stage + 2 * (size_t)pl.stage_bytes;     // 2 digit buffers
+  int* Erun = reinterpret_cast<int*>(dig + 2 * (size_t)pl.dig_bytes);
   int* pmax = Erun + nslots;  // two panels' column maxima
-  __shared__ __align__(8) unsigned long long full_bar[2], ready_bar[2];
+  __shared__ __align__(8) unsigned long long full_bar[2], ready_bar[2], stage_bar[2];
   __shared__ unsigned tmem_base;
   __shared__ int flag, bad, fresh_flag[2];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int SP = P + 2;  // staging stride per column (doubles): conflict-free 16-byte reads
 
   // ---- set-up: TMEM (accumulators in columns 0..255, running sums in 256..511),
   // barriers, zero slabs, exponents
@@ -340,6 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&full_bar[b]), 1);
       mbar_init(smem_u32(&ready_bar[b]), kConvThreads);
+      mbar_init(smem_u32(&stage_bar[b]), 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     flag = 0;
@@ -367,7 +431,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t r1 = min(n, r0 + rows_per_chunk);
   const int npan = r0 < r1 ? (int)((r1 - r0 + P - 1) / P) : 0;
   const unsigned dig_s = smem_u32(dig);
-  const unsigned fb0 = smem_u32(&full_bar[0]), rb0 = smem_u32(&ready_bar[0]);
+  const unsigned fb0 = smem_u32(&full_bar[0]), rb0 = smem_u32(&ready_bar[0]), sb0 = smem_u32(&stage_bar[0]);
+  // TMA loads of panel p into staging buffer p & 1: P / 16 boxes of 16 rows per operand
+  const unsigned xbox = (unsigned)kxp * 128u, ybox = (unsigned)KYP * 128u;
+  auto load_panel = [&](int p) {
+    const unsigned bar = sb0 + 8u * (unsigned)(p & 1);
+    const unsigned dst = smem_u32(stage) + (unsigned)(p & 1) * pl.stage_bytes;
+    const int xr = (int)(r0 + (int64_t)p * P);
+    mbar_arrive_expect_tx(bar, pl.stage_bytes);
+    for (int h = 0; h < P / 16; ++h) {
+      tma_load_2d(dst + (unsigned)h * xbox, &tmx, xr + 16 * h, x0, bar);
+      if (!pl.shared) tma_load_2d(dst + (unsigned)(P / 16) * xbox + (unsigned)h * ybox, &tmy, xr + 16 * h, y0, bar);
+    }
+  };
+  if (tid == 0) {
+    for (int p = 0; p < 2 && p < npan; ++p) load_panel(p);
+  }
 
   // the partial sums of this thread's lane: lane block jl (digit phase), X column xl
   const int Lq = (warp & 3) * 32, L = Lq + lane;
@@ -421,42 +500,36 @@ __global__ void __launch_bounds__(kThreads, 1)
       tmem_wait_st();
     }
 
-    auto issue = [&](int p) {
-      const int64_t pr = r0 + (int64_t)p * P;
-      const int rows = (int)min((int64_t)P, r1 - pr);
-      const unsigned sdst = smem_u32(stage) + (unsigned)(p & 1) * pl.stage_bytes;
-      const int lgh = __ffs(P) - 2;  // log2(P / 2)
-      for (int e = tid; e < nslots << lgh; e += kConvThreads) {
-        const int c = e >> lgh, r = (e & ((1 << lgh) - 1)) * 2;
-        const bool isx = pl.shared || c < kxp;
-        const int col = isx ? x0 + c : y0 + (c - kxp);
-        const bool valid = col < (isx ? kx : ky);
-        const double* src = valid ? (isx ? X + (size_t)col * ldx : Y + (size_t)col * ldy) + pr : X;
-        const int have = valid ? max(0, min(2, rows - r)) : 0;
-        const unsigned dst = sdst + (unsigned)(c * SP + r) * 8u;
-        if (aligned16) {
-          cp_async16(dst, have ? src + r : src, (unsigned)have * 8u);
-        } else {
-          cp_async8(dst, have >= 1 ? src + r : src, have >= 1 ? 8u : 0u);
-          cp_async8(dst + 8, have >= 2 ? src + r + 1 : src, have >= 2 ? 8u : 0u);
-        }
-      }
-      cp_async_commit();
-    };
-
     auto drain = [&]() {  // TMEM accumulators -> TMEM running sums (column block c of lane block jl: diagonal c + jl)
-#pragma unroll
-      for (int c0 = 0; c0 < NS; c0 += 3) {
-        unsigned v[3][NY], sm[3][NY];
-        tmem_ld3x2<NY>(tacc + c0 * KYP, tacc + (c0 + 1) * KYP, tacc + (c0 + 2) * KYP, tsum + c0 * KYP,
-                       tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, v, sm);
+      // five groups of three column blocks; the loads of group g + 1 are in flight while group g is added
+      unsigned va[3][NY], sa[3][NY], vb[3][NY], sb[3][NY];
+      auto load = [&](int c0, unsigned (&v)[3][NY], unsigned (&sm)[3][NY]) {
+        tmem_ld3x2_nowait<NY>(tacc + c0 * KYP, tacc + (c0 + 1) * KYP, tacc + (c0 + 2) * KYP, tsum + c0 * KYP,
+                              tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, v, sm);
+      };
+      auto add_store = [&](int c0, unsigned (&v)[3][NY], unsigned (&sm)[3][NY]) {
         // (column blocks with c + jl > 14 collect no kept diagonal: the fold skips them)
 #pragma unroll
         for (int u = 0; u < 3; ++u)
 #pragma unroll
           for (int y = 0; y < NY; ++y) sm[u][y] += (unsigned)__float2int_rn(__uint_as_float(v[u][y]) * 0x1p48f);
         tmem_st3<NY>(tsum + c0 * KYP, tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, sm);
-      }
+      };
+      load(0, va, sa);
+      tmem_wait_ld_regs<NY>(va, sa);
+      load(3, vb, sb);
+      add_store(0, va, sa);
+      tmem_wait_ld_regs<NY>(vb, sb);
+      load(6, va, sa);
+      add_store(3, vb, sb);
+      tmem_wait_ld_regs<NY>(va, sa);
+      load(9, vb, sb);
+      add_store(6, va, sa);
+      tmem_wait_ld_regs<NY>(vb, sb);
+      load(12, va, sa);
+      add_store(9, vb, sb);
+      tmem_wait_ld_regs<NY>(va, sa);
+      add_store(12, va, sa);
       tmem_wait_st();
     };
     auto fold = [&]() {  // running sums -> W (units 2^(Ax + Ay - 2148)), sums back to zero
@@ -485,8 +558,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     // This thread's items (two rows of one column) of every panel: i = tid +
     // k * 512.  Within a warp, lanes l, l ^ 8, l ^ 16, l ^ 24 share a column,
-    // and the 32 digit words a warp stores per slab fill 128 contiguous
-    // bytes.  it_s: column << 16 | staging offset; it_d: digit offset | B operand << 31.
+    // the eight columns of a quarter warp read distinct 16-byte chunks of the
+    // swizzled boxes, and the 32 digit words a warp stores per slab fill 128
+    // contiguous bytes.  it_s: column << 16 | staging offset / 16; it_d:
+    // digit offset | B operand << 31.
     const int half = P >> 1, ncg = nslots >> 3;
     const int nitems = nslots * half;
     unsigned it_s[kMaxItems], it_d[kMaxItems];
@@ -497,7 +572,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int c = (rest % ncg) * 8 + cl, rh = rest / ncg, r = (rh * 4 + rl) * 2;
       const bool isb = !pl.shared && c >= kxp;
       const int lc = isb ? c - kxp : c;
-      it_s[k] = ((unsigned)c << 16) | (unsigned)(c * SP + r);
+      const unsigned so = (isb ? (unsigned)(P / 16) * xbox : 0u) + (unsigned)(r >> 4) * (isb ? ybox : xbox) +
+                          (unsigned)lc * 128u + ((((unsigned)(r & 15) >> 1) ^ (unsigned)(lc & 7)) << 4);
+      it_s[k] = ((unsigned)c << 16) | (so >> 4);
       it_d[k] = ((isb ? pl.a_bytes : 0u) + (unsigned)(lc >> 3) * SBO + (unsigned)rh * 128u +
                  (unsigned)(lc & 7) * 16u + (unsigned)rl * 4u) |
                 ((unsigned)isb << 31);
@@ -507,37 +584,41 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     int undrained = 0, drains = 0;
     bool fresh = true;
-    if (npan > 0) issue(0);
     for (int p = 0; p < npan; ++p) {
       const int db = p & 1;
-      const double* st = reinterpret_cast<const double*>(reinterpret_cast<const unsigned char*>(stage) +
-                                                          (size_t)db * pl.stage_bytes);
+      const unsigned char* st = stage + (size_t)db * pl.stage_bytes;
       int* pm = pmax + db * nslots;  // this panel's column maxima
-      cp_async_wait0();
-      bar_conv();  // panel p staged; panel p-1's conversion has read the other staging buffer
+      mbar_wait(sb0 + 8u * db, (unsigned)(p >> 1) & 1u, &bad);  // panel p staged
+      bar_conv();  // every converter is past panel p-1
       if (p > 0 && tid < nslots) {  // fold panel p-1's maxima into the running exponents
         int* pq = pmax + ((p - 1) & 1) * nslots;
         Erun[tid] = max(Erun[tid], pq[tid]);
         pq[tid] = 0;
       }
-      if (p + 1 < npan) issue(p + 1);
 
+      // this thread's values of the panel (kept in registers for the conversion)
+      double2 v[kMaxItems];
+#pragma unroll
+      for (int k = 0; k < kMaxItems; ++k)
+        v[k] = tid + k * kConvThreads < nitems ? *reinterpret_cast<const double2*>(st + ((it_s[k] & 0xffffu) << 4))
+                                               : make_double2(0.0, 0.0);
       // largest exponent of each column in the panel: max of |x| bit patterns
+      unsigned m[kMaxItems];
+#pragma unroll
+      for (int k = 0; k < kMaxItems; ++k)
+        m[k] = max((hi32(v[k].x) & 0x7fffffffu) | min(lo32(v[k].x), 1u),
+                   (hi32(v[k].y) & 0x7fffffffu) | min(lo32(v[k].y), 1u));
+#pragma unroll
+      for (int k = 0; k < kMaxItems; ++k) m[k] = max(m[k], __shfl_xor_sync(0xffffffffu, m[k], 8));
+#pragma unroll
+      for (int k = 0; k < kMaxItems; ++k) m[k] = max(m[k], __shfl_xor_sync(0xffffffffu, m[k], 16));
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
-        if (tid + k * kConvThreads < nitems) {
-          const double2 v = *reinterpret_cast<const double2*>(st + (it_s[k] & 0xffffu));
-          const unsigned ka = (hi32(v.x) & 0x7fffffffu) | min(lo32(v.x), 1u);
-          const unsigned kb = (hi32(v.y) & 0x7fffffffu) | min(lo32(v.y), 1u);
-          unsigned m = max(ka, kb);
-          m = max(m, __shfl_xor_sync(0xffffffffu, m, 8));
-          m = max(m, __shfl_xor_sync(0xffffffffu, m, 16));
-          if (scan_lead && m) {
-            int e = (int)(m >> 20);
-            if (e == 0) e = 1;  // subnormal
-            if (e == 2047) flag = 1;
-            atomicMax(&pm[it_s[k] >> 16], e);
-          }
+        if (scan_lead && m[k] && tid + k * kConvThreads < nitems) {
+          int e = (int)(m[k] >> 20);
+          if (e == 0) e = 1;  // subnormal
+          if (e == 2047) flag = 1;
+          atomicMax(&pm[it_s[k] >> 16], e);
         }
       }
       bar_conv();
@@ -548,21 +629,28 @@ __global__ void __launch_bounds__(kThreads, 1)
 
       // digits of panel p
       unsigned char* dbuf = dig + (size_t)db * pl.dig_bytes;
+      int A[kMaxItems];
+#pragma unroll
+      for (int k = 0; k < kMaxItems; ++k) {
+        const int c = (int)(it_s[k] >> 16);
+        A[k] = max(max(Erun[c], pm[c]), 1);
+      }
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
         if (tid + k * kConvThreads < nitems) {
-          const int c = (int)(it_s[k] >> 16);
-          const double2 v = *reinterpret_cast<const double2*>(st + (it_s[k] & 0xffffu));
-          const int A = max(max(Erun[c], pm[c]), 1);
           unsigned wa[4], wb[4];
-          xwords(v.x, A, wa);
-          xwords(v.y, A, wb);
-          const unsigned signs = ((hi32(v.x) >> 31) << 15) | (hi32(v.y) & 0x80000000u);
+          xwords(v[k].x, A[k], wa);
+          xwords(v[k].y, A[k], wb);
+          const unsigned signs = ((hi32(v[k].x) >> 31) << 15) | (hi32(v[k].y) & 0x80000000u);
           store_digits<0>(dbuf + (it_d[k] & 0x7fffffffu), (it_d[k] >> 31) ? stride_b : stride_a, wa, wb, signs);
         }
       }
       fence_proxy_async();
       const bool grew = bar_conv_or(grew_local);
+      if (tid == 0 && p + 2 < npan) {  // staging buffer db is free: panel p + 2
+        fence_proxy_async();
+        load_panel(p + 2);
+      }
 
       if ((grew || undrained >= pl.drain_panels) && undrained > 0) {
         // all MMAs so far (the last commit is panel p-1's) are done before TMEM is read
@@ -666,9 +754,9 @@ UPlan make_plan(int kx, int ky, bool sym) {
   for (int P = 16; P <= 128; P *= 2) {
     if (P > rows_cap || (size_t)p.nslots * P / 2 > (size_t)kMaxItems * kConvThreads) break;
     const size_t dig = (size_t)32 * P * (p.shared ? p.kxp : p.kxp + p.kyp);
-    const size_t stg = (size_t)p.nslots * (P + 2) * 8;
+    const size_t stg = (size_t)p.nslots * P * 8;
     const size_t red = (size_t)kLanes * p.kyp * 16;
-    if (std::max(2 * dig, red) + 2 * stg + 12 * (size_t)p.nslots > kSmemCap) break;
+    if (std::max(2 * dig, red) + 2 * stg + 12 * (size_t)p.nslots + 1024 > kSmemCap) break;
     best = P;
   }
   p.P = best;
@@ -679,13 +767,13 @@ UPlan make_plan(int kx, int ky, bool sym) {
                                                           ((1ll << 31) - 1) / per_drain));
   p.a_bytes = (unsigned)(32 * p.P * p.kxp);
   p.dig_bytes = (unsigned)(32 * p.P * (p.shared ? p.kxp : p.kxp + p.kyp));
-  p.stage_bytes = (unsigned)(p.nslots * (p.P + 2) * 8);
+  p.stage_bytes = (unsigned)(p.nslots * p.P * 8);
   return p;
 }
 
 size_t plan_smem(const UPlan& p) {
   const size_t red = (size_t)kLanes * p.kyp * 16;
-  return std::max(2 * (size_t)p.dig_bytes, red) + 2 * (size_t)p.stage_bytes + 3 * sizeof(int) * p.nslots;
+  return std::max(2 * (size_t)p.dig_bytes, red) + 2 * (size_t)p.stage_bytes + 3 * sizeof(int) * p.nslots + 1024;
 }
 
 int num_chunks(int64_t n, const UPlan& p) {
@@ -696,17 +784,43 @@ int num_chunks(int64_t n, const UPlan& p) {
   return (int)std::max<int64_t>(1, std::min(by_rows, std::max(want, need)));
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// Tensor map of a column-major n-by-k FP64 matrix: boxes of 16 rows x w columns.
+bool make_map(CUtensorMap* m, const double* A, int64_t n, int k, int64_t ld, int w) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)std::max<int64_t>(n, 1), (cuuint64_t)k};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 8u};
+  const cuuint32_t box[2] = {16u, (cuuint32_t)w};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(A), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int KYP>
 cudaError_t launch_kernel(const UPlan& plan, int chunks, int64_t n, int kx, const double* X, int64_t ldx, int ky,
-                          const double* Y, int64_t ldy, int64_t rpc, int aligned16, FxPart* parts, const int* gate,
-                          cudaStream_t st) {
+                          const double* Y, int64_t ldy, int64_t rpc, const CUtensorMap& tmx, const CUtensorMap& tmy,
+                          FxPart* parts, const int* gate, cudaStream_t st) {
   const size_t smem = plan_smem(plan);
   cudaError_t e =
       cudaFuncSetAttribute(umma_gram_partial_kernel<KYP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(plan.ntx * plan.nty, chunks);
   umma_gram_partial_kernel<KYP>
-      <<<grid, kThreads, smem, st>>>(n, kx, X, ldx, ky, Y, ldy, plan, rpc, aligned16, parts, gate);
+      <<<grid, kThreads, smem, st>>>(n, kx, X, ldx, ky, Y, ldy, plan, rpc, tmx, tmy, parts, gate);
   return cudaGetLastError();
 }
 
@@ -726,14 +840,19 @@ cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, in
     ky = kx;
   }
   const UPlan plan = make_plan(kx, ky, sym);
+  // TMA addresses 16-byte aligned bases and leading dimensions of whole 16-byte units
+  alignas(64) CUtensorMap tmx, tmy;
+  const bool tma_ok = (uintptr_t)X % 16 == 0 && (uintptr_t)Y % 16 == 0 && ldx % 2 == 0 && ldy % 2 == 0 &&
+                      n < (1ll << 31) && make_map(&tmx, X, n, kx, ldx, plan.kxp) &&
+                      make_map(&tmy, Y, n, ky, ldy, plan.kyp);
+  if (!tma_ok) return launch_fx_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st);
   const int chunks = num_chunks(n, plan);
   int64_t rpc = (n + chunks - 1) / chunks;
   rpc = std::max<int64_t>(plan.P, (rpc + plan.P - 1) / plan.P * plan.P);
-  const int aligned16 = ((uintptr_t)X % 16 == 0) && ((uintptr_t)Y % 16 == 0) && ldx % 2 == 0 && ldy % 2 == 0;
   FxPart* parts = static_cast<FxPart*>(scratch);
   cudaError_t e = plan.kyp == 16
-                      ? launch_kernel<16>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, aligned16, parts, gate, st)
-                      : launch_kernel<8>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, aligned16, parts, gate, st);
+                      ? launch_kernel<16>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st)
+                      : launch_kernel<8>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st);
   if (e != cudaSuccess) return e;
   return launch_fx_reduce(kx, ky, sym, chunks, parts, G_hi, G_lo, ldg, gate, st);
 }
