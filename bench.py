@@ -4,8 +4,9 @@
 Workload (one "step" = one pass of the whole path over one block):
   V: 4,000,000 x 64 FP64 orthonormal basis, Y: 4,000,000 x 16 FP64 with
   singular values log-spaced 1 .. 1e-10 (seeded, synthetic; see synth.py).
-  step = eo_gram          (C = V^T Y, compensated)
-       + eo_project_apply (Y~ = Y - V C and M = Y~^T Y~, compensated)
+  step = eo_gram          (C = V^T Y, compensated; tcgen05 digit engine)
+       + eo_project_apply (Y~ = Y - V C, compensated)
+       + eo_gram          (M = Y~^T Y~, compensated; tcgen05 digit engine)
        + eo_cholqr        (compensated, first pass from M, automatic second pass).
 The inputs (2.6 GB per step) are larger than L2 (129 MB), so no flush is
 needed between steps.
@@ -32,7 +33,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Gram/CholQR HBM GB/s and blocks/s at ||Q^TQ-I||<=1e-14, DD vs plain FP64; p50/p99"
-WORKLOAD = "projection plus orthogonalization: V 4,000,000x64 orthonormal FP64, Y 4,000,000x16 FP64 (sigma 1..1e-10); V^T Y, Y - V(V^T Y), DD-Gram CholQR"
+WORKLOAD = ("projection plus orthogonalization: V {n:,}x{kv} orthonormal FP64, Y {n:,}x{k} FP64 (sigma 1..1/{kappa:g}); "
+            "V^T Y, Y - V(V^T Y), DD-Gram CholQR")
 
 
 def parse():
@@ -202,7 +204,8 @@ def run_eo(a):
     def step(prec=eo.DD, out=None, passes=0):
         out = Yt if out is None else out
         c = eo.gram(ctx, V, Y, prec=prec)
-        _, m = eo.project_apply(ctx, V, Y, c, Yout=out, prec=prec)
+        eo.project_apply(ctx, V, Y, c, Yout=out, prec=prec, want_m=False)
+        m = eo.gram(ctx, out, prec=prec)
         return eo.cholqr(ctx, out, passes=passes, prec=prec, M=m)
 
     for _ in range(max(3, a.warmup)):
@@ -219,7 +222,7 @@ def run_eo(a):
     cross_err = float(np.linalg.norm(cross[0].cpu().numpy() + cross[1].cpu().numpy(), 2))
 
     nbytes = step_bytes(n, kv, k, two_passes)
-    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(4)) for _ in range(a.steps)]
+    ev = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(5)) for _ in range(a.steps)]
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -234,36 +237,44 @@ def run_eo(a):
             ev[i][0].record(stream)
             c = eo.gram(ctx, V, Y, prec=eo.DD)
             ev[i][1].record(stream)
-            _, m = eo.project_apply(ctx, V, Y, c, Yout=Yt, prec=eo.DD)
+            eo.project_apply(ctx, V, Y, c, Yout=Yt, prec=eo.DD, want_m=False)
             ev[i][2].record(stream)
-            eo.cholqr(ctx, Yt, passes=0, prec=eo.DD, M=m)
+            m = eo.gram(ctx, Yt, prec=eo.DD)
             ev[i][3].record(stream)
+            eo.cholqr(ctx, Yt, passes=0, prec=eo.DD, M=m)
+            ev[i][4].record(stream)
         t_all1.record(stream)
         torch.cuda.synchronize()
     launches = ctx.launches() - l0
     if ws > 1:
         dist.barrier()
     total_ms = max_over_ranks(t_all0.elapsed_time(t_all1), dev)
-    per = [e[0].elapsed_time(e[3]) for e in ev]
+    per = [e[0].elapsed_time(e[4]) for e in ev]
     gram_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     apply_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
-    chol_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
+    gram_m_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in ev)
+    chol_ms = statistics.mean(e[3].elapsed_time(e[4]) for e in ev)
     ms = total_ms / a.steps
     value = weak_scaling_value(ws, nbytes, ms)
 
-    # roofline of the dominant kernel: the compensated Gram V^T Y (fx_gram_partial
-    # + its fixed-order reduction), bound by the integer multiply-add pipe
+    # roofline of the dominant kernel: the compensated projection Y - V C
+    # (fx_rowprod_kernel, exact limb products on the integer multiply-add pipe)
     hbm_peak, peak_kind = peak_hbm()
-    gram_flops = 2.0 * n * kv * k
-    achieved = gram_flops / (gram_ms * 1e-3) / 1e12
+    apply_flops = 2.0 * n * kv * k
+    achieved = apply_flops / (apply_ms * 1e-3) / 1e12
     peak = alu_peak_tflops()
+    apply_bytes = 8 * n * (kv + 2 * k)
     gram_bytes = 8 * n * (kv + k)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "fx_gram_partial_kernel (compensated V^T Y, 4e6 x 64 x 16)",
+            "traffic": None, "kernel": "fx_rowprod_kernel<0> (compensated Y - V C, 4e6 x 64 x 16)",
             "peak_source": "derived: 64 IMAD lanes/clk/SM x 152 SMs x 2070 MHz / 10 limb products x 2 flops",
-            "launch_ms": gram_ms, "hbm_achieved_gbs": gram_bytes / (gram_ms * 1e-3) / 1e9,
-            "hbm_frac": gram_bytes / (gram_ms * 1e-3) / 1e9 / hbm_peak, "hbm_peak_gbs": hbm_peak,
-            "hbm_peak_source": peak_kind, "apply_ms": apply_ms, "cholqr_ms": chol_ms}
+            "launch_ms": apply_ms, "hbm_achieved_gbs": apply_bytes / (apply_ms * 1e-3) / 1e9,
+            "hbm_frac": apply_bytes / (apply_ms * 1e-3) / 1e9 / hbm_peak, "hbm_peak_gbs": hbm_peak,
+            "hbm_peak_source": peak_kind,
+            "phases_ms": {"gram_vty": gram_ms, "apply": apply_ms, "gram_m": gram_m_ms, "cholqr": chol_ms},
+            "gram_vty": {"kernel": "umma_gram_partial_kernel<16> + fx_gram_reduce_kernel (tcgen05)",
+                         "ms": gram_ms, "hbm_gbs": gram_bytes / (gram_ms * 1e-3) / 1e9,
+                         "tflops_algorithmic": 2.0 * n * kv * k / (gram_ms * 1e-3) / 1e12}}
 
     # plain FP64 comparator on the same input (two passes; breaks down at this kappa)
     Yp = torch.empty_like(Yt.t()).t()
@@ -309,7 +320,8 @@ def run_eo(a):
             Vd.copy_(Vh, non_blocking=True)
             Yd.copy_(Yh, non_blocking=True)
             c = eo.gram(ctx, Vd.t(), Yd.t(), prec=eo.DD)
-            _, m = eo.project_apply(ctx, Vd.t(), Yd.t(), c, Yout=Qd.t(), prec=eo.DD)
+            eo.project_apply(ctx, Vd.t(), Yd.t(), c, Yout=Qd.t(), prec=eo.DD, want_m=False)
+            m = eo.gram(ctx, Qd.t(), prec=eo.DD)
             r, _, _ = eo.cholqr(ctx, Qd.t(), passes=0, prec=eo.DD, M=m)
             Qh.copy_(Qd, non_blocking=True)
             Rh.copy_(r.t(), non_blocking=True)
@@ -336,7 +348,7 @@ def run_eo(a):
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded; V Haar-orthonormal, Y = U diag(sigma) W^T, sigma 1..1e-10)",
-        "config": {"workload": WORKLOAD, "n": n, "kv": kv, "k": k, "kappa": a.kappa, "prec": "dd",
+        "config": {"workload": WORKLOAD.format(n=n, kv=kv, k=k, kappa=a.kappa), "n": n, "kv": kv, "k": k, "kappa": a.kappa, "prec": "dd",
                    "passes": 2 if two_passes else 1, "parallelism": f"replicas x{ws}",
                    "l2": "inputs (2.6 GB/step) larger than L2; no flush"},
         "blocks_per_s": ws * 1000.0 / ms, "p50_ms": float(np.percentile(per, 50)),
@@ -375,7 +387,8 @@ def run_reference(a):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f128", "data": "synthetic (seeded, same recipe)",
-           "config": {"workload": WORKLOAD, "n": n, "kv": kv, "k": k, "kappa": a.kappa, "sample_rows": rows},
+           "config": {"workload": WORKLOAD.format(n=n, kv=kv, k=k, kappa=a.kappa), "n": n, "kv": kv, "k": k,
+                      "kappa": a.kappa, "sample_rows": rows},
            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
                             "sample": f"{rows} rows per step of the same workload recipe"},
            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
