@@ -91,6 +91,14 @@ size_t fx_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym);
 cudaError_t launch_fx_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
                            bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
                            cudaStream_t st);
+// Row products of the compensated mode on the tcgen05 tensor cores
+// (umma_rowprod.cu): Out = Yin - A B (update = false) or Out = A B (update =
+// true), A n-by-kin, B kin-by-kout double-double (column j at Bh + j ldb);
+// kin <= 64, kout <= 16 (umma_rowprod_supported); Out may be A (in place).
+bool umma_rowprod_supported(int kin, int kout);
+cudaError_t launch_umma_rowprod(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout,
+                                const double* Bh, const double* Bl, int ldb, bool tri, const double* Yin,
+                                int64_t ldyin, double* Out, int64_t ldo, const int* gate, cudaStream_t st);
 // X <- X Z in place (Z: k-by-k double-double, leading dimension KMAX).
 cudaError_t launch_fx_update(int64_t n, int k, double* X, int64_t ldx, const double* Zh, const double* Zl, bool tri,
                              const int* gate, cudaStream_t st);

@@ -164,14 +164,21 @@ cudaError_t launch_rowprod(bool update, int64_t n, int kin, const double* A, int
 
 }  // namespace
 
+// Both row products go to the tensor-core engine (umma_rowprod.cu) when their
+// sizes fit it (kin <= 64, kout <= 16), to the integer limbs otherwise;
+// EO_DD_ROW_ENGINE=int forces the integer limbs.
 cudaError_t launch_fx_update(int64_t n, int k, double* X, int64_t ldx, const double* Zh, const double* Zl, bool tri,
                              const int* gate, cudaStream_t st) {
+  if (umma_rowprod_supported(k, k))
+    return launch_umma_rowprod(true, n, k, X, ldx, k, Zh, Zl, KMAX, tri, nullptr, 0, X, ldx, gate, st);
   return launch_rowprod(true, n, k, X, ldx, k, Zh, Zl, KMAX, tri, nullptr, 0, X, ldx, gate, st);
 }
 
 cudaError_t launch_fx_project(int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y, int64_t ldy,
                               double* Yout, int64_t ldyo, const double* C_hi, const double* C_lo, int ldc,
                               const int* gate, cudaStream_t st) {
+  if (umma_rowprod_supported(kv, k))
+    return launch_umma_rowprod(false, n, kv, V, ldv, k, C_hi, C_lo, ldc, false, Y, ldy, Yout, ldyo, gate, st);
   return launch_rowprod(false, n, kv, V, ldv, k, C_hi, C_lo, ldc, false, Y, ldy, Yout, ldyo, gate, st);
 }
 

@@ -45,22 +45,22 @@
 
 #include "common.cuh"
 #include "fx.cuh"
+#include "umma.cuh"
 
 namespace eo {
 namespace {
 
 using namespace fx;
+using namespace umma;
 
 constexpr int kConvWarps = 16;                // staging, conversion and drains
 constexpr int kConvThreads = 32 * kConvWarps;
 constexpr int kThreads = kConvThreads + 32;  // plus one MMA-issuing warp
-constexpr int NS = 15;        // digits per value
 constexpr int kLanes = 128;   // MMA M = TMEM lanes
 constexpr int kMaxItems = 3;  // items (two rows of one column) per thread and panel
 constexpr int kOffsetDigits = 2148;
 constexpr int kFoldRows = 8192;  // rows between folds of the 32-bit running sums
 constexpr size_t kSmemCap = 225 * 1024;
-constexpr unsigned long long kWaitNs = 2000000000ull;  // bound of every mbarrier wait
 
 struct UPlan {
   int kxp, kyp, J, nq;  // X tile width (J = 128 / kxp lane blocks), Y tile width, MMAs per k-step
@@ -74,295 +74,6 @@ struct UPlan {
   unsigned a_bytes;     // A part of a digit buffer
   unsigned stage_bytes; // one staging buffer: P / 16 TMA boxes of X (16 rows x kxp), then of Y
 };
-
-// ------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Wait for the phase of the given parity to complete.  Gives up (false) once
-// *abort is set or after kWaitNs, and then sets *abort so that every other
-// wait of the CTA gives up at once.
-__device__ __noinline__ bool mbar_wait(unsigned bar, unsigned parity, volatile int* abort) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = gtimer();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort || gtimer() - t0 > kWaitNs) {
-      *abort = 1;
-      return false;
-    }
-  }
-  return true;
-}
-// The same, but only the time limit ends it (waits for MMAs already issued).
-__device__ __noinline__ bool mbar_wait_final(unsigned bar, unsigned parity, volatile int* abort) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = gtimer();
-  while (!mbar_try_wait(bar, parity)) {
-    if (gtimer() - t0 > kWaitNs) {
-      *abort = 1;
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void mbar_arrive(unsigned bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-// Barrier 1 among the converter warps only.
-__device__ __forceinline__ void bar_conv() { asm volatile("bar.sync 1, %0;" ::"n"(kConvThreads) : "memory"); }
-__device__ __forceinline__ bool bar_conv_or(bool v) {
-  unsigned r;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
-      : "=r"(r)
-      : "r"((unsigned)v), "n"(kConvThreads)
-      : "memory");
-  return r != 0;
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(unsigned dst, unsigned ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(unsigned taddr, unsigned ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// Shared-memory matrix descriptor: no swizzle, K-major canonical layout;
-// lbo = bytes between core matrices adjacent in K, sbo = in M/N.
-__device__ __forceinline__ unsigned long long sdesc(unsigned addr, unsigned lbo, unsigned sbo) {
-  return (unsigned long long)((addr >> 4) & 0x3fffu) | ((unsigned long long)((lbo >> 4) & 0x3fffu) << 16) |
-         ((unsigned long long)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
-}
-// Instruction descriptor of kind::f16: FP16 A and B (K-major), FP32 D.
-__host__ __device__ constexpr unsigned idesc_f16(int M, int N) {
-  return (1u << 4) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma_f16(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
-                                        unsigned accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(unsigned bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-               : "memory");
-}
-
-// Three column groups of NY consecutive TMEM columns (this warp's 32 lanes),
-// loaded and waited for in one step.
-template <int NY>
-__device__ __forceinline__ void tmem_ld3(unsigned a0, unsigned a1, unsigned a2, unsigned (&v)[3][NY]) {
-  if constexpr (NY == 4) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%12];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%13];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%14];\n"
-        "tcgen05.wait::ld.sync.aligned;\n"
-        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[0][2]), "=r"(v[0][3]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[1][2]),
-          "=r"(v[1][3]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(v[2][2]), "=r"(v[2][3])
-        : "r"(a0), "r"(a1), "r"(a2)
-        : "memory");
-  } else {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%6];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2,%3}, [%7];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4,%5}, [%8];\n"
-        "tcgen05.wait::ld.sync.aligned;\n"
-        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[2][0]), "=r"(v[2][1])
-        : "r"(a0), "r"(a1), "r"(a2)
-        : "memory");
-  }
-}
-
-// Six groups: three of the accumulators and three of the running sums.
-template <int NY>
-__device__ __forceinline__ void tmem_ld3x2(unsigned a0, unsigned a1, unsigned a2, unsigned b0, unsigned b1,
-                                           unsigned b2, unsigned (&v)[3][NY], unsigned (&w)[3][NY]) {
-  if constexpr (NY == 4) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%24];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%25];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%26];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12,%13,%14,%15}, [%27];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16,%17,%18,%19}, [%28];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%20,%21,%22,%23}, [%29];\n"
-        "tcgen05.wait::ld.sync.aligned;\n"
-        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[0][2]), "=r"(v[0][3]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[1][2]),
-          "=r"(v[1][3]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(v[2][2]), "=r"(v[2][3]), "=r"(w[0][0]), "=r"(w[0][1]),
-          "=r"(w[0][2]), "=r"(w[0][3]), "=r"(w[1][0]), "=r"(w[1][1]), "=r"(w[1][2]), "=r"(w[1][3]), "=r"(w[2][0]),
-          "=r"(w[2][1]), "=r"(w[2][2]), "=r"(w[2][3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(b0), "r"(b1), "r"(b2)
-        : "memory");
-  } else {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%12];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2,%3}, [%13];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4,%5}, [%14];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6,%7}, [%15];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8,%9}, [%16];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10,%11}, [%17];\n"
-        "tcgen05.wait::ld.sync.aligned;\n"
-        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(w[0][0]),
-          "=r"(w[0][1]), "=r"(w[1][0]), "=r"(w[1][1]), "=r"(w[2][0]), "=r"(w[2][1])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(b0), "r"(b1), "r"(b2)
-        : "memory");
-  }
-}
-// The same loads without the wait; tmem_wait_ld_regs completes them (it names
-// the destination registers so that no use can move above the wait).
-template <int NY>
-__device__ __forceinline__ void tmem_ld3x2_nowait(unsigned a0, unsigned a1, unsigned a2, unsigned b0, unsigned b1,
-                                                  unsigned b2, unsigned (&v)[3][NY], unsigned (&w)[3][NY]) {
-  if constexpr (NY == 4) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%24];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%25];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%26];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12,%13,%14,%15}, [%27];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16,%17,%18,%19}, [%28];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%20,%21,%22,%23}, [%29];\n"
-        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[0][2]), "=r"(v[0][3]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[1][2]),
-          "=r"(v[1][3]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(v[2][2]), "=r"(v[2][3]), "=r"(w[0][0]), "=r"(w[0][1]),
-          "=r"(w[0][2]), "=r"(w[0][3]), "=r"(w[1][0]), "=r"(w[1][1]), "=r"(w[1][2]), "=r"(w[1][3]), "=r"(w[2][0]),
-          "=r"(w[2][1]), "=r"(w[2][2]), "=r"(w[2][3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(b0), "r"(b1), "r"(b2)
-        : "memory");
-  } else {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%12];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2,%3}, [%13];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4,%5}, [%14];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6,%7}, [%15];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8,%9}, [%16];\n"
-        "tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10,%11}, [%17];\n"
-        : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(w[0][0]),
-          "=r"(w[0][1]), "=r"(w[1][0]), "=r"(w[1][1]), "=r"(w[2][0]), "=r"(w[2][1])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(b0), "r"(b1), "r"(b2)
-        : "memory");
-  }
-}
-template <int NY>
-__device__ __forceinline__ void tmem_wait_ld_regs(unsigned (&v)[3][NY], unsigned (&w)[3][NY]) {
-  if constexpr (NY == 4) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(v[0][0]), "+r"(v[0][1]), "+r"(v[0][2]), "+r"(v[0][3]), "+r"(v[1][0]), "+r"(v[1][1]),
-                   "+r"(v[1][2]), "+r"(v[1][3]), "+r"(v[2][0]), "+r"(v[2][1]), "+r"(v[2][2]), "+r"(v[2][3]),
-                   "+r"(w[0][0]), "+r"(w[0][1]), "+r"(w[0][2]), "+r"(w[0][3]), "+r"(w[1][0]), "+r"(w[1][1]),
-                   "+r"(w[1][2]), "+r"(w[1][3]), "+r"(w[2][0]), "+r"(w[2][1]), "+r"(w[2][2]), "+r"(w[2][3])
-                 :
-                 : "memory");
-  } else {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(v[0][0]), "+r"(v[0][1]), "+r"(v[1][0]), "+r"(v[1][1]), "+r"(v[2][0]), "+r"(v[2][1]),
-                   "+r"(w[0][0]), "+r"(w[0][1]), "+r"(w[1][0]), "+r"(w[1][1]), "+r"(w[2][0]), "+r"(w[2][1])
-                 :
-                 : "memory");
-  }
-}
-template <int NY>
-__device__ __forceinline__ void tmem_st3(unsigned a0, unsigned a1, unsigned a2, const unsigned (&v)[3][NY]) {
-  if constexpr (NY == 4) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%3,%4,%5,%6};\n"
-        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%1], {%7,%8,%9,%10};\n"
-        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%2], {%11,%12,%13,%14};\n" ::"r"(a0),
-        "r"(a1), "r"(a2), "r"(v[0][0]), "r"(v[0][1]), "r"(v[0][2]), "r"(v[0][3]), "r"(v[1][0]), "r"(v[1][1]),
-        "r"(v[1][2]), "r"(v[1][3]), "r"(v[2][0]), "r"(v[2][1]), "r"(v[2][2]), "r"(v[2][3])
-        : "memory");
-  } else {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%3,%4};\n"
-        "tcgen05.st.sync.aligned.32x32b.x2.b32 [%1], {%5,%6};\n"
-        "tcgen05.st.sync.aligned.32x32b.x2.b32 [%2], {%7,%8};\n" ::"r"(a0),
-        "r"(a1), "r"(a2), "r"(v[0][0]), "r"(v[0][1]), "r"(v[1][0]), "r"(v[1][1]), "r"(v[2][0]), "r"(v[2][1])
-        : "memory");
-  }
-}
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-// 2-D TMA tile load (box of the tensor map at coordinates (x, y) = (row, column)).
-__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-// ------------------------------------------------------------ digits
-// X = floor(|x| 2^(1127 - A)) < 2^105 as four 32-bit words (w[0] least
-// significant); A >= align_exp(x).  X = m 2^t with m the 53-bit significand.
-__device__ __forceinline__ void xwords(double x, int A, unsigned (&w)[4]) {
-  const unsigned hi = hi32(x), lo = lo32(x);
-  const int e = (hi >> 20) & 0x7ff;
-  const unsigned mh = (hi & 0xfffffu) | (e ? 0x100000u : 0u);
-  const int t = 52 - A + max(e, 1);
-  if (t >= 0) {
-    const int bo = t & 31;
-    const unsigned s0 = lo << bo, s1 = __funnelshift_l(lo, mh, bo), s2 = __funnelshift_l(mh, 0u, bo);
-    const bool up = t >= 32;
-    w[0] = up ? 0u : s0;
-    w[1] = up ? s0 : s1;
-    w[2] = up ? s1 : s2;
-    w[3] = up ? s2 : 0u;
-  } else {  // more than 52 binades below the column's largest value
-    const int r = -t;
-    const unsigned long long m = ((unsigned long long)mh << 32) | lo;
-    const unsigned long long v = r < 64 ? m >> r : 0ull;
-    w[0] = (unsigned)v;
-    w[1] = (unsigned)(v >> 32);
-    w[2] = 0u;
-    w[3] = 0u;
-  }
-}
-
-// Bits [q, q + 7) of X in the low bits of the result (higher bits: junk).
-template <int S>
-__device__ __forceinline__ unsigned digit_field(const unsigned (&w)[4]) {
-  constexpr int q = 98 - 7 * S, wi = q >> 5, bo = q & 31;
-  if constexpr (bo + 7 <= 32) return w[wi] >> bo;
-  else return __funnelshift_r(w[wi], w[wi + 1], bo);
-}
-
-// The 15 digit words of two consecutive rows (low half: row r, high half:
-// row r + 1; each +-D 2^-24 as FP16) into their slabs, slab s at dst + s * stride.
-template <int S>
-__device__ __forceinline__ void store_digits(unsigned char* dst, unsigned stride, const unsigned (&a)[4],
-                                             const unsigned (&b)[4], unsigned signs) {
-  if constexpr (S < NS) {
-    const unsigned w = (__byte_perm(digit_field<S>(a), digit_field<S>(b), 0x5410) & 0x007f007fu) | signs;
-    *reinterpret_cast<unsigned*>(dst + S * stride) = w;
-    store_digits<S + 1>(dst, stride, a, b, signs);
-  }
-}
 
 // ------------------------------------------------------------ kernel
 // Warps 0..15 stage, scan, convert and drain (named barrier 1); warp 16
@@ -589,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const unsigned char* st = stage + (size_t)db * pl.stage_bytes;
       int* pm = pmax + db * nslots;  // this panel's column maxima
       mbar_wait(sb0 + 8u * db, (unsigned)(p >> 1) & 1u, &bad);  // panel p staged
-      bar_conv();  // every converter is past panel p-1
+      bar_conv<kConvThreads>();  // every converter is past panel p-1
       if (p > 0 && tid < nslots) {  // fold panel p-1's maxima into the running exponents
         int* pq = pmax + ((p - 1) & 1) * nslots;
         Erun[tid] = max(Erun[tid], pq[tid]);
@@ -621,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           atomicMax(&pm[it_s[k] >> 16], e);
         }
       }
-      bar_conv();
+      bar_conv<kConvThreads>();
       const bool grew_local = tid < nslots && Erun[tid] != 0 && pm[tid] > Erun[tid];
 
       // the digit buffer db is free once the MMAs of panel p-2 are done
@@ -646,7 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       fence_proxy_async();
-      const bool grew = bar_conv_or(grew_local);
+      const bool grew = bar_conv_or<kConvThreads>(grew_local);
       if (tid == 0 && p + 2 < npan) {  // staging buffer db is free: panel p + 2
         fence_proxy_async();
         load_panel(p + 2);
@@ -690,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       fold();
       tc_fence_before();
     }
-    bar_conv();
+    bar_conv<kConvThreads>();
     if (npan > 0 && tid < nslots) Erun[tid] = max(Erun[tid], pmax[((npan - 1) & 1) * nslots + tid]);
   }
 

@@ -1,0 +1,380 @@
+// umma_rowprod.cu — compensated row products on the tcgen05 tensor cores:
+//   projection  Y~ = Y - V C   (arXiv:1806.01036, Sec. 4.2, phase I, with
+//                               C = V^T Y a double-double kv-by-k matrix);
+//   update      Q  = X Z       (the final multiplication of phase II; Z the
+//                               double-double R^{-1} or M^{-1/2}).
+// Every output is the exact sum of its products (up to the dropped digit
+// pairs), rounded once; the projection subtracts the exact sum from y before
+// rounding.
+//
+// Digits (umma.cuh): a row of the streamed matrix (V or X) is aligned to its
+// own largest exponent A_r, a column j of the small matrix (C or Z) to
+// B_j = its largest exponent + 1 (room for the low part); both are cut into
+// fifteen 7-bit digits.  A tile is 128 rows = the 128 TMEM lanes; the K
+// dimension is the kin columns of the row (kin <= 64), the N dimension the
+// digit slab t and the output column j (16 columns, padded).  One MMA
+// multiplies digit slab s of the tile (M = 128, K = 16) by the slabs
+// t = 0 .. 14 - s of the small matrix (N = 16 (15 - s)) and writes at TMEM
+// column offset 16 s: column block d of a lane collects the digit diagonal
+// d = s + t of its row.  A diagonal sum has at most kin x 15 products of
+// magnitude <= 127^2, below 2^24 for kin <= 64, so the FP32 accumulators are
+// exact over the whole row: a tile needs no drains, only an epilogue that
+// combines its 15 diagonals per output in 128-bit integers,
+//   h = sum_d S_d 2^(7 (14 - d)),   sum_i v_i c_ij ~= h 2^(A_r + B_j - 2156),
+// and rounds y - h 2^(...) (or h 2^(...)) to FP64 in integer arithmetic.
+//
+// Pipeline (one CTA per SM, tiles round-robin): the 16 converter warps load
+// a tile's values straight into registers (8 rows x 4 column groups per
+// warp, coalesced along rows), find each row's exponent by shuffles, and
+// write the digits in three groups of five slabs into two alternating
+// shared-memory buffers; one warp issues the group's MMAs and commits them
+// to an mbarrier per buffer; TMEM holds two accumulators, so the epilogue of
+// tile i - 1 (tcgen05.ld, exact rounding, stores) runs while the tensor
+// cores work on tile i.  Every wait is bounded (the outputs of a CTA whose
+// wait ran out are NaN).  The tile's loads precede its stores, so the update
+// may run in place.
+#include <algorithm>
+#include <cstdlib>
+
+#include "common.cuh"
+#include "fx.cuh"
+#include "umma.cuh"
+
+namespace eo {
+namespace {
+
+using namespace fx;
+using namespace umma;
+
+constexpr int kConvWarps = 16;
+constexpr int kConvThreads = 32 * kConvWarps;
+constexpr int kThreads = kConvThreads + 32;  // plus one MMA-issuing warp
+constexpr int kRows = 128;                   // rows per tile (MMA M, TMEM lanes)
+constexpr int kOut = 16;                     // output columns of the MMA (padded)
+constexpr int kGroupSlabs = 5;               // digit slabs per group (three groups)
+constexpr int kScaleProd = 2156;             // value of h: h 2^(A_r + B_j - 2156)
+constexpr unsigned kAccCols = 256;           // TMEM columns per accumulator (240 used)
+constexpr size_t kMinSmem = 120 * 1024;      // keeps one CTA per SM (TMEM: 512 columns)
+
+__device__ __forceinline__ void st_shared_v4(unsigned addr, unsigned a, unsigned b, unsigned c, unsigned d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+__device__ __forceinline__ void st_shared_v2(unsigned addr, unsigned a, unsigned b) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+
+// Three groups of four TMEM columns (this warp's 32 lanes), loaded and waited for in one step.
+__device__ __forceinline__ void tmem_ld3x4(unsigned a0, unsigned a1, unsigned a2, unsigned (&v)[3][4]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%12];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%13];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%14];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[0][2]), "=r"(v[0][3]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[1][2]),
+        "=r"(v[1][3]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(v[2][2]), "=r"(v[2][3])
+      : "r"(a0), "r"(a1), "r"(a2)
+      : "memory");
+}
+
+// Digit words of slab S for W values of one row (two values per word, low
+// half first), stored at dst (W = 16: two 16-byte chunks 128 bytes apart;
+// W = 8: one chunk; W = 4: half a chunk).
+template <int S, int W>
+__device__ __forceinline__ void store_slab(unsigned dst, const unsigned (&X)[W][4], const unsigned (&sg)[W / 2]) {
+  unsigned w[W / 2];
+#pragma unroll
+  for (int m = 0; m < W / 2; ++m)
+    w[m] = (__byte_perm(digit_field<S>(X[2 * m]), digit_field<S>(X[2 * m + 1]), 0x5410) & 0x007f007fu) | sg[m];
+  if constexpr (W == 16) {
+    st_shared_v4(dst, w[0], w[1], w[2], w[3]);
+    st_shared_v4(dst + 128u, w[4], w[5], w[6], w[7]);
+  } else if constexpr (W == 8) {
+    st_shared_v4(dst, w[0], w[1], w[2], w[3]);
+  } else {
+    st_shared_v2(dst, w[0], w[1]);
+  }
+}
+
+template <int G, int W>
+__device__ __forceinline__ void store_group(unsigned dst, unsigned slab_bytes, const unsigned (&X)[W][4],
+                                            const unsigned (&sg)[W / 2]) {
+  store_slab<G * kGroupSlabs + 0, W>(dst, X, sg);
+  store_slab<G * kGroupSlabs + 1, W>(dst + slab_bytes, X, sg);
+  store_slab<G * kGroupSlabs + 2, W>(dst + 2 * slab_bytes, X, sg);
+  store_slab<G * kGroupSlabs + 3, W>(dst + 3 * slab_bytes, X, sg);
+  store_slab<G * kGroupSlabs + 4, W>(dst + 4 * slab_bytes, X, sg);
+}
+
+// x 2^(1127 - A) as a signed 128-bit integer, truncated toward zero.
+__device__ __forceinline__ i128 fixed_trunc(double x, int A) {
+  const unsigned hi = hi32(x), lo = lo32(x);
+  int be = (hi >> 20) & 0x7ff;
+  unsigned mh = hi & 0xfffffu;
+  if (be) mh |= 0x100000u; else be = 1;
+  const unsigned long long m = ((unsigned long long)mh << 32) | lo;
+  const int t = 52 - (A - be);
+  u128 X;
+  if (t >= 0) X = (u128)m << t;
+  else if (t > -64) X = (u128)(m >> (-t));
+  else X = 0;
+  return (hi >> 31) ? -(i128)X : (i128)X;
+}
+
+// KP = 4 W: the K dimension (kin padded to 16, 32 or 64).
+template <int W>
+__global__ void __launch_bounds__(kThreads, 1)
+    umma_rowprod_kernel(int update, int64_t n, int kin, const double* A, int64_t lda, int kout,
+                        const double* __restrict__ Bh, const double* __restrict__ Bl, int ldb, int tri,
+                        const double* Yin, int64_t ldyin, double* Out, int64_t ldo, const int* gate) {
+  if (gate && *gate == 0) return;
+  constexpr int KP = 4 * W;
+  constexpr int KC = KP / 16;             // MMAs (K = 16) per slab
+  constexpr unsigned SBO = 16u * KP;      // bytes between 8-row groups of an operand
+  constexpr unsigned SLAB_A = 16u * SBO;  // one digit slab of the tile (128 rows)
+  constexpr unsigned B_BYTES = 32u * SBO; // 16 slabs x 16 columns
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* bdig = smem;                                  // the small matrix's digits
+  unsigned char* adig = smem + B_BYTES;                        // two group buffers of 5 slabs
+  int* Arow = reinterpret_cast<int*>(adig + 2 * kGroupSlabs * SLAB_A);  // [2][128] row exponents
+  int* Rbad = Arow + 2 * kRows;                                // [2][128] non-finite rows
+  int* Bexp = Rbad + 2 * kRows;                                // [16] column exponents
+  int* Bbad = Bexp + kOut;                                     // [16] non-finite columns
+  __shared__ __align__(8) unsigned long long full_bar[2], ready_bar[2];
+  __shared__ unsigned tmem_base;
+  __shared__ int bad;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (n + kRows - 1) / kRows;
+
+  // ---- set-up: TMEM (two accumulators), barriers, the small matrix's digits
+  if (warp == 0) tmem_alloc(smem_u32(&tmem_base), 2 * kAccCols);
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&full_bar[b]), 1);
+      mbar_init(smem_u32(&ready_bar[b]), kConvThreads);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bad = 0;
+  }
+  if (tid < kOut) {
+    const int j = tid;
+    int e = 0, nf = 0;
+    if (j < kout) {
+      for (int i = 0; i < kin; ++i) {
+        if (tri && i > j) continue;
+        const int ae = align_exp(Bh[(size_t)j * ldb + i]);
+        e = max(e, ae);
+        if (ae == 2047 || (Bl && align_exp(Bl[(size_t)j * ldb + i]) == 2047)) nf = 1;
+      }
+    }
+    Bexp[j] = e + 1;  // one binade of headroom: |h + l| may round up past the largest h
+    Bbad[j] = nf;
+  }
+  __syncthreads();
+  for (int e = tid; e < kOut * KP; e += kThreads) {  // B row R = t * 16 + j (slab t), K index i
+    const int j = e / KP, i = e % KP;
+    i128 x = 0;
+    if (j < kout && i < kin && !(tri && i > j) && !Bbad[j]) {
+      const double h = Bh[(size_t)j * ldb + i], l = Bl ? Bl[(size_t)j * ldb + i] : 0.0;
+      x = fixed_trunc(h, Bexp[j]) + fixed_trunc(l, Bexp[j]);
+    }
+    const unsigned sign = x < 0 ? 0x8000u : 0u;
+    const u128 U = x < 0 ? (u128)(-x) : (u128)x;  // < 2^104
+    for (int t = 0; t < 16; ++t) {
+      const unsigned dgt = t < NS ? ((unsigned)(U >> (98 - 7 * t)) & 127u) | sign : 0u;
+      const int R = t * kOut + j;
+      *reinterpret_cast<unsigned short*>(bdig + (R >> 3) * SBO + (i >> 3) * 128 + (R & 7) * 16 + (i & 7) * 2) =
+          (unsigned short)dgt;
+    }
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned taddr = tmem_base;
+  const unsigned fb0 = smem_u32(&full_bar[0]), rb0 = smem_u32(&ready_bar[0]);
+  const unsigned adig_s = smem_u32(adig), bdig_s = smem_u32(bdig);
+
+  if (warp == kConvWarps) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      int G = 0;  // groups issued
+      bool ok = true;
+      for (int64_t T = blockIdx.x, i = 0; T < ntiles && ok; T += gridDim.x, ++i) {
+        const unsigned acc = taddr + (unsigned)(i & 1) * kAccCols;
+#pragma unroll 1
+        for (int g = 0; g < 3; ++g, ++G) {
+          const int b = G & 1;
+          if (!mbar_wait(rb0 + 8u * b, (unsigned)(G >> 1) & 1u, &bad)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const unsigned abuf = adig_s + (unsigned)b * kGroupSlabs * SLAB_A;
+          for (int sg = 0; sg < kGroupSlabs; ++sg) {
+            const int s = g * kGroupSlabs + sg;
+            const unsigned idesc = idesc_f16(kRows, kOut * (NS - s));
+#pragma unroll
+            for (int kc = 0; kc < KC; ++kc) {
+              const unsigned long long ad = sdesc(abuf + (unsigned)sg * SLAB_A + (unsigned)kc * 256u, 128u, SBO);
+              const unsigned long long bd = sdesc(bdig_s + (unsigned)kc * 256u, 128u, SBO);
+              mma_f16(acc + (unsigned)(kOut * s), ad, bd, idesc, (s == 0 && kc == 0) ? 0u : 1u);
+            }
+          }
+          mma_commit(fb0 + 8u * b);
+        }
+      }
+      // the last committed MMAs finish before TMEM and shared memory are released
+      if (G > 0) mbar_wait_final(fb0 + 8u * ((G - 1) & 1), (unsigned)((G - 1) >> 1) & 1u, &bad);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- converters: loads, row exponents, digits; epilogues
+    const int rlo = lane & 7, cg = lane >> 3;
+    const int r = warp * 8 + rlo;  // tile row of this thread's values
+    const int c0 = cg * W;         // first of its W columns
+    // digit offset of (row r, column c0) within a slab
+    const unsigned dofs = (unsigned)(r >> 3) * SBO + (unsigned)(c0 >> 3) * 128u + (unsigned)(r & 7) * 16u +
+                          (unsigned)(c0 & 7) * 2u;
+    // epilogue mapping: TMEM lane quarter warp % 4, outputs 4 (warp / 4) .. + 3
+    const int eq = warp & 3, ep = warp >> 2;
+    const int L = eq * 32 + lane;
+    const unsigned tq = taddr + ((unsigned)(eq * 32) << 16) + (unsigned)(ep * 4);
+
+    auto epilogue = [&](int64_t T, int64_t i) {
+      const unsigned tb = tq + (unsigned)(i & 1) * kAccCols;
+      i128 h[4] = {0, 0, 0, 0};
+#pragma unroll
+      for (int d0 = 0; d0 < NS; d0 += 3) {
+        unsigned v[3][4];
+        tmem_ld3x4(tb + (unsigned)(d0 * kOut), tb + (unsigned)((d0 + 1) * kOut), tb + (unsigned)((d0 + 2) * kOut), v);
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+          for (int y = 0; y < 4; ++y) h[y] = (h[y] << 7) + (i128)__float2int_rn(__uint_as_float(v[u][y]) * 0x1p48f);
+      }
+      const int64_t grow = T * kRows + L;
+      const int Ar = Arow[(i & 1) * kRows + L];
+      const bool rbad = Rbad[(i & 1) * kRows + L] != 0;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int j = ep * 4 + y;
+        if (j < kout && grow < n) {
+          const int S = Ar + Bexp[j] - kScaleProd;
+          double o = update ? w_to_double(h[y], S) : sub_round(Yin[(size_t)j * ldyin + grow], h[y], S);
+          if (rbad || Bbad[j] || bad) o = __longlong_as_double(0x7ff8000000000000ll);
+          Out[(size_t)j * ldo + grow] = o;
+        }
+      }
+    };
+
+    int G = 0;
+    int64_t Tprev = -1, iprev = 0;
+    for (int64_t T = blockIdx.x, i = 0; T < ntiles; T += gridDim.x, ++i) {
+      // this thread's W values of row r (zero beyond the matrix)
+      const int64_t gr = T * kRows + r;
+      double v[W];
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        const int col = c0 + k;
+        v[k] = (gr < n && col < kin) ? A[(size_t)col * lda + gr] : 0.0;
+      }
+      // the row's exponent: max of |x| bit patterns over the four threads of the row
+      unsigned key = 0;
+#pragma unroll
+      for (int k = 0; k < W; ++k) key = max(key, (hi32(v[k]) & 0x7fffffffu) | min(lo32(v[k]), 1u));
+      key = max(key, __shfl_xor_sync(0xffffffffu, key, 8));
+      key = max(key, __shfl_xor_sync(0xffffffffu, key, 16));
+      int e = (int)(key >> 20);
+      if (e == 0 && key) e = 1;  // subnormal
+      const int Ar = max(e, 1);
+      if (cg == 0) {
+        Arow[(i & 1) * kRows + r] = Ar;
+        Rbad[(i & 1) * kRows + r] = e == 2047;
+      }
+      unsigned X[W][4];
+#pragma unroll
+      for (int k = 0; k < W; ++k) xwords(v[k], Ar, X[k]);
+      unsigned sg[W / 2];
+#pragma unroll
+      for (int m = 0; m < W / 2; ++m) sg[m] = ((hi32(v[2 * m]) >> 31) << 15) | (hi32(v[2 * m + 1]) & 0x80000000u);
+
+      // three groups of five slabs into the alternating buffers
+#pragma unroll
+      for (int g = 0; g < 3; ++g, ++G) {
+        const int b = G & 1;
+        if (G >= 2) mbar_wait(fb0 + 8u * b, (unsigned)((G - 2) >> 1) & 1u, &bad);  // MMAs of group G - 2 done
+        const unsigned dst = adig_s + (unsigned)b * kGroupSlabs * SLAB_A + dofs;
+        if (g == 0) store_group<0, W>(dst, SLAB_A, X, sg);
+        else if (g == 1) store_group<1, W>(dst, SLAB_A, X, sg);
+        else store_group<2, W>(dst, SLAB_A, X, sg);
+        fence_proxy_async();
+        mbar_arrive(rb0 + 8u * b);
+      }
+      // the previous tile's MMAs completed (its last group G - 4 was waited for
+      // before group G - 2 was written): its epilogue overlaps this tile's MMAs
+      if (Tprev >= 0) {
+        tc_fence_after();
+        epilogue(Tprev, iprev);
+        tc_fence_before();
+      }
+      bar_conv<kConvThreads>();  // row exponents of buffer (i - 1) & 1 are free again
+      Tprev = T;
+      iprev = i;
+    }
+    if (Tprev >= 0) {  // the last tile
+      mbar_wait(fb0 + 8u * ((G - 1) & 1), (unsigned)((G - 1) >> 1) & 1u, &bad);
+      tc_fence_after();
+      epilogue(Tprev, iprev);
+      tc_fence_before();
+    }
+  }
+
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(taddr, 2 * kAccCols);
+  }
+}
+
+template <int W>
+size_t smem_bytes() {
+  constexpr int KP = 4 * W;
+  const size_t sbo = 16u * KP;
+  const size_t b = 32 * sbo, a = 2 * kGroupSlabs * 16 * sbo, small = (4 * kRows + 2 * kOut) * sizeof(int);
+  return std::max(b + a + small, kMinSmem);
+}
+
+template <int W>
+cudaError_t launch_w(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout, const double* Bh,
+                     const double* Bl, int ldb, bool tri, const double* Yin, int64_t ldyin, double* Out, int64_t ldo,
+                     const int* gate, cudaStream_t st) {
+  const size_t smem = smem_bytes<W>();
+  cudaError_t e = cudaFuncSetAttribute(umma_rowprod_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t ntiles = (n + kRows - 1) / kRows;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 152));
+  umma_rowprod_kernel<W><<<grid, kThreads, smem, st>>>(update ? 1 : 0, n, kin, A, lda, kout, Bh, Bl, ldb, tri ? 1 : 0,
+                                                       Yin, ldyin, Out, ldo, gate);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool umma_rowprod_supported(int kin, int kout) {
+  const char* e = getenv("EO_DD_ROW_ENGINE");
+  if (e && e[0] == 'i') return false;
+  return kin >= 1 && kin <= 64 && kout >= 1 && kout <= kOut;
+}
+
+cudaError_t launch_umma_rowprod(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout,
+                                const double* Bh, const double* Bl, int ldb, bool tri, const double* Yin,
+                                int64_t ldyin, double* Out, int64_t ldo, const int* gate, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if (kin <= 16) return launch_w<4>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st);
+  if (kin <= 32) return launch_w<8>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st);
+  return launch_w<16>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st);
+}
+
+}  // namespace eo
