@@ -298,26 +298,39 @@ __device__ __forceinline__ void xwords(double x, int A, unsigned (&w)[4]) {
   }
 }
 
-// Bits [q, q + 7) of X in the low bits of the result (higher bits: junk).
-template <int S>
-__device__ __forceinline__ unsigned digit_field(const unsigned (&w)[4]) {
-  constexpr int q = 98 - 7 * S, wi = q >> 5, bo = q & 31;
-  if constexpr (bo + 7 <= 32) return w[wi] >> bo;
-  else return __funnelshift_r(w[wi], w[wi + 1], bo);
+// A pair of values (a, b) interleaved in 16-bit lanes: Z[k] holds bits
+// 16k .. 16k + 15 of a in its low half and of b in its high half (k = 0..6),
+// Z8[k] the same for bits 16k + 8 .. 16k + 23 (k = 0..5).  Every 7-bit digit
+// field of both values then lies inside one lane of one word.
+struct PairLanes {
+  unsigned Z[7], Z8[6];
+};
+__device__ __forceinline__ PairLanes pair_lanes(const unsigned (&a)[4], const unsigned (&b)[4]) {
+  PairLanes p;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) p.Z[k] = __byte_perm(a[k >> 1], b[k >> 1], (k & 1) ? 0x7632 : 0x5410);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p.Z8[k] = __byte_perm(p.Z[k], p.Z[k + 1], 0x6341);
+  return p;
 }
-
-// The 15 digit words of two consecutive rows (low half: row r, high half:
-// row r + 1; each +-D 2^-24 as FP16) into their slabs, slab s at dst + s * stride.
+// Digit word of slab S for the pair: (D_S(a) | sign a) | ((D_S(b) | sign b) << 16),
+// both halves FP16 subnormals +-D 2^-24 (signs: bit 15 and bit 31).
 template <int S>
-__device__ __forceinline__ void store_digits(unsigned char* dst, unsigned stride, const unsigned (&a)[4],
-                                             const unsigned (&b)[4], unsigned signs) {
+__device__ __forceinline__ unsigned pair_word(const PairLanes& p, unsigned signs) {
+  constexpr int q = 98 - 7 * S, k = q >> 4, o = q & 15;
+  if constexpr (o <= 9) return ((p.Z[k] >> o) & 0x007f007fu) | signs;
+  else return ((p.Z8[k] >> (o - 8)) & 0x007f007fu) | signs;
+}
+// The 15 digit words of two consecutive rows (low half: row r, high half:
+// row r + 1) into their slabs, slab s at dst + s * stride.
+template <int S>
+__device__ __forceinline__ void store_digits(unsigned char* dst, unsigned stride, const PairLanes& p,
+                                             unsigned signs) {
   if constexpr (S < NS) {
-    const unsigned w = (__byte_perm(digit_field<S>(a), digit_field<S>(b), 0x5410) & 0x007f007fu) | signs;
-    *reinterpret_cast<unsigned*>(dst + S * stride) = w;
-    store_digits<S + 1>(dst, stride, a, b, signs);
+    *reinterpret_cast<unsigned*>(dst + S * stride) = pair_word<S>(p, signs);
+    store_digits<S + 1>(dst, stride, p, signs);
   }
 }
-
 
 }  // namespace umma
 }  // namespace eo

@@ -353,7 +353,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           xwords(v[k].x, A[k], wa);
           xwords(v[k].y, A[k], wb);
           const unsigned signs = ((hi32(v[k].x) >> 31) << 15) | (hi32(v[k].y) & 0x80000000u);
-          store_digits<0>(dbuf + (it_d[k] & 0x7fffffffu), (it_d[k] >> 31) ? stride_b : stride_a, wa, wb, signs);
+          store_digits<0>(dbuf + (it_d[k] & 0x7fffffffu), (it_d[k] >> 31) ? stride_b : stride_a, pair_lanes(wa, wb),
+                          signs);
         }
       }
       fence_proxy_async();

@@ -80,11 +80,10 @@ __device__ __forceinline__ void tmem_ld3x4(unsigned a0, unsigned a1, unsigned a2
 // half first), stored at dst (W = 16: two 16-byte chunks 128 bytes apart;
 // W = 8: one chunk; W = 4: half a chunk).
 template <int S, int W>
-__device__ __forceinline__ void store_slab(unsigned dst, const unsigned (&X)[W][4], const unsigned (&sg)[W / 2]) {
+__device__ __forceinline__ void store_slab(unsigned dst, const PairLanes (&P)[W / 2], const unsigned (&sg)[W / 2]) {
   unsigned w[W / 2];
 #pragma unroll
-  for (int m = 0; m < W / 2; ++m)
-    w[m] = (__byte_perm(digit_field<S>(X[2 * m]), digit_field<S>(X[2 * m + 1]), 0x5410) & 0x007f007fu) | sg[m];
+  for (int m = 0; m < W / 2; ++m) w[m] = pair_word<S>(P[m], sg[m]);
   if constexpr (W == 16) {
     st_shared_v4(dst, w[0], w[1], w[2], w[3]);
     st_shared_v4(dst + 128u, w[4], w[5], w[6], w[7]);
@@ -96,13 +95,13 @@ __device__ __forceinline__ void store_slab(unsigned dst, const unsigned (&X)[W][
 }
 
 template <int G, int W>
-__device__ __forceinline__ void store_group(unsigned dst, unsigned slab_bytes, const unsigned (&X)[W][4],
+__device__ __forceinline__ void store_group(unsigned dst, unsigned slab_bytes, const PairLanes (&P)[W / 2],
                                             const unsigned (&sg)[W / 2]) {
-  store_slab<G * kGroupSlabs + 0, W>(dst, X, sg);
-  store_slab<G * kGroupSlabs + 1, W>(dst + slab_bytes, X, sg);
-  store_slab<G * kGroupSlabs + 2, W>(dst + 2 * slab_bytes, X, sg);
-  store_slab<G * kGroupSlabs + 3, W>(dst + 3 * slab_bytes, X, sg);
-  store_slab<G * kGroupSlabs + 4, W>(dst + 4 * slab_bytes, X, sg);
+  store_slab<G * kGroupSlabs + 0, W>(dst, P, sg);
+  store_slab<G * kGroupSlabs + 1, W>(dst + slab_bytes, P, sg);
+  store_slab<G * kGroupSlabs + 2, W>(dst + 2 * slab_bytes, P, sg);
+  store_slab<G * kGroupSlabs + 3, W>(dst + 3 * slab_bytes, P, sg);
+  store_slab<G * kGroupSlabs + 4, W>(dst + 4 * slab_bytes, P, sg);
 }
 
 // x 2^(1127 - A) as a signed 128-bit integer, truncated toward zero.
@@ -244,16 +243,26 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     auto epilogue = [&](int64_t T, int64_t i) {
       const unsigned tb = tq + (unsigned)(i & 1) * kAccCols;
-      i128 h[4] = {0, 0, 0, 0};
+      // h = p0 2^70 + p1 2^35 + p2 with p_c = sum over the five diagonals
+      // d = 5c .. 5c + 4 of S_d 2^(7 (5c + 4 - d)) (|p_c| < 2^53: 64-bit chains)
+      long long p[3][4];
 #pragma unroll
       for (int d0 = 0; d0 < NS; d0 += 3) {
         unsigned v[3][4];
         tmem_ld3x4(tb + (unsigned)(d0 * kOut), tb + (unsigned)((d0 + 1) * kOut), tb + (unsigned)((d0 + 2) * kOut), v);
 #pragma unroll
-        for (int u = 0; u < 3; ++u)
+        for (int u = 0; u < 3; ++u) {
+          const int d = d0 + u, c = d / 5;
 #pragma unroll
-          for (int y = 0; y < 4; ++y) h[y] = (h[y] << 7) + (i128)__float2int_rn(__uint_as_float(v[u][y]) * 0x1p48f);
+          for (int y = 0; y < 4; ++y) {
+            const long long sd = __float2int_rn(__uint_as_float(v[u][y]) * 0x1p48f);
+            p[c][y] = (d % 5 == 0) ? sd : p[c][y] * 128 + sd;
+          }
+        }
       }
+      i128 h[4];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) h[y] = ((i128)p[0][y] << 70) + ((i128)p[1][y] << 35) + (i128)p[2][y];
       const int64_t grow = T * kRows + L;
       const int Ar = Arow[(i & 1) * kRows + L];
       const bool rbad = Rbad[(i & 1) * kRows + L] != 0;
@@ -293,12 +302,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         Arow[(i & 1) * kRows + r] = Ar;
         Rbad[(i & 1) * kRows + r] = e == 2047;
       }
-      unsigned X[W][4];
-#pragma unroll
-      for (int k = 0; k < W; ++k) xwords(v[k], Ar, X[k]);
+      PairLanes P[W / 2];  // the W values as interleaved pairs
       unsigned sg[W / 2];
 #pragma unroll
-      for (int m = 0; m < W / 2; ++m) sg[m] = ((hi32(v[2 * m]) >> 31) << 15) | (hi32(v[2 * m + 1]) & 0x80000000u);
+      for (int m = 0; m < W / 2; ++m) {
+        unsigned xa[4], xb[4];
+        xwords(v[2 * m], Ar, xa);
+        xwords(v[2 * m + 1], Ar, xb);
+        P[m] = pair_lanes(xa, xb);
+        sg[m] = ((hi32(v[2 * m]) >> 31) << 15) | (hi32(v[2 * m + 1]) & 0x80000000u);
+      }
 
       // three groups of five slabs into the alternating buffers
 #pragma unroll
@@ -306,9 +319,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int b = G & 1;
         if (G >= 2) mbar_wait(fb0 + 8u * b, (unsigned)((G - 2) >> 1) & 1u, &bad);  // MMAs of group G - 2 done
         const unsigned dst = adig_s + (unsigned)b * kGroupSlabs * SLAB_A + dofs;
-        if (g == 0) store_group<0, W>(dst, SLAB_A, X, sg);
-        else if (g == 1) store_group<1, W>(dst, SLAB_A, X, sg);
-        else store_group<2, W>(dst, SLAB_A, X, sg);
+        if (g == 0) store_group<0, W>(dst, SLAB_A, P, sg);
+        else if (g == 1) store_group<1, W>(dst, SLAB_A, P, sg);
+        else store_group<2, W>(dst, SLAB_A, P, sg);
         fence_proxy_async();
         mbar_arrive(rb0 + 8u * b);
       }
