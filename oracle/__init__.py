@@ -57,6 +57,7 @@ def lib():
             L.eoq_gram.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int]
             L.eoq_gram_f32.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int]
             L.eoq_project.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _p, _p, _int]
+            L.eoq_project_apply.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int, _p, _i64]
             L.eoq_cholesky.argtypes = [_int, _p, _p, _int, _p, _p, _int]
             L.eoq_cholesky.restype = _int
             L.eoq_triinv.argtypes = [_int, _p, _p, _int, _p, _p, _int]
@@ -142,6 +143,20 @@ def project(v, y, with_gram=True):
     lib().eoq_project(n, kv, _ptr(v), n, k, _ptr(y), n, _ptr(yt), n, _ptr(chi), _ptr(clo), kv,
                       _ptr(mhi), _ptr(mlo), k)
     return yt, (chi, clo), ((mhi, mlo) if with_gram else None)
+
+
+def project_apply(v, y, c_hi, c_lo=None):
+    """Yt = Y - V (C_hi + C_lo) in binary128, rounded once to FP64 (phase I with C given)."""
+    v = _f64(v)
+    y = _f64(y)
+    n, kv = v.shape
+    k = y.shape[1]
+    c_hi = _f64(c_hi)
+    c_lo = None if c_lo is None else _f64(c_lo)
+    assert c_hi.shape == (kv, k)
+    yt = np.zeros((n, k), order="F")
+    lib().eoq_project_apply(n, kv, _ptr(v), n, k, _ptr(y), n, _ptr(c_hi), _ptr(c_lo), kv, _ptr(yt), n)
+    return yt
 
 
 def cholesky(m_hi, m_lo=None):

@@ -15,6 +15,7 @@
  * Functions and the passage each follows:
  *   eoq_gram       M = X^T Y, the Gram product of phase II            (Sec. 4.2, M = Y~^T Y~)
  *   eoq_project    C = W^T X, Y~ = X - W C, then M = Y~^T Y~          (Sec. 4.2, phase I)
+ *   eoq_project_apply  Y~ = X - W C for a given double-double C          (Sec. 4.2, phase I)
  *   eoq_cholesky   M = R^T R, R upper with positive diagonal          (Sec. 4.2, CholQR)
  *   eoq_triinv     Z = R^{-1}                                         (Sec. 4.2, CholQR: Z = R^{-1})
  *   eoq_jacobi     M = U Lambda U^T by cyclic Jacobi rotations         (Sec. 4.2, SVQB eigendecomposition)
@@ -145,6 +146,23 @@ void eoq_project(int64_t n, int kv, const double* W, int64_t ldw, int k, const d
     }
   free(C);
   if (M_hi) eoq_gram(n, k, Yt, ldyt, k, NULL, 0, M_hi, M_lo, ldm);
+}
+
+/* The application step of phase I with C supplied (C = C_hi + C_lo, kv-by-k,
+ * C_lo may be NULL): Y~ = X - W C, every entry summed in binary128 and
+ * rounded once to FP64. */
+void eoq_project_apply(int64_t n, int kv, const double* W, int64_t ldw, int k, const double* X, int64_t ldx,
+                       const double* C_hi, const double* C_lo, int ldc, double* Yt, int64_t ldyt) {
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < n; ++r)
+    for (int j = 0; j < k; ++j) {
+      qreal s = (qreal)AT(X, ldx, r, j);
+      for (int i = 0; i < kv; ++i) {
+        const qreal c = (qreal)AT(C_hi, ldc, i, j) + (C_lo ? (qreal)AT(C_lo, ldc, i, j) : (qreal)0);
+        s -= (qreal)AT(W, ldw, r, i) * c;
+      }
+      AT(Yt, ldyt, r, j) = (double)s;
+    }
 }
 
 /* -------------------------------------------------- k-by-k factorizations */

@@ -119,6 +119,40 @@ def test_project_matches_exact_rational():
             assert abs(dd_fr(mhi, mlo, i, j) - ex_m[i][j]) <= F(2.0 ** -104) * (abs(ex_m[i][j]) + 1)
 
 
+def test_project_apply_matches_exact_rational():
+    g = synth.rng(22)
+    n, kv, k = 17, 4, 3
+    v = wide_range(g, n, kv)
+    y = wide_range(g, n, k)
+    chi = g.standard_normal((kv, k))
+    clo = chi * 2.0 ** -60 * g.standard_normal((kv, k))  # a genuine low part
+    yt = oracle.project_apply(v, y, chi, clo)
+    vs, ys = fr(v), fr(y)
+    for r in range(n):
+        for j in range(k):
+            ex = ys[r][j] - sum((vs[r][i] * dd_fr(chi, clo, i, j) for i in range(kv)), F(0))
+            # round-to-nearest of the exact value (float(Fraction) rounds correctly); binary128
+            # sums of four products move it by far less than the FP64 half-ulp
+            assert abs(F(float(yt[r, j])) - ex) <= abs(F(float(ex)) - ex) + F(2.0 ** -100) * (
+                abs(ys[r][j]) + sum((abs(vs[r][i] * dd_fr(chi, clo, i, j)) for i in range(kv)), F(0)))
+
+
+def test_project_apply_integer_inputs_and_consistency():
+    g = synth.rng(23)
+    n, kv, k = 300, 6, 4
+    vi = g.integers(-1000, 1001, size=(n, kv))
+    ci = g.integers(-1000, 1001, size=(kv, k))
+    yi = g.integers(-2 ** 40, 2 ** 40, size=(n, k))
+    yt = oracle.project_apply(vi.astype(np.float64), yi.astype(np.float64), ci.astype(np.float64))
+    assert np.array_equal(yt, (yi - vi @ ci).astype(np.float64))
+    # with the C that eoq_project computes, the result is eoq_project's own Y~
+    v = synth.orthonormal_basis(500, 5, 24)
+    y = synth.conditioned(500, 3, 1e4, 25)
+    yt_p, (chi, clo), _ = oracle.project(v, y)
+    yt_a = oracle.project_apply(v, y, chi, clo)
+    assert np.max(np.abs(yt_a - yt_p)) <= 2 * U64 * np.max(np.abs(y))
+
+
 def test_project_special_cases():
     v = synth.orthonormal_basis(200, 4, 7)
     a = synth.rng(8).standard_normal((4, 2))
