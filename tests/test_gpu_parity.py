@@ -285,6 +285,61 @@ def test_project_apply_equals_project(eo, ctx, engine):
     assert np.array_equal(host(m1[0]), host(m2[0])) and np.array_equal(host(m1[1]), host(m2[1]))
 
 
+@pytest.mark.parametrize("engine", ["int", "umma"])
+@pytest.mark.parametrize("n,kv,k", [(3001, 8, 5), (40_000, 16, 16), (20_011, 40, 16), (5000, 64, 7)])
+def test_project_apply_integer_inputs_are_exact(eo, ctx, monkeypatch, engine, n, kv, k):
+    """Integer V, C and Y: Y - V C is exact in FP64, so both row engines
+    (integer limbs, tensor-core digits) must return it bit for bit."""
+    monkeypatch.setenv("EO_DD_ROW_ENGINE", engine)
+    torch = torch_mod()
+    g = synth.rng(61)
+    vi = g.integers(-1000, 1001, size=(n, kv))
+    ci = g.integers(-1000, 1001, size=(kv, k))
+    yi = g.integers(-2 ** 40, 2 ** 40, size=(n, k))
+    c_hi = dev(ci.astype(np.float64))
+    c_lo = torch.zeros_like(c_hi)
+    out, _ = eo.project_apply(ctx, dev(vi.astype(np.float64)), dev(yi.astype(np.float64)), (c_hi, c_lo),
+                              prec=eo.DD, want_m=False)
+    exact = yi - vi @ ci  # |.| < 2^53: exact in int64 and in FP64
+    assert np.array_equal(host(out), exact.astype(np.float64))
+
+
+@pytest.mark.parametrize("n,kv,k", [(77_777, 64, 16), (10_001, 12, 16), (30_000, 33, 3)])
+def test_project_apply_row_engines_agree(eo, ctx, monkeypatch, n, kv, k):
+    """The tensor-core and integer row engines against the oracle on the same C."""
+    v = synth.orthonormal_basis(n, kv, 71)
+    y = synth.conditioned(n, k, 1e8, 72)
+    V, Y = dev(v), dev(y)
+    c = eo.gram(ctx, V, Y, prec=eo.DD)
+    outs = {}
+    for engine in ("int", "umma"):
+        monkeypatch.setenv("EO_DD_ROW_ENGINE", engine)
+        outs[engine] = host(eo.project_apply(ctx, V, Y, c, prec=eo.DD, want_m=False)[0])
+    ch, cl = host(c[0]), host(c[1])
+    ref = oracle.project_apply(v, y, ch, cl)
+    row_max = np.max(np.abs(v), axis=1)[:, None] * np.max(np.abs(ch), axis=0)[None, :]
+    tol = 2 * U * np.abs(ref) + kv * 2.0 ** -99 * row_max
+    for engine, out in outs.items():
+        assert np.all(np.abs(out - ref) <= tol), engine
+
+
+def test_cholqr_update_engines_agree(eo, ctx, monkeypatch):
+    """One DD CholQR pass with either row engine for Q = X R^-1 (k = 16)."""
+    n, k = 60_000, 16
+    x = synth.conditioned(n, k, 1e6, 81)
+    qs = {}
+    for engine in ("int", "umma"):
+        monkeypatch.setenv("EO_DD_ROW_ENGINE", engine)
+        d = dev(x)
+        eo.cholqr(ctx, d, passes=1, prec=eo.DD)
+        qs[engine] = host(d)
+    q_o, _, _ = oracle.cholqr(x, passes=1)
+    tol = cholqr_tol(n, k, 1e6)
+    for engine, q in qs.items():
+        assert np.max(np.abs(q - q_o)) <= tol, engine
+        assert oracle.orth_err(q)[0] <= 1e-14, engine
+
+
 def test_project_in_place_and_fp64(eo, ctx):
     n, kv, k = 12_345, 12, 3
     v = synth.orthonormal_basis(n, kv, 41)
