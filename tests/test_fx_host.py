@@ -210,4 +210,3 @@ def test_acc256_sums_exactly(fx):
             assert got == total
         else:
             assert got == (total >> ex.value) or got == -((-total) >> ex.value)
-
