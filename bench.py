@@ -172,6 +172,16 @@ class Clocks:
 DIGIT_PAIRS = 120  # FP16 digit-pair products per multiply-add of the compensated tensor-core kernels
 
 
+def gram_traffic(n, kv, k):
+    """DRAM bytes of one V^T Y launch of the tensor-core Gram kernel, from one
+    ncu capture at n = 1e6, kv = 64, k = 16 (dram__bytes_read.sum 640.1 MB,
+    dram__bytes_write.sum 3.6 MB of row-chunk partials); reads scale with
+    the rows, the partials do not.  None for other shapes."""
+    if (kv, k) != (64, 16):
+        return None
+    return 640.118528e6 * n / 1e6 + 3.632384e6
+
+
 def peak_tensor():
     """Sustained dense BF16 (= FP16) tensor peak in TFLOP/s: the kernels run inside a long step."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -283,7 +293,7 @@ def run_eo(a):
     gram_bytes = 8 * n * (kv + k)
     apply_bytes = 8 * n * (kv + 2 * k)
     roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "umma_gram_partial_kernel<16> (compensated V^T Y, 4e6 x 64 x 16)",
+            "traffic": gram_traffic(n, kv, k), "kernel": "umma_gram_partial_kernel<16> (compensated V^T Y, 4e6 x 64 x 16)",
             "peak_source": f"{tc_kind} FP16/BF16 dense sustained {tc_peak:.1f} TFLOP/s / {DIGIT_PAIRS} digit pairs "
                            "per multiply-add",
             "launch_ms": gram_ms, "hbm_achieved_gbs": gram_bytes / (gram_ms * 1e-3) / 1e9,
