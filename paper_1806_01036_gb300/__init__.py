@@ -85,6 +85,34 @@ def _mat(t, name, dtype=None):
     return t, int(t.shape[0]), int(t.shape[1]), int(max(ld, t.shape[0], 1))
 
 
+def _ld(t):
+    """Leading dimension of a column-major 2-D tensor (torch normalises the
+    stride of a one-column tensor, so that one is taken from its rows)."""
+    ld = t.stride(1) if t.shape[1] > 1 else max(1, t.shape[0])
+    return int(max(ld, t.shape[0], 1))
+
+
+def _dd_pair(pair, rows, cols, name, copy_ok):
+    """(hi, lo, ld) of a double-double pair of rows x cols column-major FP64
+    CUDA tensors (lo may be None) laid out with one leading dimension; an
+    input pair with different layouts is copied to one (copy_ok), an output
+    pair must already share one."""
+    import torch
+    hi, lo = pair
+    hi, r, c, _ = _mat(hi, name + "_hi", torch.float64)
+    if (r, c) != (rows, cols):
+        raise ValueError(f"{name}_hi must be {rows} x {cols}")
+    if lo is not None:
+        lo, r2, c2, _ = _mat(lo, name + "_lo", torch.float64)
+        if (r2, c2) != (rows, cols):
+            raise ValueError(f"{name}_lo must be {rows} x {cols}")
+        if _ld(lo) != _ld(hi):
+            if not copy_ok:
+                raise ValueError(f"{name}_hi and {name}_lo must share one leading dimension")
+            hi, lo = colmajor(hi.clone()), colmajor(lo.clone())
+    return hi, lo, _ld(hi)
+
+
 def _small(k1, k2, device):
     import torch
     hi = torch.zeros((k2, k1), dtype=torch.float64, device=device).t()
@@ -142,10 +170,10 @@ def gram(ctx: Context, X, Y=None, prec: int = DD, out=None):
             raise ValueError("X and Y must have the same number of rows")
     else:
         ky, ldy = kx, ldx
-    hi, lo = out if out is not None else _small(kx, ky, X.device)
+    hi, lo, ldg = _dd_pair(out if out is not None else _small(kx, ky, X.device), kx, ky, "G", False)
     ctx.set_stream()
     ctx.check(lib().eo_gram(ctx.h, n, kx, X.data_ptr(), ldx, ky, None if Y is None else Y.data_ptr(), ldy,
-                            hi.data_ptr(), None if lo is None else lo.data_ptr(), hi.stride(1) if kx > 0 else 1, prec))
+                            hi.data_ptr(), None if lo is None else lo.data_ptr(), ldg, prec))
     return hi, lo
 
 
@@ -163,7 +191,7 @@ def project(ctx: Context, V, Y, Yout=None, prec: int = DD, want_m: bool = True):
     mh, ml = _small(k, k, V.device) if want_m else (None, None)
     ctx.set_stream()
     ctx.check(lib().eo_project(ctx.h, n, kv, V.data_ptr(), ldv, k, Y.data_ptr(), ldy, Yout.data_ptr(), ldyo,
-                               ch.data_ptr(), cl.data_ptr(), ch.stride(1), None if mh is None else mh.data_ptr(),
+                               ch.data_ptr(), cl.data_ptr(), _ld(ch), None if mh is None else mh.data_ptr(),
                                None if ml is None else ml.data_ptr(), k, prec))
     return Yout, (ch, cl), ((mh, ml) if want_m else None)
 
@@ -175,14 +203,14 @@ def project_apply(ctx: Context, V, Y, C, Yout=None, prec: int = DD, want_m: bool
     Y, ny, k, ldy = _mat(Y, "Y", torch.float64)
     if ny != n:
         raise ValueError("V and Y must have the same number of rows")
-    ch, cl = C
+    ch, cl, ldc = _dd_pair(C, kv, k, "C", True)
     if Yout is None:
         Yout = colmajor(torch.empty((n, k), dtype=torch.float64, device=Y.device))
     Yout, _, _, ldyo = _mat(Yout, "Yout", torch.float64)
     mh, ml = _small(k, k, V.device) if want_m else (None, None)
     ctx.set_stream()
     ctx.check(lib().eo_project_apply(ctx.h, n, kv, V.data_ptr(), ldv, k, Y.data_ptr(), ldy, Yout.data_ptr(), ldyo,
-                                     ch.data_ptr(), None if cl is None else cl.data_ptr(), ch.stride(1),
+                                     ch.data_ptr(), None if cl is None else cl.data_ptr(), ldc,
                                      None if mh is None else mh.data_ptr(), None if ml is None else ml.data_ptr(),
                                      k, prec))
     return Yout, ((mh, ml) if want_m else None)
@@ -197,11 +225,10 @@ def cholqr(ctx: Context, X, passes: int = 1, prec: int = DD, M=None, info=None):
         info = torch.zeros(1, dtype=torch.int32, device=X.device)
     mh, ml, ldm = None, None, k
     if M is not None:
-        mh, ml = M
-        ldm = mh.stride(1)
+        mh, ml, ldm = _dd_pair(M, k, k, "M", True)
     ctx.set_stream()
     ctx.check(lib().eo_cholqr(ctx.h, n, k, X.data_ptr(), ldx, None if mh is None else mh.data_ptr(),
-                              None if ml is None else ml.data_ptr(), ldm, rh.data_ptr(), rl.data_ptr(), rh.stride(1),
+                              None if ml is None else ml.data_ptr(), ldm, rh.data_ptr(), rl.data_ptr(), _ld(rh),
                               int(passes), prec, info.data_ptr()))
     return rh, rl, info
 
@@ -215,11 +242,10 @@ def svqb(ctx: Context, X, passes: int = 1, prec: int = DD, tol: float = -1.0, M=
         rank = torch.zeros(1, dtype=torch.int32, device=X.device)
     mh, ml, ldm = None, None, k
     if M is not None:
-        mh, ml = M
-        ldm = mh.stride(1)
+        mh, ml, ldm = _dd_pair(M, k, k, "M", True)
     ctx.set_stream()
     ctx.check(lib().eo_svqb(ctx.h, n, k, X.data_ptr(), ldx, None if mh is None else mh.data_ptr(),
-                            None if ml is None else ml.data_ptr(), ldm, zh.data_ptr(), zl.data_ptr(), zh.stride(1),
+                            None if ml is None else ml.data_ptr(), ldm, zh.data_ptr(), zl.data_ptr(), _ld(zh),
                             float(tol), int(passes), prec, rank.data_ptr()))
     return zh, zl, rank
 
@@ -255,9 +281,9 @@ def gram_dd_noalloc(X, Y=None, out=None):
             raise ValueError("X and Y must have the same number of rows")
     else:
         ky, ldy = kx, ldx
-    hi, lo = out if out is not None else _small(kx, ky, X.device)
+    hi, lo, ldg = _dd_pair(out if out is not None else _small(kx, ky, X.device), kx, ky, "G", False)
     st = lib().eo_gram_dd_noalloc(n, kx, X.data_ptr(), ldx, ky, None if Y is None else Y.data_ptr(), ldy,
-                                  hi.data_ptr(), None if lo is None else lo.data_ptr(), hi.stride(1),
+                                  hi.data_ptr(), None if lo is None else lo.data_ptr(), ldg,
                                   C.c_void_p(torch.cuda.current_stream(X.device).cuda_stream))
     if st != OK:
         raise EoError(st, "eo_gram_dd_noalloc failed")

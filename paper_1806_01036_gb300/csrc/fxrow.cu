@@ -25,11 +25,14 @@ constexpr int JG = 4;  // output columns per thread
 
 // Limbs of the columns of a double-double matrix B (rows x cols, leading
 // dimension ldb, hi/lo arrays), each column aligned to its largest exponent:
-// Bl[j * rows + i], Eb[j].
+// Bl[j * rows + i], Eb[j] (>= 2048 when the column holds an Inf or NaN).
 __device__ void load_small_limbs(int rows, int cols, const double* Bh, const double* Bl_, int ldb, int4* Bl, int* Eb) {
   for (int j = threadIdx.x; j < cols; j += blockDim.x) {
     int e = 0;
-    for (int i = 0; i < rows; ++i) e = max(e, align_exp(Bh[(size_t)j * ldb + i]));
+    for (int i = 0; i < rows; ++i) {
+      e = max(e, align_exp(Bh[(size_t)j * ldb + i]));
+      if (Bl_ && align_exp(Bl_[(size_t)j * ldb + i]) == 2047) e = 2047;
+    }
     Eb[j] = e + 1;  // one binade of headroom: |h + l| may round up past the largest h
   }
   __syncthreads();
@@ -112,6 +115,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             out = w_to_double(w, S);
           else
             out = sub_round(Yin[(size_t)j * ldyin + r], w, S);
+          if (Er[my_r] >= 2047 || Eb[j] >= 2048) out = __longlong_as_double(0x7ff8000000000000ll);  // Inf/NaN input
           Out[(size_t)j * ldo + r] = out;
         }
       }

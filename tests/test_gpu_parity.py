@@ -323,6 +323,63 @@ def test_project_apply_row_engines_agree(eo, ctx, monkeypatch, n, kv, k):
         assert np.all(np.abs(out - ref) <= tol), engine
 
 
+def _random_dd(g, rows, cols):
+    hi = np.asfortranarray(g.standard_normal((rows, cols)))
+    lo = np.asfortranarray(hi * 2.0 ** -55 * g.uniform(-1, 1, (rows, cols)))
+    return hi, lo
+
+
+@pytest.mark.parametrize("engine", ["int", "umma"])
+@pytest.mark.parametrize("n,kv,k", [(1, 64, 16), (127, 16, 1), (129, 17, 7), (255, 32, 16), (1000, 33, 2),
+                                    (4097, 48, 16), (2049, 1, 16), (3333, 64, 5)])
+def test_project_apply_shapes_against_oracle(eo, ctx, monkeypatch, engine, n, kv, k):
+    """Row tails, every tile width of the tensor-core row engine (kv <= 16, 32,
+    64) and odd output counts, with a genuine double-double C."""
+    monkeypatch.setenv("EO_DD_ROW_ENGINE", engine)
+    torch = torch_mod()
+    g = synth.rng(90 + kv + k)
+    v = synth.gaussian(n, kv, 91 + kv)
+    y = synth.gaussian(n, k, 92 + k) * 1e-3
+    ch, cl = _random_dd(g, kv, k)
+    out, _ = eo.project_apply(ctx, dev(v), dev(y), (dev(ch), dev(cl)), prec=eo.DD, want_m=False)
+    ref = oracle.project_apply(v, y, ch, cl)
+    row_max = np.max(np.abs(v), axis=1)[:, None] * np.max(np.abs(ch) + np.abs(cl), axis=0)[None, :]
+    assert np.all(np.abs(host(out) - ref) <= 2 * U * np.abs(ref) + kv * 2.0 ** -99 * row_max)
+
+
+@pytest.mark.parametrize("engine", ["int", "umma"])
+def test_project_apply_nonfinite_and_padding(eo, ctx, monkeypatch, engine):
+    """NaN in a row of V poisons that row only; NaN in C poisons its column;
+    padding rows of V and Y (leading dimension > n, filled with NaN) are not read."""
+    monkeypatch.setenv("EO_DD_ROW_ENGINE", engine)
+    torch = torch_mod()
+    n, kv, k, ld = 1500, 24, 6, 1531
+    g = synth.rng(95)
+    v = synth.gaussian(n, kv, 96)
+    y = synth.gaussian(n, k, 97)
+    ch, cl = _random_dd(g, kv, k)
+
+    def padded(a):
+        buf = synth.with_ld(a, ld, fill=np.nan)
+        return torch.from_numpy(np.ascontiguousarray(buf.T)).cuda().t()[: a.shape[0], :]
+
+    out, _ = eo.project_apply(ctx, padded(v), padded(y), (dev(ch), dev(cl)), prec=eo.DD, want_m=False)
+    assert np.all(np.isfinite(host(out)))
+    ref = oracle.project_apply(v, y, ch, cl)
+    row_max = np.max(np.abs(v), axis=1)[:, None] * np.max(np.abs(ch) + np.abs(cl), axis=0)[None, :]
+    assert np.all(np.abs(host(out) - ref) <= 2 * U * np.abs(ref) + kv * 2.0 ** -99 * row_max)
+    v2 = v.copy()
+    v2[700, 3] = np.nan
+    ch2 = ch.copy()
+    ch2[5, 4] = np.inf
+    o2 = host(eo.project_apply(ctx, dev(v2), dev(y), (dev(ch2), dev(cl)), prec=eo.DD, want_m=False)[0])
+    assert np.all(np.isnan(o2[700, :])) and np.all(np.isnan(o2[:, 4]))
+    rest = np.ones_like(o2, dtype=bool)
+    rest[700, :] = False
+    rest[:, 4] = False
+    assert np.all(np.isfinite(o2[rest]))
+
+
 def test_cholqr_update_engines_agree(eo, ctx, monkeypatch):
     """One DD CholQR pass with either row engine for Q = X R^-1 (k = 16)."""
     n, k = 60_000, 16
