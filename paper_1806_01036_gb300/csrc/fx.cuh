@@ -271,13 +271,41 @@ FX_HD Rounded round53(u128 u, int S) {
   return r;
 }
 
-// Nearest double to w * 2^S.
+// Nearest double to w * 2^S (ties to even).  The top 64 bits of |w| and a
+// sticky bit for the rest decide the rounding; results outside the normal
+// range take the general path.
 FX_HD double w_to_double(i128 w, int S) {
   if (w == 0) return 0.0;
   const bool neg = w < 0;
   const u128 u = neg ? (u128)(-w) : (u128)w;
-  const Rounded r = round53(u, S);
-  return make_double(neg, r.m, r.e2);
+  const unsigned long long uh = (unsigned long long)(u >> 64), ul = (unsigned long long)u;
+  int lz;
+  unsigned long long t;
+  bool sticky;
+  if (uh) {
+    lz = clz64(uh);
+    t = lz ? (uh << lz) | (ul >> (64 - lz)) : uh;
+    sticky = (ul << lz) != 0;
+  } else {
+    lz = 64 + clz64(ul);
+    t = ul << (lz - 64);
+    sticky = false;
+  }
+  // t holds bits p .. p - 63 of u, p = 127 - lz its top bit: m = bits p .. p - 52
+  unsigned long long m = t >> 11;
+  const unsigned long long rb = t & 0x7ffull;
+  if (rb > 0x400ull || (rb == 0x400ull && (sticky || (m & 1ull)))) ++m;
+  int e2 = S + (127 - lz) - 52;
+  if (m >> 53) {
+    m >>= 1;
+    ++e2;
+  }
+  const int be = e2 + 52 + 1023;
+  if (be < 1 || be > 2046) {
+    const Rounded r = round53(u, S);
+    return make_double(neg, r.m, r.e2);
+  }
+  return from_bits(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1)));
 }
 
 // Double-double (hi, lo) nearest to w * 2^S: hi = RN(w 2^S), lo = RN(w 2^S - hi).

@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(kThreads) chol_small_kernel(int k, const doubl
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dd* A = reinterpret_cast<dd*>(smem_raw);  // A(i,j) = A[j*k+i]; R overwrites the upper triangle
   dd* Z = A + k * k;
+  dd* Tb = Z + k * k;  // products B C^{-1} of the block inversion
   __shared__ int flag;
   __shared__ dd inv;
   const int tid = threadIdx.x;
@@ -114,16 +115,31 @@ __global__ void __launch_bounds__(kThreads) chol_small_kernel(int k, const doubl
     }
     return;
   }
-  // Z = R^{-1}: diagonal first, then rows i = k-2 .. 0, all columns j > i at once.
+  // Z = R^{-1} by doubling blocks: with R = [P B; 0 Q] and P^{-1}, Q^{-1}
+  // known, the off-diagonal block of R^{-1} is -P^{-1} (B Q^{-1}).  Every
+  // level is two products of independent inner products of length <= b, so
+  // the dependent chain is 2 (1 + 2 + 4 + ...) multiply-adds, not ~k^2/2.
   for (int t = tid; t < k * k; t += kThreads) Z[t] = dd{0.0, 0.0};
   __syncthreads();
   for (int i = tid; i < k; i += kThreads) Z[i * k + i] = A_::div(dd{1.0, 0.0}, A[i * k + i]);
   __syncthreads();
-  for (int i = k - 2; i >= 0; --i) {
-    for (int j = i + 1 + tid; j < k; j += kThreads) {
-      dd s = dd{0.0, 0.0};
-      for (int l = i + 1; l <= j; ++l) s = A_::fma(A[l * k + i], Z[j * k + l], s);
-      Z[j * k + i] = A_::mul(dd_neg(s), Z[i * k + i]);
+  for (int b = 1; b < k; b *= 2) {
+    // pairs (i, j): i in a block's upper half [o, o + b), j in its lower half [o + b, e)
+    const int nblk = (k + 2 * b - 1) / (2 * b);
+    for (int t = tid; t < nblk * b * b; t += kThreads) {  // Tb(i, j) = sum_{l = o+b}^{j} B(i, l) Q^{-1}(l, j)
+      const int blk = t / (b * b), i = blk * 2 * b + (t % (b * b)) % b, j = blk * 2 * b + b + (t % (b * b)) / b;
+      if (j >= k) continue;
+      dd acc = dd{0.0, 0.0};
+      for (int l = blk * 2 * b + b; l <= j; ++l) acc = A_::fma(A[l * k + i], Z[j * k + l], acc);
+      Tb[j * k + i] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < nblk * b * b; t += kThreads) {  // Z(i, j) = -sum_{l = i}^{o+b-1} P^{-1}(i, l) Tb(l, j)
+      const int blk = t / (b * b), i = blk * 2 * b + (t % (b * b)) % b, j = blk * 2 * b + b + (t % (b * b)) / b;
+      if (j >= k) continue;
+      dd acc = dd{0.0, 0.0};
+      for (int l = i; l < blk * 2 * b + b; ++l) acc = A_::fma(Z[l * k + i], Tb[j * k + l], acc);
+      Z[j * k + i] = dd_neg(acc);
     }
     __syncthreads();
   }
@@ -402,7 +418,7 @@ cudaError_t launch_status_init(DevStatus* s, int k, cudaStream_t st) {
 cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
                               double* R_hi, double* R_lo, int ldr, DevStatus* s, SmallGates g, int pass, int passes,
                               int* info_user, cudaStream_t st) {
-  const size_t smem = 2 * (size_t)k * k * sizeof(dd);
+  const size_t smem = 3 * (size_t)k * k * sizeof(dd);
   cudaError_t e;
   if (mode == MODE_DD) {
     e = cudaFuncSetAttribute(chol_small_kernel<MODE_DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -171,6 +171,33 @@ def test_w_to_double_ties_to_even(fx):
         assert fx.fxs_w_to_double(lo_, hi_, 0) == want
 
 
+def test_w_to_double_rounds_to_nearest(fx):
+    """Random 128-bit integers (and halfway cases) against exact rational
+    rounding, across the normal range and its edges (subnormal, overflow)."""
+    g = np.random.default_rng(7)
+    cases = []
+    for _ in range(4000):
+        bits = int(g.integers(1, 127))
+        w = (int(g.integers(0, 2 ** 62)) << 64 | int(g.integers(0, 2 ** 62)) << 2) % (1 << bits)
+        if g.random() < 0.25 and bits > 60:  # a tie: the bit right below the 53rd set, nothing below it
+            top = bits - 53
+            w = (w >> top << top) | (1 << (top - 1))
+        if g.random() < 0.5:
+            w = -w
+        S = int(g.integers(-1200, 900)) if g.random() < 0.2 else int(g.integers(-300, 100))
+        cases.append((w, S))
+    cases += [(1, -1074), (3, -1075), ((1 << 53) - 1, 971), ((1 << 53) + 1, 971), (-(1 << 120) - 1, -30)]
+    for w, S in cases:
+        lo_, hi_ = split_w(w)
+        got = fx.fxs_w_to_double(lo_, hi_, S)
+        exact = F(w) * F(2) ** S
+        try:
+            want = rn(exact)
+        except OverflowError:  # beyond the largest double: infinity, as IEEE rounding gives
+            want = float("inf") if exact > 0 else float("-inf")
+        assert got == want, (w, S)
+
+
 def test_sub_round_is_correctly_rounded(fx):
     g = np.random.default_rng(5)
     for _ in range(3000):
