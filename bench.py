@@ -50,9 +50,12 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU-oracle sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["project", "iterated"], default="project",
+    ap.add_argument("--workload", choices=["project", "iterated", "batched"], default="project",
                     help="project: the default line; iterated: the iterated two-phase algorithm on the "
-                         "runtime-figure shapes (n = 8e6 unless --n is given)")
+                         "runtime-figure shapes (n = 8e6 unless --n is given); batched: many SVQB blocks of "
+                         "uneven n and k in one graph launch")
+    ap.add_argument("--blocks", type=int, default=512, help="blocks of the batched workload")
+    ap.add_argument("--branches", type=int, default=0, help="graph branches of the batched workload (0 = auto)")
     return ap.parse_args()
 
 
@@ -498,12 +501,150 @@ def run_iterated(a):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------- batched SVQB
+
+BATCH_METRIC = "batched SVQB: HBM GB/s and blocks/s of one CUDA-graph launch, DD vs plain FP64; p50/p99"
+
+
+def run_batched(a):
+    """Many blocks of uneven n and k in one graph launch (eo_batch_*): 512
+    blocks with n log-uniform in [1e4, 2e6], k uniform in {4, 8, 16, 32},
+    kappa log-uniform in [1e2, 1e10]; SVQB in the compensated mode with the
+    automatic second pass, launch shapes from the autotuner.  Blocks are
+    X = G diag(sigma) Q^T with G Gaussian / sqrt(n) (its condition number is
+    within (1 + sqrt(k/n)) / (1 - sqrt(k/n)) <= 1.13 of 1), sigma log-spaced
+    1 .. 1/kappa and Q a Haar k x k rotation, generated on the GPU from a
+    seeded generator.  A step restores the blocks from a pristine copy
+    (untimed) and runs the graph once (timed with CUDA events)."""
+    import torch
+    import paper_1806_01036_gb300 as eo
+
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    nblk = a.blocks
+    rng = np.random.default_rng(20180604 + 3 + 1000 * rank)
+    ns = np.exp(rng.uniform(np.log(1e4), np.log(2e6), nblk)).astype(np.int64)
+    ks = rng.choice([4, 8, 16, 32], nblk)
+    kappas = np.exp(rng.uniform(np.log(1e2), np.log(1e10), nblk))
+    g = torch.Generator(device=dev)
+    g.manual_seed(20180604 + 3 + 1000 * rank)
+    f64 = torch.float64
+    X, X0 = [], []
+    for n, k, kap in zip(ns, ks, kappas):
+        n, k = int(n), int(k)
+        q, r = torch.linalg.qr(torch.randn(k, k, dtype=f64, device=dev, generator=g))
+        q = q * torch.sign(torch.diagonal(r))[None, :]
+        s = torch.logspace(0.0, -float(np.log10(kap)), k, dtype=f64, device=dev)
+        x0 = (torch.randn(n, k, dtype=f64, device=dev, generator=g) * (s / float(np.sqrt(n)))[None, :]) @ q.t()
+        x0 = x0.t().contiguous().t()
+        X0.append(x0)
+        X.append(torch.empty_like(x0.t()).t())
+    ctx = eo.Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def restore():
+        for x, x0 in zip(X, X0):
+            x.copy_(x0)
+
+    def make(prec, tune, branches=0):
+        t0 = time.perf_counter()
+        b = eo.Batch(ctx, X, method=eo.BATCH_SVQB, passes=0, prec=prec, tune=tune, branches=branches)
+        return b, time.perf_counter() - t0
+
+    def timed(run, steps):
+        times = []
+        for _ in range(steps):
+            restore()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times
+
+    bt, create_s = make(eo.DD, True, a.branches)
+    for _ in range(max(3, a.warmup)):
+        restore()
+        bt.run()
+    torch.cuda.synchronize()
+    passes = bt.passes()
+    nbytes = int(sum(24 * int(n) * int(k) * p for n, k, p in zip(ns, ks, passes)))
+    # accuracy of the last run: max over blocks of ||Q^T Q - I||_2 (library DD Gram)
+    orth = 0.0
+    for x, k in zip(X, ks):
+        gh, gl = eo.gram(ctx, x, prec=eo.DD)
+        e = (gh.cpu().numpy() - np.eye(int(k))) + gl.cpu().numpy()
+        orth = max(orth, float(np.linalg.norm(e, 2)))
+    ranks = bt.out.cpu().numpy()
+
+    torch.cuda.synchronize()
+    l0 = ctx.launches()
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_batched_rank{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/eo_clocks_b_{os.getpid()}.csv", local)
+    with clk:
+        times = timed(bt.run, a.steps)
+    launches = (ctx.launches() - l0)
+    ms = statistics.mean(times)
+    value = weak_scaling_value(ws, nbytes, max_over_ranks(ms, dev))
+
+    # comparators on the same blocks: untuned shapes, one call per block on
+    # one stream (no graph), and plain FP64 in the same graph form
+    bu, _ = make(eo.DD, False, a.branches)
+    untuned = statistics.mean(timed(bu.run, max(1, a.steps // 2)))
+    bu.close()
+
+    def sequential():
+        for x in X:
+            eo.svqb(ctx, x, passes=0, prec=eo.DD)
+
+    seq = statistics.mean(timed(sequential, max(1, a.steps // 2)))
+    bf, _ = make(eo.FP64, False, a.branches)
+    fp64 = statistics.mean(timed(bf.run, max(1, a.steps // 2)))
+    orth_fp64 = 0.0
+    for x, k in zip(X, ks):
+        gh, gl = eo.gram(ctx, x, prec=eo.DD)
+        e = (gh.cpu().numpy() - np.eye(int(k))) + gl.cpu().numpy()
+        orth_fp64 = max(orth_fp64, float(np.linalg.norm(e, 2))) if np.all(np.isfinite(e)) else float("inf")
+    bf.close()
+    hbm_peak, peak_kind = peak_hbm()
+    tiles = {}
+    for i in range(nblk):
+        key = f"k{int(ks[i])}_n2^{int(np.log2(ns[i]))}"
+        tiles[key] = bt.tile(i)
+    out = {
+        "metric": BATCH_METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded on the GPU: Gaussian x diag(sigma) x Haar rotation)",
+        "config": {"workload": f"batched SVQB: {nblk} blocks, n log-uniform [1e4, 2e6], k in 4/8/16/32, "
+                               "kappa log-uniform [1e2, 1e10], DD with automatic second pass, one graph launch",
+                   "blocks": nblk, "rows_total": int(ns.sum()), "branches": bt.branches(),
+                   "two_pass_blocks": int(sum(p == 2 for p in passes)),
+                   "l2": "blocks total %.1f GB, larger than L2; no flush" % (8 * float(np.sum(ns * ks)) / 1e9)},
+        "blocks_per_s": ws * nblk / (ms * 1e-3), "p50_ms": float(np.percentile(times, 50)),
+        "p99_ms": float(np.percentile(times, 99)), "orth_err_max": orth, "min_rank_over_k": float(np.min(ranks / ks)),
+        "bytes_per_step": nbytes,
+        "roofline": {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": nbytes / (ms * 1e-3) / 1e9 / hbm_peak, "traffic": None,
+                     "peak_source": peak_kind, "kernel": "whole graph (Gram + eigensolve + update per block)"},
+        "gpu_launches": launches, "graph_kernels": bt.kernels(), "create_s": create_s,
+        "comparators": {"untuned_ms": untuned, "sequential_calls_ms": seq, "fp64_graph_ms": fp64,
+                        "fp64_orth_err_max": orth_fp64},
+        "tiles": tiles, "clocks": clk.summary(),
+    }
+    bt.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "iterated":
         run_iterated(a)
+    elif a.workload == "batched":
+        run_batched(a)
     else:
         run_eo(a)
 

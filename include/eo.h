@@ -190,6 +190,81 @@ EO_API eo_status eo_orthogonalize(eo_ctx* ctx, int64_t n, int kv, const double* 
                                   int* rank_dev);
 
 /*
+ * Batched orthogonalization (no counterpart in the paper, whose solvers
+ * orthogonalize one block at a time): many independent blocks of uneven n and
+ * k, each orthogonalized by the kernels of one eo_svqb (EO_BATCH_SVQB) or
+ * eo_cholqr (EO_BATCH_CHOLQR) call with the same tol, passes and prec,
+ * captured once into a CUDA graph and run by one graph launch.  With the
+ * default launch shapes (EO_BATCH_NO_TUNE, and always outside EO_DD) every
+ * block's result is bitwise that of the single call.  Tuned shapes split a
+ * block's rows into other chunks; each chunk aligns its sums to its own
+ * exponents, so the results move within the EO_DD error bound (last bits of
+ * the low parts) and are again bitwise reproducible for that shape.  A
+ * block's shape depends only on its own (k, n) and the context's tuned caps,
+ * never on the other blocks: a result is the same alone and in any mix.
+ *
+ * eo_batch_create checks the blocks, picks the launch shapes, spreads the
+ * blocks over `branches` concurrent graph branches (0 = min(nblocks, 16);
+ * at most 64), allocates one device workspace per block (about 200 KB) and
+ * captures the graph.  It launches nothing on the context's stream, but in
+ * EO_DD it may run the autotuner first (below), which launches and
+ * synchronizes on a private stream.  The blocks' pointers are captured: the
+ * batch must be destroyed before any block's memory is freed.
+ *   blocks: host array of nblocks descriptors (read during the call only).
+ *   out_dev: optional device int[nblocks]: per block the rank (SVQB) or the
+ *   info (CholQR) of the single call.
+ *   flags: EO_BATCH_NO_TUNE = default launch shapes, no autotuning;
+ *   EO_BATCH_CHAINS = each block's whole sequence on its branch (default:
+ *   by phase -- the blocks' Gram matrices of a pass on the branches, then all
+ *   their k-by-k factorizations in one launch of one CTA per block, then the
+ *   updates on the branches; the factorizations, which run on one SM each,
+ *   then spread over every SM).  Both give the same results.
+ * eo_batch_run enqueues one launch of the graph on the context's stream; it
+ * may be called any number of times (each run orthogonalizes the blocks'
+ * current contents in place).  eo_batch_destroy waits for the context's
+ * stream and frees the batch.
+ *
+ * Autotuner (EO_DD): the Gram and update kernels of a block run with a cap on
+ * their CTAs, picked per (k, floor(log2 n)) for n >= 4096 by timing both
+ * kernels on a synthetic n-by-k buffer for a coarse set of caps and then
+ * around the best, keeping the cap with the least SM time (CTAs x duration)
+ * and preferring more CTAs within 5 %.  Tuned caps are kept in the context;
+ * eo_tune_cache(ctx, path) also loads them from, and saves new ones to, a
+ * text file (one line per key, tagged with the device name; NULL = memory
+ * only).
+ */
+typedef struct eo_block {
+  int64_t n;      /* rows (>= 0)                                             */
+  int k;          /* columns, 1..EO_KMAX                                     */
+  void* X;        /* device, column-major n-by-k (float* in EO_F32), in place */
+  int64_t ldx;    /* >= max(1, n)                                            */
+  double* Z_hi;   /* optional k-by-k output: Z (SVQB) or R (CholQR)          */
+  double* Z_lo;   /* optional low part                                       */
+  int ldz;        /* >= k when Z_hi or Z_lo is given                         */
+} eo_block;
+
+typedef enum { EO_BATCH_SVQB = 0, EO_BATCH_CHOLQR = 1 } eo_batch_method;
+#define EO_BATCH_NO_TUNE 1
+#define EO_BATCH_CHAINS 2
+
+typedef struct eo_batch eo_batch;
+
+EO_API eo_status eo_tune_cache(eo_ctx* ctx, const char* path);
+EO_API eo_status eo_batch_create(eo_ctx* ctx, int nblocks, const eo_block* blocks, eo_batch_method method,
+                                 double tol, int passes, eo_prec prec, int* out_dev, int branches, int flags,
+                                 eo_batch** batch);
+EO_API eo_status eo_batch_run(eo_batch* batch);
+EO_API eo_status eo_batch_destroy(eo_batch* batch);
+/* CTA caps chosen for a block (0 = default shape). */
+EO_API eo_status eo_batch_tile(const eo_batch* batch, int block, int* gram_ctas, int* row_ctas);
+/* Passes each block took in the last run (1 or 2) into host int[nblocks];
+ * waits for the context's stream. */
+EO_API eo_status eo_batch_passes(eo_batch* batch, int* passes_host);
+/* Kernels one eo_batch_run launches (-1 for NULL), and the graph's branches. */
+EO_API int64_t eo_batch_kernels(const eo_batch* batch);
+EO_API int eo_batch_branches(const eo_batch* batch);
+
+/*
  * Allocation-free compensated Gram product (no counterpart in the paper).
  *
  * eo_gram_dd_noalloc computes the same G = X^T Y as eo_gram(..., EO_DD) for

@@ -25,6 +25,15 @@ _lib = None
 _p, _i64, _int, _dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
 
 
+class Block(C.Structure):
+    """eo_block: one block of a batch (include/eo.h)."""
+    _fields_ = [("n", _i64), ("k", _int), ("X", _p), ("ldx", _i64), ("Z_hi", _p), ("Z_lo", _p), ("ldz", _int)]
+
+
+BATCH_SVQB, BATCH_CHOLQR = 0, 1
+BATCH_NO_TUNE, BATCH_CHAINS = 1, 2
+
+
 class EoError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"eo status {status}: {msg}")
@@ -59,8 +68,20 @@ def lib():
         L.eo_cholqr.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _int, _int, _p]
         L.eo_svqb.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _dbl, _int, _int, _p]
         L.eo_gram_dd_noalloc.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int, _p]
+        L.eo_tune_cache.argtypes = [_p, C.c_char_p]
+        L.eo_batch_create.argtypes = [_p, _int, C.POINTER(Block), _int, _dbl, _int, _int, _p, _int, _int,
+                                      C.POINTER(_p)]
+        L.eo_batch_run.argtypes = [_p]
+        L.eo_batch_destroy.argtypes = [_p]
+        L.eo_batch_tile.argtypes = [_p, _int, C.POINTER(_int), C.POINTER(_int)]
+        L.eo_batch_passes.argtypes = [_p, _p]
+        L.eo_batch_kernels.argtypes = [_p]
+        L.eo_batch_kernels.restype = C.c_int64
+        L.eo_batch_branches.argtypes = [_p]
+        L.eo_batch_branches.restype = _int
         for f in ("eo_create", "eo_destroy", "eo_set_stream", "eo_gram", "eo_project", "eo_project_apply",
-                  "eo_cholqr", "eo_svqb", "eo_orthogonalize", "eo_gram_dd_noalloc"):
+                  "eo_cholqr", "eo_svqb", "eo_orthogonalize", "eo_gram_dd_noalloc", "eo_tune_cache",
+                  "eo_batch_create", "eo_batch_run", "eo_batch_destroy", "eo_batch_tile", "eo_batch_passes"):
             getattr(L, f).restype = _int
         _lib = L
     return _lib
@@ -154,6 +175,10 @@ class Context:
     def check(self, st: int):
         if st != OK:
             raise EoError(st, lib().eo_last_error(self.h).decode())
+
+    def tune_cache(self, path=None):
+        """Load (and later save) tuned launch shapes from a text file (eo_tune_cache)."""
+        self.check(lib().eo_tune_cache(self.h, None if path is None else os.fsencode(path)))
 
 
 def _dtype(prec):
@@ -288,3 +313,78 @@ def gram_dd_noalloc(X, Y=None, out=None):
     if st != OK:
         raise EoError(st, "eo_gram_dd_noalloc failed")
     return hi, lo
+
+
+class Batch:
+    """Many blocks orthogonalized by one CUDA graph launch (eo_batch_create).
+
+    blocks: list of column-major CUDA tensors X_b (n_b x k_b; FP64, or FP32
+    with prec F32), orthogonalized in place by each run().  method:
+    BATCH_SVQB or BATCH_CHOLQR.  want_z: also return each block's Z (SVQB)
+    or R (CholQR) as a (hi, lo) pair.  chains: each block's whole sequence on
+    its branch instead of the phase order.  out: device int32 tensor with one
+    rank (SVQB) or info (CholQR) per block.  The tensors must outlive the
+    batch (the graph holds their addresses)."""
+
+    def __init__(self, ctx: Context, blocks, method: int = BATCH_SVQB, passes: int = 0, prec: int = DD,
+                 tol: float = -1.0, branches: int = 0, tune: bool = True, want_z: bool = False,
+                 chains: bool = False):
+        import torch
+        if not blocks:
+            raise ValueError("a batch needs at least one block")
+        self.ctx = ctx
+        self.blocks = []
+        self.z = []
+        desc = (Block * len(blocks))()
+        for i, X in enumerate(blocks):
+            X, n, k, ldx = _mat(X, f"blocks[{i}]", _dtype(prec))
+            self.blocks.append(X)
+            zh = zl = None
+            if want_z:
+                zh, zl = _small(k, k, X.device)
+                self.z.append((zh, zl))
+            desc[i] = Block(n, k, X.data_ptr(), ldx, None if zh is None else zh.data_ptr(),
+                            None if zl is None else zl.data_ptr(), k)
+        self.out = torch.zeros(len(blocks), dtype=torch.int32, device=self.blocks[0].device)
+        h = _p()
+        ctx.check(lib().eo_batch_create(ctx.h, len(blocks), desc, int(method), float(tol), int(passes), int(prec),
+                                        self.out.data_ptr(), int(branches),
+                                        (0 if tune else BATCH_NO_TUNE) | (BATCH_CHAINS if chains else 0),
+                                        C.byref(h)))
+        self.h = h
+
+    def run(self):
+        """Enqueue one graph launch on torch's current stream."""
+        self.ctx.set_stream()
+        self.ctx.check(lib().eo_batch_run(self.h))
+
+    def tile(self, i: int):
+        """(gram_ctas, row_ctas) caps chosen for block i (0 = default)."""
+        g, r = _int(), _int()
+        self.ctx.check(lib().eo_batch_tile(self.h, int(i), C.byref(g), C.byref(r)))
+        return g.value, r.value
+
+    def passes(self):
+        """Passes each block took in the last run (list of 1 or 2); waits for the stream."""
+        out = (_int * len(self.blocks))()
+        self.ctx.set_stream()
+        self.ctx.check(lib().eo_batch_passes(self.h, C.cast(out, _p)))
+        return list(out)
+
+    def kernels(self) -> int:
+        return int(lib().eo_batch_kernels(self.h))
+
+    def branches(self) -> int:
+        return int(lib().eo_batch_branches(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.set_stream()
+            lib().eo_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

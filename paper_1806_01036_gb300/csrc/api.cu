@@ -8,43 +8,11 @@
 #include <cstring>
 #include <string>
 
-#include "common.cuh"
-
-struct eo_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  void* scratch = nullptr;
-  size_t scratch_bytes = 0;
-  uint64_t launches = 0;
-  std::string err;
-};
+#include "ctx.cuh"
 
 namespace eo {
-namespace {
 
-constexpr size_t kAlign = 256;
-constexpr uint64_t kGramLaunches = 2;  // partial sums + fixed-order reduction
-constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-
-// Scratch layout: [DevStatus][SmallWs][C hi/lo (KMAX x KMAX)][partials ...]
-constexpr size_t kOffStatus = 0;
-constexpr size_t kOffWs = align_up(sizeof(DevStatus));
-constexpr size_t kOffC = kOffWs + align_up(sizeof(SmallWs));
-constexpr size_t kOffParts = kOffC + align_up(2 * sizeof(double) * KMAX * KMAX);
-
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
-eo_status fail(eo_ctx* c, eo_status s, const char* fmt, const char* a = "", long long b = 0) {
+eo_status fail(eo_ctx* c, eo_status s, const char* fmt, const char* a, long long b) {
   if (c) {
     char buf[512];
     snprintf(buf, sizeof buf, fmt, a, b);
@@ -58,6 +26,37 @@ eo_status cuda_fail(eo_ctx* c, const char* where, cudaError_t e) {
   cudaGetLastError();  // a failed attribute call or launch must not surface in the next call
   return EO_ECUDA;
 }
+
+bool valid_prec(int p) { return p == EO_FP64 || p == EO_DD || p == EO_F32 || p == EO_DD_EFT; }
+
+int dyn_smem_limit() {
+  static int cache[64] = {0};  // per device; concurrent first calls store the same value
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  if (!cache[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 227 * 1024;
+    }
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Scratch layout: [DevStatus][SmallWs][C hi/lo (KMAX x KMAX)][partials ...]
+constexpr size_t kOffStatus = 0;
+constexpr size_t kOffWs = align_up(sizeof(DevStatus));
+constexpr size_t kOffC = kOffWs + align_up(sizeof(SmallWs));
+constexpr size_t kOffParts = kOffC + align_up(2 * sizeof(double) * KMAX * KMAX);
 
 eo_status ensure_scratch(eo_ctx* c, size_t parts_bytes) {
   const size_t need = kOffParts + align_up(std::max<size_t>(parts_bytes, kAlign));
@@ -95,14 +94,14 @@ __global__ void copy_small_kernel(int rows, int cols, const double* sh, const do
   }
 }
 
-bool valid_prec(int p) { return p == EO_FP64 || p == EO_DD || p == EO_F32 || p == EO_DD_EFT; }
+}  // namespace
 
 // Engine of a compensated Gram product: the tcgen05 digit engine
 // (umma_gram.cu) once one side has 16 columns or more (its 128-lane tensor-
 // memory tiles are then reasonably filled), the integer limbs (fxgram.cu)
 // otherwise.  EO_DD_GRAM_ENGINE=int|umma overrides the choice (both engines
 // give results within the same bound).
-bool use_umma_gram(int kx, int ky) {
+static bool use_umma_gram(int kx, int ky) {
   const char* e = getenv("EO_DD_GRAM_ENGINE");
   if (e && e[0] == 'u') return true;
   if (e && e[0] == 'i') return false;
@@ -115,27 +114,84 @@ size_t dd_gram_scratch(int64_t n, int kx, int ky, bool sym) {
 
 cudaError_t launch_dd_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
                            bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
-                           cudaStream_t st) {
+                           cudaStream_t st, int ctas) {
   if (use_umma_gram(kx, sym ? kx : ky))
-    return launch_umma_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st);
-  return launch_fx_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st);
+    return launch_umma_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st, ctas);
+  return launch_fx_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st, ctas);
 }
 
-// Mode of the FP64-pipe kernels for a precision (EO_DD_EFT runs them in DD).
-Mode pipe_mode(eo_prec p) { return p == EO_DD_EFT ? MODE_DD : (Mode)p; }
+int dd_gram_ctas(int64_t n, int kx, int ky, bool sym, int ctas) {
+  return use_umma_gram(kx, sym ? kx : ky) ? umma_gram_ctas(n, kx, ky, sym, ctas) : fx_gram_ctas(n, kx, ky, sym, ctas);
+}
 
-#define EO_CHECK(cond, code, ...) \
-  do {                            \
-    if (!(cond)) return fail(ctx, code, __VA_ARGS__); \
-  } while (0)
+size_t orth_scratch(int64_t n, int k, eo_prec prec) {
+  return prec == EO_DD ? dd_gram_scratch(n, k, k, true) : gram_scratch_bytes(n, k, k, true);
+}
 
-#define EO_CUDA(expr, where)                          \
-  do {                                                \
-    cudaError_t e_ = (expr);                          \
-    if (e_ != cudaSuccess) return cuda_fail(ctx, where, e_); \
-  } while (0)
+cudaError_t enqueue_orth_step(const OrthArgs& a, const OrthRes& r, int p, OrthStep step, uint64_t* launches) {
+  const bool fx = a.prec == EO_DD;
+  const Mode mode = pipe_mode(a.prec);
+  const Mode small_mode = mode == MODE_DD ? MODE_DD : MODE_FP64;
+  DevStatus* st = r.st;
+  SmallWs* ws = r.ws;
+  const int npass = a.passes == 1 ? 1 : 2;
+  cudaError_t e = cudaSuccess;
+  switch (step) {
+    case OrthStep::kGram:
+      if (p == 0 && a.M_hi) return cudaSuccess;  // the caller's Gram matrix
+      if (fx) {
+        const double* X = static_cast<const double*>(a.X);
+        e = launch_dd_gram(a.n, a.k, X, a.ldx, a.k, X, a.ldx, true, r.parts, ws->Mh, ws->Ml, KMAX, &st->gate[2 * p],
+                           r.stream, r.tile.gram);
+      } else {
+        e = launch_gram(mode, a.n, a.k, a.X, a.ldx, a.k, a.X, a.ldx, true, r.parts, ws->Mh, ws->Ml, KMAX,
+                        &st->gate[2 * p], r.stream);
+      }
+      *launches += kGramLaunches;
+      return e;
+    case OrthStep::kSmall: {
+      const bool given = p == 0 && a.M_hi;
+      const double* mh = given ? a.M_hi : ws->Mh;
+      const double* ml = given ? a.M_lo : ws->Ml;
+      const int ld = given ? a.ldm : KMAX;
+      const SmallGates gates{&st->gate[2 * p], &st->gate[2 * p + 1], p + 1 < npass ? &st->gate[2 * p + 2] : nullptr};
+      e = a.chol ? launch_chol_small(small_mode, a.k, mh, ml, ld, ws, a.O_hi, a.O_lo, a.ldo, st, gates, p, a.passes,
+                                     a.out_dev, r.stream)
+                 : launch_svqb_small(small_mode, a.k, mh, ml, ld, ws, a.O_hi, a.O_lo, a.ldo, a.tol, st, gates, p,
+                                     a.passes, a.out_dev, r.stream);
+      *launches += 1;
+      return e;
+    }
+    case OrthStep::kUpdate:
+      e = fx ? launch_fx_update(a.n, a.k, static_cast<double*>(a.X), a.ldx, ws->Zh, ws->Zl, a.chol,
+                                &st->gate[2 * p + 1], r.stream, r.tile.row)
+             : launch_update(mode, a.n, a.k, a.X, a.ldx, ws->Zh, ws->Zl, a.chol, &st->gate[2 * p + 1], r.stream);
+      *launches += 1;
+      return e;
+  }
+  return cudaErrorInvalidValue;
+}
 
-}  // namespace
+cudaError_t enqueue_orth(const OrthArgs& a, const OrthRes& r, uint64_t* launches, const char** where) {
+  cudaError_t e = launch_status_init(r.st, a.k, r.stream);
+  *launches += 1;
+  if (e != cudaSuccess) {
+    *where = "status init";
+    return e;
+  }
+  const int npass = a.passes == 1 ? 1 : 2;
+  static const char* names[3] = {"Gram", "factorization", "update"};
+  for (int p = 0; p < npass; ++p)
+    for (OrthStep step : {OrthStep::kGram, OrthStep::kSmall, OrthStep::kUpdate}) {
+      e = enqueue_orth_step(a, r, p, step, launches);
+      if (e != cudaSuccess) {
+        *where = names[(int)step];
+        return e;
+      }
+    }
+  return cudaSuccess;
+}
+
 }  // namespace eo
 
 namespace eo {
@@ -183,52 +239,13 @@ eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, 
   EO_CHECK(passes >= 0 && passes <= 2, EO_EINVAL, "%s: passes must be 0, 1 or 2 (%lld)", name, (long long)passes);
   DeviceGuard g(ctx->device);
   EO_CHECK(g.ok, EO_ECUDA, "%s: cannot select device", name);
-  const bool fx = prec == EO_DD;
-  eo_status s = ensure_scratch(ctx, fx ? dd_gram_scratch(n, k, k, true) : gram_scratch_bytes(n, k, k, true));
+  eo_status s = ensure_scratch(ctx, orth_scratch(n, k, prec));
   if (s != EO_OK) return s;
-  DevStatus* st = status_of(ctx);
-  SmallWs* ws = ws_of(ctx);
-  const Mode mode = pipe_mode(prec);
-  const Mode small_mode = mode == MODE_DD ? MODE_DD : MODE_FP64;
-  EO_CUDA(launch_status_init(st, k, ctx->stream), name);
-  ctx->launches += 1;
-  const int npass = passes == 1 ? 1 : 2;
-  for (int p = 0; p < npass; ++p) {
-    const double* mh = ws->Mh;
-    const double* ml = ws->Ml;
-    int ld = KMAX;
-    if (p == 0 && M_hi) {
-      mh = M_hi;
-      ml = M_lo;
-      ld = ldm;
-    } else if (fx) {
-      EO_CUDA(launch_dd_gram(n, k, static_cast<const double*>(X), ldx, k, static_cast<const double*>(X), ldx, true,
-                             parts_of(ctx), ws->Mh, ws->Ml, KMAX, &st->gate[2 * p], ctx->stream),
-              name);
-      ctx->launches += kGramLaunches;
-    } else {
-      EO_CUDA(launch_gram(mode, n, k, X, ldx, k, X, ldx, true, parts_of(ctx), ws->Mh, ws->Ml, KMAX, &st->gate[2 * p],
-                          ctx->stream),
-              name);
-      ctx->launches += kGramLaunches;
-    }
-    const SmallGates gates{&st->gate[2 * p], &st->gate[2 * p + 1], p + 1 < npass ? &st->gate[2 * p + 2] : nullptr};
-    if (CHOL)
-      EO_CUDA(launch_chol_small(small_mode, k, mh, ml, ld, ws, O_hi, O_lo, ldo, st, gates, p, passes, out_dev,
-                                ctx->stream),
-              name);
-    else
-      EO_CUDA(launch_svqb_small(small_mode, k, mh, ml, ld, ws, O_hi, O_lo, ldo, tol, st, gates, p, passes, out_dev,
-                                ctx->stream),
-              name);
-    if (fx)
-      EO_CUDA(launch_fx_update(n, k, static_cast<double*>(X), ldx, ws->Zh, ws->Zl, CHOL, &st->gate[2 * p + 1],
-                               ctx->stream),
-              name);
-    else
-      EO_CUDA(launch_update(mode, n, k, X, ldx, ws->Zh, ws->Zl, CHOL, &st->gate[2 * p + 1], ctx->stream), name);
-    ctx->launches += 2;  // factorization + update
-  }
+  const OrthArgs a{CHOL, n, k, X, ldx, M_hi, M_lo, ldm, O_hi, O_lo, ldo, tol, passes, prec, out_dev};
+  const OrthRes r{status_of(ctx), ws_of(ctx), parts_of(ctx), ctx->stream, Tile{}};
+  const char* where = "";
+  cudaError_t e = enqueue_orth(a, r, &ctx->launches, &where);
+  if (e != cudaSuccess) return cuda_fail(ctx, (std::string(name) + " (" + where + ")").c_str(), e);
   return EO_OK;
 }
 

@@ -17,6 +17,20 @@ enum Mode : int { MODE_FP64 = EO_FP64, MODE_DD = EO_DD, MODE_F32 = EO_F32 };
 
 constexpr int KMAX = EO_KMAX;
 
+// Dynamic shared memory limit of a kernel: always the device's opt-in
+// maximum less its static shared memory, so that launches of one kernel with different sizes (several in
+// one CUDA graph, say) never run under a smaller limit set for another.
+int dyn_smem_limit();
+template <class K>
+cudaError_t set_dyn_smem(K kernel, size_t need) {
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  const int lim = dyn_smem_limit() - (int)fa.sharedSizeBytes;  // the opt-in maximum covers static + dynamic
+  if (lim <= 0 || need > (size_t)lim) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
 // Device-resident status of one call.  gate[2p] enables the Gram and the
 // small factorization of pass p, gate[2p+1] the streaming update of pass p;
 // the factorization of pass p sets the gates of what follows, so a call never
@@ -83,25 +97,35 @@ struct __align__(16) FxPart {
 cudaError_t launch_fx_reduce(int kx, int ky, bool sym, int nchunks, const FxPart* parts, double* G_hi, double* G_lo,
                              int ldg, const int* gate, cudaStream_t st);
 // The same product on the tcgen05 tensor cores (umma_gram.cu); same partial format.
+// ctas > 0 caps the CTAs of the partial-sum launch (a launch shape picked by
+// the batch autotuner); 0 = one CTA per SM.  The scratch sizes below hold for
+// every cap.
 size_t umma_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym);
 cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
                              bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
-                             cudaStream_t st);
+                             cudaStream_t st, int ctas = 0);
 size_t fx_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym);
+// CTAs of the partial-sum launch of each engine under a cap (0 = none).
+int umma_gram_ctas(int64_t n, int kx, int ky, bool sym, int ctas);
+int fx_gram_ctas(int64_t n, int kx, int ky, bool sym, int ctas);
 cudaError_t launch_fx_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
                            bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
-                           cudaStream_t st);
+                           cudaStream_t st, int ctas = 0);
 // Row products of the compensated mode on the tcgen05 tensor cores
 // (umma_rowprod.cu): Out = Yin - A B (update = false) or Out = A B (update =
 // true), A n-by-kin, B kin-by-kout double-double (column j at Bh + j ldb);
 // kin <= 64, kout <= 16 (umma_rowprod_supported); Out may be A (in place).
+// ctas > 0 caps the CTAs of the launch (0 = one per SM).
 bool umma_rowprod_supported(int kin, int kout);
 cudaError_t launch_umma_rowprod(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout,
                                 const double* Bh, const double* Bl, int ldb, bool tri, const double* Yin,
-                                int64_t ldyin, double* Out, int64_t ldo, const int* gate, cudaStream_t st);
-// X <- X Z in place (Z: k-by-k double-double, leading dimension KMAX).
+                                int64_t ldyin, double* Out, int64_t ldo, const int* gate, cudaStream_t st,
+                                int ctas = 0);
+// CTAs of an X Z launch (n-by-k) under a cap (0 = none).
+int fx_update_ctas(int64_t n, int k, int ctas);
+// X <- X Z in place (Z: k-by-k double-double, leading dimension KMAX); ctas as above.
 cudaError_t launch_fx_update(int64_t n, int k, double* X, int64_t ldx, const double* Zh, const double* Zl, bool tri,
-                             const int* gate, cudaStream_t st);
+                             const int* gate, cudaStream_t st, int ctas = 0);
 // Yout = Y - V C (C: kv-by-k double-double with leading dimension ldc).
 cudaError_t launch_fx_project(int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y, int64_t ldy,
                               double* Yout, int64_t ldyo, const double* C_hi, const double* C_lo, int ldc,
@@ -126,6 +150,24 @@ cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* 
 cudaError_t launch_svqb_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
                               double* Z_hi, double* Z_lo, int ldz, double tol, DevStatus* s, SmallGates g, int pass,
                               int passes, int* rank_user, cudaStream_t st);
+// Many independent factorizations in one launch (one CTA per job): the
+// Gram matrix of job j is in jobs[j].ws->Mh/Ml (leading dimension KMAX) and
+// its gates in jobs[j].st (pass p as in the single launches); tol < 0 is
+// replaced by the default of the job's k on the host.
+struct SmallJob {
+  int k;
+  SmallWs* ws;
+  DevStatus* st;
+  double *Oh, *Ol;  // optional R (CholQR) or Z (SVQB) output
+  int ldo;
+  double tol;       // SVQB eigenvalue cut
+  int* out;         // optional info (CholQR) or rank (SVQB)
+};
+double svqb_default_tol(Mode mode, int k);
+cudaError_t launch_status_init_batched(const SmallJob* jobs, int njobs, cudaStream_t st);
+cudaError_t launch_small_batched(bool chol, Mode mode, int njobs, int kmax, const SmallJob* jobs, int pass,
+                                 int passes, cudaStream_t st);
+
 // Convergence test of iteration `iter` of eo_orthogonalize: converged when
 // max |C_ij| <= eps and max |M_ij - delta_ij| <= eps (C kv-by-k, M k-by-k,
 // hi + lo).  Sets the SVQB/update gates of this iteration and the run gate of

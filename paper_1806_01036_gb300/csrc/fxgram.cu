@@ -422,10 +422,17 @@ size_t plan_smem(const GramPlan& p) {
          sizeof(i128) * kMaxTiles * TI * TJ + 3 * sizeof(int) * p.max_slots;
 }
 
-int num_chunks(int64_t n, const GramPlan& p) {
+// Row chunks: one resident CTA per SM over the grid, and at most 2^22 rows per
+// chunk (a 128-bit total then holds the sum of a chunk's products, each below
+// 2^104 units, with room to spare).  ctas > 0 caps the CTAs (fewer chunks).
+int num_chunks(int64_t n, const GramPlan& p, int ctas = 0) {
   const int64_t by_rows = (n + p.P - 1) / p.P;
-  const int64_t want = (152 + p.groups - 1) / p.groups;  // one resident CTA per SM over the grid
-  return (int)std::max<int64_t>(1, std::min(by_rows, want));
+  const int64_t want = (152 + p.groups - 1) / p.groups;
+  const int64_t need = (n + (1ll << 22) - 1) >> 22;
+  const int64_t c = std::max<int64_t>(1, std::min(by_rows, std::max(want, need)));
+  if (ctas <= 0) return (int)c;
+  const int64_t cap = std::max<int64_t>(1, ctas / p.groups);
+  return (int)std::max<int64_t>(std::max<int64_t>(1, need), std::min(c, cap));
 }
 
 }  // namespace
@@ -443,22 +450,28 @@ size_t fx_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym) {
   return (size_t)num_chunks(n, make_plan(kx, ky, sym)) * (size_t)kx * ky * sizeof(FxPart);
 }
 
+int fx_gram_ctas(int64_t n, int kx, int ky, bool sym, int ctas) {
+  if (sym) ky = kx;
+  const GramPlan plan = make_plan(kx, ky, sym);
+  return plan.groups * num_chunks(n, plan, ctas);
+}
+
 cudaError_t launch_fx_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
                            bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
-                           cudaStream_t st) {
+                           cudaStream_t st, int ctas) {
   if (sym) {
     Y = X;
     ldy = ldx;
     ky = kx;
   }
   const GramPlan plan = make_plan(kx, ky, sym);
-  const int chunks = num_chunks(n, plan);
+  const int chunks = num_chunks(n, plan, ctas);
   int64_t rpc = (n + chunks - 1) / chunks;
   rpc = std::max<int64_t>(plan.P, (rpc + plan.P - 1) / plan.P * plan.P);
   FxPart* parts = static_cast<FxPart*>(scratch);
   dim3 grid(plan.groups, chunks);
   const size_t smem = plan_smem(plan);
-  cudaError_t e = cudaFuncSetAttribute(fx_gram_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_dyn_smem(fx_gram_partial_kernel, smem);
   if (e != cudaSuccess) return e;
   fx_gram_partial_kernel<<<grid, kThreads, smem, st>>>(n, kx, X, ldx, ky, Y, ldy, plan, rpc, parts, gate);
   const int E = kx * ky;

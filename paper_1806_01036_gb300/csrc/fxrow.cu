@@ -142,23 +142,27 @@ size_t smem_bytes(int kin, int kout, int P) {
   return sizeof(int4) * ((size_t)kout * kin + (size_t)kin * P) + sizeof(int) * (kout + P);
 }
 
+int grid_of(int64_t n, int P, int ctas) {
+  const int64_t panels = (n + P - 1) / P;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(panels, ctas > 0 ? ctas : 152 * 2));
+}
+
 cudaError_t launch_rowprod(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout, const double* Bh,
                            const double* Bl, int ldb, bool tri, const double* Yin, int64_t ldyin, double* Out,
-                           int64_t ldo, const int* gate, cudaStream_t st) {
+                           int64_t ldo, const int* gate, cudaStream_t st, int ctas = 0) {
   const int P = rows_per_panel(kin, kout);
   int lgP = 0;
   while ((1 << lgP) < P) ++lgP;
   const size_t smem = smem_bytes(kin, kout, P);
-  const int64_t panels = (n + P - 1) / P;
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(panels, 152 * 2));
+  const int blocks = grid_of(n, P, ctas);
   cudaError_t e;
   if (update) {
-    e = cudaFuncSetAttribute(fx_rowprod_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_dyn_smem(fx_rowprod_kernel<1>, smem);
     if (e != cudaSuccess) return e;
     fx_rowprod_kernel<1><<<blocks, kThreads, smem, st>>>(n, kin, A, lda, kout, Bh, Bl, ldb, tri ? 1 : 0, nullptr, 0,
                                                          Out, ldo, P, lgP, gate);
   } else {
-    e = cudaFuncSetAttribute(fx_rowprod_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_dyn_smem(fx_rowprod_kernel<0>, smem);
     if (e != cudaSuccess) return e;
     fx_rowprod_kernel<0><<<blocks, kThreads, smem, st>>>(n, kin, A, lda, kout, Bh, Bl, ldb, 0, Yin, ldyin, Out, ldo,
                                                          P, lgP, gate);
@@ -171,11 +175,19 @@ cudaError_t launch_rowprod(bool update, int64_t n, int kin, const double* A, int
 // Both row products go to the tensor-core engine (umma_rowprod.cu) when their
 // sizes fit it (kin <= 64, kout <= 16), to the integer limbs otherwise;
 // EO_DD_ROW_ENGINE=int forces the integer limbs.
+int fx_update_ctas(int64_t n, int k, int ctas) {
+  if (umma_rowprod_supported(k, k)) {
+    const int64_t ntiles = (n + 127) / 128;  // 128-row tiles of the tensor-core engine
+    return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, ctas > 0 ? ctas : 152));
+  }
+  return grid_of(n, rows_per_panel(k, k), ctas);
+}
+
 cudaError_t launch_fx_update(int64_t n, int k, double* X, int64_t ldx, const double* Zh, const double* Zl, bool tri,
-                             const int* gate, cudaStream_t st) {
+                             const int* gate, cudaStream_t st, int ctas) {
   if (umma_rowprod_supported(k, k))
-    return launch_umma_rowprod(true, n, k, X, ldx, k, Zh, Zl, KMAX, tri, nullptr, 0, X, ldx, gate, st);
-  return launch_rowprod(true, n, k, X, ldx, k, Zh, Zl, KMAX, tri, nullptr, 0, X, ldx, gate, st);
+    return launch_umma_rowprod(true, n, k, X, ldx, k, Zh, Zl, KMAX, tri, nullptr, 0, X, ldx, gate, st, ctas);
+  return launch_rowprod(true, n, k, X, ldx, k, Zh, Zl, KMAX, tri, nullptr, 0, X, ldx, gate, st, ctas);
 }
 
 cudaError_t launch_fx_project(int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y, int64_t ldy,

@@ -223,13 +223,13 @@ cudaError_t launch_project_fused(Mode mode, int64_t n, int kv, const double* V, 
   const int want_m = M_hi != nullptr;
   cudaError_t e;
   if (mode == MODE_DD) {
-    e = cudaFuncSetAttribute(project_fused_kernel<MODE_DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_dyn_smem(project_fused_kernel<MODE_DD>, smem);
     if (e != cudaSuccess) return e;
     project_fused_kernel<MODE_DD><<<np, kThreads, smem, st>>>(n, kv, V, ldv, k, Y, ldy, Yout, ldyo, C_hi, C_lo, ldc, P,
                                                               want_m, parts, gate);
     if (want_m) sym_reduce_kernel<MODE_DD><<<(k * k * 32 + kThreads - 1) / kThreads, kThreads, 0, st>>>(k, np, parts, M_hi, M_lo, ldm, gate);
   } else {
-    e = cudaFuncSetAttribute(project_fused_kernel<MODE_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_dyn_smem(project_fused_kernel<MODE_FP64>, smem);
     if (e != cudaSuccess) return e;
     project_fused_kernel<MODE_FP64><<<np, kThreads, smem, st>>>(n, kv, V, ldv, k, Y, ldy, Yout, ldyo, C_hi, C_lo, ldc,
                                                                 P, want_m, parts, gate);

@@ -59,10 +59,9 @@ __device__ void finish_gates(const SmallGates& g, int run_update, int want_next)
 // ------------------------------------------------------------ Cholesky
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) chol_small_kernel(int k, const double* Mh, const double* Ml, int ldm,
-                                                              SmallWs* ws, double* Rh_u, double* Rl_u, int ldr,
-                                                              DevStatus* st, SmallGates g, int pass, int passes,
-                                                              double thr, int* info_user) {
+__device__ __forceinline__ void chol_small_body(int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
+                                                double* Rh_u, double* Rl_u, int ldr, DevStatus* st, SmallGates g,
+                                                int pass, int passes, double thr, int* info_user) {
   using A_ = Ar<MODE>;
   if (*g.run == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -187,10 +186,10 @@ __global__ void __launch_bounds__(kThreads) chol_small_kernel(int k, const doubl
 // --------------------------------------------------------------- SVQB
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) svqb_small_kernel(int k, const double* Mh, const double* Ml, int ldm,
-                                                              SmallWs* ws, double* Zh_u, double* Zl_u, int ldz,
-                                                              double tol, DevStatus* st, SmallGates g, int pass,
-                                                              int passes, double thr, double eps, int* rank_user) {
+__device__ __forceinline__ void svqb_small_body(int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
+                                                double* Zh_u, double* Zl_u, int ldz, double tol, DevStatus* st,
+                                                SmallGates g, int pass, int passes, double thr, double eps,
+                                                int* rank_user) {
   using A_ = Ar<MODE>;
   if (*g.run == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -363,6 +362,61 @@ __global__ void __launch_bounds__(kThreads) svqb_small_kernel(int k, const doubl
   }
 }
 
+// ----------------------------------------------------- kernel wrappers
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) chol_small_kernel(int k, const double* Mh, const double* Ml, int ldm,
+                                                              SmallWs* ws, double* Rh_u, double* Rl_u, int ldr,
+                                                              DevStatus* st, SmallGates g, int pass, int passes,
+                                                              double thr, int* info_user) {
+  chol_small_body<MODE>(k, Mh, Ml, ldm, ws, Rh_u, Rl_u, ldr, st, g, pass, passes, thr, info_user);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) svqb_small_kernel(int k, const double* Mh, const double* Ml, int ldm,
+                                                              SmallWs* ws, double* Zh_u, double* Zl_u, int ldz,
+                                                              double tol, DevStatus* st, SmallGates g, int pass,
+                                                              int passes, double thr, double eps, int* rank_user) {
+  svqb_small_body<MODE>(k, Mh, Ml, ldm, ws, Zh_u, Zl_u, ldz, tol, st, g, pass, passes, thr, eps, rank_user);
+}
+
+// One CTA per job: the factorization of pass `pass` of many independent
+// blocks, each from its own workspace's Gram matrix and gates.
+__device__ __forceinline__ SmallGates job_gates(const SmallJob& j, int pass, int npass) {
+  return SmallGates{&j.st->gate[2 * pass], &j.st->gate[2 * pass + 1],
+                    pass + 1 < npass ? &j.st->gate[2 * pass + 2] : nullptr};
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) chol_small_batched_kernel(const SmallJob* jobs, int pass, int passes,
+                                                                      double thr) {
+  const SmallJob j = jobs[blockIdx.x];
+  const int npass = passes == 1 ? 1 : 2;
+  chol_small_body<MODE>(j.k, j.ws->Mh, j.ws->Ml, KMAX, j.ws, j.Oh, j.Ol, j.ldo, j.st, job_gates(j, pass, npass), pass,
+                        passes, thr, j.out);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) svqb_small_batched_kernel(const SmallJob* jobs, int pass, int passes,
+                                                                      double thr, double eps) {
+  const SmallJob j = jobs[blockIdx.x];
+  const int npass = passes == 1 ? 1 : 2;
+  svqb_small_body<MODE>(j.k, j.ws->Mh, j.ws->Ml, KMAX, j.ws, j.Oh, j.Ol, j.ldo, j.tol, j.st,
+                        job_gates(j, pass, npass), pass, passes, thr, eps, j.out);
+}
+
+__global__ void status_init_batched_kernel(const SmallJob* jobs, int njobs) {
+  for (int b = blockIdx.x; b < njobs; b += gridDim.x) {
+    DevStatus* s = jobs[b].st;
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) s->gate[i] = i == 0;
+    if (threadIdx.x == 0) {
+      s->info = 0;
+      s->rank = jobs[b].k;
+      s->iters = 0;
+    }
+  }
+}
+
 // ------------------------------------------------------ convergence test
 
 __global__ void __launch_bounds__(kThreads) converge_kernel(const int* run, const double* Ch, const double* Cl, int ldc,
@@ -415,18 +469,23 @@ cudaError_t launch_status_init(DevStatus* s, int k, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+size_t chol_smem(int k) { return 3 * (size_t)k * k * sizeof(dd); }
+size_t svqb_smem(int k) {
+  return 2 * (size_t)k * k * sizeof(dd) + 2 * (size_t)(k / 2 + 1) * sizeof(dd) + 2 * (size_t)(k / 2 + 1) * sizeof(int);
+}
+
 cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
                               double* R_hi, double* R_lo, int ldr, DevStatus* s, SmallGates g, int pass, int passes,
                               int* info_user, cudaStream_t st) {
-  const size_t smem = 3 * (size_t)k * k * sizeof(dd);
+  const size_t smem = chol_smem(k);
   cudaError_t e;
   if (mode == MODE_DD) {
-    e = cudaFuncSetAttribute(chol_small_kernel<MODE_DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_dyn_smem(chol_small_kernel<MODE_DD>, smem);
     if (e != cudaSuccess) return e;
     chol_small_kernel<MODE_DD><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, R_hi, R_lo, ldr, s, g, pass, passes,
                                                          1e7, info_user);
   } else {
-    e = cudaFuncSetAttribute(chol_small_kernel<MODE_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_dyn_smem(chol_small_kernel<MODE_FP64>, smem);
     if (e != cudaSuccess) return e;
     chol_small_kernel<MODE_FP64><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, R_hi, R_lo, ldr, s, g, pass, passes,
                                                            1e4, info_user);
@@ -437,21 +496,47 @@ cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* 
 cudaError_t launch_svqb_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
                               double* Z_hi, double* Z_lo, int ldz, double tol, DevStatus* s, SmallGates g, int pass,
                               int passes, int* rank_user, cudaStream_t st) {
-  const size_t smem = 2 * (size_t)k * k * sizeof(dd) + 2 * (size_t)(k / 2 + 1) * sizeof(dd) +
-                      2 * (size_t)(k / 2 + 1) * sizeof(int);
+  const size_t smem = svqb_smem(k);
   cudaError_t e;
   if (mode == MODE_DD) {
     if (tol < 0) tol = k * 0x1p-104;
-    e = cudaFuncSetAttribute(svqb_small_kernel<MODE_DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_dyn_smem(svqb_small_kernel<MODE_DD>, smem);
     if (e != cudaSuccess) return e;
     svqb_small_kernel<MODE_DD><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, Z_hi, Z_lo, ldz, tol, s, g, pass,
                                                          passes, 1e7, 0x1p-106, rank_user);
   } else {
     if (tol < 0) tol = k * 0x1p-52;
-    e = cudaFuncSetAttribute(svqb_small_kernel<MODE_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_dyn_smem(svqb_small_kernel<MODE_FP64>, smem);
     if (e != cudaSuccess) return e;
     svqb_small_kernel<MODE_FP64><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, Z_hi, Z_lo, ldz, tol, s, g, pass,
                                                            passes, 1e4, 0x1p-53, rank_user);
+  }
+  return cudaGetLastError();
+}
+
+double svqb_default_tol(Mode mode, int k) { return mode == MODE_DD ? k * 0x1p-104 : k * 0x1p-52; }
+
+cudaError_t launch_status_init_batched(const SmallJob* jobs, int njobs, cudaStream_t st) {
+  status_init_batched_kernel<<<std::min(njobs, 1024), 64, 0, st>>>(jobs, njobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small_batched(bool chol, Mode mode, int njobs, int kmax, const SmallJob* jobs, int pass,
+                                 int passes, cudaStream_t st) {
+  const bool ddm = mode == MODE_DD;
+  cudaError_t e;
+  if (chol) {
+    const size_t smem = chol_smem(kmax);
+    auto kern = ddm ? chol_small_batched_kernel<MODE_DD> : chol_small_batched_kernel<MODE_FP64>;
+    e = set_dyn_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<njobs, kThreads, smem, st>>>(jobs, pass, passes, ddm ? 1e7 : 1e4);
+  } else {
+    const size_t smem = svqb_smem(kmax);
+    auto kern = ddm ? svqb_small_batched_kernel<MODE_DD> : svqb_small_batched_kernel<MODE_FP64>;
+    e = set_dyn_smem(kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<njobs, kThreads, smem, st>>>(jobs, pass, passes, ddm ? 1e7 : 1e4, ddm ? 0x1p-106 : 0x1p-53);
   }
   return cudaGetLastError();
 }

@@ -496,6 +496,16 @@ int num_chunks(int64_t n, const UPlan& p) {
   return (int)std::max<int64_t>(1, std::min(by_rows, std::max(want, need)));
 }
 
+// Row chunks under a cap of ctas CTAs (0 = none): never more than num_chunks
+// (the scratch is sized for it), never fewer than the 2^22-row bound needs.
+int capped_chunks(int64_t n, const UPlan& p, int ctas) {
+  const int c = num_chunks(n, p);
+  if (ctas <= 0) return c;
+  const int64_t need = (n + (1ll << 22) - 1) >> 22;
+  const int64_t cap = std::max<int64_t>(1, ctas / (p.ntx * p.nty));
+  return (int)std::max<int64_t>(std::max<int64_t>(1, need), std::min<int64_t>(c, cap));
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -528,7 +538,7 @@ cudaError_t launch_kernel(const UPlan& plan, int chunks, int64_t n, int kx, cons
                           FxPart* parts, const int* gate, cudaStream_t st) {
   const size_t smem = plan_smem(plan);
   cudaError_t e =
-      cudaFuncSetAttribute(umma_gram_partial_kernel<KYP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      set_dyn_smem(umma_gram_partial_kernel<KYP>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(plan.ntx * plan.nty, chunks);
   umma_gram_partial_kernel<KYP>
@@ -543,9 +553,15 @@ size_t umma_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym) {
   return (size_t)num_chunks(n, make_plan(kx, ky, sym)) * (size_t)kx * ky * sizeof(FxPart);
 }
 
+int umma_gram_ctas(int64_t n, int kx, int ky, bool sym, int ctas) {
+  if (sym) ky = kx;
+  const UPlan plan = make_plan(kx, ky, sym);
+  return plan.ntx * plan.nty * capped_chunks(n, plan, ctas);
+}
+
 cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
                              bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
-                             cudaStream_t st) {
+                             cudaStream_t st, int ctas) {
   if (sym) {
     Y = X;
     ldy = ldx;
@@ -557,8 +573,8 @@ cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, in
   const bool tma_ok = (uintptr_t)X % 16 == 0 && (uintptr_t)Y % 16 == 0 && ldx % 2 == 0 && ldy % 2 == 0 &&
                       n < (1ll << 31) && make_map(&tmx, X, n, kx, ldx, plan.kxp) &&
                       make_map(&tmy, Y, n, ky, ldy, plan.kyp);
-  if (!tma_ok) return launch_fx_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st);
-  const int chunks = num_chunks(n, plan);
+  if (!tma_ok) return launch_fx_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st, ctas);
+  const int chunks = capped_chunks(n, plan, ctas);
   int64_t rpc = (n + chunks - 1) / chunks;
   rpc = std::max<int64_t>(plan.P, (rpc + plan.P - 1) / plan.P * plan.P);
   FxPart* parts = static_cast<FxPart*>(scratch);

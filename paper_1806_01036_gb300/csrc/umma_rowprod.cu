@@ -362,12 +362,12 @@ size_t smem_bytes() {
 template <int W>
 cudaError_t launch_w(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout, const double* Bh,
                      const double* Bl, int ldb, bool tri, const double* Yin, int64_t ldyin, double* Out, int64_t ldo,
-                     const int* gate, cudaStream_t st) {
+                     const int* gate, cudaStream_t st, int ctas) {
   const size_t smem = smem_bytes<W>();
-  cudaError_t e = cudaFuncSetAttribute(umma_rowprod_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_dyn_smem(umma_rowprod_kernel<W>, smem);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (n + kRows - 1) / kRows;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, 152));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, ctas > 0 ? ctas : 152));
   umma_rowprod_kernel<W><<<grid, kThreads, smem, st>>>(update ? 1 : 0, n, kin, A, lda, kout, Bh, Bl, ldb, tri ? 1 : 0,
                                                        Yin, ldyin, Out, ldo, gate);
   return cudaGetLastError();
@@ -383,11 +383,14 @@ bool umma_rowprod_supported(int kin, int kout) {
 
 cudaError_t launch_umma_rowprod(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout,
                                 const double* Bh, const double* Bl, int ldb, bool tri, const double* Yin,
-                                int64_t ldyin, double* Out, int64_t ldo, const int* gate, cudaStream_t st) {
+                                int64_t ldyin, double* Out, int64_t ldo, const int* gate, cudaStream_t st,
+                                int ctas) {
   if (n <= 0) return cudaSuccess;
-  if (kin <= 16) return launch_w<4>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st);
-  if (kin <= 32) return launch_w<8>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st);
-  return launch_w<16>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st);
+  if (kin <= 16)
+    return launch_w<4>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
+  if (kin <= 32)
+    return launch_w<8>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
+  return launch_w<16>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
 }
 
 }  // namespace eo

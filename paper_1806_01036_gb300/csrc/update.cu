@@ -71,7 +71,7 @@ cudaError_t launch_k(int64_t n, int k, void* X, int64_t ldx, const double* Zh, c
   } else if (k <= 32) {
     update_kernel<MODE, T, 32><<<blocks, kThreads, smem, st>>>(n, k, x, ldx, Zh, Zl, t, gate);
   } else {
-    e = cudaFuncSetAttribute(update_kernel<MODE, T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = set_dyn_smem(update_kernel<MODE, T, 64>, smem);
     if (e != cudaSuccess) return e;
     update_kernel<MODE, T, 64><<<blocks, kThreads, smem, st>>>(n, k, x, ldx, Zh, Zl, t, gate);
   }

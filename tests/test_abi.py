@@ -53,3 +53,18 @@ def test_null_context_is_rejected_without_touching_a_gpu(libeo):
     libeo.eo_last_error.argtypes = [C.c_void_p]
     assert libeo.eo_last_error(None) == b"null context"
     assert libeo.eo_version() == 1
+
+
+def test_batch_calls_reject_null_handles_without_touching_a_gpu(libeo):
+    libeo.eo_batch_run.argtypes = [C.c_void_p]
+    libeo.eo_batch_destroy.argtypes = [C.c_void_p]
+    libeo.eo_tune_cache.argtypes = [C.c_void_p, C.c_char_p]
+    libeo.eo_batch_kernels.argtypes = [C.c_void_p]
+    libeo.eo_batch_kernels.restype = C.c_int64
+    libeo.eo_batch_create.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_int,
+                                      C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+    assert libeo.eo_batch_run(None) == 1
+    assert libeo.eo_batch_destroy(None) == 1
+    assert libeo.eo_tune_cache(None, b"/nonexistent") == 1
+    assert libeo.eo_batch_kernels(None) == -1
+    assert libeo.eo_batch_create(None, 1, None, 0, -1.0, 0, 1, None, 0, 0, None) == 1
