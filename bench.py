@@ -50,11 +50,16 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU-oracle sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["project", "iterated", "batched"], default="project",
+    ap.add_argument("--workload", choices=["project", "iterated", "batched", "serve"], default="project",
                     help="project: the default line; iterated: the iterated two-phase algorithm on the "
                          "runtime-figure shapes (n = 8e6 unless --n is given); batched: many SVQB blocks of "
-                         "uneven n and k in one graph launch")
+                         "uneven n and k in one graph launch; serve: the request server under Poisson arrivals")
     ap.add_argument("--blocks", type=int, default=512, help="blocks of the batched workload")
+    ap.add_argument("--clients", type=int, default=256, help="resident bases of the serving workload")
+    ap.add_argument("--requests", type=int, default=2000, help="requests of the serving trace")
+    ap.add_argument("--rate", type=float, default=2000.0, help="offered requests/s of the serving trace")
+    ap.add_argument("--slots", type=int, default=16, help="concurrent slots of the server")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="device-memory budget of the server")
     ap.add_argument("--branches", type=int, default=0, help="graph branches of the batched workload (0 = auto)")
     return ap.parse_args()
 
@@ -637,6 +642,127 @@ def run_batched(a):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------- serving
+
+SERVE_METRIC = "serving: requests/s with p50/p99 latency, projection + compensated CholQR against resident bases"
+
+
+def run_serve(a):
+    """Request server under Poisson arrivals (eo_server_*): 256 simulated
+    eigensolves, each with a resident orthonormal basis V (n log-uniform in
+    [5e4, 8e6], kv uniform in {8, 16, 32, 64}), submit blocks Y of kv/4
+    columns (kappa log-uniform in [1e2, 1e12]) at 2,000 requests/s in total
+    (seeded exponential gaps, client uniform); each request is
+    Y - V (V^T Y) and a compensated CholQR with the automatic second pass,
+    admitted under a 150 GB device-memory budget.  Bases are seeded
+    Gaussians made orthonormal by the library's own two-pass compensated
+    CholQR; blocks are Gaussian x diag(sigma), generated on the GPU."""
+    import torch
+    import paper_1806_01036_gb300 as eo
+
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(20180604 + 4 + 1000 * rank)
+    nc = a.clients
+    ns = np.exp(rng.uniform(np.log(5e4), np.log(8e6), nc)).astype(np.int64)
+    kvs = rng.choice([8, 16, 32, 64], nc)
+    kappas = np.exp(rng.uniform(np.log(1e2), np.log(1e12), nc))
+    g = torch.Generator(device=dev)
+    g.manual_seed(20180604 + 4 + 1000 * rank)
+    f64 = torch.float64
+    ctx = eo.Context(local)
+
+    def colmajor_randn(n, k):
+        return torch.randn(k, n, dtype=f64, device=dev, generator=g).t()
+
+    V, Y, Yo = [], [], []
+    for n, kv, kap in zip(ns, kvs, kappas):
+        n, kv = int(n), int(kv)
+        v = colmajor_randn(n, kv)
+        eo.cholqr(ctx, v, passes=2, prec=eo.DD)
+        k = max(1, kv // 4)
+        s = torch.logspace(0.0, -float(np.log10(kap)), k, dtype=f64, device=dev)
+        y = colmajor_randn(n, k) * (s / float(np.sqrt(n)))[None, :]
+        V.append(v)
+        Y.append(y)
+        Yo.append(torch.empty_like(y.t()).t())
+    torch.cuda.synchronize()
+    srv = eo.Server(ctx, budget=int(a.budget_gb * 1e9), slots=a.slots)
+    ids = [srv.add_basis(v) for v in V]
+    # warm-up: one request per client
+    for i in range(nc):
+        srv.submit(ids[i], Y[i], Yout=Yo[i])
+    while True:
+        st = srv.stats()
+        if st["queued"] == 0 and st["running"] == 0:
+            break
+        time.sleep(0.001)
+    srv.poll(1 << 16)
+    # the timed trace
+    nreq = a.requests
+    gaps = rng.exponential(1.0 / a.rate, nreq)
+    arrival = np.cumsum(gaps)
+    who = rng.integers(0, nc, nreq)
+    nbytes = 0
+    for i in who:
+        n, kv = int(ns[i]), int(kvs[i])
+        k = max(1, kv // 4)
+        nbytes += 8 * n * (2 * kv + 5 * k)
+    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_serve_rank{rank}.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else f"/tmp/eo_clocks_s_{os.getpid()}.csv", local)
+    l0 = srv.stats()["kernels"]
+    with clk:
+        t0 = time.perf_counter()
+        rids = []
+        for t, i in zip(arrival, who):
+            while time.perf_counter() - t0 < t:
+                pass
+            rids.append(srv.submit(ids[i], Y[i], Yout=Yo[i]))
+        lat = []
+        for r in rids:
+            st, l = srv.wait(r, timeout=600.0)
+            if st != eo.OK:
+                raise RuntimeError("request failed")
+            lat.append(l)
+        t1 = time.perf_counter()
+    done = srv.poll(1 << 16)
+    qms = [q for _, _, q, _ in done]
+    stats = srv.stats()
+    launches = stats["kernels"] - l0
+    # accuracy of the last result of every client
+    orth, cross = 0.0, 0.0
+    for i in sorted(set(int(x) for x in who)):
+        k = Yo[i].shape[1]
+        gh, gl = eo.gram(ctx, Yo[i], prec=eo.DD)
+        e = (gh.cpu().numpy() - np.eye(k)) + gl.cpu().numpy()
+        orth = max(orth, float(np.linalg.norm(e, 2)))
+        ch, cl = eo.gram(ctx, V[i], Yo[i], prec=eo.DD)
+        cross = max(cross, float(np.linalg.norm(ch.cpu().numpy() + cl.cpu().numpy(), 2)))
+    srv.close()
+    span = t1 - t0
+    hbm_peak, peak_kind = peak_hbm()
+    out = {
+        "metric": SERVE_METRIC, "value": nreq / span, "unit": "requests/s", "n_gpus": ws, "steps": nreq,
+        "warmup": nc, "ms_per_step": 1e3 * span / nreq, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded on the GPU: bases made orthonormal by the library's DD CholQR2)",
+        "config": {"workload": f"serving: {nc} resident bases (n log-uniform [5e4, 8e6], kv in 8/16/32/64), "
+                               f"blocks of kv/4 columns (kappa log-uniform [1e2, 1e12]), Poisson arrivals at "
+                               f"{a.rate:g} requests/s, {a.budget_gb:g} GB budget, {a.slots} slots",
+                   "resident_gb": stats["resident"] / 1e9, "offered_rate": a.rate, "requests": nreq,
+                   "l2": "bases and blocks far larger than L2; no flush"},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "mean_ms": float(np.mean(lat)), "queue_p50_ms": float(np.percentile(qms, 50)) if qms else None,
+        "queue_p99_ms": float(np.percentile(qms, 99)) if qms else None,
+        "gbs": nbytes / span / 1e9, "hbm_frac": nbytes / span / 1e9 / hbm_peak, "hbm_peak_source": peak_kind,
+        "peak_running": stats["peak_running"], "peak_inflight_gb": stats["peak_inflight"] / 1e9,
+        "orth_err_max": orth, "cross_err_max": cross, "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -645,6 +771,8 @@ def main():
         run_iterated(a)
     elif a.workload == "batched":
         run_batched(a)
+    elif a.workload == "serve":
+        run_serve(a)
     else:
         run_eo(a)
 

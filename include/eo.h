@@ -32,6 +32,7 @@
 #ifndef EO_H
 #define EO_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -263,6 +264,64 @@ EO_API eo_status eo_batch_passes(eo_batch* batch, int* passes_host);
 /* Kernels one eo_batch_run launches (-1 for NULL), and the graph's branches. */
 EO_API int64_t eo_batch_kernels(const eo_batch* batch);
 EO_API int eo_batch_branches(const eo_batch* batch);
+
+/*
+ * Request server (no counterpart in the paper): many concurrent eigensolves
+ * keep their bases V resident on the device and submit blocks Y to be
+ * orthogonalized against them -- Yout = Y - V (V^T Y) followed by the
+ * compensated CholQR of Yout with the automatic second pass, as
+ * eo_project(..., M) + eo_cholqr(..., M, passes = 0, EO_DD) would do.
+ *
+ * A server thread admits queued requests onto `slots` streams (each with
+ * its own workspace, reserved up front) in submission order, one request at
+ * a time per basis, as soon as a slot is free and the device-memory budget
+ * allows: registered bases (n kv 8 bytes) and the slots' workspaces stay
+ * charged; a running request is charged for its block (n k 8 bytes, twice
+ * when Yout != Y).  Requests that arrive while others run join as slots and
+ * memory free up, and their kernels overlap on the GPU.  The first queued
+ * request that does not fit stops admission until memory frees (no
+ * overtaking on memory); a request blocked by its basis is passed over.
+ * Every slot uses the default launch shapes, so a result is bitwise the same
+ * alone and in any mix.
+ *
+ * eo_server_create: budget in bytes; slots in [1, 256]; starts the server
+ *   thread.  The context only reports errors; it is not used for work.
+ * eo_server_add_basis: registers V (device, n-by-kv, ldv; owned by the
+ *   caller, unchanged while the server lives); EO_ENOMEM if it does not fit
+ *   the budget.  May synchronize (it grows the slots' scratch).
+ * eo_server_submit: queues a request; thread-safe and non-blocking.  Y and
+ *   Yout: device n-by-k blocks (Yout may equal Y); R_hi/R_lo (k-by-k, ldr),
+ *   info_dev: optional outputs as in eo_cholqr.  EO_ENOMEM if the block can
+ *   never fit next to the resident bases.
+ * eo_server_wait: blocks until the request is done (EO_ETIMEOUT after
+ *   timeout_s seconds); *status = EO_OK or EO_ECUDA; *latency_ms = time from
+ *   submission to the end of its last kernel.
+ * eo_server_poll: up to max_out completed requests not yet reported, with
+ *   their latency and time spent queued (ms).
+ * eo_server_stats: resident bytes, peak in-flight bytes, peak requests
+ *   running at once, requests queued and running now, kernels launched by
+ *   the slots so far (any pointer may be NULL).
+ * eo_server_destroy: stops the thread, waits for the slots, frees them.
+ */
+typedef struct eo_server eo_server;
+EO_API eo_status eo_server_create(eo_ctx* ctx, size_t hbm_budget, int slots, eo_server** server);
+EO_API eo_status eo_server_destroy(eo_server* server);
+EO_API eo_status eo_server_add_basis(eo_server* server, int64_t n, int kv, const double* V, int64_t ldv,
+                                     int* basis_id);
+EO_API eo_status eo_server_submit(eo_server* server, int basis_id, int k, const double* Y, int64_t ldy, double* Yout,
+                                  int64_t ldyo, double* R_hi, double* R_lo, int ldr, int* info_dev, int64_t* req_id);
+EO_API eo_status eo_server_wait(eo_server* server, int64_t req_id, double timeout_s, int* status, double* latency_ms);
+EO_API eo_status eo_server_poll(eo_server* server, int max_out, int64_t* ids, double* latency_ms, double* queue_ms,
+                                int* statuses, int* n_out);
+EO_API eo_status eo_server_stats(eo_server* server, size_t* resident, size_t* peak_inflight, int* peak_running,
+                                 int* queued, int* running, uint64_t* kernels);
+/* The admission policy alone, in a discrete-event simulation on the host (no
+ * GPU): request i arrives at arrival[i] on basis[i], is charged bytes[i] and
+ * runs for duration[i] once admitted; start[i] receives its admission time,
+ * or -1 if it can never fit.  Returns the peak number running at once, or -1
+ * on bad arguments. */
+EO_API int eo_admission_simulate(size_t budget, int slots, size_t resident_bytes, int nreq, const int* basis,
+                                 const int64_t* bytes, const double* arrival, const double* duration, double* start);
 
 /*
  * Allocation-free compensated Gram product (no counterpart in the paper).

@@ -75,13 +75,26 @@ def lib():
         L.eo_batch_destroy.argtypes = [_p]
         L.eo_batch_tile.argtypes = [_p, _int, C.POINTER(_int), C.POINTER(_int)]
         L.eo_batch_passes.argtypes = [_p, _p]
+        _sz = C.c_size_t
+        L.eo_server_create.argtypes = [_p, _sz, _int, C.POINTER(_p)]
+        L.eo_server_destroy.argtypes = [_p]
+        L.eo_server_add_basis.argtypes = [_p, _i64, _int, _p, _i64, C.POINTER(_int)]
+        L.eo_server_submit.argtypes = [_p, _int, _int, _p, _i64, _p, _i64, _p, _p, _int, _p, C.POINTER(_i64)]
+        L.eo_server_wait.argtypes = [_p, _i64, _dbl, C.POINTER(_int), C.POINTER(_dbl)]
+        L.eo_server_poll.argtypes = [_p, _int, _p, _p, _p, _p, C.POINTER(_int)]
+        L.eo_server_stats.argtypes = [_p, C.POINTER(_sz), C.POINTER(_sz), C.POINTER(_int), C.POINTER(_int),
+                                      C.POINTER(_int), C.POINTER(C.c_uint64)]
+        L.eo_admission_simulate.argtypes = [_sz, _int, _sz, _int, _p, _p, _p, _p, _p]
+        L.eo_admission_simulate.restype = _int
         L.eo_batch_kernels.argtypes = [_p]
         L.eo_batch_kernels.restype = C.c_int64
         L.eo_batch_branches.argtypes = [_p]
         L.eo_batch_branches.restype = _int
         for f in ("eo_create", "eo_destroy", "eo_set_stream", "eo_gram", "eo_project", "eo_project_apply",
                   "eo_cholqr", "eo_svqb", "eo_orthogonalize", "eo_gram_dd_noalloc", "eo_tune_cache",
-                  "eo_batch_create", "eo_batch_run", "eo_batch_destroy", "eo_batch_tile", "eo_batch_passes"):
+                  "eo_batch_create", "eo_batch_run", "eo_batch_destroy", "eo_batch_tile", "eo_batch_passes",
+                  "eo_server_create", "eo_server_destroy", "eo_server_add_basis", "eo_server_submit",
+                  "eo_server_wait", "eo_server_poll", "eo_server_stats"):
             getattr(L, f).restype = _int
         _lib = L
     return _lib
@@ -388,3 +401,97 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Request server (eo_server_*): resident bases, blocks orthogonalized
+    against them (projection + compensated CholQR) on `slots` concurrent
+    streams under a device-memory budget (bytes)."""
+
+    def __init__(self, ctx: Context, budget: int, slots: int = 16):
+        h = _p()
+        ctx.check(lib().eo_server_create(ctx.h, int(budget), int(slots), C.byref(h)))
+        self.ctx = ctx
+        self.h = h
+        self.bases = []
+
+    def add_basis(self, V) -> int:
+        """Register a resident column-major FP64 basis; returns its id."""
+        import torch
+        V, n, kv, ldv = _mat(V, "V", torch.float64)
+        bid = _int()
+        self.ctx.check(lib().eo_server_add_basis(self.h, n, kv, V.data_ptr(), ldv, C.byref(bid)))
+        self.bases.append(V)
+        return bid.value
+
+    def submit(self, basis: int, Y, Yout=None, R=None, info=None) -> int:
+        """Queue Yout = CholQR(Y - V V^T Y); returns the request id.  R: optional
+        (hi, lo) k-by-k pair; info: optional device int32 tensor."""
+        import torch
+        Y, n, k, ldy = _mat(Y, "Y", torch.float64)
+        Yout = Y if Yout is None else Yout
+        Yout, _, _, ldyo = _mat(Yout, "Yout", torch.float64)
+        rh = rl = None
+        ldr = k
+        if R is not None:
+            rh, rl, ldr = _dd_pair(R, k, k, "R", False)
+        rid = _i64()
+        self.ctx.check(lib().eo_server_submit(self.h, int(basis), k, Y.data_ptr(), ldy, Yout.data_ptr(), ldyo,
+                                              None if rh is None else rh.data_ptr(),
+                                              None if rl is None else rl.data_ptr(), ldr,
+                                              None if info is None else info.data_ptr(), C.byref(rid)))
+        return rid.value
+
+    def wait(self, rid: int, timeout: float = 60.0):
+        """(status, latency_ms) of a request, waiting for it."""
+        st, lat = _int(), _dbl()
+        self.ctx.check(lib().eo_server_wait(self.h, int(rid), float(timeout), C.byref(st), C.byref(lat)))
+        return st.value, lat.value
+
+    def poll(self, max_out: int = 4096):
+        """Completed requests not yet reported: list of (id, latency_ms, queue_ms, status)."""
+        ids = (_i64 * max_out)()
+        lat = (_dbl * max_out)()
+        qms = (_dbl * max_out)()
+        sts = (_int * max_out)()
+        n = _int()
+        self.ctx.check(lib().eo_server_poll(self.h, max_out, C.cast(ids, _p), C.cast(lat, _p), C.cast(qms, _p),
+                                            C.cast(sts, _p), C.byref(n)))
+        return [(ids[i], lat[i], qms[i], sts[i]) for i in range(n.value)]
+
+    def stats(self):
+        r, p = C.c_size_t(), C.c_size_t()
+        pr, q, ru = _int(), _int(), _int()
+        kn = C.c_uint64()
+        self.ctx.check(lib().eo_server_stats(self.h, C.byref(r), C.byref(p), C.byref(pr), C.byref(q), C.byref(ru),
+                                             C.byref(kn)))
+        return {"resident": r.value, "peak_inflight": p.value, "peak_running": pr.value, "queued": q.value,
+                "running": ru.value, "kernels": kn.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().eo_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def admission_simulate(budget, slots, resident, basis, nbytes, arrival, duration):
+    """The server's admission policy on the host (eo_admission_simulate):
+    returns (start times, peak running).  No GPU needed."""
+    import numpy as np
+    n = len(basis)
+    b = np.ascontiguousarray(basis, dtype=np.int32)
+    by = np.ascontiguousarray(nbytes, dtype=np.int64)
+    a = np.ascontiguousarray(arrival, dtype=np.float64)
+    d = np.ascontiguousarray(duration, dtype=np.float64)
+    start = np.zeros(n, dtype=np.float64)
+    peak = lib().eo_admission_simulate(int(budget), int(slots), int(resident), n, b.ctypes.data, by.ctypes.data,
+                                       a.ctypes.data, d.ctypes.data, start.ctypes.data)
+    if peak < 0:
+        raise ValueError("bad arguments to eo_admission_simulate")
+    return start, peak

@@ -79,6 +79,12 @@ eo_status ensure_scratch(eo_ctx* c, size_t parts_bytes) {
   return EO_OK;
 }
 
+}  // namespace
+
+eo_status reserve_scratch(eo_ctx* c, size_t parts_bytes) { return ensure_scratch(c, parts_bytes); }
+
+namespace {
+
 DevStatus* status_of(eo_ctx* c) { return reinterpret_cast<DevStatus*>(static_cast<char*>(c->scratch) + kOffStatus); }
 SmallWs* ws_of(eo_ctx* c) { return reinterpret_cast<SmallWs*>(static_cast<char*>(c->scratch) + kOffWs); }
 double* c_hi_of(eo_ctx* c) { return reinterpret_cast<double*>(static_cast<char*>(c->scratch) + kOffC); }

@@ -60,6 +60,8 @@ struct DeviceGuard {
 eo_status fail(eo_ctx* c, eo_status s, const char* fmt, const char* a = "", long long b = 0);
 eo_status cuda_fail(eo_ctx* c, const char* where, cudaError_t e);
 bool valid_prec(int p);
+// Grows the context's scratch to hold parts_bytes of partial sums (may synchronize its stream).
+eo_status reserve_scratch(eo_ctx* c, size_t parts_bytes);
 // Mode of the FP64-pipe kernels for a precision (EO_DD_EFT runs them in DD).
 inline Mode pipe_mode(eo_prec p) { return p == EO_DD_EFT ? MODE_DD : (Mode)p; }
 
