@@ -69,6 +69,13 @@ def lib():
             L.eoq_svqb.argtypes = [_i64, _int, _p, _i64, _p, _p, _int, _dbl, _int, _p, _p, _int]
             L.eoq_svqb.restype = _int
             L.eoq_orth_err.argtypes = [_i64, _int, _p, _i64, _p]
+            L.eoq_orth_err_diag.argtypes = [_i64, _int, _p, _i64, _p, _p]
+            L.eoq_cholqr_b.argtypes = [_i64, _int, _p, _i64, _p, _i64, _int, _p, _p, _int]
+            L.eoq_cholqr_b.restype = _int
+            L.eoq_svqb_b.argtypes = [_i64, _int, _p, _i64, _p, _i64, _dbl, _int, _p, _p, _int]
+            L.eoq_svqb_b.restype = _int
+            L.eoq_project_b.argtypes = [_i64, _int, _p, _i64, _p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int,
+                                        _p, _p, _int]
             L.eoq_cross_err.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64]
             L.eoq_cross_err.restype = _dbl
             L.eoq_fact_err.argtypes = [_i64, _int, _p, _i64, _p, _i64, _p, _p, _int]
@@ -219,6 +226,55 @@ def svqb(x, passes=1, tol=0.0, m=None):
     rank = lib().eoq_svqb(n, k, _ptr(q), n, _ptr(mh), _ptr(ml), k, float(tol), int(passes),
                           _ptr(z_hi), _ptr(z_lo), k)
     return q, (z_hi, z_lo), int(rank)
+
+
+def cholqr_b(x, p, passes=1):
+    """(Q, BQ, (R_hi, R_lo), info): CholQR in the inner product <x, y>_B given
+    P = B X (M = sym(X^T P); X and P both updated by Z = R^{-1}), binary128."""
+    q = _f64(x).copy(order="F")
+    bq = _f64(p).copy(order="F")
+    n, k = q.shape
+    r_hi, r_lo = _sq(k)
+    info = lib().eoq_cholqr_b(n, k, _ptr(q), n, _ptr(bq), n, int(passes), _ptr(r_hi), _ptr(r_lo), k)
+    return q, bq, (r_hi, r_lo), int(info)
+
+
+def svqb_b(x, p, passes=1, tol=0.0):
+    """(Q, BQ, (Z_hi, Z_lo), rank): SVQB in the inner product <x, y>_B given P = B X, binary128."""
+    q = _f64(x).copy(order="F")
+    bq = _f64(p).copy(order="F")
+    n, k = q.shape
+    z_hi, z_lo = _sq(k)
+    rank = lib().eoq_svqb_b(n, k, _ptr(q), n, _ptr(bq), n, float(tol), int(passes), _ptr(z_hi), _ptr(z_lo), k)
+    return q, bq, (z_hi, z_lo), int(rank)
+
+
+def project_b(w, bw, x, p, with_gram=True):
+    """(Xt, Pt, (C_hi, C_lo), (M_hi, M_lo) or None): B-projection against a
+    B-orthonormal W with BW = B W: C = BW^T X, Xt = X - W C, Pt = P - BW C
+    (rounded once), M = sym(Xt^T Pt), binary128."""
+    w = _f64(w)
+    bw = _f64(bw)
+    xt = _f64(x).copy(order="F")
+    pt = _f64(p).copy(order="F")
+    n, kv = w.shape
+    k = xt.shape[1]
+    chi = np.zeros((kv, k), order="F")
+    clo = np.zeros((kv, k), order="F")
+    mhi, mlo = _sq(k) if with_gram else (None, None)
+    lib().eoq_project_b(n, kv, _ptr(w), n, _ptr(bw), n, k, _ptr(xt), n, _ptr(pt), n, _ptr(chi), _ptr(clo), kv,
+                        _ptr(mhi), _ptr(mlo), k)
+    return xt, pt, (chi, clo), ((mhi, mlo) if with_gram else None)
+
+
+def orth_err_diag(q, d):
+    """(2-norm, Frobenius, max-abs) of Q^T diag(d) Q - I, binary128."""
+    q = _f64(q)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    n, k = q.shape
+    out = np.zeros(3)
+    lib().eoq_orth_err_diag(n, k, _ptr(q), n, _ptr(d), _ptr(out))
+    return tuple(float(v) for v in out)
 
 
 def orth_err(q):

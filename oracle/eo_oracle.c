@@ -24,6 +24,14 @@
  *                  Z = U Lambda^{-1/2} U^T = M^{-1/2}                 (Sec. 4.2, SVQB with the
  *                                                                      Frobenius-optimal Z of the
  *                                                                      Procrustes argument)
+ *   eoq_cholqr_b, eoq_svqb_b, eoq_project_b
+ *                  the same with the inner product <x, y>_B = x^T B y of
+ *                  a symmetric positive definite B, given through P = B X:
+ *                  M = the symmetric part of X^T P, and every transform Z
+ *                  applied to X is applied to P as well               (Sec. 4.2, closing remark:
+ *                                                                      the method extends to
+ *                                                                      B-inner products)
+ *   eoq_orth_err_diag  ||Q^T D Q - I|| for a diagonal B = D            (B-orthonormality)
  *   eoq_orth_err   ||Q^T Q - I|| in 2-norm, Frobenius and max-abs     (Fig. "Accuracy after one iteration")
  *   eoq_cross_err  ||W^T Q||_2                                        (same figure, left panel)
  *   eoq_fact_err   ||X - Q R||_F / ||X||_F                            (definition of a QR factorization)
@@ -417,14 +425,143 @@ int eoq_svqb(int64_t n, int k, double* X, int64_t ldx, const double* M_hi, const
   return rank;
 }
 
+/* ------------------------------------------------------- B-inner products */
+
+/* M = (X^T P + P^T X) / 2: the Gram matrix of <x, y>_B = x^T B y from the
+ * given P = B X (the two triangles of X^T P differ only by the rounding of P). */
+static void q_gram_b(int64_t n, int k, const double* X, int64_t ldx, const double* P, int64_t ldp, qreal* M) {
+  qreal* G = qalloc((size_t)k * k);
+#pragma omp parallel for collapse(2) schedule(dynamic)
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      qreal s = 0;
+      for (int64_t r = 0; r < n; ++r) s += (qreal)AT(X, ldx, r, i) * (qreal)AT(P, ldp, r, j);
+      G[(size_t)j * k + i] = s;
+    }
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) M[(size_t)j * k + i] = (G[(size_t)j * k + i] + G[(size_t)i * k + j]) / 2;
+  free(G);
+}
+
+/* B-CholQR: per pass, M = sym(X^T P), M = R^T R, Z = R^{-1}, X <- X Z and
+ * P <- P Z (each rounded once).  Returns 0 or the breakdown column. */
+int eoq_cholqr_b(int64_t n, int k, double* X, int64_t ldx, double* P, int64_t ldp, int passes, double* R_hi,
+                 double* R_lo, int ldr) {
+  size_t kk = (size_t)k * k;
+  qreal *M = qalloc(kk), *R = qalloc(kk), *Z = qalloc(kk), *Rt = qalloc(kk), *T = qalloc(kk);
+  for (int i = 0; i < k; ++i) Rt[(size_t)i * k + i] = 1;
+  int info = 0;
+  for (int p = 0; p < passes; ++p) {
+    q_gram_b(n, k, X, ldx, P, ldp, M);
+    info = q_cholesky(k, M, R);
+    if (info) break;
+    q_triinv(k, R, Z);
+    q_update(n, k, X, ldx, Z);
+    q_update(n, k, P, ldp, Z);
+    q_trmul(k, R, Rt, T);
+    memcpy(Rt, T, sizeof(qreal) * kk);
+  }
+  if (R_hi) store_dd(k, Rt, R_hi, R_lo, ldr);
+  free(M); free(R); free(Z); free(Rt); free(T);
+  return info;
+}
+
+/* B-SVQB: per pass, M = sym(X^T P), Z = M^{-1/2}, X <- X Z, P <- P Z.
+ * Z_out gets the product of the passes' transforms; returns the last rank. */
+int eoq_svqb_b(int64_t n, int k, double* X, int64_t ldx, double* P, int64_t ldp, double tol, int passes,
+               double* Z_hi, double* Z_lo, int ldz) {
+  size_t kk = (size_t)k * k;
+  qreal *M = qalloc(kk), *Z = qalloc(kk), *Zt = qalloc(kk), *T = qalloc(kk);
+  for (int i = 0; i < k; ++i) Zt[(size_t)i * k + i] = 1;
+  int rank = k;
+  for (int p = 0; p < passes; ++p) {
+    q_gram_b(n, k, X, ldx, P, ldp, M);
+    rank = q_svqb_z(k, M, (qreal)tol, Z);
+    q_update(n, k, X, ldx, Z);
+    q_update(n, k, P, ldp, Z);
+    for (int j = 0; j < k; ++j)
+      for (int i = 0; i < k; ++i) {
+        qreal s = 0;
+        for (int l = 0; l < k; ++l) s += Zt[(size_t)l * k + i] * Z[(size_t)j * k + l];
+        T[(size_t)j * k + i] = s;
+      }
+    memcpy(Zt, T, sizeof(qreal) * kk);
+  }
+  if (Z_hi) store_dd(k, Zt, Z_hi, Z_lo, ldz);
+  free(M); free(Z); free(Zt); free(T);
+  return rank;
+}
+
+/* B-projection against a B-orthonormal W with BW = B W: C = (BW)^T X,
+ * X <- X - W C and P <- P - BW C (each entry summed in binary128 and rounded
+ * once, in place), then M = sym(X^T P) of the rounded results.  C and M leave
+ * as double-double pairs (M_hi may be NULL). */
+void eoq_project_b(int64_t n, int kv, const double* W, int64_t ldw, const double* BW, int64_t ldbw, int k,
+                   double* X, int64_t ldx, double* P, int64_t ldp, double* C_hi, double* C_lo, int ldc,
+                   double* M_hi, double* M_lo, int ldm) {
+  qreal* C = qalloc((size_t)kv * k);
+#pragma omp parallel for collapse(2) schedule(dynamic)
+  for (int i = 0; i < kv; ++i)
+    for (int j = 0; j < k; ++j) {
+      qreal s = 0;
+      for (int64_t r = 0; r < n; ++r) s += (qreal)AT(BW, ldbw, r, i) * (qreal)AT(X, ldx, r, j);
+      C[(size_t)j * kv + i] = s;
+    }
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < n; ++r)
+    for (int j = 0; j < k; ++j) {
+      qreal sx = (qreal)AT(X, ldx, r, j), sp = (qreal)AT(P, ldp, r, j);
+      for (int i = 0; i < kv; ++i) {
+        sx -= (qreal)AT(W, ldw, r, i) * C[(size_t)j * kv + i];
+        sp -= (qreal)AT(BW, ldbw, r, i) * C[(size_t)j * kv + i];
+      }
+      AT(X, ldx, r, j) = (double)sx;
+      AT(P, ldp, r, j) = (double)sp;
+    }
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i < kv; ++i) q_to_dd(C[(size_t)j * kv + i], &AT(C_hi, ldc, i, j), &AT(C_lo, ldc, i, j));
+  if (M_hi) {
+    qreal* M = qalloc((size_t)k * k);
+    q_gram_b(n, k, X, ldx, P, ldp, M);
+    store_dd(k, M, M_hi, M_lo, ldm);
+    free(M);
+  }
+  free(C);
+}
+
 /* --------------------------------------------------------------- measures */
+
+/* ||Q^T D Q - I|| (2-norm, Frobenius, max-abs) for a diagonal B = diag(d), in binary128. */
+void eoq_orth_err_diag(int64_t n, int k, const double* Q, int64_t ldq, const double* d, double* out);
 
 /* E = Q^T Q - I in binary128; out[0] = ||E||_2 (largest |eigenvalue| of the
  * symmetric E, by Jacobi), out[1] = ||E||_F, out[2] = max |E_ij|. */
+static void q_err_norms(int k, qreal* E, double* out);
+
 void eoq_orth_err(int64_t n, int k, const double* Q, int64_t ldq, double* out) {
-  size_t kk = (size_t)k * k;
-  qreal *E = qalloc(kk), *U = qalloc(kk), *lam = qalloc(k);
+  qreal* E = qalloc((size_t)k * k);
   q_gram_sym(n, k, Q, ldq, E);
+  q_err_norms(k, E, out);
+  free(E);
+}
+
+void eoq_orth_err_diag(int64_t n, int k, const double* Q, int64_t ldq, const double* d, double* out) {
+  qreal* E = qalloc((size_t)k * k);
+#pragma omp parallel for collapse(2) schedule(dynamic)
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) {
+      qreal s = 0;
+      for (int64_t r = 0; r < n; ++r) s += (qreal)AT(Q, ldq, r, i) * (qreal)d[r] * (qreal)AT(Q, ldq, r, j);
+      E[(size_t)j * k + i] = s;
+    }
+  q_err_norms(k, E, out);
+  free(E);
+}
+
+/* out = (||E - I||_2, ||E - I||_F, max |E - I|) for a symmetric k-by-k E (overwritten). */
+static void q_err_norms(int k, qreal* E, double* out) {
+  size_t kk = (size_t)k * k;
+  qreal *U = qalloc(kk), *lam = qalloc(k);
   for (int i = 0; i < k; ++i) E[(size_t)i * k + i] -= 1;
   qreal fro = 0, mx = 0;
   for (size_t t = 0; t < kk; ++t) {
@@ -437,7 +574,7 @@ void eoq_orth_err(int64_t n, int k, const double* Q, int64_t ldq, double* out) {
   out[0] = (double)two;
   out[1] = (double)qsqrt(fro);
   out[2] = (double)mx;
-  free(E); free(U); free(lam);
+  free(U); free(lam);
 }
 
 /* ||W^T Q||_2 = sqrt(largest eigenvalue of (W^T Q)^T (W^T Q)), binary128. */

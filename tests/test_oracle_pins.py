@@ -428,3 +428,86 @@ def test_hadamard_basis_is_exactly_orthonormal():
     assert set(np.unique(np.abs(w))) == {0.125}
     hi, lo = oracle.gram(w)
     assert np.array_equal(hi, np.eye(10)) and not np.any(lo)
+
+
+# ------------------------------------------------------ B-inner products
+# With B = diag(d) and every d a power of four, sqrt(d) is a power of two, so
+# scaling by it commutes with every rounding: the B-orthogonalization of X
+# (given P = B X) must equal D^{-1/2} times the Euclidean one of sqrt(D) X,
+# bit for bit, with the same R (or Z).  B = I must reproduce the Euclidean
+# functions exactly.  These tie the B-variants to the independently pinned
+# Euclidean oracle (and would fail for a transposed X^T P, a missing update
+# of P, or a wrong symmetrization).
+
+def pow4_diag(n, seed):
+    g = np.random.default_rng(seed)
+    return 4.0 ** g.integers(-3, 4, n).astype(np.float64)
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+def test_cholqr_b_identity_is_cholqr(passes):
+    x = synth.conditioned(500, 6, 1e5, 61)
+    q, bq, (rh, rl), info = oracle.cholqr_b(x, x, passes=passes)
+    q2, (rh2, rl2), info2 = oracle.cholqr(x, passes=passes)
+    assert info == info2 == 0
+    assert np.array_equal(q, q2) and np.array_equal(bq, q2)
+    assert np.array_equal(rh, rh2) and np.array_equal(rl, rl2)
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+def test_cholqr_b_diagonal_is_scaled_cholqr(passes):
+    n, k = 700, 5
+    x = synth.conditioned(n, k, 1e6, 62)
+    d = pow4_diag(n, 63)
+    s = np.sqrt(d)
+    q, bq, (rh, rl), info = oracle.cholqr_b(x, d[:, None] * x, passes=passes)
+    qs, (rhs, rls), infos = oracle.cholqr(s[:, None] * x, passes=passes)
+    assert info == infos == 0
+    assert np.array_equal(rh, rhs) and np.array_equal(rl, rls)
+    assert np.array_equal(q, qs / s[:, None])
+    assert np.array_equal(bq, d[:, None] * q)
+    assert oracle.orth_err_diag(q, d)[0] <= 1e-14
+
+
+def test_svqb_b_diagonal_is_scaled_svqb():
+    n, k = 600, 4
+    x = synth.conditioned(n, k, 1e4, 64)
+    d = pow4_diag(n, 65)
+    s = np.sqrt(d)
+    q, bq, (zh, zl), rank = oracle.svqb_b(x, d[:, None] * x, passes=2)
+    qs, (zhs, zls), ranks = oracle.svqb(s[:, None] * x, passes=2)
+    assert rank == ranks == k
+    assert np.array_equal(zh, zhs) and np.array_equal(zl, zls)
+    assert np.array_equal(q, qs / s[:, None])
+
+
+def test_project_b_diagonal_is_scaled_project():
+    n, kv, k = 512, 6, 3
+    d = pow4_diag(n, 66)
+    s = np.sqrt(d)
+    wt = synth.orthonormal_basis(n, kv, 67)      # Euclidean-orthonormal
+    w, bw = wt / s[:, None], wt * s[:, None]     # B-orthonormal W and B W, exactly
+    x = synth.gaussian(n, k, 68)
+    xt, pt, (ch, cl), (mh, ml) = oracle.project_b(w, bw, x, d[:, None] * x)
+    yt, (ch2, cl2), (mh2, ml2) = oracle.project(wt, s[:, None] * x)
+    assert np.array_equal(ch, ch2) and np.array_equal(cl, cl2)
+    assert np.array_equal(xt, yt / s[:, None]) and np.array_equal(pt, yt * s[:, None])
+    assert np.array_equal(mh, mh2) and np.array_equal(ml, ml2)
+
+
+def test_gram_b_takes_the_symmetric_part():
+    # P not equal to B X for any symmetric B: M must be (X^T P + P^T X) / 2
+    g = np.random.default_rng(69)
+    x = g.standard_normal((40, 3))
+    p = g.standard_normal((40, 3))
+    xt, pt, (ch, cl), (mh, ml) = oracle.project_b(np.zeros((40, 1)), np.zeros((40, 1)), x, p)
+    assert np.array_equal(xt, x) and np.array_equal(pt, p) and not ch.any()
+    ex = exact_gram(x, p)
+    for i in range(3):
+        for j in range(3):
+            assert dd_fr(mh, ml, i, j) == pytest.approx((ex[i][j] + ex[j][i]) / 2, rel=2.0 ** -104, abs=0)
+
+
+def test_orth_err_diag_with_unit_weights_is_orth_err():
+    q = synth.conditioned(300, 4, 10.0, 70)
+    assert oracle.orth_err_diag(q, np.ones(300)) == oracle.orth_err(q)
