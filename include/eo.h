@@ -191,6 +191,30 @@ EO_API eo_status eo_orthogonalize(eo_ctx* ctx, int64_t n, int kv, const double* 
                                   int* rank_dev);
 
 /*
+ * B-inner products (Sec. 4.2, closing remark: the technique extends to
+ * <x, y>_B = x^T B y, as needed for generalized eigenproblems).  B is
+ * symmetric positive definite and is never applied here: the caller passes
+ * P = B X next to X (the product with B is the caller's, e.g. a sparse
+ * matrix-vector product).  The Gram matrix is M = (X^T P + P^T X) / 2 (the
+ * two triangles of X^T P differ only by the rounding of P), and every
+ * transform Z applied to X is applied to P as well, so on return P = B Q up
+ * to rounding and Q^T B Q = I.  Layout, passes, modes and outputs as in
+ * eo_cholqr / eo_svqb / eo_project; X and BX (Y and BY) must not alias.
+ *   eo_cholqr_b:  X <- Q, BX <- BX R^{-1} per pass; R_hi/R_lo, info_dev.
+ *   eo_svqb_b:    X <- X Z, BX <- BX Z with Z = M^{-1/2}; Z_hi/Z_lo, rank_dev.
+ *   eo_project_b: against a B-orthonormal W given with BW = B W:
+ *                 C = BW^T Y, Y <- Y - W C, BY <- BY - BW C (in place), and
+ *                 optionally M = sym(Y^T BY) of the results.  FP64 data only.
+ */
+EO_API eo_status eo_cholqr_b(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, void* BX, int64_t ldbx,
+                             double* R_hi, double* R_lo, int ldr, int passes, eo_prec prec, int* info_dev);
+EO_API eo_status eo_svqb_b(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, void* BX, int64_t ldbx,
+                           double* Z_hi, double* Z_lo, int ldz, double tol, int passes, eo_prec prec, int* rank_dev);
+EO_API eo_status eo_project_b(eo_ctx* ctx, int64_t n, int kv, const double* W, int64_t ldw, const double* BW,
+                              int64_t ldbw, int k, double* Y, int64_t ldy, double* BY, int64_t ldby, double* C_hi,
+                              double* C_lo, int ldc, double* M_hi, double* M_lo, int ldm, eo_prec prec);
+
+/*
  * Batched orthogonalization (no counterpart in the paper, whose solvers
  * orthogonalize one block at a time): many independent blocks of uneven n and
  * k, each orthogonalized by the kernels of one eo_svqb (EO_BATCH_SVQB) or

@@ -68,6 +68,10 @@ def lib():
         L.eo_cholqr.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _int, _int, _p]
         L.eo_svqb.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _dbl, _int, _int, _p]
         L.eo_gram_dd_noalloc.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int, _p]
+        L.eo_cholqr_b.argtypes = [_p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _int, _int, _p]
+        L.eo_svqb_b.argtypes = [_p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _dbl, _int, _int, _p]
+        L.eo_project_b.argtypes = [_p, _i64, _int, _p, _i64, _p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _p,
+                                   _p, _int, _int]
         L.eo_tune_cache.argtypes = [_p, C.c_char_p]
         L.eo_batch_create.argtypes = [_p, _int, C.POINTER(Block), _int, _dbl, _int, _int, _p, _int, _int,
                                       C.POINTER(_p)]
@@ -92,6 +96,7 @@ def lib():
         L.eo_batch_branches.restype = _int
         for f in ("eo_create", "eo_destroy", "eo_set_stream", "eo_gram", "eo_project", "eo_project_apply",
                   "eo_cholqr", "eo_svqb", "eo_orthogonalize", "eo_gram_dd_noalloc", "eo_tune_cache",
+                  "eo_cholqr_b", "eo_svqb_b", "eo_project_b",
                   "eo_batch_create", "eo_batch_run", "eo_batch_destroy", "eo_batch_tile", "eo_batch_passes",
                   "eo_server_create", "eo_server_destroy", "eo_server_add_basis", "eo_server_submit",
                   "eo_server_wait", "eo_server_poll", "eo_server_stats"):
@@ -286,6 +291,60 @@ def svqb(ctx: Context, X, passes: int = 1, prec: int = DD, tol: float = -1.0, M=
                             None if ml is None else ml.data_ptr(), ldm, zh.data_ptr(), zl.data_ptr(), _ld(zh),
                             float(tol), int(passes), prec, rank.data_ptr()))
     return zh, zl, rank
+
+
+def cholqr_b(ctx: Context, X, BX, passes: int = 1, prec: int = DD, info=None):
+    """CholQR in the B-inner product, given BX = B X: in place X <- Q,
+    BX <- B Q.  Returns (R_hi, R_lo, info)."""
+    import torch
+    X, n, k, ldx = _mat(X, "X", _dtype(prec))
+    BX, nb, kb, ldbx = _mat(BX, "BX", _dtype(prec))
+    if (nb, kb) != (n, k):
+        raise ValueError("X and BX must have the same shape")
+    rh, rl = _small(k, k, X.device)
+    if info is None:
+        info = torch.zeros(1, dtype=torch.int32, device=X.device)
+    ctx.set_stream()
+    ctx.check(lib().eo_cholqr_b(ctx.h, n, k, X.data_ptr(), ldx, BX.data_ptr(), ldbx, rh.data_ptr(), rl.data_ptr(),
+                                _ld(rh), int(passes), prec, info.data_ptr()))
+    return rh, rl, info
+
+
+def svqb_b(ctx: Context, X, BX, passes: int = 1, prec: int = DD, tol: float = -1.0, rank=None):
+    """SVQB in the B-inner product, given BX = B X: in place X <- X Z,
+    BX <- BX Z.  Returns (Z_hi, Z_lo, rank)."""
+    import torch
+    X, n, k, ldx = _mat(X, "X", _dtype(prec))
+    BX, nb, kb, ldbx = _mat(BX, "BX", _dtype(prec))
+    if (nb, kb) != (n, k):
+        raise ValueError("X and BX must have the same shape")
+    zh, zl = _small(k, k, X.device)
+    if rank is None:
+        rank = torch.zeros(1, dtype=torch.int32, device=X.device)
+    ctx.set_stream()
+    ctx.check(lib().eo_svqb_b(ctx.h, n, k, X.data_ptr(), ldx, BX.data_ptr(), ldbx, zh.data_ptr(), zl.data_ptr(),
+                              _ld(zh), float(tol), int(passes), prec, rank.data_ptr()))
+    return zh, zl, rank
+
+
+def project_b(ctx: Context, W, BW, Y, BY, prec: int = DD, want_m: bool = True):
+    """B-projection in place: C = BW^T Y, Y <- Y - W C, BY <- BY - BW C.
+    Returns ((C_hi, C_lo), (M_hi, M_lo) or None) with M = sym(Y^T BY)."""
+    import torch
+    W, n, kv, ldw = _mat(W, "W", torch.float64)
+    BW, n2, kv2, ldbw = _mat(BW, "BW", torch.float64)
+    Y, n3, k, ldy = _mat(Y, "Y", torch.float64)
+    BY, n4, k2, ldby = _mat(BY, "BY", torch.float64)
+    if not (n == n2 == n3 == n4 and kv == kv2 and k == k2):
+        raise ValueError("W, BW and Y, BY must match in shape")
+    ch, cl = _small(kv, k, W.device)
+    mh, ml = _small(k, k, W.device) if want_m else (None, None)
+    ctx.set_stream()
+    ctx.check(lib().eo_project_b(ctx.h, n, kv, W.data_ptr(), ldw, BW.data_ptr(), ldbw, k, Y.data_ptr(), ldy,
+                                 BY.data_ptr(), ldby, ch.data_ptr(), cl.data_ptr(), _ld(ch),
+                                 None if mh is None else mh.data_ptr(), None if ml is None else ml.data_ptr(), k,
+                                 prec))
+    return (ch, cl), ((mh, ml) if want_m else None)
 
 
 def orthogonalize(ctx: Context, V, Y, eps: float = 1e-10, max_iter: int = 8, prec: int = DD, tol: float = -1.0):

@@ -130,8 +130,10 @@ int dd_gram_ctas(int64_t n, int kx, int ky, bool sym, int ctas) {
   return use_umma_gram(kx, sym ? kx : ky) ? umma_gram_ctas(n, kx, ky, sym, ctas) : fx_gram_ctas(n, kx, ky, sym, ctas);
 }
 
-size_t orth_scratch(int64_t n, int k, eo_prec prec) {
-  return prec == EO_DD ? dd_gram_scratch(n, k, k, true) : gram_scratch_bytes(n, k, k, true);
+size_t orth_scratch(int64_t n, int k, eo_prec prec, bool b_inner) {
+  const size_t s = prec == EO_DD ? dd_gram_scratch(n, k, k, true) : gram_scratch_bytes(n, k, k, true);
+  if (!b_inner) return s;
+  return std::max(s, prec == EO_DD ? dd_gram_scratch(n, k, k, false) : gram_scratch_bytes(n, k, k, false));
 }
 
 cudaError_t enqueue_orth_step(const OrthArgs& a, const OrthRes& r, int p, OrthStep step, uint64_t* launches) {
@@ -143,18 +145,25 @@ cudaError_t enqueue_orth_step(const OrthArgs& a, const OrthRes& r, int p, OrthSt
   const int npass = a.passes == 1 ? 1 : 2;
   cudaError_t e = cudaSuccess;
   switch (step) {
-    case OrthStep::kGram:
+    case OrthStep::kGram: {
       if (p == 0 && a.M_hi) return cudaSuccess;  // the caller's Gram matrix
+      const bool b = a.P != nullptr;             // X^T P, then its symmetric part
+      const void* Y = b ? a.P : a.X;
+      const int64_t ldy = b ? a.ldp : a.ldx;
       if (fx) {
-        const double* X = static_cast<const double*>(a.X);
-        e = launch_dd_gram(a.n, a.k, X, a.ldx, a.k, X, a.ldx, true, r.parts, ws->Mh, ws->Ml, KMAX, &st->gate[2 * p],
-                           r.stream, r.tile.gram);
+        e = launch_dd_gram(a.n, a.k, static_cast<const double*>(a.X), a.ldx, a.k, static_cast<const double*>(Y), ldy,
+                           !b, r.parts, ws->Mh, ws->Ml, KMAX, &st->gate[2 * p], r.stream, r.tile.gram);
       } else {
-        e = launch_gram(mode, a.n, a.k, a.X, a.ldx, a.k, a.X, a.ldx, true, r.parts, ws->Mh, ws->Ml, KMAX,
-                        &st->gate[2 * p], r.stream);
+        e = launch_gram(mode, a.n, a.k, a.X, a.ldx, a.k, Y, ldy, !b, r.parts, ws->Mh, ws->Ml, KMAX, &st->gate[2 * p],
+                        r.stream);
       }
       *launches += kGramLaunches;
+      if (e == cudaSuccess && b) {
+        e = launch_symmetrize(a.k, ws->Mh, ws->Ml, KMAX, &st->gate[2 * p], r.stream);
+        *launches += 1;
+      }
       return e;
+    }
     case OrthStep::kSmall: {
       const bool given = p == 0 && a.M_hi;
       const double* mh = given ? a.M_hi : ws->Mh;
@@ -169,10 +178,14 @@ cudaError_t enqueue_orth_step(const OrthArgs& a, const OrthRes& r, int p, OrthSt
       return e;
     }
     case OrthStep::kUpdate:
-      e = fx ? launch_fx_update(a.n, a.k, static_cast<double*>(a.X), a.ldx, ws->Zh, ws->Zl, a.chol,
-                                &st->gate[2 * p + 1], r.stream, r.tile.row)
-             : launch_update(mode, a.n, a.k, a.X, a.ldx, ws->Zh, ws->Zl, a.chol, &st->gate[2 * p + 1], r.stream);
-      *launches += 1;
+      for (int t = 0; t < (a.P ? 2 : 1) && e == cudaSuccess; ++t) {  // X, then P with the same Z
+        void* A = t ? a.P : a.X;
+        const int64_t lda = t ? a.ldp : a.ldx;
+        e = fx ? launch_fx_update(a.n, a.k, static_cast<double*>(A), lda, ws->Zh, ws->Zl, a.chol,
+                                  &st->gate[2 * p + 1], r.stream, r.tile.row)
+               : launch_update(mode, a.n, a.k, A, lda, ws->Zh, ws->Zl, a.chol, &st->gate[2 * p + 1], r.stream);
+        *launches += 1;
+      }
       return e;
   }
   return cudaErrorInvalidValue;
@@ -233,7 +246,7 @@ size_t apply_scratch(int64_t n, int kv, int k, eo_prec prec) {
 template <bool CHOL>
 eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, int64_t ldx, const double* M_hi,
                       const double* M_lo, int ldm, double* O_hi, double* O_lo, int ldo, double tol, int passes,
-                      eo_prec prec, int* out_dev) {
+                      eo_prec prec, int* out_dev, void* P = nullptr, int64_t ldp = 0) {
   if (!ctx) return EO_EINVAL;
   ctx->err.clear();
   EO_CHECK(valid_prec(prec), EO_EINVAL, "%s: bad precision mode %lld", name, (long long)prec);
@@ -245,9 +258,11 @@ eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, 
   EO_CHECK(passes >= 0 && passes <= 2, EO_EINVAL, "%s: passes must be 0, 1 or 2 (%lld)", name, (long long)passes);
   DeviceGuard g(ctx->device);
   EO_CHECK(g.ok, EO_ECUDA, "%s: cannot select device", name);
-  eo_status s = ensure_scratch(ctx, orth_scratch(n, k, prec));
+  eo_status s = ensure_scratch(ctx, orth_scratch(n, k, prec, P != nullptr));
   if (s != EO_OK) return s;
-  const OrthArgs a{CHOL, n, k, X, ldx, M_hi, M_lo, ldm, O_hi, O_lo, ldo, tol, passes, prec, out_dev};
+  OrthArgs a{CHOL, n, k, X, ldx, M_hi, M_lo, ldm, O_hi, O_lo, ldo, tol, passes, prec, out_dev};
+  a.P = P;
+  a.ldp = ldp;
   const OrthRes r{status_of(ctx), ws_of(ctx), parts_of(ctx), ctx->stream, Tile{}};
   const char* where = "";
   cudaError_t e = enqueue_orth(a, r, &ctx->launches, &where);
@@ -405,6 +420,82 @@ eo_status eo_svqb(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, const dou
                   int ldm, double* Z_hi, double* Z_lo, int ldz, double tol, int passes, eo_prec prec, int* rank_dev) {
   return orth_common<false>(ctx, "eo_svqb", n, k, X, ldx, M_hi, M_lo, ldm, Z_hi, Z_lo, ldz, tol, passes, prec,
                             rank_dev);
+}
+
+eo_status eo_cholqr_b(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, void* BX, int64_t ldbx, double* R_hi,
+                      double* R_lo, int ldr, int passes, eo_prec prec, int* info_dev) {
+  if (!ctx) return EO_EINVAL;
+  EO_CHECK(BX != nullptr || n == 0, EO_EINVAL, "eo_cholqr_b: null BX%s", "");
+  EO_CHECK(ldbx >= std::max<int64_t>(1, n), EO_EINVAL, "eo_cholqr_b: ldbx too small%s", "");
+  EO_CHECK(BX != X || n == 0, EO_EINVAL, "eo_cholqr_b: BX must not alias X (pass a copy for B = I)%s", "");
+  return orth_common<true>(ctx, "eo_cholqr_b", n, k, X, ldx, nullptr, nullptr, 0, R_hi, R_lo, ldr, 0.0, passes, prec,
+                           info_dev, BX, ldbx);
+}
+
+eo_status eo_svqb_b(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, void* BX, int64_t ldbx, double* Z_hi,
+                    double* Z_lo, int ldz, double tol, int passes, eo_prec prec, int* rank_dev) {
+  if (!ctx) return EO_EINVAL;
+  EO_CHECK(BX != nullptr || n == 0, EO_EINVAL, "eo_svqb_b: null BX%s", "");
+  EO_CHECK(ldbx >= std::max<int64_t>(1, n), EO_EINVAL, "eo_svqb_b: ldbx too small%s", "");
+  EO_CHECK(BX != X || n == 0, EO_EINVAL, "eo_svqb_b: BX must not alias X (pass a copy for B = I)%s", "");
+  return orth_common<false>(ctx, "eo_svqb_b", n, k, X, ldx, nullptr, nullptr, 0, Z_hi, Z_lo, ldz, tol, passes, prec,
+                            rank_dev, BX, ldbx);
+}
+
+eo_status eo_project_b(eo_ctx* ctx, int64_t n, int kv, const double* W, int64_t ldw, const double* BW, int64_t ldbw,
+                       int k, double* Y, int64_t ldy, double* BY, int64_t ldby, double* C_hi, double* C_lo, int ldc,
+                       double* M_hi, double* M_lo, int ldm, eo_prec prec) {
+  if (!ctx) return EO_EINVAL;
+  ctx->err.clear();
+  EO_CHECK(valid_prec(prec), EO_EINVAL, "eo_project_b: bad precision mode%s %lld", "", (long long)prec);
+  EO_CHECK(prec != EO_F32, EO_EUNSUPPORTED, "eo_project_b: FP32 inputs are not supported%s", "");
+  EO_CHECK(n >= 0 && kv >= 1 && kv <= KMAX && k >= 1 && k <= KMAX, EO_EINVAL, "eo_project_b: bad sizes%s", "");
+  EO_CHECK((W && BW && Y && BY) || n == 0, EO_EINVAL, "eo_project_b: null pointer%s", "");
+  EO_CHECK(Y != BY || n == 0, EO_EINVAL, "eo_project_b: BY must not alias Y%s", "");
+  const int64_t mn = std::max<int64_t>(1, n);
+  EO_CHECK(ldw >= mn && ldbw >= mn && ldy >= mn && ldby >= mn, EO_EINVAL,
+           "eo_project_b: leading dimension too small%s", "");
+  EO_CHECK(!(C_hi || C_lo) || ldc >= kv, EO_EINVAL, "eo_project_b: ldc too small%s", "");
+  EO_CHECK(!M_hi || ldm >= k, EO_EINVAL, "eo_project_b: ldm too small%s", "");
+  DeviceGuard g(ctx->device);
+  EO_CHECK(g.ok, EO_ECUDA, "eo_project_b: cannot select device%s", "");
+  const bool fx = prec == EO_DD;
+  const size_t need = fx ? std::max(dd_gram_scratch(n, kv, k, false), dd_gram_scratch(n, k, k, false))
+                         : std::max({gram_scratch_bytes(n, kv, k, false), gram_scratch_bytes(n, k, k, false),
+                                     project_scratch_bytes(n, kv, k)});
+  eo_status s = ensure_scratch(ctx, need);
+  if (s != EO_OK) return s;
+  double* ch = c_hi_of(ctx);
+  double* cl = c_lo_of(ctx);
+  const Mode mode = pipe_mode(prec);
+  // C = (B W)^T Y
+  if (fx)
+    EO_CUDA(launch_dd_gram(n, kv, BW, ldbw, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, nullptr, ctx->stream),
+            "eo_project_b (BW^T Y)");
+  else
+    EO_CUDA(launch_gram(mode, n, kv, BW, ldbw, k, Y, ldy, false, parts_of(ctx), ch, cl, KMAX, nullptr, ctx->stream),
+            "eo_project_b (BW^T Y)");
+  ctx->launches += kGramLaunches;
+  if (C_hi || C_lo) {
+    copy_small_kernel<<<4, 256, 0, ctx->stream>>>(kv, k, ch, cl, KMAX, C_hi, C_lo, ldc);
+    EO_CUDA(cudaGetLastError(), "eo_project_b (copy C)");
+    ctx->launches += 1;
+  }
+  // Y <- Y - W C and BY <- BY - BW C, in place
+  s = apply_projection(ctx, n, kv, W, ldw, k, Y, ldy, Y, ldy, ch, cl, KMAX, nullptr, nullptr, 0, prec);
+  if (s == EO_OK) s = apply_projection(ctx, n, kv, BW, ldbw, k, BY, ldby, BY, ldby, ch, cl, KMAX, nullptr, nullptr, 0,
+                                       prec);
+  if (s != EO_OK || !M_hi) return s;
+  // M = the symmetric part of Y^T (BY)
+  if (fx)
+    EO_CUDA(launch_dd_gram(n, k, Y, ldy, k, BY, ldby, false, parts_of(ctx), M_hi, M_lo, ldm, nullptr, ctx->stream),
+            "eo_project_b (Y^T BY)");
+  else
+    EO_CUDA(launch_gram(mode, n, k, Y, ldy, k, BY, ldby, false, parts_of(ctx), M_hi, M_lo, ldm, nullptr, ctx->stream),
+            "eo_project_b (Y^T BY)");
+  EO_CUDA(launch_symmetrize(k, M_hi, M_lo, ldm, nullptr, ctx->stream), "eo_project_b (symmetrize)");
+  ctx->launches += kGramLaunches + 1;
+  return EO_OK;
 }
 
 eo_status eo_orthogonalize(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ldv, int k, double* Y,

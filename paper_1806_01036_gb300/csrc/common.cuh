@@ -142,6 +142,9 @@ struct SmallGates {
 };
 
 cudaError_t launch_status_init(DevStatus* s, int k, cudaStream_t st);
+// M <- (M + M^T) / 2 in double-double (k-by-k, leading dimension ld; Ml may
+// be null), when *gate != 0 (gate may be null).
+cudaError_t launch_symmetrize(int k, double* Mh, double* Ml, int ld, const int* gate, cudaStream_t st);
 // One CholQR factorization step of pass `pass` (0 or 1): M -> R, Z = R^{-1},
 // T <- R T.  passes: 1, 2 or 0 (automatic).
 cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,

@@ -89,6 +89,10 @@ struct OrthArgs {
   int passes;
   eo_prec prec;
   int* out_dev;               // info (CholQR) or rank (SVQB)
+  // B-inner product <x, y>_B = x^T B y: P = B X (n-by-k, ldp) is given, the
+  // Gram matrix is the symmetric part of X^T P, and P is updated with X.
+  void* P = nullptr;
+  int64_t ldp = 0;
 };
 struct OrthRes {
   DevStatus* st;
@@ -97,7 +101,7 @@ struct OrthRes {
   cudaStream_t stream;
   Tile tile;
 };
-size_t orth_scratch(int64_t n, int k, eo_prec prec);
+size_t orth_scratch(int64_t n, int k, eo_prec prec, bool b_inner = false);
 // Enqueues the sequence; on a CUDA error returns it and names the step in *where.
 cudaError_t enqueue_orth(const OrthArgs& a, const OrthRes& r, uint64_t* launches, const char** where);
 // One step of pass p of the sequence (the status must have been initialized).

@@ -464,6 +464,25 @@ cudaError_t launch_converge(const int* run, const double* Ch, const double* Cl, 
   return cudaGetLastError();
 }
 
+__global__ void symmetrize_kernel(int k, double* Mh, double* Ml, int ld, const int* gate) {
+  if (gate && *gate == 0) return;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int i = t % k, j = t / k;
+    if (i >= j) continue;  // one thread per pair i < j
+    const size_t u = (size_t)j * ld + i, l = (size_t)i * ld + j;
+    dd s = dd_add(dd{Mh[u], Ml ? Ml[u] : 0.0}, dd{Mh[l], Ml ? Ml[l] : 0.0});
+    s.hi *= 0.5;  // halving is exact
+    s.lo *= 0.5;
+    Mh[u] = Mh[l] = s.hi;
+    if (Ml) Ml[u] = Ml[l] = s.lo;
+  }
+}
+
+cudaError_t launch_symmetrize(int k, double* Mh, double* Ml, int ld, const int* gate, cudaStream_t st) {
+  symmetrize_kernel<<<1, 256, 0, st>>>(k, Mh, Ml, ld, gate);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_status_init(DevStatus* s, int k, cudaStream_t st) {
   status_init_kernel<<<1, 32, 0, st>>>(s, k);
   return cudaGetLastError();
