@@ -285,6 +285,9 @@ EO_API eo_status eo_batch_tile(const eo_batch* batch, int block, int* gram_ctas,
 /* Passes each block took in the last run (1 or 2) into host int[nblocks];
  * waits for the context's stream. */
 EO_API eo_status eo_batch_passes(eo_batch* batch, int* passes_host);
+/* Jacobi sweeps of each block's last SVQB eigensolve in the last run (0 for
+ * CholQR; at most 40) into host int[nblocks]; waits for the context's stream. */
+EO_API eo_status eo_batch_sweeps(eo_batch* batch, int* sweeps_host);
 /* Kernels one eo_batch_run launches (-1 for NULL), and the graph's branches. */
 EO_API int64_t eo_batch_kernels(const eo_batch* batch);
 EO_API int eo_batch_branches(const eo_batch* batch);

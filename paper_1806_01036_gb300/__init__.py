@@ -79,6 +79,7 @@ def lib():
         L.eo_batch_destroy.argtypes = [_p]
         L.eo_batch_tile.argtypes = [_p, _int, C.POINTER(_int), C.POINTER(_int)]
         L.eo_batch_passes.argtypes = [_p, _p]
+        L.eo_batch_sweeps.argtypes = [_p, _p]
         _sz = C.c_size_t
         L.eo_server_create.argtypes = [_p, _sz, _int, C.POINTER(_p)]
         L.eo_server_destroy.argtypes = [_p]
@@ -97,7 +98,7 @@ def lib():
         for f in ("eo_create", "eo_destroy", "eo_set_stream", "eo_gram", "eo_project", "eo_project_apply",
                   "eo_cholqr", "eo_svqb", "eo_orthogonalize", "eo_gram_dd_noalloc", "eo_tune_cache",
                   "eo_cholqr_b", "eo_svqb_b", "eo_project_b",
-                  "eo_batch_create", "eo_batch_run", "eo_batch_destroy", "eo_batch_tile", "eo_batch_passes",
+                  "eo_batch_create", "eo_batch_run", "eo_batch_destroy", "eo_batch_tile", "eo_batch_passes", "eo_batch_sweeps",
                   "eo_server_create", "eo_server_destroy", "eo_server_add_basis", "eo_server_submit",
                   "eo_server_wait", "eo_server_poll", "eo_server_stats"):
             getattr(L, f).restype = _int
@@ -441,6 +442,13 @@ class Batch:
         out = (_int * len(self.blocks))()
         self.ctx.set_stream()
         self.ctx.check(lib().eo_batch_passes(self.h, C.cast(out, _p)))
+        return list(out)
+
+    def sweeps(self):
+        """Jacobi sweeps of each block's last SVQB eigensolve (0 for CholQR)."""
+        out = (_int * len(self.blocks))()
+        self.ctx.set_stream()
+        self.ctx.check(lib().eo_batch_sweeps(self.h, C.cast(out, _p)))
         return list(out)
 
     def kernels(self) -> int:

@@ -551,19 +551,29 @@ eo_status eo_batch_tile(const eo_batch* bt, int block, int* gram_ctas, int* row_
   return EO_OK;
 }
 
-eo_status eo_batch_passes(eo_batch* bt, int* passes_host) {
-  if (!bt || !passes_host) return EO_EINVAL;
+// One int of every block's status (at byte offset `off` of DevStatus) into host memory.
+static eo_status copy_status_field(eo_batch* bt, size_t off, int* host, const char* name) {
+  if (!bt || !host) return EO_EINVAL;
   eo_ctx* ctx = bt->ctx;
   ctx->err.clear();
   DeviceGuard g(ctx->device);
-  EO_CHECK(g.ok, EO_ECUDA, "eo_batch_passes: cannot select device%s", "");
-  EO_CUDA(cudaStreamSynchronize(ctx->stream), "eo_batch_passes (sync)");
+  EO_CHECK(g.ok, EO_ECUDA, "%s: cannot select device", name);
+  EO_CUDA(cudaStreamSynchronize(ctx->stream), name);
+  const char* src = static_cast<const char*>(bt->mem) + offsetof(Slot, st) + off;
+  EO_CUDA(cudaMemcpy2D(host, sizeof(int), src, bt->slot_bytes, sizeof(int), bt->nb, cudaMemcpyDeviceToHost), name);
+  return EO_OK;
+}
+
+eo_status eo_batch_passes(eo_batch* bt, int* passes_host) {
   // gate[2] of a block's status enables its second pass
-  const char* src = static_cast<const char*>(bt->mem) + offsetof(Slot, st) + offsetof(DevStatus, gate) + 2 * sizeof(int);
-  EO_CUDA(cudaMemcpy2D(passes_host, sizeof(int), src, bt->slot_bytes, sizeof(int), bt->nb, cudaMemcpyDeviceToHost),
-          "eo_batch_passes (copy)");
+  eo_status s = copy_status_field(bt, offsetof(DevStatus, gate) + 2 * sizeof(int), passes_host, "eo_batch_passes");
+  if (s != EO_OK) return s;
   for (int b = 0; b < bt->nb; ++b) passes_host[b] = passes_host[b] ? 2 : 1;
   return EO_OK;
+}
+
+eo_status eo_batch_sweeps(eo_batch* bt, int* sweeps_host) {
+  return copy_status_field(bt, offsetof(DevStatus, sweeps), sweeps_host, "eo_batch_sweeps");
 }
 
 int64_t eo_batch_kernels(const eo_batch* bt) { return bt ? (int64_t)bt->nodes : -1; }

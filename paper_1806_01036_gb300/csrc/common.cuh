@@ -39,7 +39,7 @@ struct DevStatus {
   int info;
   int rank;
   int iters;
-  int pad;
+  int sweeps;  // Jacobi sweeps of the last SVQB eigensolve (0: none ran)
   int gate[64];
 };
 

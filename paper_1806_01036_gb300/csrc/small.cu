@@ -19,6 +19,12 @@ namespace eo {
 namespace {
 
 constexpr int kThreads = 256;
+// Jacobi rotates a pair while |a_pq| > eps sqrt(|a_pp a_qq|).  The rotations
+// of a sweep leave off-diagonal entries at the rounding level of the
+// arithmetic (2^-106 in DD, 2^-53 in FP64), so eps sits a few bits above it:
+// at the rounding level itself a sweep would never end without rotations.
+constexpr double kJacobiEpsDD = 0x1p-100;
+constexpr double kJacobiEpsFP64 = 0x1p-48;
 
 template <int MODE>
 struct Ar {
@@ -48,6 +54,7 @@ __global__ void status_init_kernel(DevStatus* s, int k) {
     s->info = 0;
     s->rank = k;
     s->iters = 0;
+    s->sweeps = 0;
   }
 }
 
@@ -193,8 +200,9 @@ __device__ __forceinline__ void svqb_small_body(int k, const double* Mh, const d
   using A_ = Ar<MODE>;
   if (*g.run == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  dd* A = reinterpret_cast<dd*>(smem_raw);  // k*k
-  dd* U = A + k * k;                         // k*k
+  dd* A = reinterpret_cast<dd*>(smem_raw);  // k*k (upper triangle read during the sweeps)
+  dd* A2 = A + k * k;                        // k*k: the next A
+  dd* U = A2 + k * k;                        // k*k
   dd* cs = U + k * k;                        // 2 * (k/2 + 1): c, s per pair
   int* pr = reinterpret_cast<int*>(cs + 2 * (k / 2 + 1));  // 2 * (k/2 + 1): p, q per pair
   __shared__ int flag, rot_count;
@@ -221,6 +229,14 @@ __device__ __forceinline__ void svqb_small_body(int k, const double* Mh, const d
     }
     return;
   }
+  // Sweeps of the parallel (round-robin) ordering.  Per step: (1) each pair's
+  // rotation: the angle in FP64 from the hi parts (t = tan(phi)), then
+  // c = 1 / sqrt(1 + t^2) and s = t c in the mode's arithmetic, so that the
+  // rotation is orthogonal to that precision while it zeroes a_pq only to
+  // FP64 accuracy (the remainder is left in A and removed by later sweeps);
+  // (2) A' = J^T A J by 2x2 blocks of pairs on the upper triangle, into the
+  // second buffer, and U <- U J in place.
+  auto upper = [&](const dd* B, int r, int c) { return B[max(r, c) * k + min(r, c)]; };
   for (int sweep = 0; sweep < 40; ++sweep) {
     if (tid == 0) rot_count = 0;
     __syncthreads();
@@ -230,66 +246,84 @@ __device__ __forceinline__ void svqb_small_body(int k, const double* Mh, const d
         auto player = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + step) % (kk - 1); };
         int a = player(p), b = player(kk - 1 - p);
         int lo = min(a, b), hi = max(a, b);
-        dd c = dd{1.0, 0.0}, s = dd{0.0, 0.0};
+        dd c = dd{1.0, 0.0}, sn = dd{0.0, 0.0};
         if (hi < k) {
           const dd apq = A[hi * k + lo];
           const dd app = A[lo * k + lo], aqq = A[hi * k + hi];
           const double scale = sqrt(dabs(app.hi) * dabs(aqq.hi));
           if (dabs(apq.hi) > eps * scale && apq.hi != 0.0) {
-            const dd theta = A_::div(A_::sub(aqq, app), A_::add(apq, apq));
-            const dd th2 = A_::add(A_::mul(theta, theta), dd{1.0, 0.0});
-            dd t = A_::div(dd{1.0, 0.0}, A_::add(dd{dabs(theta.hi), theta.hi < 0 ? -theta.lo : theta.lo},
-                                                  A_::sqrt(th2)));
-            if (theta.hi < 0) t = dd_neg(t);
-            c = A_::div(dd{1.0, 0.0}, A_::sqrt(A_::add(A_::mul(t, t), dd{1.0, 0.0})));
-            s = A_::mul(t, c);
+            const double th = A_::sub(aqq, app).hi / (2.0 * apq.hi);
+            const double t = dabs(th) > 1e150 ? 0.5 / th : copysign(1.0 / (dabs(th) + sqrt(fma(th, th, 1.0))), th);
+            c = A_::div(dd{1.0, 0.0}, A_::sqrt(A_::add(dd{1.0, 0.0}, A_::mul(dd{t, 0.0}, dd{t, 0.0}))));
+            sn = A_::mul(c, dd{t, 0.0});
             atomicAdd(&rot_count, 1);
           }
         }
         cs[2 * p] = c;
-        cs[2 * p + 1] = s;
+        cs[2 * p + 1] = sn;
         pr[2 * p] = lo;
         pr[2 * p + 1] = hi;
       }
       __syncthreads();
-      // rows p, q of A: A <- J^T A
-      for (int t = tid; t < npairs * k; t += kThreads) {
-        const int p = t % npairs, m = t / npairs;
-        const int a = pr[2 * p], b = pr[2 * p + 1];
-        if (b >= k) continue;
-        const dd c = cs[2 * p], s = cs[2 * p + 1];
-        const dd x = A[m * k + a], y = A[m * k + b];
-        A[m * k + a] = A_::sub(A_::mul(c, x), A_::mul(s, y));
-        A[m * k + b] = A_::add(A_::mul(s, x), A_::mul(c, y));
-      }
-      __syncthreads();
-      // columns p, q of A and of U: A <- A J, U <- U J
-      for (int t = tid; t < npairs * k; t += kThreads) {
-        const int p = t % npairs, m = t / npairs;
-        const int a = pr[2 * p], b = pr[2 * p + 1];
-        if (b >= k) continue;
-        const dd c = cs[2 * p], s = cs[2 * p + 1];
-        dd x = A[a * k + m], y = A[b * k + m];
-        A[a * k + m] = A_::sub(A_::mul(c, x), A_::mul(s, y));
-        A[b * k + m] = A_::add(A_::mul(s, x), A_::mul(c, y));
-        x = U[a * k + m];
-        y = U[b * k + m];
-        U[a * k + m] = A_::sub(A_::mul(c, x), A_::mul(s, y));
-        U[b * k + m] = A_::add(A_::mul(s, x), A_::mul(c, y));
-      }
-      __syncthreads();
-      for (int p = tid; p < npairs; p += kThreads) {
-        const int a = pr[2 * p], b = pr[2 * p + 1];
-        if (b < k && !(cs[2 * p + 1].hi == 0.0 && cs[2 * p + 1].lo == 0.0)) {
-          A[b * k + a] = dd{0.0, 0.0};
-          A[a * k + b] = dd{0.0, 0.0};
+      // A2 = J^T A J, block (P, Q) of rows {lo_P, hi_P} and columns {lo_Q, hi_Q}, P <= Q
+      for (int t = tid; t < npairs * (npairs + 1) / 2; t += kThreads) {
+        int Q = (int)((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+        while ((Q + 1) * (Q + 2) / 2 <= t) ++Q;
+        while (Q * (Q + 1) / 2 > t) --Q;
+        const int P = t - Q * (Q + 1) / 2;
+        const int r0 = pr[2 * P], r1 = pr[2 * P + 1], c0 = pr[2 * Q], c1 = pr[2 * Q + 1];
+        const dd cP = cs[2 * P], sP = cs[2 * P + 1], cQ = cs[2 * Q], sQ = cs[2 * Q + 1];
+        const bool v1 = r1 < k, w1 = c1 < k;  // r0, c0 < k always (the dummy index is the larger)
+        dd b00 = upper(A, r0, c0), b01 = w1 ? upper(A, r0, c1) : dd{0.0, 0.0};
+        dd b10 = v1 ? upper(A, r1, c0) : dd{0.0, 0.0}, b11 = v1 && w1 ? upper(A, r1, c1) : dd{0.0, 0.0};
+        if (!(sQ.hi == 0.0 && sQ.lo == 0.0)) {  // B J_Q
+          const dd t00 = A_::sub(A_::mul(b00, cQ), A_::mul(b01, sQ)), t01 = A_::add(A_::mul(b00, sQ), A_::mul(b01, cQ));
+          const dd t10 = A_::sub(A_::mul(b10, cQ), A_::mul(b11, sQ)), t11 = A_::add(A_::mul(b10, sQ), A_::mul(b11, cQ));
+          b00 = t00; b01 = t01; b10 = t10; b11 = t11;
+        }
+        if (!(sP.hi == 0.0 && sP.lo == 0.0)) {  // J_P^T (B J_Q)
+          const dd t00 = A_::sub(A_::mul(cP, b00), A_::mul(sP, b10)), t10 = A_::add(A_::mul(sP, b00), A_::mul(cP, b10));
+          const dd t01 = A_::sub(A_::mul(cP, b01), A_::mul(sP, b11)), t11 = A_::add(A_::mul(sP, b01), A_::mul(cP, b11));
+          b00 = t00; b01 = t01; b10 = t10; b11 = t11;
+        }
+        auto put = [&](int r, int c, dd v) { A2[max(r, c) * k + min(r, c)] = v; };
+        put(r0, c0, b00);
+        if (w1) put(r0, c1, b01);
+        if (P == Q) {
+          if (v1) put(r1, c1, b11);  // (r1, c0) is the mirror of (r0, c1)
+        } else {
+          if (v1) put(r1, c0, b10);
+          if (v1 && w1) put(r1, c1, b11);
         }
       }
+      // U <- U J, columns lo_Q, hi_Q of row m
+      for (int t = tid; t < npairs * k; t += kThreads) {
+        const int q = t % npairs, m = t / npairs;
+        const int a = pr[2 * q], b = pr[2 * q + 1];
+        const dd c = cs[2 * q], sn = cs[2 * q + 1];
+        if (b >= k || (sn.hi == 0.0 && sn.lo == 0.0)) continue;
+        const dd x = U[a * k + m], y = U[b * k + m];
+        U[a * k + m] = A_::sub(A_::mul(c, x), A_::mul(sn, y));
+        U[b * k + m] = A_::add(A_::mul(sn, x), A_::mul(c, y));
+      }
       __syncthreads();
+      dd* sw = A;
+      A = A2;
+      A2 = sw;
     }
-    if (rot_count == 0) break;
+    if (rot_count == 0) {
+      if (tid == 0) st->sweeps = sweep + 1;
+      break;
+    }
     __syncthreads();
+    if (sweep == 39 && tid == 0) st->sweeps = 40;
   }
+  // the upper triangle holds the result: mirror it (the diagonal is eigenvalues)
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    if (i > j) A[t] = A[i * k + j];
+  }
+  __syncthreads();
   // w_l = lambda_l^{-1/2} for kept eigenvalues; Z = U diag(w) U^T into A's storage.
   __shared__ double lmax_s, lmin_s;
   __shared__ int rank_s;
@@ -413,6 +447,7 @@ __global__ void status_init_batched_kernel(const SmallJob* jobs, int njobs) {
       s->info = 0;
       s->rank = jobs[b].k;
       s->iters = 0;
+      s->sweeps = 0;
     }
   }
 }
@@ -490,7 +525,7 @@ cudaError_t launch_status_init(DevStatus* s, int k, cudaStream_t st) {
 
 size_t chol_smem(int k) { return 3 * (size_t)k * k * sizeof(dd); }
 size_t svqb_smem(int k) {
-  return 2 * (size_t)k * k * sizeof(dd) + 2 * (size_t)(k / 2 + 1) * sizeof(dd) + 2 * (size_t)(k / 2 + 1) * sizeof(int);
+  return 3 * (size_t)k * k * sizeof(dd) + 2 * (size_t)(k / 2 + 1) * sizeof(dd) + 2 * (size_t)(k / 2 + 1) * sizeof(int);
 }
 
 cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
@@ -522,13 +557,13 @@ cudaError_t launch_svqb_small(Mode mode, int k, const double* Mh, const double* 
     e = set_dyn_smem(svqb_small_kernel<MODE_DD>, smem);
     if (e != cudaSuccess) return e;
     svqb_small_kernel<MODE_DD><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, Z_hi, Z_lo, ldz, tol, s, g, pass,
-                                                         passes, 1e7, 0x1p-106, rank_user);
+                                                         passes, 1e7, kJacobiEpsDD, rank_user);
   } else {
     if (tol < 0) tol = k * 0x1p-52;
     e = set_dyn_smem(svqb_small_kernel<MODE_FP64>, smem);
     if (e != cudaSuccess) return e;
     svqb_small_kernel<MODE_FP64><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, Z_hi, Z_lo, ldz, tol, s, g, pass,
-                                                           passes, 1e4, 0x1p-53, rank_user);
+                                                           passes, 1e4, kJacobiEpsFP64, rank_user);
   }
   return cudaGetLastError();
 }
@@ -555,7 +590,7 @@ cudaError_t launch_small_batched(bool chol, Mode mode, int njobs, int kmax, cons
     auto kern = ddm ? svqb_small_batched_kernel<MODE_DD> : svqb_small_batched_kernel<MODE_FP64>;
     e = set_dyn_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<njobs, kThreads, smem, st>>>(jobs, pass, passes, ddm ? 1e7 : 1e4, ddm ? 0x1p-106 : 0x1p-53);
+    kern<<<njobs, kThreads, smem, st>>>(jobs, pass, passes, ddm ? 1e7 : 1e4, ddm ? kJacobiEpsDD : kJacobiEpsFP64);
   }
   return cudaGetLastError();
 }
