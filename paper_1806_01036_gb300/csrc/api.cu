@@ -131,9 +131,10 @@ int dd_gram_ctas(int64_t n, int kx, int ky, bool sym, int ctas) {
 }
 
 size_t orth_scratch(int64_t n, int k, eo_prec prec, bool b_inner) {
-  const size_t s = prec == EO_DD ? dd_gram_scratch(n, k, k, true) : gram_scratch_bytes(n, k, k, true);
-  if (!b_inner) return s;
-  return std::max(s, prec == EO_DD ? dd_gram_scratch(n, k, k, false) : gram_scratch_bytes(n, k, k, false));
+  size_t s = prec == EO_DD ? dd_gram_scratch(n, k, k, true) : gram_scratch_bytes(n, k, k, true);
+  if (b_inner) s = std::max(s, prec == EO_DD ? dd_gram_scratch(n, k, k, false) : gram_scratch_bytes(n, k, k, false));
+  if (prec == EO_DD) s = std::max(s, fx_update_tmp_bytes(n, k));  // the partials are consumed before the update
+  return s;
 }
 
 cudaError_t enqueue_orth_step(const OrthArgs& a, const OrthRes& r, int p, OrthStep step, uint64_t* launches) {
@@ -182,9 +183,9 @@ cudaError_t enqueue_orth_step(const OrthArgs& a, const OrthRes& r, int p, OrthSt
         void* A = t ? a.P : a.X;
         const int64_t lda = t ? a.ldp : a.ldx;
         e = fx ? launch_fx_update(a.n, a.k, static_cast<double*>(A), lda, ws->Zh, ws->Zl, a.chol,
-                                  &st->gate[2 * p + 1], r.stream, r.tile.row)
+                                  &st->gate[2 * p + 1], r.stream, r.tile.row, r.parts, r.parts_bytes)
                : launch_update(mode, a.n, a.k, A, lda, ws->Zh, ws->Zl, a.chol, &st->gate[2 * p + 1], r.stream);
-        *launches += 1;
+        *launches += fx ? fx_update_launches(a.n, a.k, r.parts_bytes) : 1;
       }
       return e;
   }
@@ -222,7 +223,7 @@ eo_status apply_projection(eo_ctx* ctx, int64_t n, int kv, const double* V, int6
                            double* M_hi, double* M_lo, int ldm, eo_prec prec, const int* gate = nullptr) {
   if (prec == EO_DD) {
     EO_CUDA(launch_fx_project(n, kv, V, ldv, k, Y, ldy, Yout, ldyo, ch, cl, ldc, gate, ctx->stream), "eo_project");
-    ctx->launches += 1;
+    ctx->launches += fx_project_launches(n, kv, k);
     if (M_hi) {
       EO_CUDA(launch_dd_gram(n, k, Yout, ldyo, k, Yout, ldyo, true, parts_of(ctx), M_hi, M_lo, ldm, gate,
                              ctx->stream),
@@ -263,7 +264,8 @@ eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, 
   OrthArgs a{CHOL, n, k, X, ldx, M_hi, M_lo, ldm, O_hi, O_lo, ldo, tol, passes, prec, out_dev};
   a.P = P;
   a.ldp = ldp;
-  const OrthRes r{status_of(ctx), ws_of(ctx), parts_of(ctx), ctx->stream, Tile{}};
+  OrthRes r{status_of(ctx), ws_of(ctx), parts_of(ctx), ctx->stream, Tile{}};
+  r.parts_bytes = ctx->scratch_bytes - kOffParts;
   const char* where = "";
   cudaError_t e = enqueue_orth(a, r, &ctx->launches, &where);
   if (e != cudaSuccess) return cuda_fail(ctx, (std::string(name) + " (" + where + ")").c_str(), e);
@@ -515,7 +517,8 @@ eo_status eo_orthogonalize(eo_ctx* ctx, int64_t n, int kv, const double* V, int6
   DeviceGuard g(ctx->device);
   EO_CHECK(g.ok, EO_ECUDA, "eo_orthogonalize: cannot select device%s", "");
   const bool fx = prec == EO_DD;
-  const size_t need = fx ? std::max(dd_gram_scratch(n, kv, k, false), dd_gram_scratch(n, k, k, true))
+  const size_t need = fx ? std::max({dd_gram_scratch(n, kv, k, false), dd_gram_scratch(n, k, k, true),
+                                     fx_update_tmp_bytes(n, k)})
                          : std::max(gram_scratch_bytes(n, kv, k, false), project_scratch_bytes(n, kv, k));
   eo_status s = ensure_scratch(ctx, need);
   if (s != EO_OK) return s;
@@ -549,13 +552,14 @@ eo_status eo_orthogonalize(eo_ctx* ctx, int64_t n, int kv, const double* V, int6
                               rank_dev, ctx->stream),
             "eo_orthogonalize (SVQB)");
     if (fx)
-      EO_CUDA(launch_fx_update(n, k, Y, ldy, ws->Zh, ws->Zl, false, &st->gate[kItUpd + it], ctx->stream),
+      EO_CUDA(launch_fx_update(n, k, Y, ldy, ws->Zh, ws->Zl, false, &st->gate[kItUpd + it], ctx->stream, 0,
+                               parts_of(ctx), ctx->scratch_bytes - kOffParts),
               "eo_orthogonalize (update)");
     else
       EO_CUDA(launch_update(pipe_mode(prec), n, k, Y, ldy, ws->Zh, ws->Zl, false, &st->gate[kItUpd + it],
                             ctx->stream),
               "eo_orthogonalize (update)");
-    ctx->launches += 3;
+    ctx->launches += 2 + (fx ? fx_update_launches(n, k, ctx->scratch_bytes - kOffParts) : 1);  // test, SVQB, update
   }
   return EO_OK;
 }

@@ -119,7 +119,8 @@ class Tuner {
     if (e == cudaSuccess) e = cudaEventCreate(&e1_);
     if (e != cudaSuccess) return e;
     elems_ = (size_t)n_max * k_max;
-    parts_bytes_ = align_up(std::max<size_t>(dd_gram_scratch(n_max, k_max, k_max, true), kAlign));
+    parts_bytes_ = align_up(std::max<size_t>(
+        {dd_gram_scratch(n_max, k_max, k_max, true), fx_update_tmp_bytes(n_max, k_max), kAlign}));
     const size_t bytes = align_up(elems_ * sizeof(double)) + parts_bytes_ + align_up(sizeof(SmallWs)) +
                          align_up(2 * sizeof(double) * KMAX * KMAX);
     e = cudaMalloc(&buf_, bytes);
@@ -145,7 +146,9 @@ class Tuner {
     auto gram = [&](int cap) {
       return launch_dd_gram(n, k, x_, n, k, x_, n, true, parts_, g_, g_ + KMAX * KMAX, KMAX, nullptr, s_, cap);
     };
-    auto update = [&](int cap) { return launch_fx_update(n, k, x_, n, ws_->Zh, ws_->Zl, false, nullptr, s_, cap); };
+    auto update = [&](int cap) {
+      return launch_fx_update(n, k, x_, n, ws_->Zh, ws_->Zl, false, nullptr, s_, cap, parts_, parts_bytes_);
+    };
     int gcap = 0, rcap = 0;
     e = search([&](int cap) { return dd_gram_ctas(n, k, k, true, cap); }, gram, &gcap);
     if (e != cudaSuccess) return e;
@@ -480,7 +483,9 @@ eo_status eo_batch_create(eo_ctx* ctx, int nblocks, const eo_block* blocks, eo_b
   };
   auto res_of = [&](int b) {
     const int s = branch_of[b];
-    return OrthRes{&slot_of(b)->st, &slot_of(b)->ws, parts0 + parts * s, c.br[s], tiles[b]};
+    OrthRes r{&slot_of(b)->st, &slot_of(b)->ws, parts0 + parts * s, c.br[s], tiles[b]};
+    r.parts_bytes = parts;
+    return r;
   };
   if (flags & EO_BATCH_CHAINS) {
     // each block's whole sequence on its branch

@@ -123,9 +123,18 @@ cudaError_t launch_umma_rowprod(bool update, int64_t n, int kin, const double* A
                                 int ctas = 0);
 // CTAs of an X Z launch (n-by-k) under a cap (0 = none).
 int fx_update_ctas(int64_t n, int k, int ctas);
-// X <- X Z in place (Z: k-by-k double-double, leading dimension KMAX); ctas as above.
+// Device scratch that lets an update with k > 16 run on the tensor cores
+// (groups of 16 output columns; 0 when not needed).
+size_t fx_update_tmp_bytes(int64_t n, int k);
+// X <- X Z in place (Z: k-by-k double-double, leading dimension KMAX); ctas as
+// above.  With k > 16 the tensor-core groups need tmp_bytes >= 
+// fx_update_tmp_bytes(n, k) of scratch at tmp; otherwise the integer limbs run.
 cudaError_t launch_fx_update(int64_t n, int k, double* X, int64_t ldx, const double* Zh, const double* Zl, bool tri,
-                             const int* gate, cudaStream_t st, int ctas = 0);
+                             const int* gate, cudaStream_t st, int ctas = 0, void* tmp = nullptr,
+                             size_t tmp_bytes = 0);
+// Kernels one launch_fx_update / launch_fx_project call launches.
+int fx_update_launches(int64_t n, int k, size_t tmp_bytes);
+int fx_project_launches(int64_t n, int kv, int k);
 // Yout = Y - V C (C: kv-by-k double-double with leading dimension ldc).
 cudaError_t launch_fx_project(int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y, int64_t ldy,
                               double* Yout, int64_t ldyo, const double* C_hi, const double* C_lo, int ldc,

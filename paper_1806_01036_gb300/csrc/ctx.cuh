@@ -97,9 +97,10 @@ struct OrthArgs {
 struct OrthRes {
   DevStatus* st;
   SmallWs* ws;
-  void* parts;  // Gram partials, orth_scratch() bytes
+  void* parts;        // Gram partials, and the scratch of the updates: orth_scratch() bytes
   cudaStream_t stream;
   Tile tile;
+  size_t parts_bytes = 0;  // its size (0: too small for the tensor-core updates of k > 16)
 };
 size_t orth_scratch(int64_t n, int k, eo_prec prec, bool b_inner = false);
 // Enqueues the sequence; on a CUDA error returns it and names the step in *where.

@@ -175,8 +175,37 @@ cudaError_t launch_rowprod(bool update, int64_t n, int kin, const double* A, int
 // Both row products go to the tensor-core engine (umma_rowprod.cu) when their
 // sizes fit it (kin <= 64, kout <= 16), to the integer limbs otherwise;
 // EO_DD_ROW_ENGINE=int forces the integer limbs.
+// Columns [0, cols) of dst <- src (n rows), when *gate != 0.
+__global__ void copy_cols_kernel(int64_t n, int cols, const double* __restrict__ src, int64_t lds,
+                                 double* __restrict__ dst, int64_t ldd, const int* gate) {
+  if (gate && *gate == 0) return;
+  const int64_t total = n * cols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % n, j = t / n;
+    dst[j * ldd + i] = src[j * lds + i];
+  }
+}
+
+size_t fx_update_tmp_bytes(int64_t n, int k) {
+  if (k <= 16 || !umma_rowprod_supported(k, 16)) return 0;
+  return (size_t)n * 16 * ((k + 15) / 16 - 1) * sizeof(double);
+}
+
+int fx_update_launches(int64_t n, int k, size_t tmp_bytes) {
+  if (umma_rowprod_supported(k, k)) return n > 0 ? 1 : 0;
+  const size_t need = fx_update_tmp_bytes(n, k);
+  if (n > 0 && need > 0 && tmp_bytes >= need) return (k + 15) / 16 + 1;
+  return 1;
+}
+
+int fx_project_launches(int64_t n, int kv, int k) {
+  if (umma_rowprod_supported(kv, k)) return n > 0 ? 1 : 0;
+  if (umma_rowprod_supported(kv, 16)) return n > 0 ? (k + 15) / 16 : 0;
+  return 1;
+}
+
 int fx_update_ctas(int64_t n, int k, int ctas) {
-  if (umma_rowprod_supported(k, k)) {
+  if (umma_rowprod_supported(k, k) || fx_update_tmp_bytes(n, k) > 0) {
     const int64_t ntiles = (n + 127) / 128;  // 128-row tiles of the tensor-core engine
     return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, ctas > 0 ? ctas : 152));
   }
@@ -184,9 +213,31 @@ int fx_update_ctas(int64_t n, int k, int ctas) {
 }
 
 cudaError_t launch_fx_update(int64_t n, int k, double* X, int64_t ldx, const double* Zh, const double* Zl, bool tri,
-                             const int* gate, cudaStream_t st, int ctas) {
+                             const int* gate, cudaStream_t st, int ctas, void* tmp, size_t tmp_bytes) {
   if (umma_rowprod_supported(k, k))
     return launch_umma_rowprod(true, n, k, X, ldx, k, Zh, Zl, KMAX, tri, nullptr, 0, X, ldx, gate, st, ctas);
+  const size_t need = fx_update_tmp_bytes(n, k);
+  if (n > 0 && need > 0 && tmp && tmp_bytes >= need) {
+    // groups of 16 output columns on the tensor cores: every group reads all
+    // k columns of X, so all but the last write to tmp, the last runs in
+    // place (a tile's loads precede its stores), and tmp is copied back
+    const int G = (k + 15) / 16;
+    double* T = static_cast<double*>(tmp);
+    for (int g = 0; g < G; ++g) {
+      const int c0 = 16 * g, kc = std::min(16, k - c0);
+      const bool last = g == G - 1;
+      double* out = last ? X + (size_t)c0 * ldx : T + (size_t)c0 * n;
+      // a column slice of a triangular Z is not triangular in its own indices:
+      // pass it whole (its zero entries cost nothing extra)
+      cudaError_t e = launch_umma_rowprod(true, n, k, X, ldx, kc, Zh + (size_t)c0 * KMAX, Zl + (size_t)c0 * KMAX,
+                                          KMAX, false, nullptr, 0, out, last ? ldx : n, gate, st, ctas);
+      if (e != cudaSuccess) return e;
+    }
+    const int64_t total = n * 16 * (G - 1);
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 8);
+    copy_cols_kernel<<<blocks, 256, 0, st>>>(n, 16 * (G - 1), T, n, X, ldx, gate);
+    return cudaGetLastError();
+  }
   return launch_rowprod(true, n, k, X, ldx, k, Zh, Zl, KMAX, tri, nullptr, 0, X, ldx, gate, st, ctas);
 }
 
@@ -195,6 +246,18 @@ cudaError_t launch_fx_project(int64_t n, int kv, const double* V, int64_t ldv, i
                               const int* gate, cudaStream_t st) {
   if (umma_rowprod_supported(kv, k))
     return launch_umma_rowprod(false, n, kv, V, ldv, k, C_hi, C_lo, ldc, false, Y, ldy, Yout, ldyo, gate, st);
+  if (umma_rowprod_supported(kv, 16)) {
+    // groups of 16 columns: each reads V and its own columns of Y and writes
+    // the same columns of Yout, so groups never disturb one another (in place too)
+    for (int c0 = 0; c0 < k; c0 += 16) {
+      const int kc = std::min(16, k - c0);
+      cudaError_t e = launch_umma_rowprod(false, n, kv, V, ldv, kc, C_hi + (size_t)c0 * ldc,
+                                          C_lo ? C_lo + (size_t)c0 * ldc : nullptr, ldc, false, Y + (size_t)c0 * ldy,
+                                          ldy, Yout + (size_t)c0 * ldyo, ldyo, gate, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   return launch_rowprod(false, n, kv, V, ldv, k, C_hi, C_lo, ldc, false, Y, ldy, Yout, ldyo, gate, st);
 }
 

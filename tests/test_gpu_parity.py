@@ -286,7 +286,8 @@ def test_project_apply_equals_project(eo, ctx, engine):
 
 
 @pytest.mark.parametrize("engine", ["int", "umma"])
-@pytest.mark.parametrize("n,kv,k", [(3001, 8, 5), (40_000, 16, 16), (20_011, 40, 16), (5000, 64, 7)])
+@pytest.mark.parametrize("n,kv,k", [(3001, 8, 5), (40_000, 16, 16), (20_011, 40, 16), (5000, 64, 7),
+                                    (3000, 24, 40), (2049, 64, 64)])
 def test_project_apply_integer_inputs_are_exact(eo, ctx, monkeypatch, engine, n, kv, k):
     """Integer V, C and Y: Y - V C is exact in FP64, so both row engines
     (integer limbs, tensor-core digits) must return it bit for bit."""
@@ -331,7 +332,8 @@ def _random_dd(g, rows, cols):
 
 @pytest.mark.parametrize("engine", ["int", "umma"])
 @pytest.mark.parametrize("n,kv,k", [(1, 64, 16), (127, 16, 1), (129, 17, 7), (255, 32, 16), (1000, 33, 2),
-                                    (4097, 48, 16), (2049, 1, 16), (3333, 64, 5)])
+                                    (4097, 48, 16), (2049, 1, 16), (3333, 64, 5), (1000, 64, 33), (5000, 16, 64),
+                                    (257, 8, 17)])
 def test_project_apply_shapes_against_oracle(eo, ctx, monkeypatch, engine, n, kv, k):
     """Row tails, every tile width of the tensor-core row engine (kv <= 16, 32,
     64) and odd output counts, with a genuine double-double C."""
@@ -380,9 +382,10 @@ def test_project_apply_nonfinite_and_padding(eo, ctx, monkeypatch, engine):
     assert np.all(np.isfinite(o2[rest]))
 
 
-def test_cholqr_update_engines_agree(eo, ctx, monkeypatch):
-    """One DD CholQR pass with either row engine for Q = X R^-1 (k = 16)."""
-    n, k = 60_000, 16
+@pytest.mark.parametrize("n,k", [(60_000, 16), (30_001, 33), (20_000, 64), (9_000, 17)])
+def test_cholqr_update_engines_agree(eo, ctx, monkeypatch, n, k):
+    """One DD CholQR pass with either row engine for Q = X R^-1 (k > 16: the
+    tensor cores in groups of 16 output columns through a scratch copy)."""
     x = synth.conditioned(n, k, 1e6, 81)
     qs = {}
     for engine in ("int", "umma"):
@@ -601,3 +604,21 @@ def test_invalid_arguments_are_rejected(eo, ctx):
     assert L.eo_cholqr(h, 100, 3, x.data_ptr(), 100, None, None, 3, None, None, 3, 3, 1, None) == eo.EINVAL
     assert L.eo_project(h, 100, 3, x.data_ptr(), 100, 3, x.data_ptr(), 100, x.data_ptr(), 100, None, None, 3,
                         None, None, 3, eo.F32) == eo.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("k", [24, 32, 64])
+def test_svqb_update_engines_agree(eo, ctx, monkeypatch, k):
+    """SVQB's full Z with k > 16: grouped tensor-core update vs integer limbs, both against the oracle."""
+    n, kappa = 12_000, 1e4
+    x = synth.conditioned(n, k, kappa, 83 + k)
+    qs = {}
+    for engine in ("int", "umma"):
+        monkeypatch.setenv("EO_DD_ROW_ENGINE", engine)
+        d = dev(x)
+        eo.svqb(ctx, d, passes=1, prec=eo.DD)
+        qs[engine] = host(d)
+    q_o, _, _ = oracle.svqb(x, passes=1)
+    tol = cholqr_tol(n, k, kappa)
+    for engine, q in qs.items():
+        assert np.max(np.abs(q - q_o)) <= tol, engine
+        assert oracle.orth_err(q)[0] <= 1e-14, engine
