@@ -50,10 +50,12 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU-oracle sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["project", "iterated", "batched", "serve"], default="project",
+    ap.add_argument("--workload", choices=["project", "iterated", "batched", "serve", "sweep", "single"],
+                    default="project",
                     help="project: the default line; iterated: the iterated two-phase algorithm on the "
                          "runtime-figure shapes (n = 8e6 unless --n is given); batched: many SVQB blocks of "
-                         "uneven n and k in one graph launch; serve: the request server under Poisson arrivals")
+                         "uneven n and k in one graph launch; serve: the request server under Poisson arrivals; "
+                         "sweep: the Gram precision sweep (n = 32e6, k 1..64); single: one 100,000 x 8 CholQR")
     ap.add_argument("--blocks", type=int, default=512, help="blocks of the batched workload")
     ap.add_argument("--clients", type=int, default=256, help="resident bases of the serving workload")
     ap.add_argument("--requests", type=int, default=2000, help="requests of the serving trace")
@@ -763,6 +765,126 @@ def run_serve(a):
         print(json.dumps(out), flush=True)
 
 
+# --------------------------------------------------- precision sweep, single
+
+SWEEP_METRIC = "Gram X^T X and X^T Y: HBM GB/s per mode (FP64, DD, FP32-in, DD-EFT) and k"
+
+
+def run_sweep(a):
+    """The precision sweep of the Gram products: n rows (32e6 unless --n is
+    given), k in {1, 2, 4, 8, 16, 32, 64}, X built with kappa = 1e8 (seeded
+    Gaussian / sqrt(n) times sigma log-spaced 1 .. 1e-8 on the GPU; an FP32
+    copy for the FP32-input mode), Y a second such block; modes FP64, DD
+    (compensated), FP32 inputs with FP64 accumulation, and the paper's FP64
+    error-free transformations (DD-EFT, k <= 16).  Each entry: median of
+    --steps launches after --warmup, CUDA events; bytes 8nk (X^T X) or 16nk
+    (X^T Y), 4nk / 8nk for FP32 inputs.  Accuracy: max |G - G_DD| / max |G_DD|."""
+    import torch
+    import paper_1806_01036_gb300 as eo
+
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    n = a.n if a.n != 4_000_000 else 32_000_000
+    ctx = eo.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(20180604 + 2 + 1000 * rank)
+
+    def block(k):
+        s = torch.logspace(0.0, -8.0, k, dtype=torch.float64, device=dev) if k > 1 else torch.ones(
+            1, dtype=torch.float64, device=dev)
+        return (torch.randn(k, n, dtype=torch.float64, device=dev, generator=g) * (s / n ** 0.5)[:, None]).t()
+
+    def timed(f):
+        for _ in range(max(1, a.warmup)):
+            f()
+        ts = []
+        for _ in range(max(1, a.steps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    hbm_peak, peak_kind = peak_hbm()
+    rows = []
+    for k in (1, 2, 4, 8, 16, 32, 64):
+        X, Y = block(k), block(k)
+        X32, Y32 = X.float().t().contiguous().t(), Y.float().t().contiguous().t()
+        ref = eo.gram(ctx, X, prec=eo.DD)
+        refxy = eo.gram(ctx, X, Y, prec=eo.DD)
+        scale = float(ref[0].abs().max())
+        scalexy = float(refxy[0].abs().max())
+        for prec, name in ((eo.FP64, "fp64"), (eo.DD, "dd"), (eo.F32, "f32"), (eo.DD_EFT, "dd_eft")):
+            if prec == eo.DD_EFT and k > 16:
+                continue
+            A, B, w = (X32, Y32, 4) if prec == eo.F32 else (X, Y, 8)
+            ms = timed(lambda: eo.gram(ctx, A, prec=prec))
+            msxy = timed(lambda: eo.gram(ctx, A, B, prec=prec))
+            gh, gl = eo.gram(ctx, A, prec=prec)
+            ghxy, glxy = eo.gram(ctx, A, B, prec=prec)
+            err = float(((gh - ref[0]) + (gl - ref[1])).abs().max()) / scale
+            errxy = float(((ghxy - refxy[0]) + (glxy - refxy[1])).abs().max()) / scalexy
+            rows.append({"k": k, "mode": name, "xtx_ms": ms, "xtx_gbs": w * n * k / (ms * 1e-3) / 1e9,
+                         "xty_ms": msxy, "xty_gbs": 2 * w * n * k / (msxy * 1e-3) / 1e9,
+                         "xtx_err_vs_dd": err, "xty_err_vs_dd": errxy})
+        del X, Y, X32, Y32
+        torch.cuda.empty_cache()
+    out = {"metric": SWEEP_METRIC, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup, "dtype": "f64",
+           "data": "synthetic (seeded on the GPU)", "hbm_peak_gbs": hbm_peak, "hbm_peak_source": peak_kind,
+           "config": {"workload": f"precision sweep: n = {n:,}, k in 1..64, kappa = 1e8, X^T X and X^T Y",
+                      "l2": "inputs of k >= 1 are 256 MB or more, larger than L2; no flush"},
+           "results": rows}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+SINGLE_METRIC = "single CholQR of 100,000 x 8: blocks/s, FP64 CholQR2 vs DD one pass (L2-resident)"
+
+
+def run_single(a):
+    """A small block that fits in L2 (6.4 MB): X 100,000 x 8 with sigma
+    log-spaced 1 .. 1e-6 (synth.single_cholqr), orthogonalized in place from
+    a device copy each call: plain FP64 CholQR2 against compensated CholQR
+    (automatic pass count).  Reported L2-warm, as the block stays resident."""
+    import torch
+    import paper_1806_01036_gb300 as eo
+    import synth
+
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    x = synth.single_cholqr()
+    X0 = torch.from_numpy(np.ascontiguousarray(x.T)).to(dev).t()
+    X = torch.empty_like(X0.t()).t()
+    ctx = eo.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for prec, passes, name in ((eo.FP64, 2, "fp64_cholqr2"), (eo.DD, 0, "dd_auto")):
+        for _ in range(max(3, a.warmup)):
+            X.copy_(X0)
+            eo.cholqr(ctx, X, passes=passes, prec=prec)
+        ts = []
+        for _ in range(max(50, a.steps)):
+            X.copy_(X0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            eo.cholqr(ctx, X, passes=passes, prec=prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        gh, gl = eo.gram(ctx, X, prec=eo.DD)
+        orth = float(np.linalg.norm((gh.cpu().numpy() - np.eye(8)) + gl.cpu().numpy(), 2))
+        res[name] = {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
+                     "blocks_per_s": 1e3 / float(np.percentile(ts, 50)), "orth_err": orth}
+    out = {"metric": SINGLE_METRIC, "n_gpus": ws, "dtype": "f64", "data": "synthetic (synth.single_cholqr)",
+           "config": {"workload": "single CholQR, X 100,000 x 8, sigma 1 .. 1e-6", "l2": "L2-warm (6.4 MB)"},
+           "results": res}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -773,6 +895,10 @@ def main():
         run_batched(a)
     elif a.workload == "serve":
         run_serve(a)
+    elif a.workload == "sweep":
+        run_sweep(a)
+    elif a.workload == "single":
+        run_single(a)
     else:
         run_eo(a)
 

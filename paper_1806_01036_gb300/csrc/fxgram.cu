@@ -408,12 +408,16 @@ GramPlan make_plan(int kx, int ky, bool sym) {
     worst = std::max(worst, s);
   }
   p.max_slots = worst;
-  // rows per panel: a multiple of 32 that fits the limbs and two panels of values
+  // rows per panel: a power of two >= 32 that fits the limbs and two panels
+  // of values; up to 2048 rows when few columns are held, so that a group
+  // with few tiles (all 512 threads on one tile: small k) still gives every
+  // thread rows and amortizes the per-panel barriers
   const size_t fixed = sizeof(i128) * kMaxTiles * TI * TJ + 3 * sizeof(int) * worst + 64;
-  int P = 128;
+  int P = 2048;
   while (P > 32 && fixed + (size_t)worst * P * (sizeof(int4) + 2 * sizeof(double)) > kSmemBudget) P /= 2;
   p.P = P;
-  p.lgP = P == 128 ? 7 : (P == 64 ? 6 : 5);
+  p.lgP = 0;
+  while ((1 << p.lgP) < P) ++p.lgP;
   return p;
 }
 
