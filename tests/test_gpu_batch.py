@@ -234,3 +234,40 @@ def test_batch_rejects_bad_blocks(eo, ctx):
     assert e.value.status == eo.EINVAL
     with pytest.raises(eo.EoError):
         eo.Batch(ctx, [x], branches=65)
+
+
+def test_batch_wide_odd_and_tiny_blocks_equal_single_calls(eo, ctx):
+    """k = 64 and odd k above 16 (tensor-core updates in groups of 16
+    columns through the branch scratch), one-row blocks, default shapes."""
+    import torch
+    shapes = [(3000, 64, 1e3), (5001, 33, 1e6), (1, 5, 1.0), (2048, 17, 1e9), (40_000, 48, 1e4)]
+    xs = []
+    for i, (n, k, kappa) in enumerate(shapes):
+        xs.append(synth.conditioned(n, k, kappa, 4300 + i) if n >= k else synth.gaussian(n, k, 4300 + i))
+    ds = [dev(x) for x in xs]
+    b = eo.Batch(ctx, ds, passes=0, prec=eo.DD, tune=False, branches=2, want_z=True)
+    b.run()
+    torch.cuda.synchronize()
+    for i, x in enumerate(xs):
+        d = dev(x)
+        zh, zl, rank = eo.svqb(ctx, d, passes=0, prec=eo.DD)
+        assert same(host(ds[i]), host(d)), i
+        assert same(host(b.z[i][0]), host(zh)) and same(host(b.z[i][1]), host(zl)), i
+        assert int(b.out[i].item()) == int(rank.item())
+    b.close()
+
+
+def test_batch_f32_inputs_equal_single_calls(eo, ctx):
+    import torch
+    shapes = [(10_000, 8, 1e2), (20_001, 16, 1e3), (3_000, 32, 1e2)]
+    xs = [np.asfortranarray(synth.conditioned(n, k, kappa, 4400 + i).astype(np.float32))
+          for i, (n, k, kappa) in enumerate(shapes)]
+    ds = [dev(x) for x in xs]
+    b = eo.Batch(ctx, ds, method=eo.BATCH_CHOLQR, passes=2, prec=eo.F32)
+    b.run()
+    torch.cuda.synchronize()
+    for i, x in enumerate(xs):
+        d = dev(x)
+        eo.cholqr(ctx, d, passes=2, prec=eo.F32)
+        assert same(host(ds[i]), host(d)), i
+    b.close()

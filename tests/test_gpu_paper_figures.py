@@ -119,3 +119,17 @@ def test_iterated_orthogonalization_stops_at_once_when_done(eo, ctx):
     iters, rank = eo.orthogonalize(ctx, _dev(w), y, eps=1e-12, max_iter=4, prec=eo.DD)
     assert int(iters.item()) == 0 and int(rank.item()) == 3
     assert np.max(np.abs(_host(y) - q)) <= 1e-15
+
+
+def test_iterated_orthogonalization_wide_block(eo, ctx):
+    """k = 24 > 16: the SVQB update runs in groups of 16 columns on the
+    tensor cores through the context's scratch."""
+    n, kb = 16_384, 24
+    ww = synth.hadamard_basis(n, KW, 1813)
+    x = synth.near_span(ww, kb, 1e8, seed=1814, kappa=1e4)
+    y = _dev(x)
+    iters, rank = eo.orthogonalize(ctx, _dev(ww), y, eps=1e-10, max_iter=8, prec=eo.DD)
+    assert int(iters.item()) >= 1 and int(rank.item()) == kb
+    q = _host(y)
+    assert oracle.cross_err(ww, q) <= 1e-10
+    assert oracle.orth_err(q)[2] <= 1e-10

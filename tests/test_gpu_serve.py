@@ -158,3 +158,19 @@ def test_server_same_basis_runs_in_order(eo, ctx):
     assert srv.wait(r2)[0] == eo.OK and srv.wait(r1)[0] == eo.OK
     assert np.array_equal(host(o1), host(a)) and np.array_equal(host(o2), host(bref))
     srv.close()
+
+
+def test_server_wide_request_equals_single_calls(eo, ctx):
+    """A block of 24 columns (its CholQR update runs in groups of 16 columns
+    and may grow the slot's scratch on first use)."""
+    n, kv, k = 30_000, 32, 24
+    V = dev(synth.orthonormal_basis(n, kv, 7600))
+    Y = dev(synth.conditioned(n, k, 1e6, 7601))
+    ref = single_calls(eo, ctx, V, Y)
+    srv = eo.Server(ctx, budget=8 << 30, slots=2)
+    b = srv.add_basis(V)
+    out = empty_like(Y)
+    rid = srv.submit(b, Y, Yout=out)
+    assert srv.wait(rid)[0] == eo.OK
+    assert np.array_equal(host(out), ref[0])
+    srv.close()
