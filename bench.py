@@ -265,6 +265,7 @@ def run_eo(a):
     clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
         os.path.join(ROOT, "gpurun_out")) else f"/tmp/eo_clocks_{os.getpid()}.csv", local)
     with clk:
+        torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed launches
         t_all0 = torch.cuda.Event(enable_timing=True)
         t_all1 = torch.cuda.Event(enable_timing=True)
         t_all0.record(stream)
@@ -280,6 +281,7 @@ def run_eo(a):
             ev[i][4].record(stream)
         t_all1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     launches = ctx.launches() - l0
     if ws > 1:
         dist.barrier()
@@ -519,9 +521,9 @@ def run_batched(a):
     kappa log-uniform in [1e2, 1e10]; SVQB in the compensated mode with the
     automatic second pass, launch shapes from the autotuner.  Blocks are
     X = G diag(sigma) Q^T with G Gaussian / sqrt(n) (its condition number is
-    within (1 + sqrt(k/n)) / (1 - sqrt(k/n)) <= 1.13 of 1), sigma log-spaced
-    1 .. 1/kappa and Q a Haar k x k rotation, generated on the GPU from a
-    seeded generator.  A step restores the blocks from a pristine copy
+    within (1 + sqrt(k/n)) / (1 - sqrt(k/n)) <= 1.13 of 1; seeded, on the GPU),
+    sigma log-spaced 1 .. 1/kappa and Q a Haar k x k rotation (seeded numpy
+    QR on the host).  A step restores the blocks from a pristine copy
     (untimed) and runs the graph once (timed with CUDA events)."""
     import torch
     import paper_1806_01036_gb300 as eo
@@ -539,8 +541,8 @@ def run_batched(a):
     X, X0 = [], []
     for n, k, kap in zip(ns, ks, kappas):
         n, k = int(n), int(k)
-        q, r = torch.linalg.qr(torch.randn(k, k, dtype=f64, device=dev, generator=g))
-        q = q * torch.sign(torch.diagonal(r))[None, :]
+        qn, rn = np.linalg.qr(rng.standard_normal((k, k)))  # Haar k x k rotation (host: k is small)
+        q = torch.from_numpy(qn * np.sign(np.diag(rn))[None, :]).to(dev)
         s = torch.logspace(0.0, -float(np.log10(kap)), k, dtype=f64, device=dev)
         x0 = (torch.randn(n, k, dtype=f64, device=dev, generator=g) * (s / float(np.sqrt(n)))[None, :]) @ q.t()
         x0 = x0.t().contiguous().t()
@@ -590,7 +592,9 @@ def run_batched(a):
     clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_batched_rank{rank}.csv") if os.path.isdir(
         os.path.join(ROOT, "gpurun_out")) else f"/tmp/eo_clocks_b_{os.getpid()}.csv", local)
     with clk:
+        torch.cuda.nvtx.range_push("timed")
         times = timed(bt.run, a.steps)
+        torch.cuda.nvtx.range_pop()
     launches = (ctx.launches() - l0)
     ms = statistics.mean(times)
     value = weak_scaling_value(ws, nbytes, max_over_ranks(ms, dev))
