@@ -467,6 +467,9 @@ eo_status eo_batch_create(eo_ctx* ctx, int nblocks, const eo_block* blocks, eo_b
                        tol < 0 ? svqb_default_tol(small_mode, x.k) : tol, out_dev ? out_dev + b : nullptr};
     kmax = std::max(kmax, x.k);
   }
+  // longest first: CTAs start in index order, so the widest factorizations
+  // take SMs of their own and the short ones fill in around them
+  std::stable_sort(jobs.begin(), jobs.end(), [](const SmallJob& a, const SmallJob& b) { return a.k > b.k; });
   if ((e = cudaMemcpy(jobs_dev, jobs.data(), sizeof(SmallJob) * nblocks, cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_fail(ctx, "eo_batch_create (job list)", e);
 
