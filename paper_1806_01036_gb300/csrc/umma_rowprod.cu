@@ -56,6 +56,19 @@ constexpr int kScaleProd = 2156;             // value of h: h 2^(A_r + B_j - 215
 constexpr unsigned kAccCols = 256;           // TMEM columns per accumulator (240 used)
 constexpr size_t kMinSmem = 120 * 1024;      // keeps one CTA per SM (TMEM: 512 columns)
 
+// 8-byte asynchronous copy global -> shared; src_bytes 0 writes zeros.
+__device__ __forceinline__ void cp_async8z(unsigned dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// With kin <= 32 the digit buffers leave room below the shared-memory floor
+// that keeps one CTA per SM: every converter thread then stages its own
+// values of the next tile there (two buffers) while the current one runs.
+template <int W>
+constexpr bool kStageValues = W <= 8;
+
 __device__ __forceinline__ void st_shared_v4(unsigned addr, unsigned a, unsigned b, unsigned c, unsigned d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
@@ -139,6 +152,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   int* Rbad = Arow + 2 * kRows;                                // [2][128] non-finite rows
   int* Bexp = Rbad + 2 * kRows;                                // [16] column exponents
   int* Bbad = Bexp + kOut;                                     // [16] non-finite columns
+  double* stg = reinterpret_cast<double*>(Bbad + kOut);        // [2][W][512] staged values (W <= 8)
   __shared__ __align__(8) unsigned long long full_bar[2], ready_bar[2];
   __shared__ unsigned tmem_base;
   __shared__ int bad;
@@ -241,6 +255,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int L = eq * 32 + lane;
     const unsigned tq = taddr + ((unsigned)(eq * 32) << 16) + (unsigned)(ep * 4);
 
+    // value k of this thread for tile T into staging buffer b (zeros beyond the matrix)
+    const unsigned stg_s = smem_u32(stg);
+    auto prefetch = [&](int64_t T, int b) {
+      const int64_t gr = T * kRows + r;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        const int col = c0 + k;
+        const bool ok = T < ntiles && gr < n && col < kin;
+        cp_async8z(stg_s + (unsigned)(((b * W + k) * kConvThreads + tid) * 8), ok ? A + (size_t)col * lda + gr : A,
+                   ok ? 8u : 0u);
+      }
+      cp_async_commit_group();
+    };
+    if constexpr (kStageValues<W>) prefetch(blockIdx.x, 0);
+
     auto epilogue = [&](int64_t T, int64_t i) {
       const unsigned tb = tq + (unsigned)(i & 1) * kAccCols;
       // h = p0 2^70 + p1 2^35 + p2 with p_c = sum over the five diagonals
@@ -282,12 +311,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     int64_t Tprev = -1, iprev = 0;
     for (int64_t T = blockIdx.x, i = 0; T < ntiles; T += gridDim.x, ++i) {
       // this thread's W values of row r (zero beyond the matrix)
-      const int64_t gr = T * kRows + r;
       double v[W];
+      if constexpr (kStageValues<W>) {
+        prefetch(T + gridDim.x, (int)((i + 1) & 1));  // the next tile's values, while this one runs
+        cp_async_wait_1();                           // this tile's copies (issued a tile ago) are done
 #pragma unroll
-      for (int k = 0; k < W; ++k) {
-        const int col = c0 + k;
-        v[k] = (gr < n && col < kin) ? A[(size_t)col * lda + gr] : 0.0;
+        for (int k = 0; k < W; ++k) v[k] = stg[((int)(i & 1) * W + k) * kConvThreads + tid];
+      } else {
+        const int64_t gr = T * kRows + r;
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          const int col = c0 + k;
+          v[k] = (gr < n && col < kin) ? A[(size_t)col * lda + gr] : 0.0;
+        }
       }
       // the row's exponent: max of |x| bit patterns over the four threads of the row
       unsigned key = 0;
@@ -342,6 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       epilogue(Tprev, iprev);
       tc_fence_before();
     }
+    if constexpr (kStageValues<W>) asm volatile("cp.async.wait_all;" ::: "memory");  // the last (empty) prefetch
   }
 
   __syncthreads();
@@ -356,7 +393,8 @@ size_t smem_bytes() {
   constexpr int KP = 4 * W;
   const size_t sbo = 16u * KP;
   const size_t b = 32 * sbo, a = 2 * kGroupSlabs * 16 * sbo, small = (4 * kRows + 2 * kOut) * sizeof(int);
-  return std::max(b + a + small, kMinSmem);
+  const size_t stage = kStageValues<W> ? 2 * W * kConvThreads * sizeof(double) : 0;
+  return std::max(b + a + small + stage, kMinSmem);
 }
 
 template <int W>
