@@ -51,7 +51,11 @@ constexpr int kConvThreads = 32 * kConvWarps;
 constexpr int kThreads = kConvThreads + 32;  // plus one MMA-issuing warp
 constexpr int kRows = 128;                   // rows per tile (MMA M, TMEM lanes)
 constexpr int kOut = 16;                     // output columns of the MMA (padded)
-constexpr int kGroupSlabs = 5;               // digit slabs per group (three groups)
+// Digit slabs per group (three groups per tile).
+template <int W>
+constexpr int kGroupSlabs = 5;
+template <int W>
+constexpr int kGroups = NS / kGroupSlabs<W>;
 constexpr int kScaleProd = 2156;             // value of h: h 2^(A_r + B_j - 2156)
 constexpr unsigned kAccCols = 256;           // TMEM columns per accumulator (240 used)
 constexpr size_t kMinSmem = 120 * 1024;      // keeps one CTA per SM (TMEM: 512 columns)
@@ -61,11 +65,13 @@ __device__ __forceinline__ void cp_async8z(unsigned dst, const void* src, unsign
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // With kin <= 32 the digit buffers leave room below the shared-memory floor
 // that keeps one CTA per SM: every converter thread then stages its own
-// values of the next tile there (two buffers) while the current one runs.
+// values of the next tile there (one buffer: a tile's values are read before
+// the next tile's copies are issued into the same slots) while the current
+// tile runs.  kin <= 64 has no room left (and smaller digit groups, to make
+// some, cost more than the staging saves): its loads stay direct.
 template <int W>
 constexpr bool kStageValues = W <= 8;
 
@@ -107,14 +113,26 @@ __device__ __forceinline__ void store_slab(unsigned dst, const PairLanes (&P)[W 
   }
 }
 
-template <int G, int W>
+template <int G, int W, int J = 0>
 __device__ __forceinline__ void store_group(unsigned dst, unsigned slab_bytes, const PairLanes (&P)[W / 2],
                                             const unsigned (&sg)[W / 2]) {
-  store_slab<G * kGroupSlabs + 0, W>(dst, P, sg);
-  store_slab<G * kGroupSlabs + 1, W>(dst + slab_bytes, P, sg);
-  store_slab<G * kGroupSlabs + 2, W>(dst + 2 * slab_bytes, P, sg);
-  store_slab<G * kGroupSlabs + 3, W>(dst + 3 * slab_bytes, P, sg);
-  store_slab<G * kGroupSlabs + 4, W>(dst + 4 * slab_bytes, P, sg);
+  if constexpr (J < kGroupSlabs<W>) {
+    store_slab<G * kGroupSlabs<W> + J, W>(dst + J * slab_bytes, P, sg);
+    store_group<G, W, J + 1>(dst, slab_bytes, P, sg);
+  }
+}
+
+// store_group for a group index known at run time
+template <int W>
+__device__ __forceinline__ void store_group_rt(int g, unsigned dst, unsigned slab_bytes, const PairLanes (&P)[W / 2],
+                                               const unsigned (&sg)[W / 2]) {
+  switch (g) {
+    case 0: store_group<0, W>(dst, slab_bytes, P, sg); break;
+    case 1: store_group<1, W>(dst, slab_bytes, P, sg); break;
+    case 2: store_group<2, W>(dst, slab_bytes, P, sg); break;
+    case 3: if constexpr (kGroups<W> > 3) store_group<3, W>(dst, slab_bytes, P, sg); break;
+    default: if constexpr (kGroups<W> > 4) store_group<4, W>(dst, slab_bytes, P, sg); break;
+  }
 }
 
 // x 2^(1127 - A) as a signed 128-bit integer, truncated toward zero.
@@ -148,11 +166,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* bdig = smem;                                  // the small matrix's digits
   unsigned char* adig = smem + B_BYTES;                        // two group buffers of 5 slabs
-  int* Arow = reinterpret_cast<int*>(adig + 2 * kGroupSlabs * SLAB_A);  // [2][128] row exponents
+  constexpr int GS = kGroupSlabs<W>, NG = kGroups<W>;
+  int* Arow = reinterpret_cast<int*>(adig + 2 * GS * SLAB_A);  // [2][128] row exponents
   int* Rbad = Arow + 2 * kRows;                                // [2][128] non-finite rows
   int* Bexp = Rbad + 2 * kRows;                                // [16] column exponents
   int* Bbad = Bexp + kOut;                                     // [16] non-finite columns
-  double* stg = reinterpret_cast<double*>(Bbad + kOut);        // [2][W][512] staged values (W <= 8)
+  double* stg = reinterpret_cast<double*>(Bbad + kOut);        // [W][512] staged values (kin <= 32)
   __shared__ __align__(8) unsigned long long full_bar[2], ready_bar[2];
   __shared__ unsigned tmem_base;
   __shared__ int bad;
@@ -217,16 +236,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t T = blockIdx.x, i = 0; T < ntiles && ok; T += gridDim.x, ++i) {
         const unsigned acc = taddr + (unsigned)(i & 1) * kAccCols;
 #pragma unroll 1
-        for (int g = 0; g < 3; ++g, ++G) {
+        for (int g = 0; g < NG; ++g, ++G) {
           const int b = G & 1;
           if (!mbar_wait(rb0 + 8u * b, (unsigned)(G >> 1) & 1u, &bad)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const unsigned abuf = adig_s + (unsigned)b * kGroupSlabs * SLAB_A;
-          for (int sg = 0; sg < kGroupSlabs; ++sg) {
-            const int s = g * kGroupSlabs + sg;
+          const unsigned abuf = adig_s + (unsigned)b * GS * SLAB_A;
+          for (int sg = 0; sg < GS; ++sg) {
+            const int s = g * GS + sg;
             const unsigned idesc = idesc_f16(kRows, kOut * (NS - s));
 #pragma unroll
             for (int kc = 0; kc < KC; ++kc) {
@@ -255,20 +274,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int L = eq * 32 + lane;
     const unsigned tq = taddr + ((unsigned)(eq * 32) << 16) + (unsigned)(ep * 4);
 
-    // value k of this thread for tile T into staging buffer b (zeros beyond the matrix)
+    // value k of this thread for tile T into its staging slots (zeros beyond the matrix)
     const unsigned stg_s = smem_u32(stg);
-    auto prefetch = [&](int64_t T, int b) {
+    auto prefetch = [&](int64_t T) {
       const int64_t gr = T * kRows + r;
 #pragma unroll
       for (int k = 0; k < W; ++k) {
         const int col = c0 + k;
         const bool ok = T < ntiles && gr < n && col < kin;
-        cp_async8z(stg_s + (unsigned)(((b * W + k) * kConvThreads + tid) * 8), ok ? A + (size_t)col * lda + gr : A,
+        cp_async8z(stg_s + (unsigned)((k * kConvThreads + tid) * 8), ok ? A + (size_t)col * lda + gr : A,
                    ok ? 8u : 0u);
       }
       cp_async_commit_group();
     };
-    if constexpr (kStageValues<W>) prefetch(blockIdx.x, 0);
+    if constexpr (kStageValues<W>) prefetch(blockIdx.x);
 
     auto epilogue = [&](int64_t T, int64_t i) {
       const unsigned tb = tq + (unsigned)(i & 1) * kAccCols;
@@ -313,10 +332,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       // this thread's W values of row r (zero beyond the matrix)
       double v[W];
       if constexpr (kStageValues<W>) {
-        prefetch(T + gridDim.x, (int)((i + 1) & 1));  // the next tile's values, while this one runs
-        cp_async_wait_1();                           // this tile's copies (issued a tile ago) are done
+        asm volatile("cp.async.wait_all;" ::: "memory");  // this tile's copies, issued a tile ago
 #pragma unroll
-        for (int k = 0; k < W; ++k) v[k] = stg[((int)(i & 1) * W + k) * kConvThreads + tid];
+        for (int k = 0; k < W; ++k) v[k] = stg[k * kConvThreads + tid];
+        prefetch(T + gridDim.x);  // the next tile's values into the same slots, while this one runs
       } else {
         const int64_t gr = T * kRows + r;
 #pragma unroll
@@ -349,20 +368,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         sg[m] = ((hi32(v[2 * m]) >> 31) << 15) | (hi32(v[2 * m + 1]) & 0x80000000u);
       }
 
-      // three groups of five slabs into the alternating buffers
+      // NG groups of GS slabs into the alternating buffers
 #pragma unroll
-      for (int g = 0; g < 3; ++g, ++G) {
+      for (int g = 0; g < NG; ++g, ++G) {
         const int b = G & 1;
         if (G >= 2) mbar_wait(fb0 + 8u * b, (unsigned)((G - 2) >> 1) & 1u, &bad);  // MMAs of group G - 2 done
-        const unsigned dst = adig_s + (unsigned)b * kGroupSlabs * SLAB_A + dofs;
-        if (g == 0) store_group<0, W>(dst, SLAB_A, P, sg);
-        else if (g == 1) store_group<1, W>(dst, SLAB_A, P, sg);
-        else store_group<2, W>(dst, SLAB_A, P, sg);
+        const unsigned dst = adig_s + (unsigned)b * GS * SLAB_A + dofs;
+        store_group_rt<W>(g, dst, SLAB_A, P, sg);
         fence_proxy_async();
         mbar_arrive(rb0 + 8u * b);
       }
-      // the previous tile's MMAs completed (its last group G - 4 was waited for
-      // before group G - 2 was written): its epilogue overlaps this tile's MMAs
+      // the previous tile's MMAs completed (its last group was waited for before
+      // this tile's second group was written): its epilogue overlaps this tile's MMAs
       if (Tprev >= 0) {
         tc_fence_after();
         epilogue(Tprev, iprev);
@@ -392,8 +409,8 @@ template <int W>
 size_t smem_bytes() {
   constexpr int KP = 4 * W;
   const size_t sbo = 16u * KP;
-  const size_t b = 32 * sbo, a = 2 * kGroupSlabs * 16 * sbo, small = (4 * kRows + 2 * kOut) * sizeof(int);
-  const size_t stage = kStageValues<W> ? 2 * W * kConvThreads * sizeof(double) : 0;
+  const size_t b = 32 * sbo, a = 2 * kGroupSlabs<W> * 16 * sbo, small = (4 * kRows + 2 * kOut) * sizeof(int);
+  const size_t stage = kStageValues<W> ? (size_t)W * kConvThreads * sizeof(double) : 0;
   return std::max(b + a + small + stage, kMinSmem);
 }
 
