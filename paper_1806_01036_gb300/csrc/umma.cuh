@@ -301,6 +301,12 @@ __device__ __forceinline__ void xwords(double x, int A, unsigned (&w)[4]) {
   }
 }
 
+// 8-byte asynchronous copy global -> shared; src_bytes 0 writes zeros.
+__device__ __forceinline__ void cp_async8z(unsigned dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
 // A pair of values (a, b) interleaved in 16-bit lanes: Z[k] holds bits
 // 16k .. 16k + 15 of a in its low half and of b in its high half (k = 0..6),
 // Z8[k] the same for bits 16k + 8 .. 16k + 23 (k = 0..5).  Every 7-bit digit

@@ -81,7 +81,14 @@ struct UPlan {
 // digits of p are in buffer p & 1 and TMEM is drained if due), issues the
 // MMAs and commits them to full[p & 1], which the converters wait on before
 // they reuse the buffer (panel p + 2) or read TMEM.
-template <int KYP>
+// DIRECT: the operands cannot be read by TMA (a leading dimension that is
+// not a whole number of 16-byte units, or a base that is not 16-byte
+// aligned): every converter thread then copies its own items of panel p + 2
+// into private shared-memory slots with 8-byte cp.async (zeros beyond the
+// matrix) and reads them back at panel p; the rest is the same.
+constexpr unsigned kDirectStageBytes = 2u * kMaxItems * kConvThreads * 16u;
+
+template <int KYP, bool DIRECT>
 __global__ void __launch_bounds__(kThreads, 1)
     umma_gram_partial_kernel(int64_t n, int kx, const double* __restrict__ X, int64_t ldx, int ky,
                              const double* __restrict__ Y, int64_t ldy, UPlan pl, int64_t rows_per_chunk,
@@ -97,8 +104,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned base (the 128-byte swizzle of the TMA boxes is anchored there)
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  unsigned char* stage = smem;                                 // 2 staging buffers (TMA boxes)
-  unsigned char* dig = stage + 2 * (size_t)pl.stage_bytes;     // 2 digit buffers
+  unsigned char* stage = smem;                                 // 2 staging buffers (TMA boxes; DIRECT: slots)
+  const size_t stage_region = DIRECT ? max(2 * (size_t)pl.stage_bytes, (size_t)kDirectStageBytes)
+                                     : 2 * (size_t)pl.stage_bytes;
+  unsigned char* dig = stage + stage_region;                   // 2 digit buffers
   int* Erun = reinterpret_cast<int*>(dig + 2 * (size_t)pl.dig_bytes);
   int* pmax = Erun + nslots;  // two panels' column maxima
   __shared__ __align__(8) unsigned long long full_bar[2], ready_bar[2], stage_bar[2];
@@ -155,7 +164,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!pl.shared) tma_load_2d(dst + (unsigned)(P / 16) * xbox + (unsigned)h * ybox, &tmy, xr + 16 * h, y0, bar);
     }
   };
-  if (tid == 0) {
+  if (!DIRECT && tid == 0) {
     for (int p = 0; p < 2 && p < npan; ++p) load_panel(p);
   }
 
@@ -293,13 +302,46 @@ __global__ void __launch_bounds__(kThreads, 1)
     const unsigned stride_a = (unsigned)kxp / 8u * SBO, stride_b = (unsigned)KYP / 8u * SBO;
     const bool scan_lead = (lane & 24) == 0;  // one lane of the four that share a column
 
+    // DIRECT: each item's column (null: zeros) and row offset in the panel
+    const double* gcol[kMaxItems];
+    int irow[kMaxItems];
+    const unsigned slot0 = smem_u32(stage) + (unsigned)tid * 16u;
+    auto prefetch = [&](int pp) {  // this thread's items of panel pp into slot buffer pp & 1
+      const int64_t base = r0 + (int64_t)pp * P;
+#pragma unroll
+      for (int k = 0; k < kMaxItems; ++k) {
+        if (!gcol[k]) continue;
+        const int64_t row = base + irow[k];
+        const unsigned d = slot0 + (unsigned)(((pp & 1) * kMaxItems + k) * kConvThreads) * 16u;
+        cp_async8z(d, row < r1 ? gcol[k] + row : gcol[k], row < r1 ? 8u : 0u);
+        cp_async8z(d + 8u, row + 1 < r1 ? gcol[k] + row + 1 : gcol[k], row + 1 < r1 ? 8u : 0u);
+      }
+      cp_async_commit_group();
+    };
+    if constexpr (DIRECT) {
+#pragma unroll
+      for (int k = 0; k < kMaxItems; ++k) {
+        const int i = tid + k * kConvThreads;
+        const int cl = i & 7, rl = (i >> 3) & 3, rest = i >> 5;
+        const int c = (rest % ncg) * 8 + cl, rh = rest / ncg;
+        const bool isb = !pl.shared && c >= kxp;
+        const int lc = isb ? c - kxp : c, gc = isb ? y0 + lc : x0 + lc;
+        const bool ok = i < nitems && gc < (isb ? ky : kx);
+        gcol[k] = ok ? (isb ? Y + (size_t)gc * ldy : X + (size_t)gc * ldx) : nullptr;
+        irow[k] = (rh * 4 + rl) * 2;
+      }
+      prefetch(0);
+      prefetch(1);
+    }
+
     int undrained = 0, drains = 0;
     bool fresh = true;
     for (int p = 0; p < npan; ++p) {
       const int db = p & 1;
       const unsigned char* st = stage + (size_t)db * pl.stage_bytes;
       int* pm = pmax + db * nslots;  // this panel's column maxima
-      mbar_wait(sb0 + 8u * db, (unsigned)(p >> 1) & 1u, &bad);  // panel p staged
+      if constexpr (DIRECT) asm volatile("cp.async.wait_group 1;" ::: "memory");  // this thread's items of panel p
+      else mbar_wait(sb0 + 8u * db, (unsigned)(p >> 1) & 1u, &bad);             // panel p staged
       bar_conv<kConvThreads>();  // every converter is past panel p-1
       if (p > 0 && tid < nslots) {  // fold panel p-1's maxima into the running exponents
         int* pq = pmax + ((p - 1) & 1) * nslots;
@@ -309,10 +351,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 
       // this thread's values of the panel (kept in registers for the conversion)
       double2 v[kMaxItems];
+      if constexpr (DIRECT) {
 #pragma unroll
-      for (int k = 0; k < kMaxItems; ++k)
-        v[k] = tid + k * kConvThreads < nitems ? *reinterpret_cast<const double2*>(st + ((it_s[k] & 0xffffu) << 4))
-                                               : make_double2(0.0, 0.0);
+        for (int k = 0; k < kMaxItems; ++k)
+          v[k] = gcol[k] ? *reinterpret_cast<const double2*>(stage + ((size_t)(db * kMaxItems + k) * kConvThreads +
+                                                                      tid) * 16u)
+                         : make_double2(0.0, 0.0);
+        prefetch(p + 2);  // into the slots just read (zeros past the chunk)
+      } else {
+#pragma unroll
+        for (int k = 0; k < kMaxItems; ++k)
+          v[k] = tid + k * kConvThreads < nitems
+                     ? *reinterpret_cast<const double2*>(st + ((it_s[k] & 0xffffu) << 4))
+                     : make_double2(0.0, 0.0);
+      }
       // largest exponent of each column in the panel: max of |x| bit patterns
       unsigned m[kMaxItems];
 #pragma unroll
@@ -359,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       fence_proxy_async();
       const bool grew = bar_conv_or<kConvThreads>(grew_local);
-      if (tid == 0 && p + 2 < npan) {  // staging buffer db is free: panel p + 2
+      if (!DIRECT && tid == 0 && p + 2 < npan) {  // staging buffer db is free: panel p + 2
         fence_proxy_async();
         load_panel(p + 2);
       }
@@ -394,6 +446,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       ++undrained;
     }
 
+    if constexpr (DIRECT) asm volatile("cp.async.wait_all;" ::: "memory");  // the last (empty) copies
     // last drain and fold
     if (npan > 0) {
       mbar_wait(fb0 + 8u * ((npan - 1) & 1), (unsigned)((npan - 1) >> 1) & 1u, &bad);
@@ -532,16 +585,19 @@ bool make_map(CUtensorMap* m, const double* A, int64_t n, int k, int64_t ld, int
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int KYP>
+size_t plan_smem_direct(const UPlan& p) {
+  return plan_smem(p) - 2 * (size_t)p.stage_bytes + std::max<size_t>(2 * (size_t)p.stage_bytes, kDirectStageBytes);
+}
+
+template <int KYP, bool DIRECT>
 cudaError_t launch_kernel(const UPlan& plan, int chunks, int64_t n, int kx, const double* X, int64_t ldx, int ky,
                           const double* Y, int64_t ldy, int64_t rpc, const CUtensorMap& tmx, const CUtensorMap& tmy,
                           FxPart* parts, const int* gate, cudaStream_t st) {
-  const size_t smem = plan_smem(plan);
-  cudaError_t e =
-      set_dyn_smem(umma_gram_partial_kernel<KYP>, smem);
+  const size_t smem = DIRECT ? plan_smem_direct(plan) : plan_smem(plan);
+  cudaError_t e = set_dyn_smem(umma_gram_partial_kernel<KYP, DIRECT>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(plan.ntx * plan.nty, chunks);
-  umma_gram_partial_kernel<KYP>
+  umma_gram_partial_kernel<KYP, DIRECT>
       <<<grid, kThreads, smem, st>>>(n, kx, X, ldx, ky, Y, ldy, plan, rpc, tmx, tmy, parts, gate);
   return cudaGetLastError();
 }
@@ -569,18 +625,27 @@ cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, in
   }
   const UPlan plan = make_plan(kx, ky, sym);
   // TMA addresses 16-byte aligned bases and leading dimensions of whole 16-byte units
-  alignas(64) CUtensorMap tmx, tmy;
+  alignas(64) CUtensorMap tmx{}, tmy{};
   const bool tma_ok = (uintptr_t)X % 16 == 0 && (uintptr_t)Y % 16 == 0 && ldx % 2 == 0 && ldy % 2 == 0 &&
                       n < (1ll << 31) && make_map(&tmx, X, n, kx, ldx, plan.kxp) &&
                       make_map(&tmy, Y, n, ky, ldy, plan.kyp);
-  if (!tma_ok) return launch_fx_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st, ctas);
+  // without TMA: the converters copy their own items (when the slots fit), else the integer limbs
+  const bool direct = !tma_ok && (uintptr_t)X % 8 == 0 && (uintptr_t)Y % 8 == 0 && plan_smem_direct(plan) <= kSmemCap;
+  if (!tma_ok && !direct)
+    return launch_fx_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st, ctas);
   const int chunks = capped_chunks(n, plan, ctas);
   int64_t rpc = (n + chunks - 1) / chunks;
   rpc = std::max<int64_t>(plan.P, (rpc + plan.P - 1) / plan.P * plan.P);
   FxPart* parts = static_cast<FxPart*>(scratch);
-  cudaError_t e = plan.kyp == 16
-                      ? launch_kernel<16>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st)
-                      : launch_kernel<8>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st);
+  cudaError_t e;
+  if (direct)
+    e = plan.kyp == 16
+            ? launch_kernel<16, true>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st)
+            : launch_kernel<8, true>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st);
+  else
+    e = plan.kyp == 16
+            ? launch_kernel<16, false>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st)
+            : launch_kernel<8, false>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st);
   if (e != cudaSuccess) return e;
   return launch_fx_reduce(kx, ky, sym, chunks, parts, G_hi, G_lo, ldg, gate, st);
 }

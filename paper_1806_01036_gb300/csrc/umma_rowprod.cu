@@ -60,11 +60,6 @@ constexpr int kScaleProd = 2156;             // value of h: h 2^(A_r + B_j - 215
 constexpr unsigned kAccCols = 256;           // TMEM columns per accumulator (240 used)
 constexpr size_t kMinSmem = 120 * 1024;      // keeps one CTA per SM (TMEM: 512 columns)
 
-// 8-byte asynchronous copy global -> shared; src_bytes 0 writes zeros.
-__device__ __forceinline__ void cp_async8z(unsigned dst, const void* src, unsigned src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 // With kin <= 32 the digit buffers leave room below the shared-memory floor
 // that keeps one CTA per SM: every converter thread then stages its own

@@ -622,3 +622,37 @@ def test_svqb_update_engines_agree(eo, ctx, monkeypatch, k):
     for engine, q in qs.items():
         assert np.max(np.abs(q - q_o)) <= tol, engine
         assert oracle.orth_err(q)[0] <= 1e-14, engine
+
+
+@pytest.mark.parametrize("n,kx,ky", [(5001, 16, None), (4097, 32, None), (2049, 64, 64), (3001, 64, 8),
+                                     (70_001, 16, 16), (999, 20, None)])
+def test_gram_umma_direct_loads_against_oracle(eo, ctx, monkeypatch, n, kx, ky):
+    """Packed blocks with odd n (leading dimension n): not addressable by TMA,
+    so the tensor-core engine's converters copy their own items."""
+    monkeypatch.setenv("EO_DD_GRAM_ENGINE", "umma")
+    x = synth.gaussian(n, kx, 300 + kx)
+    y = None if ky is None else synth.gaussian(n, ky, 400 + ky)
+    gh, gl = eo.gram(ctx, dev(x), None if y is None else dev(y), prec=eo.DD)
+    rh, rl = oracle.gram(x, y)
+    assert np.all(dd_err(host(gh), host(gl), rh, rl) <= dd_gram_tol(x, x if y is None else y, rh, 1))
+
+
+@pytest.mark.parametrize("kx,ky", [(16, None), (64, 16), (32, None)])
+def test_gram_umma_direct_equals_tma(eo, ctx, monkeypatch, kx, ky):
+    """The same values with an even (TMA) and an odd (direct copies) leading
+    dimension: the same panels, chunks and digits, so bitwise the same result."""
+    monkeypatch.setenv("EO_DD_GRAM_ENGINE", "umma")
+    torch = torch_mod()
+    n = 40_000
+    x = synth.conditioned(n, kx, 1e6, 500 + kx)
+    y = None if ky is None else synth.gaussian(n, ky, 501)
+
+    def odd(a):
+        buf = synth.with_ld(a, n + 1, fill=np.nan)
+        return torch.from_numpy(np.ascontiguousarray(buf.T)).cuda().t()[:n, :]
+
+    g1 = eo.gram(ctx, dev(x), None if y is None else dev(y), prec=eo.DD)
+    xo = odd(x)
+    assert xo.stride(1) == n + 1
+    g2 = eo.gram(ctx, xo, None if y is None else odd(y), prec=eo.DD)
+    assert np.array_equal(host(g1[0]), host(g2[0])) and np.array_equal(host(g1[1]), host(g2[1]))
