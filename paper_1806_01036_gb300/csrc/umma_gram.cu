@@ -41,6 +41,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 #include "common.cuh"
@@ -629,8 +630,12 @@ cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, in
   const bool tma_ok = (uintptr_t)X % 16 == 0 && (uintptr_t)Y % 16 == 0 && ldx % 2 == 0 && ldy % 2 == 0 &&
                       n < (1ll << 31) && make_map(&tmx, X, n, kx, ldx, plan.kxp) &&
                       make_map(&tmy, Y, n, ky, ldy, plan.kyp);
-  // without TMA: the converters copy their own items (when the slots fit), else the integer limbs
-  const bool direct = !tma_ok && (uintptr_t)X % 8 == 0 && (uintptr_t)Y % 8 == 0 && plan_smem_direct(plan) <= kSmemCap;
+  // without TMA: the converters copy their own items (when the slots fit), else the integer limbs.
+  // EO_DD_GRAM_LOADS=direct uses the copies for TMA-addressable operands too.
+  const char* lm = getenv("EO_DD_GRAM_LOADS");
+  const bool force_direct = lm && lm[0] == 'd';
+  const bool direct = (!tma_ok || force_direct) && (uintptr_t)X % 8 == 0 && (uintptr_t)Y % 8 == 0 &&
+                      plan_smem_direct(plan) <= kSmemCap;
   if (!tma_ok && !direct)
     return launch_fx_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st, ctas);
   const int chunks = capped_chunks(n, plan, ctas);
