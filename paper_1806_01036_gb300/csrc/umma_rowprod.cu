@@ -215,6 +215,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           (unsigned short)dgt;
     }
   }
+  // the digit slots of padded columns (c >= kin) stay zero: written once here
+  for (unsigned e = tid; e < 2u * GS * SLAB_A / 16u; e += kThreads)
+    reinterpret_cast<uint4*>(adig)[e] = make_uint4(0u, 0u, 0u, 0u);
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
@@ -285,6 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if constexpr (kStageValues<W>) prefetch(blockIdx.x);
 
     auto epilogue = [&](int64_t T, int64_t i) {
+      if (ep * 4 >= kout) return;  // all four outputs of this warp are padding (warp-uniform)
       const unsigned tb = tq + (unsigned)(i & 1) * kAccCols;
       // h = p0 2^70 + p1 2^35 + p2 with p_c = sum over the five diagonals
       // d = 5c .. 5c + 4 of S_d 2^(7 (5c + 4 - d)) (|p_c| < 2^53: 64-bit chains)
@@ -352,24 +356,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         Arow[(i & 1) * kRows + r] = Ar;
         Rbad[(i & 1) * kRows + r] = e == 2047;
       }
+      // some of this thread's columns are real (else its digits stay zero); kin <= 64 keeps
+      // every thread converting (there the test costs more than it saves)
+      const bool live = W == 16 || c0 < kin;
       PairLanes P[W / 2];  // the W values as interleaved pairs
       unsigned sg[W / 2];
+      if (live) {
 #pragma unroll
-      for (int m = 0; m < W / 2; ++m) {
-        unsigned xa[4], xb[4];
-        xwords(v[2 * m], Ar, xa);
-        xwords(v[2 * m + 1], Ar, xb);
-        P[m] = pair_lanes(xa, xb);
-        sg[m] = ((hi32(v[2 * m]) >> 31) << 15) | (hi32(v[2 * m + 1]) & 0x80000000u);
+        for (int m = 0; m < W / 2; ++m) {
+          unsigned xa[4], xb[4];
+          xwords(v[2 * m], Ar, xa);
+          xwords(v[2 * m + 1], Ar, xb);
+          P[m] = pair_lanes(xa, xb);
+          sg[m] = ((hi32(v[2 * m]) >> 31) << 15) | (hi32(v[2 * m + 1]) & 0x80000000u);
+        }
       }
 
       // NG groups of GS slabs into the alternating buffers
 #pragma unroll
       for (int g = 0; g < NG; ++g, ++G) {
         const int b = G & 1;
+        // every thread waits (the next epilogue relies on it), only live ones store
         if (G >= 2) mbar_wait(fb0 + 8u * b, (unsigned)((G - 2) >> 1) & 1u, &bad);  // MMAs of group G - 2 done
-        const unsigned dst = adig_s + (unsigned)b * GS * SLAB_A + dofs;
-        store_group_rt<W>(g, dst, SLAB_A, P, sg);
+        if (live) store_group_rt<W>(g, adig_s + (unsigned)b * GS * SLAB_A + dofs, SLAB_A, P, sg);
         fence_proxy_async();
         mbar_arrive(rb0 + 8u * b);
       }
