@@ -89,7 +89,9 @@ struct UPlan {
 // matrix) and reads them back at panel p; the rest is the same.
 constexpr unsigned kDirectStageBytes = 2u * kMaxItems * kConvThreads * 16u;
 
-template <int KYP, bool DIRECT>
+// PAD: the tile has padded columns (beyond kx or ky, e.g. kx = 40 in a
+// 64-column plan): their digits are zeroed once and never converted.
+template <int KYP, bool DIRECT, bool PAD>
 __global__ void __launch_bounds__(kThreads, 1)
     umma_gram_partial_kernel(int64_t n, int kx, const double* __restrict__ X, int64_t ldx, int ky,
                              const double* __restrict__ Y, int64_t ldy, UPlan pl, int64_t rows_per_chunk,
@@ -299,9 +301,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       it_d[k] = ((isb ? pl.a_bytes : 0u) + (unsigned)(lc >> 3) * SBO + (unsigned)rh * 128u +
                  (unsigned)(lc & 7) * 16u + (unsigned)rl * 4u) |
                 ((unsigned)isb << 31);
+      if constexpr (PAD) {  // bit 30: a padded column, whose digits stay zero
+        if (i < nitems && !(isb ? y0 + lc < ky : x0 + lc < kx)) it_d[k] |= 1u << 30;
+      }
     }
     const unsigned stride_a = (unsigned)kxp / 8u * SBO, stride_b = (unsigned)KYP / 8u * SBO;
     const bool scan_lead = (lane & 24) == 0;  // one lane of the four that share a column
+    if constexpr (PAD) {  // the digit words of padded columns: zero once, in both buffers
+#pragma unroll
+      for (int k = 0; k < kMaxItems; ++k) {
+        if (it_d[k] & 0x40000000u) {
+          for (int b = 0; b < 2; ++b) {
+            unsigned char* d = dig + (size_t)b * pl.dig_bytes + (it_d[k] & 0x3fffffffu);
+            const unsigned strd = (it_d[k] >> 31) ? stride_b : stride_a;
+            for (int sl = 0; sl < NS; ++sl) *reinterpret_cast<unsigned*>(d + sl * strd) = 0u;
+          }
+        }
+      }
+    }
 
     // DIRECT: each item's column (null: zeros) and row offset in the panel
     const double* gcol[kMaxItems];
@@ -401,12 +418,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
-        if (tid + k * kConvThreads < nitems) {
+        if (tid + k * kConvThreads < nitems && (!PAD || !(it_d[k] & 0x40000000u))) {
           unsigned wa[4], wb[4];
           xwords(v[k].x, A[k], wa);
           xwords(v[k].y, A[k], wb);
           const unsigned signs = ((hi32(v[k].x) >> 31) << 15) | (hi32(v[k].y) & 0x80000000u);
-          store_digits<0>(dbuf + (it_d[k] & 0x7fffffffu), (it_d[k] >> 31) ? stride_b : stride_a, pair_lanes(wa, wb),
+          store_digits<0>(dbuf + (it_d[k] & (PAD ? 0x3fffffffu : 0x7fffffffu)), (it_d[k] >> 31) ? stride_b : stride_a,
+                          pair_lanes(wa, wb),
                           signs);
         }
       }
@@ -590,15 +608,15 @@ size_t plan_smem_direct(const UPlan& p) {
   return plan_smem(p) - 2 * (size_t)p.stage_bytes + std::max<size_t>(2 * (size_t)p.stage_bytes, kDirectStageBytes);
 }
 
-template <int KYP, bool DIRECT>
+template <int KYP, bool DIRECT, bool PAD>
 cudaError_t launch_kernel(const UPlan& plan, int chunks, int64_t n, int kx, const double* X, int64_t ldx, int ky,
                           const double* Y, int64_t ldy, int64_t rpc, const CUtensorMap& tmx, const CUtensorMap& tmy,
                           FxPart* parts, const int* gate, cudaStream_t st) {
   const size_t smem = DIRECT ? plan_smem_direct(plan) : plan_smem(plan);
-  cudaError_t e = set_dyn_smem(umma_gram_partial_kernel<KYP, DIRECT>, smem);
+  cudaError_t e = set_dyn_smem(umma_gram_partial_kernel<KYP, DIRECT, PAD>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(plan.ntx * plan.nty, chunks);
-  umma_gram_partial_kernel<KYP, DIRECT>
+  umma_gram_partial_kernel<KYP, DIRECT, PAD>
       <<<grid, kThreads, smem, st>>>(n, kx, X, ldx, ky, Y, ldy, plan, rpc, tmx, tmy, parts, gate);
   return cudaGetLastError();
 }
@@ -642,15 +660,17 @@ cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, in
   int64_t rpc = (n + chunks - 1) / chunks;
   rpc = std::max<int64_t>(plan.P, (rpc + plan.P - 1) / plan.P * plan.P);
   FxPart* parts = static_cast<FxPart*>(scratch);
+  const bool pad = plan.ntx * plan.kxp > kx || (!plan.shared && plan.nty * plan.kyp > ky);
   cudaError_t e;
-  if (direct)
-    e = plan.kyp == 16
-            ? launch_kernel<16, true>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st)
-            : launch_kernel<8, true>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st);
+#define EO_UMMA_LAUNCH(K, D, PD) \
+  launch_kernel<K, D, PD>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st)
+  if (plan.kyp == 16)
+    e = direct ? (pad ? EO_UMMA_LAUNCH(16, true, true) : EO_UMMA_LAUNCH(16, true, false))
+               : (pad ? EO_UMMA_LAUNCH(16, false, true) : EO_UMMA_LAUNCH(16, false, false));
   else
-    e = plan.kyp == 16
-            ? launch_kernel<16, false>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st)
-            : launch_kernel<8, false>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st);
+    e = direct ? (pad ? EO_UMMA_LAUNCH(8, true, true) : EO_UMMA_LAUNCH(8, true, false))
+               : (pad ? EO_UMMA_LAUNCH(8, false, true) : EO_UMMA_LAUNCH(8, false, false));
+#undef EO_UMMA_LAUNCH
   if (e != cudaSuccess) return e;
   return launch_fx_reduce(kx, ky, sym, chunks, parts, G_hi, G_lo, ldg, gate, st);
 }
