@@ -145,8 +145,9 @@ __device__ __forceinline__ i128 fixed_trunc(double x, int A) {
   return (hi >> 31) ? -(i128)X : (i128)X;
 }
 
-// KP = 4 W: the K dimension (kin padded to 16, 32 or 64).
-template <int W>
+// KP = 4 W: the K dimension (kin padded to 16, 32 or 64).  PAD: kin < KP,
+// so the threads whose columns are all padding skip their conversion.
+template <int W, bool PAD>
 __global__ void __launch_bounds__(kThreads, 1)
     umma_rowprod_kernel(int update, int64_t n, int kin, const double* A, int64_t lda, int kout,
                         const double* __restrict__ Bh, const double* __restrict__ Bl, int ldb, int tri,
@@ -215,9 +216,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           (unsigned short)dgt;
     }
   }
-  // the digit slots of padded columns (c >= kin) stay zero: written once here
-  for (unsigned e = tid; e < 2u * GS * SLAB_A / 16u; e += kThreads)
-    reinterpret_cast<uint4*>(adig)[e] = make_uint4(0u, 0u, 0u, 0u);
+  if constexpr (PAD) {  // the digit slots of padded columns (c >= kin) stay zero: written once here
+    for (unsigned e = tid; e < 2u * GS * SLAB_A / 16u; e += kThreads)
+      reinterpret_cast<uint4*>(adig)[e] = make_uint4(0u, 0u, 0u, 0u);
+  }
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
@@ -356,9 +358,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         Arow[(i & 1) * kRows + r] = Ar;
         Rbad[(i & 1) * kRows + r] = e == 2047;
       }
-      // some of this thread's columns are real (else its digits stay zero); kin <= 64 keeps
-      // every thread converting (there the test costs more than it saves)
-      const bool live = W == 16 || c0 < kin;
+      // some of this thread's columns are real (else its digits stay zero)
+      const bool live = !PAD || c0 < kin;
       PairLanes P[W / 2];  // the W values as interleaved pairs
       unsigned sg[W / 2];
       if (live) {
@@ -418,17 +419,17 @@ size_t smem_bytes() {
   return std::max(b + a + small + stage, kMinSmem);
 }
 
-template <int W>
+template <int W, bool PAD>
 cudaError_t launch_w(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout, const double* Bh,
                      const double* Bl, int ldb, bool tri, const double* Yin, int64_t ldyin, double* Out, int64_t ldo,
                      const int* gate, cudaStream_t st, int ctas) {
   const size_t smem = smem_bytes<W>();
-  cudaError_t e = set_dyn_smem(umma_rowprod_kernel<W>, smem);
+  cudaError_t e = set_dyn_smem(umma_rowprod_kernel<W, PAD>, smem);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (n + kRows - 1) / kRows;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, ctas > 0 ? ctas : 152));
-  umma_rowprod_kernel<W><<<grid, kThreads, smem, st>>>(update ? 1 : 0, n, kin, A, lda, kout, Bh, Bl, ldb, tri ? 1 : 0,
-                                                       Yin, ldyin, Out, ldo, gate);
+  umma_rowprod_kernel<W, PAD><<<grid, kThreads, smem, st>>>(update ? 1 : 0, n, kin, A, lda, kout, Bh, Bl, ldb,
+                                                            tri ? 1 : 0, Yin, ldyin, Out, ldo, gate);
   return cudaGetLastError();
 }
 
@@ -453,10 +454,19 @@ cudaError_t launch_umma_rowprod(bool update, int64_t n, int kin, const double* A
                                 int ctas) {
   if (n <= 0) return cudaSuccess;
   if (kin <= 16)
-    return launch_w<4>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
+    return kin < 16 ? launch_w<4, true>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate,
+                                        st, ctas)
+                    : launch_w<4, false>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate,
+                                         st, ctas);
   if (kin <= 32)
-    return launch_w<8>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
-  return launch_w<16>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
+    return kin < 32 ? launch_w<8, true>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate,
+                                        st, ctas)
+                    : launch_w<8, false>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate,
+                                         st, ctas);
+  return kin < 64 ? launch_w<16, true>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st,
+                                       ctas)
+                  : launch_w<16, false>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st,
+                                        ctas);
 }
 
 }  // namespace eo
