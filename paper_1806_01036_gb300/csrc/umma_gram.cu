@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                      : 2 * (size_t)pl.stage_bytes;
   unsigned char* dig = stage + stage_region;                   // 2 digit buffers
   int* Erun = reinterpret_cast<int*>(dig + 2 * (size_t)pl.dig_bytes);
-  int* pmax = Erun + nslots;  // two panels' column maxima
+  int* pmax = Erun + 2 * nslots;  // three panels' column maxima (Erun: running exponents, two buffers)
   __shared__ __align__(8) unsigned long long full_bar[2], ready_bar[2], stage_bar[2];
   __shared__ unsigned tmem_base;
   __shared__ int flag, bad, fresh_flag[2];
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     flag = 0;
     bad = 0;
   }
-  for (int c = tid; c < 3 * nslots; c += kThreads) Erun[c] = 0;  // Erun and both pmax
+  for (int c = tid; c < 5 * nslots; c += kThreads) Erun[c] = 0;  // Erun and pmax
   {  // slab 15 of every operand stays zero
     const unsigned za = (unsigned)kxp / 8u * SBO, zb = (unsigned)KYP / 8u * SBO;  // bytes of one slab
     for (int b = 0; b < 2; ++b) {
@@ -352,38 +352,36 @@ __global__ void __launch_bounds__(kThreads, 1)
       prefetch(1);
     }
 
-    int undrained = 0, drains = 0;
-    bool fresh = true;
-    for (int p = 0; p < npan; ++p) {
-      const int db = p & 1;
-      const unsigned char* st = stage + (size_t)db * pl.stage_bytes;
-      int* pm = pmax + db * nslots;  // this panel's column maxima
-      if constexpr (DIRECT) asm volatile("cp.async.wait_group 1;" ::: "memory");  // this thread's items of panel p
-      else mbar_wait(sb0 + 8u * db, (unsigned)(p >> 1) & 1u, &bad);             // panel p staged
-      bar_conv<kConvThreads>();  // every converter is past panel p-1
-      if (p > 0 && tid < nslots) {  // fold panel p-1's maxima into the running exponents
-        int* pq = pmax + ((p - 1) & 1) * nslots;
-        Erun[tid] = max(Erun[tid], pq[tid]);
-        pq[tid] = 0;
-      }
-
-      // this thread's values of the panel (kept in registers for the conversion)
-      double2 v[kMaxItems];
+    // One barrier per panel.  The values of panel p are in registers and
+    // the maxima of its columns complete in pmax[p % 3] when panel p begins
+    // (both done during panel p-1): a converter aligns and converts p, drains
+    // TMEM if due, marks p ready for the MMA warp, then reads and scans panel
+    // p+1 while those MMAs run; the barrier that ends the panel completes
+    // that scan.  The running exponents through panel q sit in Erun[q & 1],
+    // the maxima of panel q in pmax[q % 3]; a buffer is rewritten only after
+    // the barrier that follows its last read.
+    auto stage_values = [&](int q, double2 (&v)[kMaxItems]) {  // this thread's items of panel q
       if constexpr (DIRECT) {
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // panel q's copies (q + 1's may be in flight)
 #pragma unroll
         for (int k = 0; k < kMaxItems; ++k)
-          v[k] = gcol[k] ? *reinterpret_cast<const double2*>(stage + ((size_t)(db * kMaxItems + k) * kConvThreads +
+          v[k] = gcol[k] ? *reinterpret_cast<const double2*>(stage + ((size_t)((q & 1) * kMaxItems + k) * kConvThreads +
                                                                       tid) * 16u)
                          : make_double2(0.0, 0.0);
-        prefetch(p + 2);  // into the slots just read (zeros past the chunk)
+        prefetch(q + 2);  // into the slots just read (zeros past the chunk)
       } else {
+        mbar_wait(sb0 + 8u * (unsigned)(q & 1), (unsigned)(q >> 1) & 1u, &bad);  // panel q staged
+        const unsigned char* st = stage + (size_t)(q & 1) * pl.stage_bytes;
 #pragma unroll
         for (int k = 0; k < kMaxItems; ++k)
-          v[k] = tid + k * kConvThreads < nitems
-                     ? *reinterpret_cast<const double2*>(st + ((it_s[k] & 0xffffu) << 4))
-                     : make_double2(0.0, 0.0);
+          v[k] = tid + k * kConvThreads < nitems ? *reinterpret_cast<const double2*>(st + ((it_s[k] & 0xffffu) << 4))
+                                                 : make_double2(0.0, 0.0);
       }
-      // largest exponent of each column in the panel: max of |x| bit patterns
+    };
+    // largest exponent of each column of a panel (max of |x| bit patterns)
+    // into pmq; true if one of this thread's columns exceeds max(ea, eb), a
+    // nonzero running exponent
+    auto scan = [&](const double2 (&v)[kMaxItems], int* pmq, const int* ea, const int* eb) -> bool {
       unsigned m[kMaxItems];
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k)
@@ -393,29 +391,56 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int k = 0; k < kMaxItems; ++k) m[k] = max(m[k], __shfl_xor_sync(0xffffffffu, m[k], 8));
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) m[k] = max(m[k], __shfl_xor_sync(0xffffffffu, m[k], 16));
+      bool g = false;
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
         if (scan_lead && m[k] && tid + k * kConvThreads < nitems) {
           int e = (int)(m[k] >> 20);
           if (e == 0) e = 1;  // subnormal
           if (e == 2047) flag = 1;
-          atomicMax(&pm[it_s[k] >> 16], e);
+          const int c = (int)(it_s[k] >> 16);
+          atomicMax(&pmq[c], e);
+          const int t = max(ea[c], eb[c]);
+          g |= t != 0 && e > t;
         }
       }
-      bar_conv<kConvThreads>();
-      const bool grew_local = tid < nslots && Erun[tid] != 0 && pm[tid] > Erun[tid];
+      return g;
+    };
 
-      // the digit buffer db is free once the MMAs of panel p-2 are done
-      if (p >= 2) mbar_wait(fb0 + 8u * db, (unsigned)((p - 2) >> 1) & 1u, &bad);
+    double2 v[kMaxItems];
+    bool grew = false;  // a column of the current panel exceeds its running exponent
+    if (npan > 0) {
+      stage_values(0, v);
+      (void)scan(v, pmax, Erun + nslots, Erun + nslots);  // nothing has accumulated yet
+    }
+    bar_conv<kConvThreads>();
+    if (!DIRECT && tid == 0 && 2 < npan) {  // staging buffer 0 is read: panel 2
+      fence_proxy_async();
+      load_panel(2);
+    }
 
-      // digits of panel p
-      unsigned char* dbuf = dig + (size_t)db * pl.dig_bytes;
+    int undrained = 0, drains = 0, pc = 0;
+    bool fresh = true;
+    for (int p = 0; p < npan; ++p) {
+      const int db = p & 1;
+      const int pn = pc == 2 ? 0 : pc + 1, pz = pn == 2 ? 0 : pn + 1;  // (p + 1) % 3, (p + 2) % 3
+      const int* eprev = Erun + (db ^ 1) * nslots;  // through panel p-1
+      const int* pcur = pmax + pc * nslots;         // panel p
+      if (tid < nslots) {
+        Erun[db * nslots + tid] = max(eprev[tid], pcur[tid]);  // through panel p
+        pmax[pz * nslots + tid] = 0;                           // panel p-1's, read for the last time in p-1
+      }
       int A[kMaxItems];
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
         const int c = (int)(it_s[k] >> 16);
-        A[k] = max(max(Erun[c], pm[c]), 1);
+        A[k] = max(max(eprev[c], pcur[c]), 1);
       }
+
+      // the digit buffer db is free once the MMAs of panel p-2 are done
+      if (p >= 2) mbar_wait(fb0 + 8u * db, (unsigned)((p - 2) >> 1) & 1u, &bad);
+      // digits of panel p
+      unsigned char* dbuf = dig + (size_t)db * pl.dig_bytes;
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
         if (tid + k * kConvThreads < nitems && (!PAD || !(it_d[k] & 0x40000000u))) {
@@ -429,12 +454,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       fence_proxy_async();
-      const bool grew = bar_conv_or<kConvThreads>(grew_local);
-      if (!DIRECT && tid == 0 && p + 2 < npan) {  // staging buffer db is free: panel p + 2
-        fence_proxy_async();
-        load_panel(p + 2);
-      }
 
+      // this thread's accumulators (its own TMEM lanes and columns) are drained
+      // before it marks panel p ready
       if ((grew || undrained >= pl.drain_panels) && undrained > 0) {
         // all MMAs so far (the last commit is panel p-1's) are done before TMEM is read
         mbar_wait(fb0 + 8u * ((p - 1) & 1), (unsigned)((p - 1) >> 1) & 1u, &bad);
@@ -450,8 +472,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int y = 0; y < NY; ++y) {
             const int cx = xl, cy = ysb + yq + y;
-            const int dx = Erun[cx] ? max(Erun[cx], pm[cx]) - Erun[cx] : 0;
-            const int dy = Erun[cy] ? max(Erun[cy], pm[cy]) - Erun[cy] : 0;
+            const int dx = eprev[cx] ? max(eprev[cx], pcur[cx]) - eprev[cx] : 0;
+            const int dy = eprev[cy] ? max(eprev[cy], pcur[cy]) - eprev[cy] : 0;
             W[y] = w_shift(W[y], dx + dy);
           }
         }
@@ -463,6 +485,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_arrive(rb0 + 8u * db);  // digits of p ready (and TMEM drained if it was due)
       fresh = false;
       ++undrained;
+
+      // panel p+1: values and column maxima (growth against the exponents through p)
+      bool gl = false;
+      double2 vn[kMaxItems];
+#pragma unroll
+      for (int k = 0; k < kMaxItems; ++k) vn[k] = make_double2(0.0, 0.0);
+      if (p + 1 < npan) {
+        stage_values(p + 1, vn);
+        gl = scan(vn, pmax + pn * nslots, eprev, pcur);
+      }
+      grew = bar_conv_or<kConvThreads>(gl);
+      if (!DIRECT && tid == 0 && p + 3 < npan) {  // staging buffer (p + 1) & 1 is read: panel p + 3
+        fence_proxy_async();
+        load_panel(p + 3);
+      }
+#pragma unroll
+      for (int k = 0; k < kMaxItems; ++k) v[k] = vn[k];
+      pc = pn;
     }
 
     if constexpr (DIRECT) asm volatile("cp.async.wait_all;" ::: "memory");  // the last (empty) copies
@@ -474,8 +514,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       fold();
       tc_fence_before();
     }
-    bar_conv<kConvThreads>();
-    if (npan > 0 && tid < nslots) Erun[tid] = max(Erun[tid], pmax[((npan - 1) & 1) * nslots + tid]);
   }
 
   __syncthreads();
@@ -492,6 +530,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   __syncthreads();
   const int J = pl.J;
+  const int* Efin = Erun + ((npan - 1) & 1) * nslots;  // running exponents through the last panel
   for (int e = tid; e < kxp * KYP; e += kThreads) {
     const int xo = e / KYP, yo = e % KYP;
     const int i = x0 + xo, j = y0 + yo;
@@ -502,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     FxPart o;
     o.wl = (long long)(unsigned long long)(u128)w;
     o.wh = (long long)(w >> 64);
-    o.s = max(Erun[xo], 1) + max(Erun[cy], 1) - kOffsetDigits;
+    o.s = max(Efin[xo], 1) + max(Efin[cy], 1) - kOffsetDigits;
     o.flag = flag | bad;
     o.pad = 0;
     parts[(size_t)blockIdx.y * ((size_t)kx * ky) + (size_t)j * kx + i] = o;
@@ -540,7 +579,7 @@ UPlan make_plan(int kx, int ky, bool sym) {
     const size_t dig = (size_t)32 * P * (p.shared ? p.kxp : p.kxp + p.kyp);
     const size_t stg = (size_t)p.nslots * P * 8;
     const size_t red = (size_t)kLanes * p.kyp * 16;
-    if (std::max(2 * dig, red) + 2 * stg + 12 * (size_t)p.nslots + 1024 > kSmemCap) break;
+    if (std::max(2 * dig, red) + 2 * stg + 20 * (size_t)p.nslots + 1024 > kSmemCap) break;
     best = P;
   }
   p.P = best;
@@ -557,7 +596,7 @@ UPlan make_plan(int kx, int ky, bool sym) {
 
 size_t plan_smem(const UPlan& p) {
   const size_t red = (size_t)kLanes * p.kyp * 16;
-  return std::max(2 * (size_t)p.dig_bytes, red) + 2 * (size_t)p.stage_bytes + 3 * sizeof(int) * p.nslots + 1024;
+  return std::max(2 * (size_t)p.dig_bytes, red) + 2 * (size_t)p.stage_bytes + 5 * sizeof(int) * p.nslots + 1024;
 }
 
 int num_chunks(int64_t n, const UPlan& p) {
