@@ -69,6 +69,9 @@ constexpr size_t kMinSmem = 120 * 1024;      // keeps one CTA per SM (TMEM: 512 
 // some, cost more than the staging saves): its loads stay direct.
 template <int W>
 constexpr bool kStageValues = W <= 8;
+// Without staging, the next tile's values are loaded into registers once
+// this tile's digits are stored (its values and digit words are dead then),
+// so the loads are in flight during the previous tile's epilogue.
 
 __device__ __forceinline__ void st_shared_v4(unsigned addr, unsigned a, unsigned b, unsigned c, unsigned d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
@@ -327,10 +330,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     };
 
+    // this thread's W values of row r of tile T (zero beyond the matrix)
+    auto load_direct = [&](int64_t T, double (&v)[W]) {
+      const int64_t gr = T * kRows + r;
+#pragma unroll
+      for (int k = 0; k < W; ++k) {
+        const int col = c0 + k;
+        v[k] = (T < ntiles && gr < n && col < kin) ? A[(size_t)col * lda + gr] : 0.0;
+      }
+    };
+    double vn[W];  // without staging: the values of the tile to come
+    if constexpr (!kStageValues<W>) load_direct(blockIdx.x, vn);
+
     int G = 0;
     int64_t Tprev = -1, iprev = 0;
     for (int64_t T = blockIdx.x, i = 0; T < ntiles; T += gridDim.x, ++i) {
-      // this thread's W values of row r (zero beyond the matrix)
       double v[W];
       if constexpr (kStageValues<W>) {
         asm volatile("cp.async.wait_all;" ::: "memory");  // this tile's copies, issued a tile ago
@@ -338,12 +352,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int k = 0; k < W; ++k) v[k] = stg[k * kConvThreads + tid];
         prefetch(T + gridDim.x);  // the next tile's values into the same slots, while this one runs
       } else {
-        const int64_t gr = T * kRows + r;
 #pragma unroll
-        for (int k = 0; k < W; ++k) {
-          const int col = c0 + k;
-          v[k] = (gr < n && col < kin) ? A[(size_t)col * lda + gr] : 0.0;
-        }
+        for (int k = 0; k < W; ++k) v[k] = vn[k];
       }
       // the row's exponent: max of |x| bit patterns over the four threads of the row
       unsigned key = 0;
@@ -383,6 +393,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_proxy_async();
         mbar_arrive(rb0 + 8u * b);
       }
+      if constexpr (!kStageValues<W>) load_direct(T + gridDim.x, vn);
       // the previous tile's MMAs completed (its last group was waited for before
       // this tile's second group was written): its epilogue overlaps this tile's MMAs
       if (Tprev >= 0) {
@@ -458,15 +469,12 @@ cudaError_t launch_umma_rowprod(bool update, int64_t n, int kin, const double* A
                                         st, ctas)
                     : launch_w<4, false>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate,
                                          st, ctas);
+  // kin > 16: every thread converts (its padded columns are zeros).  The
+  // skip would not pay here: with 8 or 16 values and their digit words per
+  // thread, the branch leaves too few registers (spills; measured slower).
   if (kin <= 32)
-    return kin < 32 ? launch_w<8, true>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate,
-                                        st, ctas)
-                    : launch_w<8, false>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate,
-                                         st, ctas);
-  return kin < 64 ? launch_w<16, true>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st,
-                                       ctas)
-                  : launch_w<16, false>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st,
-                                        ctas);
+    return launch_w<8, false>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
+  return launch_w<16, false>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
 }
 
 }  // namespace eo
