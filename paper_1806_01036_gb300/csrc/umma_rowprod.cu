@@ -66,13 +66,27 @@ constexpr size_t kMinSmem = 120 * 1024;      // keeps one CTA per SM (TMEM: 512 
 // values of the next tile there (one buffer: a tile's values are read before
 // the next tile's copies are issued into the same slots) while the current
 // tile runs.  kin <= 64 has no room left (and smaller digit groups, to make
-// some, cost more than the staging saves): its loads stay direct.
+// some, cost more than the staging saves): there the next tile's values are
+// loaded into registers once this tile's digits are stored (its values and
+// digit words are dead then), so the loads are in flight during the
+// previous tile's epilogue.
 template <int W>
 constexpr bool kStageValues = W <= 8;
-// Without staging, the next tile's values are loaded into registers once
-// this tile's digits are stored (its values and digit words are dead then),
-// so the loads are in flight during the previous tile's epilogue.
 
+// Diagonal d of a tile sums (d + 1) kin <= (d + 1) 4 W digit products of
+// magnitude <= 127^2.  Diagonals d <= kRoundDiag stay below 2^22 units, so
+// their integer value comes out of one FP32 add (the bit pattern of
+// 1.5 2^23 + S_d is 0x4B400000 + S_d) instead of a float-to-int conversion.
+template <int W>
+constexpr int kRoundDiag = (int)(4194303 / (4 * W * 127 * 127)) - 1;
+static_assert(kRoundDiag<4> >= 14 && kRoundDiag<8> == 7 && kRoundDiag<16> == 3, "diagonal bounds");
+// What those patterns add to chain c (diagonals 5c .. 5c + 4, weights 128^(5c + 4 - d)).
+template <int W>
+__host__ __device__ constexpr long long chain_offset(int c) {
+  long long o = 0;
+  for (int d = 5 * c; d < 5 * c + 5; ++d) o = o * 128 + (d <= kRoundDiag<W> ? 0x4B400000ll : 0ll);
+  return o;
+}
 __device__ __forceinline__ void st_shared_v4(unsigned addr, unsigned a, unsigned b, unsigned c, unsigned d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
@@ -148,9 +162,9 @@ __device__ __forceinline__ i128 fixed_trunc(double x, int A) {
   return (hi >> 31) ? -(i128)X : (i128)X;
 }
 
-// KP = 4 W: the K dimension (kin padded to 16, 32 or 64).  PAD: kin < KP,
-// so the threads whose columns are all padding skip their conversion.
-template <int W, bool PAD>
+// KP = 4 W: the K dimension (kin padded to 16, 32 or 64; padded columns
+// are converted as zeros).
+template <int W>
 __global__ void __launch_bounds__(kThreads, 1)
     umma_rowprod_kernel(int update, int64_t n, int kin, const double* A, int64_t lda, int kout,
                         const double* __restrict__ Bh, const double* __restrict__ Bl, int ldb, int tri,
@@ -218,10 +232,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       *reinterpret_cast<unsigned short*>(bdig + (R >> 3) * SBO + (i >> 3) * 128 + (R & 7) * 16 + (i & 7) * 2) =
           (unsigned short)dgt;
     }
-  }
-  if constexpr (PAD) {  // the digit slots of padded columns (c >= kin) stay zero: written once here
-    for (unsigned e = tid; e < 2u * GS * SLAB_A / 16u; e += kThreads)
-      reinterpret_cast<uint4*>(adig)[e] = make_uint4(0u, 0u, 0u, 0u);
   }
   fence_proxy_async();
   tc_fence_before();
@@ -307,14 +317,23 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int d = d0 + u, c = d / 5;
 #pragma unroll
           for (int y = 0; y < 4; ++y) {
-            const long long sd = __float2int_rn(__uint_as_float(v[u][y]) * 0x1p48f);
+            // S_d = accumulator x 2^48; diagonals below 2^22 units come out of
+            // the FP32 add of 1.5 2^23 as its bit pattern 0x4B400000 + S_d
+            // (the offsets are taken off the chains below)
+            const long long sd = d <= kRoundDiag<W>
+                                     ? (long long)__float_as_uint(fmaf(__uint_as_float(v[u][y]), 0x1p48f, 0x1.8p23f))
+                                     : (long long)__float2int_rn(__uint_as_float(v[u][y]) * 0x1p48f);
             p[c][y] = (d % 5 == 0) ? sd : p[c][y] * 128 + sd;
           }
         }
       }
       i128 h[4];
 #pragma unroll
-      for (int y = 0; y < 4; ++y) h[y] = ((i128)p[0][y] << 70) + ((i128)p[1][y] << 35) + (i128)p[2][y];
+      for (int y = 0; y < 4; ++y) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[c][y] -= chain_offset<W>(c);
+        h[y] = ((i128)p[0][y] << 70) + ((i128)p[1][y] << 35) + (i128)p[2][y];
+      }
       const int64_t grow = T * kRows + L;
       const int Ar = Arow[(i & 1) * kRows + L];
       const bool rbad = Rbad[(i & 1) * kRows + L] != 0;
@@ -368,28 +387,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         Arow[(i & 1) * kRows + r] = Ar;
         Rbad[(i & 1) * kRows + r] = e == 2047;
       }
-      // some of this thread's columns are real (else its digits stay zero)
-      const bool live = !PAD || c0 < kin;
       PairLanes P[W / 2];  // the W values as interleaved pairs
       unsigned sg[W / 2];
-      if (live) {
 #pragma unroll
-        for (int m = 0; m < W / 2; ++m) {
-          unsigned xa[4], xb[4];
-          xwords(v[2 * m], Ar, xa);
-          xwords(v[2 * m + 1], Ar, xb);
-          P[m] = pair_lanes(xa, xb);
-          sg[m] = ((hi32(v[2 * m]) >> 31) << 15) | (hi32(v[2 * m + 1]) & 0x80000000u);
-        }
+      for (int m = 0; m < W / 2; ++m) {
+        unsigned xa[4], xb[4];
+        xwords(v[2 * m], Ar, xa);
+        xwords(v[2 * m + 1], Ar, xb);
+        P[m] = pair_lanes(xa, xb);
+        sg[m] = ((hi32(v[2 * m]) >> 31) << 15) | (hi32(v[2 * m + 1]) & 0x80000000u);
       }
 
       // NG groups of GS slabs into the alternating buffers
 #pragma unroll
       for (int g = 0; g < NG; ++g, ++G) {
         const int b = G & 1;
-        // every thread waits (the next epilogue relies on it), only live ones store
         if (G >= 2) mbar_wait(fb0 + 8u * b, (unsigned)((G - 2) >> 1) & 1u, &bad);  // MMAs of group G - 2 done
-        if (live) store_group_rt<W>(g, adig_s + (unsigned)b * GS * SLAB_A + dofs, SLAB_A, P, sg);
+        store_group_rt<W>(g, adig_s + (unsigned)b * GS * SLAB_A + dofs, SLAB_A, P, sg);
         fence_proxy_async();
         mbar_arrive(rb0 + 8u * b);
       }
@@ -430,16 +444,16 @@ size_t smem_bytes() {
   return std::max(b + a + small + stage, kMinSmem);
 }
 
-template <int W, bool PAD>
+template <int W>
 cudaError_t launch_w(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout, const double* Bh,
                      const double* Bl, int ldb, bool tri, const double* Yin, int64_t ldyin, double* Out, int64_t ldo,
                      const int* gate, cudaStream_t st, int ctas) {
   const size_t smem = smem_bytes<W>();
-  cudaError_t e = set_dyn_smem(umma_rowprod_kernel<W, PAD>, smem);
+  cudaError_t e = set_dyn_smem(umma_rowprod_kernel<W>, smem);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (n + kRows - 1) / kRows;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, ctas > 0 ? ctas : 152));
-  umma_rowprod_kernel<W, PAD><<<grid, kThreads, smem, st>>>(update ? 1 : 0, n, kin, A, lda, kout, Bh, Bl, ldb,
+  umma_rowprod_kernel<W><<<grid, kThreads, smem, st>>>(update ? 1 : 0, n, kin, A, lda, kout, Bh, Bl, ldb,
                                                             tri ? 1 : 0, Yin, ldyin, Out, ldo, gate);
   return cudaGetLastError();
 }
@@ -465,16 +479,10 @@ cudaError_t launch_umma_rowprod(bool update, int64_t n, int kin, const double* A
                                 int ctas) {
   if (n <= 0) return cudaSuccess;
   if (kin <= 16)
-    return kin < 16 ? launch_w<4, true>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate,
-                                        st, ctas)
-                    : launch_w<4, false>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate,
-                                         st, ctas);
-  // kin > 16: every thread converts (its padded columns are zeros).  The
-  // skip would not pay here: with 8 or 16 values and their digit words per
-  // thread, the branch leaves too few registers (spills; measured slower).
+    return launch_w<4>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
   if (kin <= 32)
-    return launch_w<8, false>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
-  return launch_w<16, false>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
+    return launch_w<8>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
+  return launch_w<16>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
 }
 
 }  // namespace eo
