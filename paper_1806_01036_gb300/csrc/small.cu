@@ -2,15 +2,17 @@
 // (arXiv:1806.01036, Sec. 4.2: "operations on small n_b x n_b matrices are
 // cost negligible, even in extended precision").
 //
-//   chol_small:  M = R^T R (right-looking Cholesky, R upper with positive
-//                diagonal), Z = R^{-1} (column-parallel back substitution),
-//                T <- R T (R of all passes), and the gates of what follows.
+//   chol_small:  M = R^T R (R upper with positive diagonal) by the
+//                square-root-free elimination M = L D L^T, carrying
+//                L^{-1} along, so R = D^{1/2} L^T and Z = R^{-1} =
+//                L^{-T} D^{-1/2}; T <- R T (R of all passes), and the gates
+//                of what follows.
 //   svqb_small:  M = U Lambda U^T by cyclic Jacobi in the parallel
 //                (round-robin) ordering, Z = U Lambda^{+1/2} U^T = M^{-1/2}
 //                (Frobenius-nearest to I among Z with Z^T M Z = I, by the
 //                Procrustes argument of the same section), T <- T Z.
-// In EO_DD the arithmetic is DD throughout (divisions and square roots by
-// Newton-Raphson, dd.cuh); otherwise it is FP64.
+// In EO_DD the arithmetic is DD throughout (divisions, reciprocals and
+// square roots by Newton-Raphson); otherwise it is FP64.
 #include <algorithm>
 
 #include "common.cuh"
@@ -34,6 +36,7 @@ struct Ar {
   static __device__ __forceinline__ dd div(dd a, dd b) { return dd{__ddiv_rn(a.hi, b.hi), 0.0}; }
   static __device__ __forceinline__ dd sqrt(dd a) { return dd{__dsqrt_rn(a.hi), 0.0}; }
   static __device__ __forceinline__ dd fma(dd a, dd b, dd c) { return dd{__fma_rn(a.hi, b.hi, c.hi), 0.0}; }
+  static __device__ __forceinline__ dd recip(dd a) { return dd{__drcp_rn(a.hi), 0.0}; }
 };
 
 template <>
@@ -44,6 +47,15 @@ struct Ar<MODE_DD> {
   static __device__ __forceinline__ dd div(dd a, dd b) { return dd_div(a, b); }
   static __device__ __forceinline__ dd sqrt(dd a) { return dd_sqrt(a); }
   static __device__ __forceinline__ dd fma(dd a, dd b, dd c) { return dd_add(dd_mul(a, b), c); }
+  // 1/a for a > 0: y0 = RN(1/a.hi), whose residual 1 - a.hi y0 is exact in
+  // one FMA; with e = 1 - a y0 (|e| <= 2^-52), 1/a = y0 (1 + e + e^2 + ...)
+  // and y0 (e + e^2) is the low part (relative error about 2^-105).
+  static __device__ __forceinline__ dd recip(dd a) {
+    const double y0 = __drcp_rn(a.hi);
+    double e = __fma_rn(-a.hi, y0, 1.0);
+    e = __fma_rn(-a.lo, y0, e);
+    return fast_two_sum(y0, y0 * __fma_rn(e, e, e));
+  }
 };
 
 __device__ __forceinline__ double dabs(double x) { return x < 0 ? -x : x; }
@@ -74,9 +86,8 @@ __device__ __forceinline__ void chol_small_body(int k, const double* Mh, const d
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dd* A = reinterpret_cast<dd*>(smem_raw);  // A(i,j) = A[j*k+i]; R overwrites the upper triangle
   dd* Z = A + k * k;
-  dd* Tb = Z + k * k;  // products B C^{-1} of the block inversion
+  dd* Tb = Z + k * k;  // W = L^{-1}
   __shared__ int flag;
-  __shared__ dd inv;
   const int tid = threadIdx.x;
   if (tid == 0) flag = 0;
   __syncthreads();
@@ -89,26 +100,52 @@ __device__ __forceinline__ void chol_small_body(int k, const double* Mh, const d
     A[t] = v;
   }
   __syncthreads();
+  // Square-root-free (L D L^T) elimination on the upper triangle: at step j
+  // the pivot d_j = A(j,j) and the row A(j, j+1..) are those of the
+  // standard algorithm before scaling, the Schur complement takes
+  // A(a,b) -= A(j,a) A(j,b) / d_j, and W = L^{-1} (L(l,j) = A(j,l) / d_j)
+  // takes W(l,:) -= L(l,j) W(j,:).  The products do not depend on the pivot,
+  // so they run while one thread forms 1/d_j: the dependent chain of a step
+  // is one reciprocal and one multiply-subtract.  Afterwards
+  // R = D^{1/2} L^T and Z = R^{-1} = L^{-T} D^{-1/2} (W: Tb, W(l,c) = Tb[c k + l];
+  // the products: Z, as scratch).
+  __shared__ dd piv_inv;
+  for (int t = tid; t < k * k; t += kThreads) Tb[t] = dd{(t % k) == (t / k) ? 1.0 : 0.0, 0.0};
+  __syncthreads();
   if (flag == 0) {
     for (int j = 0; j < k; ++j) {
-      if (tid == 0) {
-        dd d = A[j * k + j];
-        if (!(d.hi > 0.0)) {
-          flag = j + 1;
-        } else {
-          dd r = A_::sqrt(d);
-          A[j * k + j] = r;
-          inv = A_::div(dd{1.0, 0.0}, r);
+      const int m = k - j - 1, np = m * (m + 1) / 2, nq = m * (j + 1);
+      if (tid == kThreads - 1) {
+        const dd d = A[j * k + j];
+        if (!(d.hi > 0.0)) flag = j + 1;
+        else piv_inv = A_::recip(d);
+      }
+      for (int t = tid; t < np + nq; t += kThreads) {
+        if (t < np) {  // (a, b) = j + 1 + (u, v), u <= v, t = v (v + 1) / 2 + u
+          int v = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+          if ((v + 1) * (v + 2) / 2 <= t) ++v;
+          if (v * (v + 1) / 2 > t) --v;
+          const int a = j + 1 + t - v * (v + 1) / 2, b = j + 1 + v;
+          Z[t] = A_::mul(A[a * k + j], A[b * k + j]);
+        } else {  // W row l = j + 1 + q % m, column c = q / m <= j
+          const int q = t - np, l = j + 1 + q % m, c = q / m;
+          Z[t] = A_::mul(A[l * k + j], Tb[c * k + j]);
         }
       }
       __syncthreads();
       if (flag) break;
-      for (int l = j + 1 + tid; l < k; l += kThreads) A[l * k + j] = A_::mul(A[l * k + j], inv);
-      __syncthreads();
-      const int m = k - j - 1;
-      for (int t = tid; t < m * m; t += kThreads) {
-        const int a = j + 1 + t % m, b = j + 1 + t / m;
-        if (a <= b) A[b * k + a] = A_::sub(A[b * k + a], A_::mul(A[a * k + j], A[b * k + j]));
+      const dd w = piv_inv;
+      for (int t = tid; t < np + nq; t += kThreads) {
+        if (t < np) {
+          int v = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+          if ((v + 1) * (v + 2) / 2 <= t) ++v;
+          if (v * (v + 1) / 2 > t) --v;
+          const int a = j + 1 + t - v * (v + 1) / 2, b = j + 1 + v;
+          A[b * k + a] = A_::sub(A[b * k + a], A_::mul(Z[t], w));
+        } else {
+          const int q = t - np, l = j + 1 + q % m, c = q / m;
+          Tb[c * k + l] = A_::sub(Tb[c * k + l], A_::mul(Z[t], w));
+        }
       }
       __syncthreads();
     }
@@ -121,34 +158,24 @@ __device__ __forceinline__ void chol_small_body(int k, const double* Mh, const d
     }
     return;
   }
-  // Z = R^{-1} by doubling blocks: with R = [P B; 0 Q] and P^{-1}, Q^{-1}
-  // known, the off-diagonal block of R^{-1} is -P^{-1} (B Q^{-1}).  Every
-  // level is two products of independent inner products of length <= b, so
-  // the dependent chain is 2 (1 + 2 + 4 + ...) multiply-adds, not ~k^2/2.
-  for (int t = tid; t < k * k; t += kThreads) Z[t] = dd{0.0, 0.0};
-  __syncthreads();
-  for (int i = tid; i < k; i += kThreads) Z[i * k + i] = A_::div(dd{1.0, 0.0}, A[i * k + i]);
-  __syncthreads();
-  for (int b = 1; b < k; b *= 2) {
-    // pairs (i, j): i in a block's upper half [o, o + b), j in its lower half [o + b, e)
-    const int nblk = (k + 2 * b - 1) / (2 * b);
-    for (int t = tid; t < nblk * b * b; t += kThreads) {  // Tb(i, j) = sum_{l = o+b}^{j} B(i, l) Q^{-1}(l, j)
-      const int blk = t / (b * b), i = blk * 2 * b + (t % (b * b)) % b, j = blk * 2 * b + b + (t % (b * b)) / b;
-      if (j >= k) continue;
-      dd acc = dd{0.0, 0.0};
-      for (int l = blk * 2 * b + b; l <= j; ++l) acc = A_::fma(A[l * k + i], Z[j * k + l], acc);
-      Tb[j * k + i] = acc;
-    }
-    __syncthreads();
-    for (int t = tid; t < nblk * b * b; t += kThreads) {  // Z(i, j) = -sum_{l = i}^{o+b-1} P^{-1}(i, l) Tb(l, j)
-      const int blk = t / (b * b), i = blk * 2 * b + (t % (b * b)) % b, j = blk * 2 * b + b + (t % (b * b)) / b;
-      if (j >= k) continue;
-      dd acc = dd{0.0, 0.0};
-      for (int l = i; l < blk * 2 * b + b; ++l) acc = A_::fma(Z[l * k + i], Tb[j * k + l], acc);
-      Z[j * k + i] = dd_neg(acc);
-    }
-    __syncthreads();
+  // s_j = sqrt(d_j) and 1 / s_j (kept in the diagonal of Z for the moment)
+  for (int j = tid; j < k; j += kThreads) {
+    const dd r = A_::sqrt(A[j * k + j]);
+    A[j * k + j] = r;
+    Z[j * k + j] = A_::recip(r);
   }
+  __syncthreads();
+  // R(j, l) = A(j, l) / s_j (l > j); Z(i, j) = W(j, i) / s_j (i < j)
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    if (i < j) {
+      A[j * k + i] = A_::mul(A[j * k + i], Z[i * k + i]);
+      Z[t] = A_::mul(Tb[i * k + j], Z[j * k + j]);
+    } else if (i > j) {
+      Z[t] = dd{0.0, 0.0};
+    }
+  }
+  __syncthreads();
   for (int t = tid; t < k * k; t += kThreads) {
     const int i = t % k, j = t / k;
     ws->Zh[j * KMAX + i] = Z[t].hi;
