@@ -37,6 +37,8 @@ struct Ar {
   static __device__ __forceinline__ dd sqrt(dd a) { return dd{__dsqrt_rn(a.hi), 0.0}; }
   static __device__ __forceinline__ dd fma(dd a, dd b, dd c) { return dd{__fma_rn(a.hi, b.hi, c.hi), 0.0}; }
   static __device__ __forceinline__ dd recip(dd a) { return dd{__drcp_rn(a.hi), 0.0}; }
+  static __device__ __forceinline__ dd dot2(dd a, dd x, dd b, dd y) { return add(mul(a, x), mul(b, y)); }
+  static __device__ __forceinline__ dd rsqrt(dd a) { return dd{__ddiv_rn(1.0, __dsqrt_rn(a.hi)), 0.0}; }
 };
 
 template <>
@@ -55,6 +57,33 @@ struct Ar<MODE_DD> {
     double e = __fma_rn(-a.hi, y0, 1.0);
     e = __fma_rn(-a.lo, y0, e);
     return fast_two_sum(y0, y0 * __fma_rn(e, e, e));
+  }
+  // a x + b y: the two leading products exactly, their sum exactly, the
+  // cross terms by FMAs into the low part, one renormalization.  The error
+  // is about 2^-104 (|a x| + |b y|), not relative to the result: enough for
+  // a plane rotation, whose rounding errors count against the norm of what
+  // it rotates (and it costs about 22 FP64 operations, against 34 for two
+  // products and an accurate sum).
+  static __device__ __forceinline__ dd dot2(dd a, dd x, dd b, dd y) {
+    const dd p = two_prod(a.hi, x.hi), q = two_prod(b.hi, y.hi);
+    const dd h = two_sum(p.hi, q.hi);
+    double lo = __dadd_rn(p.lo, q.lo);
+    lo = __fma_rn(a.hi, x.lo, lo);
+    lo = __fma_rn(a.lo, x.hi, lo);
+    lo = __fma_rn(b.hi, y.lo, lo);
+    lo = __fma_rn(b.lo, y.hi, lo);
+    return two_sum(h.hi, __dadd_rn(h.lo, lo));
+  }
+  // 1/sqrt(a) for a > 0: y0 = RN(1/RN(sqrt(a.hi))); r = 1 - a y0^2 to about
+  // 2^-105 (y0^2 and a.hi y0^2 split exactly, 1 - hi exact as hi is near 1);
+  // 1/sqrt(a) = y0 (1 - r)^(-1/2) = y0 (1 + r/2 + 3 r^2/8 + ...), |r| < 2^-50.
+  static __device__ __forceinline__ dd rsqrt(dd a) {
+    const double y0 = __drcp_rn(__dsqrt_rn(a.hi));
+    const dd q = two_prod(y0, y0), p = two_prod(a.hi, q.hi);
+    double r = __dsub_rn(__dsub_rn(1.0, p.hi), p.lo);
+    r = __fma_rn(-a.hi, q.lo, r);
+    r = __fma_rn(-a.lo, q.hi, r);
+    return fast_two_sum(y0, y0 * __fma_rn(0.375 * r, r, 0.5 * r));
   }
 };
 
@@ -281,7 +310,7 @@ __device__ __forceinline__ void svqb_small_body(int k, const double* Mh, const d
           if (dabs(apq.hi) > eps * scale && apq.hi != 0.0) {
             const double th = A_::sub(aqq, app).hi / (2.0 * apq.hi);
             const double t = dabs(th) > 1e150 ? 0.5 / th : copysign(1.0 / (dabs(th) + sqrt(fma(th, th, 1.0))), th);
-            c = A_::div(dd{1.0, 0.0}, A_::sqrt(A_::add(dd{1.0, 0.0}, A_::mul(dd{t, 0.0}, dd{t, 0.0}))));
+            c = A_::rsqrt(A_::add(dd{1.0, 0.0}, A_::mul(dd{t, 0.0}, dd{t, 0.0})));
             sn = A_::mul(c, dd{t, 0.0});
             atomicAdd(&rot_count, 1);
           }
@@ -304,13 +333,15 @@ __device__ __forceinline__ void svqb_small_body(int k, const double* Mh, const d
         dd b00 = upper(A, r0, c0), b01 = w1 ? upper(A, r0, c1) : dd{0.0, 0.0};
         dd b10 = v1 ? upper(A, r1, c0) : dd{0.0, 0.0}, b11 = v1 && w1 ? upper(A, r1, c1) : dd{0.0, 0.0};
         if (!(sQ.hi == 0.0 && sQ.lo == 0.0)) {  // B J_Q
-          const dd t00 = A_::sub(A_::mul(b00, cQ), A_::mul(b01, sQ)), t01 = A_::add(A_::mul(b00, sQ), A_::mul(b01, cQ));
-          const dd t10 = A_::sub(A_::mul(b10, cQ), A_::mul(b11, sQ)), t11 = A_::add(A_::mul(b10, sQ), A_::mul(b11, cQ));
+          const dd mQ = dd_neg(sQ);
+          const dd t00 = A_::dot2(b00, cQ, b01, mQ), t01 = A_::dot2(b00, sQ, b01, cQ);
+          const dd t10 = A_::dot2(b10, cQ, b11, mQ), t11 = A_::dot2(b10, sQ, b11, cQ);
           b00 = t00; b01 = t01; b10 = t10; b11 = t11;
         }
         if (!(sP.hi == 0.0 && sP.lo == 0.0)) {  // J_P^T (B J_Q)
-          const dd t00 = A_::sub(A_::mul(cP, b00), A_::mul(sP, b10)), t10 = A_::add(A_::mul(sP, b00), A_::mul(cP, b10));
-          const dd t01 = A_::sub(A_::mul(cP, b01), A_::mul(sP, b11)), t11 = A_::add(A_::mul(sP, b01), A_::mul(cP, b11));
+          const dd mP = dd_neg(sP);
+          const dd t00 = A_::dot2(cP, b00, mP, b10), t10 = A_::dot2(sP, b00, cP, b10);
+          const dd t01 = A_::dot2(cP, b01, mP, b11), t11 = A_::dot2(sP, b01, cP, b11);
           b00 = t00; b01 = t01; b10 = t10; b11 = t11;
         }
         auto put = [&](int r, int c, dd v) { A2[max(r, c) * k + min(r, c)] = v; };
@@ -330,8 +361,8 @@ __device__ __forceinline__ void svqb_small_body(int k, const double* Mh, const d
         const dd c = cs[2 * q], sn = cs[2 * q + 1];
         if (b >= k || (sn.hi == 0.0 && sn.lo == 0.0)) continue;
         const dd x = U[a * k + m], y = U[b * k + m];
-        U[a * k + m] = A_::sub(A_::mul(c, x), A_::mul(sn, y));
-        U[b * k + m] = A_::add(A_::mul(sn, x), A_::mul(c, y));
+        U[a * k + m] = A_::dot2(c, x, dd_neg(sn), y);
+        U[b * k + m] = A_::dot2(sn, x, c, y);
       }
       __syncthreads();
       dd* sw = A;
