@@ -324,6 +324,28 @@ def test_project_apply_row_engines_agree(eo, ctx, monkeypatch, n, kv, k):
         assert np.all(np.abs(out - ref) <= tol), engine
 
 
+@pytest.mark.parametrize("engine", ["int", "umma"])
+@pytest.mark.parametrize("kv", [12, 16, 32, 64])
+def test_project_apply_row_engines_largest_digits(eo, ctx, monkeypatch, engine, kv):
+    """Every mantissa bit set, one exponent per row of V and per column of C
+    (C's low part filling the next 53 bits), all of one sign: the leading
+    digits of both operands take their largest values, so the digit-diagonal
+    sums of the tensor-core row engine come as close to their bound as FP64
+    data allows, at every tile width (kin <= 16, 32, 64)."""
+    monkeypatch.setenv("EO_DD_ROW_ENGINE", engine)
+    n, k = 20_011, 16
+    top = 2.0 - 2.0 ** -52
+    g = synth.rng(37 + kv)
+    v = np.asfortranarray(np.full((n, kv), top) * np.ldexp(1.0, g.integers(-8, 9, size=n))[:, None])
+    ch = np.asfortranarray(np.full((kv, k), top) * np.ldexp(1.0, g.integers(-8, 9, size=k))[None, :])
+    cl = np.asfortranarray(ch * 2.0 ** -53)
+    y = synth.gaussian(n, k, 38 + kv)
+    out, _ = eo.project_apply(ctx, dev(v), dev(y), (dev(ch), dev(cl)), prec=eo.DD, want_m=False)
+    ref = oracle.project_apply(v, y, ch, cl)
+    row_max = np.max(np.abs(v), axis=1)[:, None] * np.max(np.abs(ch) + np.abs(cl), axis=0)[None, :]
+    assert np.all(np.abs(host(out) - ref) <= 2 * U * np.abs(ref) + kv * 2.0 ** -99 * row_max)
+
+
 def _random_dd(g, rows, cols):
     hi = np.asfortranarray(g.standard_normal((rows, cols)))
     lo = np.asfortranarray(hi * 2.0 ** -55 * g.uniform(-1, 1, (rows, cols)))
