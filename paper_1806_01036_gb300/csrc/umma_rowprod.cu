@@ -87,6 +87,8 @@ __host__ __device__ constexpr long long chain_offset(int c) {
   for (int d = 5 * c; d < 5 * c + 5; ++d) o = o * 128 + (d <= kRoundDiag<W> ? 0x4B400000ll : 0ll);
   return o;
 }
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 __device__ __forceinline__ void st_shared_v4(unsigned addr, unsigned a, unsigned b, unsigned c, unsigned d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
@@ -305,6 +307,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto epilogue = [&](int64_t T, int64_t i) {
       if (ep * 4 >= kout) return;  // all four outputs of this warp are padding (warp-uniform)
       const unsigned tb = tq + (unsigned)(i & 1) * kAccCols;
+      double yv[4];
+      {
+        const int64_t grow = T * kRows + L;
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+          yv[y] = (!update && ep * 4 + y < kout && grow < n) ? Yin[(size_t)(ep * 4 + y) * ldyin + grow] : 0.0;
+      }
       // h = p0 2^70 + p1 2^35 + p2 with p_c = sum over the five diagonals
       // d = 5c .. 5c + 4 of S_d 2^(7 (5c + 4 - d)) (|p_c| < 2^53: 64-bit chains)
       long long p[3][4];
@@ -342,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int j = ep * 4 + y;
         if (j < kout && grow < n) {
           const int S = Ar + Bexp[j] - kScaleProd;
-          double o = update ? w_to_double(h[y], S) : sub_round(Yin[(size_t)j * ldyin + grow], h[y], S);
+          double o = update ? w_to_double(h[y], S) : sub_round(yv[y], h[y], S);
           if (rbad || Bbad[j] || bad) o = __longlong_as_double(0x7ff8000000000000ll);
           Out[(size_t)j * ldo + grow] = o;
         }
@@ -408,6 +417,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_arrive(rb0 + 8u * b);
       }
       if constexpr (!kStageValues<W>) load_direct(T + gridDim.x, vn);
+      if (!update && tid < 8 * kout) {  // Y of this tile, read by its epilogue a tile from now: into L2
+        const int64_t g0 = T * kRows + (tid & 7) * 16;  // 16 rows = one 128-byte line per thread
+        if (g0 < n) prefetch_l2(Yin + (size_t)(tid >> 3) * ldyin + g0);
+      }
       // the previous tile's MMAs completed (its last group was waited for before
       // this tile's second group was written): its epilogue overlaps this tile's MMAs
       if (Tprev >= 0) {
