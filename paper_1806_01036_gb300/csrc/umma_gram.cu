@@ -306,7 +306,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     const unsigned stride_a = (unsigned)kxp / 8u * SBO, stride_b = (unsigned)KYP / 8u * SBO;
-    const bool scan_lead = (lane & 24) == 0;  // one lane of the four that share a column
     if constexpr (PAD) {  // the digit words of padded columns: zero once, in both buffers
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
@@ -378,30 +377,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                                                  : make_double2(0.0, 0.0);
       }
     };
-    // largest exponent of each column of a panel (max of |x| bit patterns)
-    // into pmq; true if one of this thread's columns exceeds max(ea, eb), a
+    // largest exponent of each column of a panel into pmq (the exponent
+    // field of the larger |x| bit pattern; bit 0 set when any bit is, so
+    // that subnormals count), one shared-memory atomic per item (cheaper
+    // than reducing the four items of a column in a warp by shuffles
+    // first); true if one of this thread's columns exceeds te[k], its
     // nonzero running exponent
-    auto scan = [&](const double2 (&v)[kMaxItems], int* pmq, const int* ea, const int* eb) -> bool {
+    auto scan = [&](const double2 (&v)[kMaxItems], int* pmq, const int (&te)[kMaxItems]) -> bool {
       unsigned m[kMaxItems];
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k)
-        m[k] = max((hi32(v[k].x) & 0x7fffffffu) | min(lo32(v[k].x), 1u),
-                   (hi32(v[k].y) & 0x7fffffffu) | min(lo32(v[k].y), 1u));
-#pragma unroll
-      for (int k = 0; k < kMaxItems; ++k) m[k] = max(m[k], __shfl_xor_sync(0xffffffffu, m[k], 8));
-#pragma unroll
-      for (int k = 0; k < kMaxItems; ++k) m[k] = max(m[k], __shfl_xor_sync(0xffffffffu, m[k], 16));
+        m[k] = max(hi32(v[k].x) & 0x7fffffffu, hi32(v[k].y) & 0x7fffffffu) |
+               min(lo32(v[k].x) | lo32(v[k].y), 1u);
       bool g = false;
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
-        if (scan_lead && m[k] && tid + k * kConvThreads < nitems) {
+        if (m[k] && tid + k * kConvThreads < nitems) {
           int e = (int)(m[k] >> 20);
           if (e == 0) e = 1;  // subnormal
           if (e == 2047) flag = 1;
-          const int c = (int)(it_s[k] >> 16);
-          atomicMax(&pmq[c], e);
-          const int t = max(ea[c], eb[c]);
-          g |= t != 0 && e > t;
+          atomicMax(&pmq[it_s[k] >> 16], e);
+          g |= te[k] != 0 && e > te[k];
         }
       }
       return g;
@@ -411,7 +407,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool grew = false;  // a column of the current panel exceeds its running exponent
     if (npan > 0) {
       stage_values(0, v);
-      (void)scan(v, pmax, Erun + nslots, Erun + nslots);  // nothing has accumulated yet
+      const int none[kMaxItems] = {};
+      (void)scan(v, pmax, none);  // nothing has accumulated yet
     }
     bar_conv<kConvThreads>();
     if (!DIRECT && tid == 0 && 2 < npan) {  // staging buffer 0 is read: panel 2
@@ -430,11 +427,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         Erun[db * nslots + tid] = max(eprev[tid], pcur[tid]);  // through panel p
         pmax[pz * nslots + tid] = 0;                           // panel p-1's, read for the last time in p-1
       }
-      int A[kMaxItems];
+      int A[kMaxItems], te[kMaxItems];  // te: running exponent through panel p of the item's column
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
         const int c = (int)(it_s[k] >> 16);
-        A[k] = max(max(eprev[c], pcur[c]), 1);
+        te[k] = max(eprev[c], pcur[c]);
+        A[k] = max(te[k], 1);
       }
 
       // the digit buffer db is free once the MMAs of panel p-2 are done
@@ -493,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int k = 0; k < kMaxItems; ++k) vn[k] = make_double2(0.0, 0.0);
       if (p + 1 < npan) {
         stage_values(p + 1, vn);
-        gl = scan(vn, pmax + pn * nslots, eprev, pcur);
+        gl = scan(vn, pmax + pn * nslots, te);
       }
       grew = bar_conv_or<kConvThreads>(gl);
       if (!DIRECT && tid == 0 && p + 3 < npan) {  // staging buffer (p + 1) & 1 is read: panel p + 3
