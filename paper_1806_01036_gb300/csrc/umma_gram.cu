@@ -379,10 +379,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     };
     // largest exponent of each column of a panel into pmq (the exponent
     // field of the larger |x| bit pattern; bit 0 set when any bit is, so
-    // that subnormals count), one shared-memory atomic per item (cheaper
-    // than reducing the four items of a column in a warp by shuffles
-    // first); true if one of this thread's columns exceeds te[k], its
-    // nonzero running exponent
+    // that subnormals count) where it exceeds the column's running
+    // exponent, one shared-memory atomic per such item (cheaper than
+    // reducing the four items of a column in a warp by shuffles first);
+    // true if one of this thread's columns exceeds te[k], its nonzero
+    // running exponent
     auto scan = [&](const double2 (&v)[kMaxItems], int* pmq, const int (&te)[kMaxItems]) -> bool {
       unsigned m[kMaxItems];
 #pragma unroll
@@ -396,8 +397,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           int e = (int)(m[k] >> 20);
           if (e == 0) e = 1;  // subnormal
           if (e == 2047) flag = 1;
-          atomicMax(&pmq[it_s[k] >> 16], e);
-          g |= te[k] != 0 && e > te[k];
+          // a panel's maxima are only ever used as max(running exponent,
+          // panel maximum): an item within its column's running exponent
+          // te[k] changes nothing (with steady exponents, nearly all items)
+          if (e > te[k]) {
+            atomicMax(&pmq[it_s[k] >> 16], e);
+            g |= te[k] != 0;
+          }
         }
       }
       return g;
