@@ -98,7 +98,7 @@ EO_API uint64_t eo_kernel_launches(const eo_ctx* ctx);
 
 /*
  * Gram product G = X^T Y (kx-by-ky), the matrix-matrix product that carries
- * "the bulk of computation" of phase II (Sec. 4.2, M = Y~^T Y~) and, with
+ * most of the arithmetic of phase II (Sec. 4.2, M = Y~^T Y~) and, with
  * Y = X and X = W, the W^T X of phase I.
  *   X: n-by-kx, Y: n-by-ky (Y == NULL: Y = X and ky must equal kx; G is then
  *   symmetric and both triangles are written).  FP64 data, or float data in
@@ -113,7 +113,7 @@ EO_API eo_status eo_gram(eo_ctx* ctx, int64_t n, int kx, const void* X, int64_t 
 /*
  * Phase I projection against an orthonormal basis V (Sec. 4.2:
  * Y~ = (I - W W^T) X), with the phase-II Gram matrix of the result fused into
- * the same pass over the data (the paper's "kernel fusion").
+ * the same pass over the data (the paper fuses these two kernels).
  *   V: n-by-kv, Y: n-by-k (FP64).  C = V^T Y is written to C_hi/C_lo (kv-by-k,
  *   ldc; C_hi may be NULL).  Yout (n-by-k, ldyo) receives Y - V C, rounded
  *   once to FP64; Yout may equal Y (in place) but must not otherwise overlap
@@ -170,10 +170,10 @@ EO_API eo_status eo_svqb(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, co
                   int ldm, double* Z_hi, double* Z_lo, int ldz, double tol, int passes, eo_prec prec, int* rank_dev);
 
 /*
- * Iterated two-phase orthogonalization (Sec. 4.2: "a robust algorithm is
- * obtained by iterating this process, alternating between the two phases and
- * using a rank-revealing technique in phase II"; the runtime figure iterates
- * "until convergence at epsilon = 1e-10").  Each iteration runs phase I
+ * Iterated two-phase orthogonalization (Sec. 4.2: the two phases are
+ * repeated in turn, with a rank-revealing factorization in phase II, which
+ * makes the method robust; the runtime figure repeats them until both
+ * measures fall below epsilon = 1e-10).  Each iteration runs phase I
  * (C = V^T Y, Y <- Y - V C) and measures max |C_ij| and max |M - I|_ij with
  * M = Y^T Y of the projected block; when both are <= eps the iteration stops
  * there, otherwise phase II applies SVQB (Z = M^{-1/2} with eigenvalue cut tol,

@@ -32,7 +32,7 @@
  *                                                                      the method extends to
  *                                                                      B-inner products)
  *   eoq_orth_err_diag  ||Q^T D Q - I|| for a diagonal B = D            (B-orthonormality)
- *   eoq_orth_err   ||Q^T Q - I|| in 2-norm, Frobenius and max-abs     (Fig. "Accuracy after one iteration")
+ *   eoq_orth_err   ||Q^T Q - I|| in 2-norm, Frobenius and max-abs     (Sec. 4.2, one-iteration accuracy figure)
  *   eoq_cross_err  ||W^T Q||_2                                        (same figure, left panel)
  *   eoq_fact_err   ||X - Q R||_F / ||X||_F                            (definition of a QR factorization)
  *

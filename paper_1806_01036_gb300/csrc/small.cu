@@ -1,6 +1,6 @@
 // small.cu — the k-by-k steps of phase II, one CTA each
-// (arXiv:1806.01036, Sec. 4.2: "operations on small n_b x n_b matrices are
-// cost negligible, even in extended precision").
+// (arXiv:1806.01036, Sec. 4.2: the k-by-k work costs little next to the
+// n-row passes, in extended precision too).
 //
 //   chol_small:  M = R^T R (R upper with positive diagonal) by the
 //                square-root-free elimination M = L D L^T, carrying

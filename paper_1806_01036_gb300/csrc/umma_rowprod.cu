@@ -23,16 +23,20 @@
 //   h = sum_d S_d 2^(7 (14 - d)),   sum_i v_i c_ij ~= h 2^(A_r + B_j - 2156),
 // and rounds y - h 2^(...) (or h 2^(...)) to FP64 in integer arithmetic.
 //
-// Pipeline (one CTA per SM, tiles round-robin): the 16 converter warps load
-// a tile's values straight into registers (8 rows x 4 column groups per
-// warp, coalesced along rows), find each row's exponent by shuffles, and
-// write the digits in three groups of five slabs into two alternating
-// shared-memory buffers; one warp issues the group's MMAs and commits them
-// to an mbarrier per buffer; TMEM holds two accumulators, so the epilogue of
-// tile i - 1 (tcgen05.ld, exact rounding, stores) runs while the tensor
-// cores work on tile i.  Every wait is bounded (the outputs of a CTA whose
-// wait ran out are NaN).  The tile's loads precede its stores, so the update
-// may run in place.
+// Pipeline (one CTA per SM, tiles round-robin): the 16 converter warps hold
+// a tile's values in registers (8 rows x 4 column groups per warp,
+// coalesced along rows), fetched a tile ahead (staged through shared memory
+// with cp.async for kin <= 32, loaded into registers after the previous
+// tile's digits are stored for kin <= 64), find each row's exponent by
+// shuffles, and write the digits in three groups of five slabs into two
+// alternating shared-memory buffers; one warp issues the group's MMAs and
+// commits them to an mbarrier per buffer; TMEM holds two accumulators, so
+// the epilogue of tile i - 1 (tcgen05.ld, exact rounding, stores) runs
+// while the tensor cores work on tile i.  The projection's Y of a tile is
+// prefetched into L2 a tile ahead and loaded before its epilogue reads
+// TMEM.  Every wait is bounded (the outputs of a CTA whose wait ran out are
+// NaN).  Each tile's loads precede its own stores, and no tile is written
+// by another CTA, so the update may run in place.
 #include <algorithm>
 #include <cstdlib>
 

@@ -1,5 +1,5 @@
 // update.cu — the final multiplication Y = Y~ Z of phase II
-// (arXiv:1806.01036, Sec. 4.2: "the final multiplication Y~ Z"; CholQR uses
+// (arXiv:1806.01036, Sec. 4.2: the multiplication by Z that ends phase II; CholQR uses
 // the upper-triangular Z = R^{-1}, SVQB the full symmetric Z).
 //
 // Each thread owns whole rows: it loads the k entries of its row, then forms

@@ -5,9 +5,9 @@ it holds none of the orthogonalization arithmetic (no Gram product, no
 Cholesky, no eigensolver of the method).  Both the CUDA path's tests and the
 CPU oracle take their inputs from here.
 
-Recipe (the paper's test matrices are "synthetic ... with varying condition",
-Sec. 4.2, Fig. "Accuracy after one iteration"; the generator itself is not
-given there):
+Recipe (the paper tests on synthetic matrices over a range of condition
+numbers, Sec. 4.2, one-iteration accuracy figure; it does not give the
+generator):
 
 * Haar-random orthonormal factors: a standard-normal matrix from
   ``numpy.random.Generator(PCG64(seed))``, its Householder QR
