@@ -24,6 +24,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -135,6 +136,15 @@ def cpu_baseline(v, y, rows):
 
 
 # -------------------------------------------------------------- clocks
+
+def clocks_path(name):
+    """Where the clock samples of a run go: $EO_CLOCKS_DIR/<name> when that
+    variable names a folder, else a file in the temporary directory."""
+    d = os.environ.get("EO_CLOCKS_DIR")
+    if d and os.path.isdir(d):
+        return os.path.join(d, name)
+    return os.path.join(tempfile.gettempdir(), f"eo_{os.getpid()}_{name}")
+
 
 class Clocks:
     def __init__(self, path, index):
@@ -262,8 +272,7 @@ def run_eo(a):
         dist.barrier()
     torch.cuda.synchronize()
     l0 = ctx.launches()
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/eo_clocks_{os.getpid()}.csv", local)
+    clk = Clocks(clocks_path(f"clocks_rank{rank}.csv"), local)
     with clk:
         torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed launches
         t_all0 = torch.cuda.Event(enable_timing=True)
@@ -589,8 +598,7 @@ def run_batched(a):
 
     torch.cuda.synchronize()
     l0 = ctx.launches()
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_batched_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/eo_clocks_b_{os.getpid()}.csv", local)
+    clk = Clocks(clocks_path(f"clocks_batched_rank{rank}.csv"), local)
     with clk:
         torch.cuda.nvtx.range_push("timed")
         times = timed(bt.run, a.steps)
@@ -714,8 +722,7 @@ def run_serve(a):
         n, kv = int(ns[i]), int(kvs[i])
         k = max(1, kv // 4)
         nbytes += 8 * n * (2 * kv + 5 * k)
-    clk = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_serve_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/eo_clocks_s_{os.getpid()}.csv", local)
+    clk = Clocks(clocks_path(f"clocks_serve_rank{rank}.csv"), local)
     l0 = srv.stats()["kernels"]
     with clk:
         t0 = time.perf_counter()
