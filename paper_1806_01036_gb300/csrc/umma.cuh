@@ -260,6 +260,26 @@ __device__ __forceinline__ void tmem_st3(unsigned a0, unsigned a1, unsigned a2, 
         : "memory");
   }
 }
+// Zeros into three column blocks of NY columns (one zero register for all).
+template <int NY>
+__device__ __forceinline__ void tmem_zero3(unsigned a0, unsigned a1, unsigned a2) {
+  const unsigned z = 0u;
+  if constexpr (NY == 4) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%3,%3,%3,%3};\n"
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%1], {%3,%3,%3,%3};\n"
+        "tcgen05.st.sync.aligned.32x32b.x4.b32 [%2], {%3,%3,%3,%3};\n" ::"r"(a0),
+        "r"(a1), "r"(a2), "r"(z)
+        : "memory");
+  } else {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%3,%3};\n"
+        "tcgen05.st.sync.aligned.32x32b.x2.b32 [%1], {%3,%3};\n"
+        "tcgen05.st.sync.aligned.32x32b.x2.b32 [%2], {%3,%3};\n" ::"r"(a0),
+        "r"(a1), "r"(a2), "r"(z)
+        : "memory");
+  }
+}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes) {

@@ -43,6 +43,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "fx.cuh"
@@ -70,6 +71,7 @@ struct UPlan {
   int P;                // rows per panel (multiple of 16)
   int drain_panels;     // panels accumulated in TMEM between drains
   int fold_drains;      // drains between folds of the running sums
+  int drain_log;        // 3 bits per group g of column blocks 3g..3g+2: log2 of the drains it may skip + 1
   int nslots;           // staged columns per CTA
   unsigned dig_bytes;   // one digit buffer (A part, then B part unless shared)
   unsigned a_bytes;     // A part of a digit buffer
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   int* pmax = Erun + 2 * nslots;  // three panels' column maxima (Erun: running exponents, two buffers)
   __shared__ __align__(8) unsigned long long full_bar[2], ready_bar[2], stage_bar[2];
   __shared__ unsigned tmem_base;
-  __shared__ int flag, bad, fresh_flag[2];
+  __shared__ int flag, bad;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -187,7 +189,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int db = p & 1;
         if (!mbar_wait(rb0 + 8u * db, (unsigned)(p >> 1) & 1u, &bad)) break;
         tc_fence_after();
-        const bool fresh = fresh_flag[db] != 0;
         const unsigned abase = dig_s + (unsigned)db * pl.dig_bytes;
         const unsigned bbase = pl.shared ? abase : abase + pl.a_bytes;
         for (int ks = 0; ks < P / 16; ++ks) {
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 sdesc(abase + (unsigned)(pl.J * q * kxp / 8) * SBO + (unsigned)ks * 256u, 128u, SBO);
             const unsigned long long bd = sdesc(bbase + (unsigned)ks * 256u, 128u, SBO);
             mma_f16(taddr + (unsigned)(KYP * pl.J * q), ad, bd, idesc_f16(kLanes, KYP * Tp),
-                    (fresh && ks == 0 && q == 0) ? 0u : 1u);
+                    1u);  // the accumulators start at zero and drains zero them
           }
         }
         mma_commit(fb0 + 8u * db);
@@ -218,42 +219,69 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int y = 0; y < NY; ++y) z[u][y] = 0u;
 #pragma unroll
-      for (int c0 = 0; c0 < NS; c0 += 3)
+      for (int c0 = 0; c0 < NS; c0 += 3) {
         tmem_st3<NY>(tsum + c0 * KYP, tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, z);
+        tmem_st3<NY>(tacc + c0 * KYP, tacc + (c0 + 1) * KYP, tacc + (c0 + 2) * KYP, z);
+      }
       tmem_wait_st();
     }
 
-    auto drain = [&]() {  // TMEM accumulators -> TMEM running sums (column block c of lane block jl: diagonal c + jl)
-      // five groups of three column blocks; the loads of group g + 1 are in flight while group g is added
+    // TMEM accumulators -> TMEM running sums (column block c of lane block
+    // jl: diagonal c + jl) for the groups of three column blocks G0 .. 4 (the
+    // groups due at a drain are always such a suffix: a group's period is a
+    // power of two no shorter than that of any later group); a drained
+    // group's accumulators are set back to zero.  The loads of the next group
+    // are in flight while a group is added.
+    auto load = [&](int c0, unsigned (&v)[3][NY], unsigned (&sm)[3][NY]) {
+      tmem_ld3x2_nowait<NY>(tacc + c0 * KYP, tacc + (c0 + 1) * KYP, tacc + (c0 + 2) * KYP, tsum + c0 * KYP,
+                            tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, v, sm);
+    };
+    auto add_store = [&](int c0, unsigned (&v)[3][NY], unsigned (&sm)[3][NY]) {
+      // (column blocks with c + jl > 14 collect no kept diagonal: the fold skips them)
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+#pragma unroll
+        for (int y = 0; y < NY; ++y) sm[u][y] += (unsigned)__float2int_rn(__uint_as_float(v[u][y]) * 0x1p48f);
+      tmem_st3<NY>(tsum + c0 * KYP, tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, sm);
+      tmem_zero3<NY>(tacc + c0 * KYP, tacc + (c0 + 1) * KYP, tacc + (c0 + 2) * KYP);
+    };
+    auto drain_from = [&](auto g0) {
+      constexpr int G0 = decltype(g0)::value;
       unsigned va[3][NY], sa[3][NY], vb[3][NY], sb[3][NY];
-      auto load = [&](int c0, unsigned (&v)[3][NY], unsigned (&sm)[3][NY]) {
-        tmem_ld3x2_nowait<NY>(tacc + c0 * KYP, tacc + (c0 + 1) * KYP, tacc + (c0 + 2) * KYP, tsum + c0 * KYP,
-                              tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, v, sm);
-      };
-      auto add_store = [&](int c0, unsigned (&v)[3][NY], unsigned (&sm)[3][NY]) {
-        // (column blocks with c + jl > 14 collect no kept diagonal: the fold skips them)
-#pragma unroll
-        for (int u = 0; u < 3; ++u)
-#pragma unroll
-          for (int y = 0; y < NY; ++y) sm[u][y] += (unsigned)__float2int_rn(__uint_as_float(v[u][y]) * 0x1p48f);
-        tmem_st3<NY>(tsum + c0 * KYP, tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, sm);
-      };
-      load(0, va, sa);
+      load(3 * G0, va, sa);
       tmem_wait_ld_regs<NY>(va, sa);
-      load(3, vb, sb);
-      add_store(0, va, sa);
-      tmem_wait_ld_regs<NY>(vb, sb);
-      load(6, va, sa);
-      add_store(3, vb, sb);
-      tmem_wait_ld_regs<NY>(va, sa);
-      load(9, vb, sb);
-      add_store(6, va, sa);
-      tmem_wait_ld_regs<NY>(vb, sb);
-      load(12, va, sa);
-      add_store(9, vb, sb);
-      tmem_wait_ld_regs<NY>(va, sa);
-      add_store(12, va, sa);
+      if constexpr (G0 + 1 <= 4) load(3 * (G0 + 1), vb, sb);
+      add_store(3 * G0, va, sa);
+      if constexpr (G0 + 1 <= 4) {
+        tmem_wait_ld_regs<NY>(vb, sb);
+        if constexpr (G0 + 2 <= 4) load(3 * (G0 + 2), va, sa);
+        add_store(3 * (G0 + 1), vb, sb);
+      }
+      if constexpr (G0 + 2 <= 4) {
+        tmem_wait_ld_regs<NY>(va, sa);
+        if constexpr (G0 + 3 <= 4) load(3 * (G0 + 3), vb, sb);
+        add_store(3 * (G0 + 2), va, sa);
+      }
+      if constexpr (G0 + 3 <= 4) {
+        tmem_wait_ld_regs<NY>(vb, sb);
+        if constexpr (G0 + 4 <= 4) load(3 * (G0 + 4), va, sa);
+        add_store(3 * (G0 + 3), vb, sb);
+      }
+      if constexpr (G0 + 4 <= 4) {
+        tmem_wait_ld_regs<NY>(va, sa);
+        add_store(3 * (G0 + 4), va, sa);
+      }
       tmem_wait_st();
+    };
+    auto drain = [&](int g0) {
+      switch (g0) {
+        case 0: drain_from(std::integral_constant<int, 0>{}); break;
+        case 1: drain_from(std::integral_constant<int, 1>{}); break;
+        case 2: drain_from(std::integral_constant<int, 2>{}); break;
+        case 3: drain_from(std::integral_constant<int, 3>{}); break;
+        case 4: drain_from(std::integral_constant<int, 4>{}); break;
+        default: break;  // no group due
+      }
     };
     auto fold = [&]() {  // running sums -> W (units 2^(Ax + Ay - 2148)), sums back to zero
       i128 h[NY];
@@ -422,8 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       load_panel(2);
     }
 
-    int undrained = 0, drains = 0, pc = 0;
-    bool fresh = true;
+    int undrained = 0, drains = 0, ev = 0, pc = 0;  // ev: drains since the last full one
     for (int p = 0; p < npan; ++p) {
       const int db = p & 1;
       const int pn = pc == 2 ? 0 : pc + 1, pz = pn == 2 ? 0 : pn + 1;  // (p + 1) % 3, (p + 2) % 3
@@ -465,11 +492,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         // all MMAs so far (the last commit is panel p-1's) are done before TMEM is read
         mbar_wait(fb0 + 8u * ((p - 1) & 1), (unsigned)((p - 1) >> 1) & 1u, &bad);
         tc_fence_after();
-        drain();
+        // a full drain before a fold or a growth; otherwise the groups whose
+        // period ends here
+        const bool full = grew || drains + 1 == pl.fold_drains;
+        int g0 = 0;  // first group due
+        if (!full) {
+          g0 = 5;
+#pragma unroll
+          for (int g = 4; g >= 0; --g) {
+            const int per = 1 << ((pl.drain_log >> (3 * g)) & 7);
+            if (g0 == g + 1 && ((ev + 1) & (per - 1)) == 0) g0 = g;
+          }
+        }
+        drain(g0);
         ++drains;
-        if (grew || drains == pl.fold_drains) {
+        ++ev;
+        if (full) {
           fold();
           drains = 0;
+          ev = 0;
         }
         if (grew) {  // totals onto the new grid: divide by 2^(growth of both columns' exponents)
           const int ysb = pl.shared ? 0 : kxp;
@@ -483,11 +524,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_before();
         undrained = 0;
-        fresh = true;
       }
-      if (tid == 0) fresh_flag[db] = fresh ? 1 : 0;
       mbar_arrive(rb0 + 8u * db);  // digits of p ready (and TMEM drained if it was due)
-      fresh = false;
       ++undrained;
 
       // panel p+1: values and column maxima (growth against the exponents through p)
@@ -514,7 +552,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (npan > 0) {
       mbar_wait(fb0 + 8u * ((npan - 1) & 1), (unsigned)((npan - 1) >> 1) & 1u, &bad);
       tc_fence_after();
-      drain();
+      drain(0);
       fold();
       tc_fence_before();
     }
@@ -592,6 +630,17 @@ UPlan make_plan(int kx, int ky, bool sym) {
   const long long per_drain = (long long)p.drain_panels * p.P * pairs * 127 * 127;
   p.fold_drains = (int)std::max(1ll, std::min<long long>(kFoldRows / (p.drain_panels * p.P),
                                                           ((1ll << 31) - 1) / per_drain));
+  // Column block c of a lane block collects at most c / J + 1 digit pairs
+  // per row, so a group of three blocks stays exact for 2^24 / (its largest
+  // pair count x 127^2) rows: it is drained every 2^g-th drain (g <= 3).
+  p.drain_log = 0;
+  for (int g = 0; g < 5; ++g) {
+    const int pg = std::min(3 * g + 2, 14) / p.J + 1;
+    const long long dmax = (1ll << 24) / ((long long)pg * 127 * 127 * p.drain_panels * p.P);
+    int lg = 0;
+    while (lg < 3 && (2ll << lg) <= dmax) ++lg;
+    p.drain_log |= lg << (3 * g);
+  }
   p.a_bytes = (unsigned)(32 * p.P * p.kxp);
   p.dig_bytes = (unsigned)(32 * p.P * (p.shared ? p.kxp : p.kxp + p.kyp));
   p.stage_bytes = (unsigned)(p.nslots * p.P * 8);
