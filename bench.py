@@ -198,11 +198,11 @@ DIGIT_PAIRS = 120  # FP16 digit-pair products per multiply-add of the compensate
 def gram_traffic(n, kv, k):
     """DRAM bytes of one V^T Y launch of the tensor-core Gram kernel, from one
     ncu capture at n = 1e6, kv = 64, k = 16 (dram__bytes_read.sum 640.1 MB,
-    dram__bytes_write.sum 3.2 MB of row-chunk partials); reads scale with
+    dram__bytes_write.sum 3.5 MB of row-chunk partials); reads scale with
     the rows, the partials do not.  None for other shapes."""
     if (kv, k) != (64, 16):
         return None
-    return 640.13696e6 * n / 1e6 + 3.241216e6
+    return 640.127488e6 * n / 1e6 + 3.512576e6
 
 
 def peak_tensor():
