@@ -21,8 +21,11 @@
 //    digit diagonal d = c + j, and the 120 digit pairs with d <= 14 take
 //    15 / J + 1 MMAs per 16 rows;
 //  * every R rows (R such that no accumulator can reach 2^24 units) the
-//    accumulators are read back (tcgen05.ld), converted to integers and added
-//    to 32-bit running sums per (lane, column); these are folded into a
+//    accumulators are read back (tcgen05.ld), converted to integers, added
+//    to 32-bit running sums per (lane, column) and set back to zero; a group
+//    of three column blocks whose blocks hold fewer digit pairs per row is
+//    drained only every 2nd, 4th or 8th time (still below 2^24 units).  The
+//    running sums are folded into a
 //    128-bit total W in the units of the integer engine (value =
 //    W 2^(Ax + Ay - 2148)) every 8192 rows, before an alignment exponent
 //    grows, and at the end.  The row-chunk partials go through the same
@@ -35,8 +38,8 @@
 // p-1, one warp issuing the MMAs and committing them to an mbarrier per
 // buffer.  Every wait is bounded; a wait that runs out marks the partials
 // non-finite, so the result is NaN.  Inputs that TMA cannot address (a base
-// address not 16-byte aligned or an odd leading dimension) go to the integer
-// engine.
+// address not 16-byte aligned or an odd leading dimension) are copied by the
+// converter threads themselves with cp.async (the DIRECT variant).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
