@@ -318,34 +318,66 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int y = 0; y < 4; ++y)
           yv[y] = (!update && ep * 4 + y < kout && grow < n) ? Yin[(size_t)(ep * 4 + y) * ldyin + grow] : 0.0;
       }
-      // h = p0 2^70 + p1 2^35 + p2 with p_c = sum over the five diagonals
-      // d = 5c .. 5c + 4 of S_d 2^(7 (5c + 4 - d)) (|p_c| < 2^53: 64-bit chains)
-      long long p[3][4];
+      i128 h[4];
+      if constexpr (kRoundDiag<W> >= NS - 1) {
+        // every diagonal below 2^22 units: q_m = S_2m 128 + S_2m+1 in 32 bits
+        // (m = 0..6; the FP32 bit patterns carry the offset 0x4B400000, taken
+        // off once per pair), r = q_a 2^14 + q_b in 64 bits, and
+        // h = r_0 2^77 + r_1 2^49 + r_2 2^21 + r_3 with r_3 = q_6 2^7 + S_14.
+        unsigned qa[4];
+        long long ra[4];
 #pragma unroll
-      for (int d0 = 0; d0 < NS; d0 += 3) {
-        unsigned v[3][4];
-        tmem_ld3x4(tb + (unsigned)(d0 * kOut), tb + (unsigned)((d0 + 1) * kOut), tb + (unsigned)((d0 + 2) * kOut), v);
+        for (int d0 = 0; d0 < NS; d0 += 3) {
+          unsigned v[3][4];
+          tmem_ld3x4(tb + (unsigned)(d0 * kOut), tb + (unsigned)((d0 + 1) * kOut), tb + (unsigned)((d0 + 2) * kOut), v);
 #pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          const int d = d0 + u, c = d / 5;
+          for (int u = 0; u < 3; ++u) {
+            const int d = d0 + u, m = d / 2;
 #pragma unroll
-          for (int y = 0; y < 4; ++y) {
-            // S_d = accumulator x 2^48; diagonals below 2^22 units come out of
-            // the FP32 add of 1.5 2^23 as its bit pattern 0x4B400000 + S_d
-            // (the offsets are taken off the chains below)
-            const long long sd = d <= kRoundDiag<W>
-                                     ? (long long)__float_as_uint(fmaf(__uint_as_float(v[u][y]), 0x1p48f, 0x1.8p23f))
-                                     : (long long)__float2int_rn(__uint_as_float(v[u][y]) * 0x1p48f);
-            p[c][y] = (d % 5 == 0) ? sd : p[c][y] * 128 + sd;
+            for (int y = 0; y < 4; ++y) {
+              const unsigned b = __float_as_uint(fmaf(__uint_as_float(v[u][y]), 0x1p48f, 0x1.8p23f));
+              if (d == NS - 1) {
+                h[y] += (i128)(ra[y] + (long long)(int)(b - 0x4B400000u));
+              } else if (d % 2 == 0) {
+                qa[y] = b;
+              } else {
+                const long long q = (long long)(int)((qa[y] << 7) + b - 129u * 0x4B400000u);
+                if (m % 2 == 0) ra[y] = q << (m == 6 ? 7 : 14);
+                else if (m == 1) h[y] = (i128)(ra[y] + q) << 77;
+                else h[y] += (i128)(ra[y] + q) << (m == 3 ? 49 : 21);
+              }
+            }
           }
         }
-      }
-      i128 h[4];
+      } else {
+        // h = p0 2^70 + p1 2^35 + p2 with p_c = sum over the five diagonals
+        // d = 5c .. 5c + 4 of S_d 2^(7 (5c + 4 - d)) (|p_c| < 2^53: 64-bit chains)
+        long long p[3][4];
 #pragma unroll
-      for (int y = 0; y < 4; ++y) {
+        for (int d0 = 0; d0 < NS; d0 += 3) {
+          unsigned v[3][4];
+          tmem_ld3x4(tb + (unsigned)(d0 * kOut), tb + (unsigned)((d0 + 1) * kOut), tb + (unsigned)((d0 + 2) * kOut), v);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) p[c][y] -= chain_offset<W>(c);
-        h[y] = ((i128)p[0][y] << 70) + ((i128)p[1][y] << 35) + (i128)p[2][y];
+          for (int u = 0; u < 3; ++u) {
+            const int d = d0 + u, c = d / 5;
+#pragma unroll
+            for (int y = 0; y < 4; ++y) {
+              // S_d = accumulator x 2^48; diagonals below 2^22 units come out of
+              // the FP32 add of 1.5 2^23 as its bit pattern 0x4B400000 + S_d
+              // (the offsets are taken off the chains below)
+              const long long sd = d <= kRoundDiag<W>
+                                       ? (long long)__float_as_uint(fmaf(__uint_as_float(v[u][y]), 0x1p48f, 0x1.8p23f))
+                                       : (long long)__float2int_rn(__uint_as_float(v[u][y]) * 0x1p48f);
+              p[c][y] = (d % 5 == 0) ? sd : p[c][y] * 128 + sd;
+            }
+          }
+        }
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c) p[c][y] -= chain_offset<W>(c);
+          h[y] = ((i128)p[0][y] << 70) + ((i128)p[1][y] << 35) + (i128)p[2][y];
+        }
       }
       const int64_t grow = T * kRows + L;
       const int Ar = Arow[(i & 1) * kRows + L];
