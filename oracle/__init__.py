@@ -4,11 +4,15 @@ TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
 CPU-baseline leg of the benchmark, never by the product path.  It shares no
 code with the CUDA library.
 
-The arithmetic lives in ``eo_oracle.c`` (IEEE binary128); this module compiles
-it on first use (gcc, ``-O2 -ffp-contract=off``, OpenMP when available) and
-wraps it for numpy column-major FP64 arrays.  Results that the oracle keeps in
-binary128 come back as (hi, lo) pairs of FP64 arrays with hi + lo equal to the
-binary128 value to about 2^-107 relative.
+The reference arithmetic lives in ``eo_oracle.c`` (IEEE binary128): every
+result from its plain definition.  ``eo_oracle_fp64.c`` holds the paper's own
+CPU arithmetic, plain FP64 and the double-double (Dot2) form, used to pin the
+kappa^2 u versus kappa^2 u^2 behaviour on the CPU and as the timed CPU
+baseline (functions ``fp64_*``).  This module compiles both on first use (gcc,
+``-O2 -ffp-contract=off``, OpenMP when available) and wraps them for numpy
+column-major FP64 arrays.  Results that the oracle keeps in binary128 come
+back as (hi, lo) pairs of FP64 arrays with hi + lo equal to the binary128
+value to about 2^-107 relative.
 """
 from __future__ import annotations
 
@@ -20,7 +24,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "eo_oracle.c")
+_SRCS = [os.path.join(_HERE, "eo_oracle.c"), os.path.join(_HERE, "eo_oracle_fp64.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -36,14 +40,14 @@ def build(force: bool = False) -> str:
     """Compile the oracle into oracle/_build/liboracle.so (returns its path)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(s) for s in _SRCS + [__file__])):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=gnu11"]
     try:
-        subprocess.run(base + ["-fopenmp", _SRC, "-o", tmp], check=True, capture_output=True)
+        subprocess.run(base + ["-fopenmp"] + _SRCS + ["-o", tmp, "-lm"], check=True, capture_output=True)
     except subprocess.CalledProcessError:
-        subprocess.run(base + [_SRC, "-o", tmp], check=True, capture_output=True)
+        subprocess.run(base + _SRCS + ["-o", tmp, "-lm"], check=True, capture_output=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -80,12 +84,25 @@ def lib():
             L.eoq_cross_err.restype = _dbl
             L.eoq_fact_err.argtypes = [_i64, _int, _p, _i64, _p, _i64, _p, _p, _int]
             L.eoq_fact_err.restype = _dbl
+            L.eoq_orthogonalize.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64, _dbl, _int, _dbl, _p]
+            L.eoq_orthogonalize.restype = _int
+            L.eoq_set_threads.argtypes = [_int]
+            L.eo64_gram.argtypes = [_int, _i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int]
+            L.eo64_project.argtypes = [_int, _i64, _int, _p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _p, _p,
+                                       _int]
+            L.eo64_cholqr.argtypes = [_int, _i64, _int, _p, _i64, _p, _p, _int, _int, _p, _p, _int]
+            L.eo64_cholqr.restype = _int
             _lib = L
     return _lib
 
 
 def threads() -> int:
     return int(lib().eoq_threads())
+
+
+def set_threads(t: int) -> None:
+    """Threads of the oracle's later parallel loops (OpenMP)."""
+    lib().eoq_set_threads(int(t))
 
 
 def _f64(a) -> np.ndarray:
@@ -302,3 +319,64 @@ def fact_err(x, q, r_hi, r_lo=None):
     r_lo = None if r_lo is None else _f64(r_lo)
     n, k = x.shape
     return float(lib().eoq_fact_err(n, k, _ptr(x), n, _ptr(q), n, _ptr(r_hi), _ptr(r_lo), k))
+
+
+def orthogonalize(w, x, eps=1e-10, max_iter=8, tol=0.0):
+    """(Q, iters, rank): the iterated two-phase algorithm in binary128 --
+    phase I, then stop if max(||W^T Y||_F, ||Y^T Y - I||_F) <= eps, else SVQB
+    (cut tol) -- repeated at most max_iter times; iters = SVQB updates applied
+    before convergence, or -max_iter."""
+    w = _f64(w)
+    q = _f64(x).copy(order="F")
+    n, kv = w.shape
+    k = q.shape[1]
+    rank = C.c_int(0)
+    iters = lib().eoq_orthogonalize(n, kv, _ptr(w), n, k, _ptr(q), n, float(eps), int(max_iter), float(tol),
+                                    C.byref(rank))
+    return q, int(iters), int(rank.value)
+
+
+# ------------------------------------------- the paper's CPU arithmetic
+
+FP64, DD = 0, 1  # modes of the fp64_* functions: plain FP64, double-double (Dot2)
+
+
+def fp64_gram(x, y=None, mode=DD):
+    """(G_hi, G_lo): X^T Y in plain FP64 (row-ordered sums, G_lo = 0) or by Dot2."""
+    x = _f64(x)
+    n, kx = x.shape
+    if y is None:
+        ky, yp, ldy = kx, None, 0
+    else:
+        y = _f64(y)
+        ky, yp, ldy = y.shape[1], y, n
+    hi = np.zeros((kx, ky), order="F")
+    lo = np.zeros((kx, ky), order="F")
+    lib().eo64_gram(int(mode), n, kx, _ptr(x), n, ky, _ptr(yp), ldy, _ptr(hi), _ptr(lo), kx)
+    return hi, lo
+
+
+def fp64_project(v, y, mode=DD, with_gram=True):
+    """(Yt, (C_hi, C_lo), (M_hi, M_lo) or None): phase I in plain FP64 or DD."""
+    v = _f64(v)
+    y = _f64(y)
+    n, kv = v.shape
+    k = y.shape[1]
+    yt = np.zeros((n, k), order="F")
+    chi = np.zeros((kv, k), order="F")
+    clo = np.zeros((kv, k), order="F")
+    mhi, mlo = _sq(k) if with_gram else (None, None)
+    lib().eo64_project(int(mode), n, kv, _ptr(v), n, k, _ptr(y), n, _ptr(yt), n, _ptr(chi), _ptr(clo), kv,
+                       _ptr(mhi), _ptr(mlo), k)
+    return yt, (chi, clo), ((mhi, mlo) if with_gram else None)
+
+
+def fp64_cholqr(x, passes=1, mode=DD, m=None):
+    """(Q, (R_hi, R_lo), info): CholQR in plain FP64 or DD, Q rounded per pass."""
+    q = _f64(x).copy(order="F")
+    n, k = q.shape
+    r_hi, r_lo = _sq(k)
+    mh, ml = (None, None) if m is None else (_f64(m[0]), None if m[1] is None else _f64(m[1]))
+    info = lib().eo64_cholqr(int(mode), n, k, _ptr(q), n, _ptr(mh), _ptr(ml), k, int(passes), _ptr(r_hi),
+                             _ptr(r_lo), k)
+    return q, (r_hi, r_lo), int(info)

@@ -24,6 +24,9 @@
  *                  Z = U Lambda^{-1/2} U^T = M^{-1/2}                 (Sec. 4.2, SVQB with the
  *                                                                      Frobenius-optimal Z of the
  *                                                                      Procrustes argument)
+ *   eoq_orthogonalize  phase I, the measures max(||W^T Y||_F, ||Y^T Y - I||_F),
+ *                  then SVQB, repeated until the measures are <= eps      (Sec. 4.2, iterated two-phase
+ *                                                                      algorithm; runtime figure)
  *   eoq_cholqr_b, eoq_svqb_b, eoq_project_b
  *                  the same with the inner product <x, y>_B = x^T B y of
  *                  a symmetric positive definite B, given through P = B X:
@@ -94,6 +97,15 @@ int eoq_threads(void) {
   return omp_get_max_threads();
 #else
   return 1;
+#endif
+}
+
+/* Threads of the later parallel loops (timing on one core or on all). */
+void eoq_set_threads(int t) {
+#ifdef _OPENMP
+  if (t > 0) omp_set_num_threads(t);
+#else
+  (void)t;
 #endif
 }
 
@@ -423,6 +435,62 @@ int eoq_svqb(int64_t n, int k, double* X, int64_t ldx, const double* M_hi, const
   if (Z_hi) store_dd(k, Zt, Z_hi, Z_lo, ldz);
   free(M); free(Z); free(Zt); free(T);
   return rank;
+}
+
+/* ------------------------------------------ iterated two-phase algorithm */
+
+/* The iterated orthogonalization of Sec. 4.2: the two phases are repeated in
+ * turn until both orthogonality measures are at or below eps (the runtime
+ * figure repeats them to eps = 1e-10).  Iteration it (0-based):
+ *   phase I   C = W^T Y (binary128), Y <- Y - W C (binary128, rounded once);
+ *   measure   M = Y^T Y of the rounded Y (binary128),
+ *             e = max(||C||_F, ||M - I||_F)  (the Frobenius norm bounds the
+ *             2-norm from above, so e <= eps certifies both 2-norm measures);
+ *   stop      if e <= eps: return it, the number of phase-II updates applied;
+ *   phase II  Z = M^{-1/2} with eigenvalue cut tol (the SVQB transform of
+ *             q_svqb_z), Y <- Y Z (binary128, rounded once).
+ * Returns -max_iter when e > eps after max_iter iterations.  *rank_out gets
+ * the rank of the last SVQB applied (k when none was). */
+int eoq_orthogonalize(int64_t n, int kv, const double* W, int64_t ldw, int k, double* Y, int64_t ldy, double eps,
+                      int max_iter, double tol, int* rank_out) {
+  size_t kk = (size_t)k * k;
+  qreal *C = qalloc((size_t)kv * k), *M = qalloc(kk), *Z = qalloc(kk);
+  int rank = k, iters = -max_iter;
+  for (int it = 0; it < max_iter; ++it) {
+#pragma omp parallel for collapse(2) schedule(dynamic)
+    for (int i = 0; i < kv; ++i)
+      for (int j = 0; j < k; ++j) {
+        qreal s = 0;
+        for (int64_t r = 0; r < n; ++r) s += (qreal)AT(W, ldw, r, i) * (qreal)AT(Y, ldy, r, j);
+        C[(size_t)j * kv + i] = s;
+      }
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < n; ++r)
+      for (int j = 0; j < k; ++j) {
+        qreal s = (qreal)AT(Y, ldy, r, j);
+        for (int i = 0; i < kv; ++i) s -= (qreal)AT(W, ldw, r, i) * C[(size_t)j * kv + i];
+        AT(Y, ldy, r, j) = (double)s;
+      }
+    q_gram_sym(n, k, Y, ldy, M);
+    qreal ec = 0, em = 0;
+    for (size_t t = 0; t < (size_t)kv * k; ++t) ec += C[t] * C[t];
+    for (int j = 0; j < k; ++j)
+      for (int i = 0; i < k; ++i) {
+        qreal e = M[(size_t)j * k + i] - (i == j ? 1 : 0);
+        em += e * e;
+      }
+    ec = qsqrt(ec);
+    em = qsqrt(em);
+    if ((ec > em ? ec : em) <= (qreal)eps) {
+      iters = it;
+      break;
+    }
+    rank = q_svqb_z(k, M, (qreal)tol, Z);
+    q_update(n, k, Y, ldy, Z);
+  }
+  if (rank_out) *rank_out = rank;
+  free(C); free(M); free(Z);
+  return iters;
 }
 
 /* ------------------------------------------------------- B-inner products */

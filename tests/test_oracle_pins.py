@@ -511,3 +511,216 @@ def test_gram_b_takes_the_symmetric_part():
 def test_orth_err_diag_with_unit_weights_is_orth_err():
     q = synth.conditioned(300, 4, 10.0, 70)
     assert oracle.orth_err_diag(q, np.ones(300)) == oracle.orth_err(q)
+
+
+# ------------------------------------------- two-pass SVQB transform
+# In exact arithmetic the first pass gives X1 = X M0^{-1/2} with X1^T X1 = I,
+# the second Z2 = I, so the accumulated transform is Z_tot = M0^{-1/2} and
+# Q = X Z_tot is the orthogonal polar factor of X.  The rounding of X1 to
+# FP64 makes Z2 = I + O(u), which leaves Z_tot within O(kappa u) of M0^{-1/2};
+# the accumulated product order (Z1 Z2, not Z2 Z1 or a transpose) shows in
+# X Z_tot = Q, whose error would then grow to the size of the commutator
+# [Z2, Z1] ~ kappa u.  Everything below is computed in mpmath.
+
+def _mp_mat(a, lo=None):
+    import mpmath as mp
+    m = mp.matrix(a.shape[0], a.shape[1])
+    for i in range(a.shape[0]):
+        for j in range(a.shape[1]):
+            m[i, j] = mp.mpf(float(a[i, j])) + (mp.mpf(float(lo[i, j])) if lo is not None else 0)
+    return m
+
+
+def _mp_maxabs(m):
+    return max(abs(m[i, j]) for i in range(m.rows) for j in range(m.cols))
+
+
+@pytest.mark.parametrize("k,kappa", [(3, 1e4), (4, 1e8), (6, 1e6)])
+def test_svqb_two_pass_transform_mpmath(k, kappa):
+    import mpmath as mp
+    mp.mp.prec = 320
+    n = 40
+    x = synth.conditioned(n, k, kappa, 1300 + k)
+    q, (zh, zl), rank = oracle.svqb(x, passes=2)
+    assert rank == k
+    X, Q, Z = _mp_mat(x), _mp_mat(q), _mp_mat(zh, zl)
+    M0 = X.T * X
+    # X Z_tot reproduces the returned Q to the rounding of the two updates
+    assert _mp_maxabs(X * Z - Q) < 1e-14
+    # Z_tot^T M0 Z_tot = I up to the FP64 rounding of the intermediate X1
+    assert _mp_maxabs(Z.T * M0 * Z - mp.eye(k)) < 1e-14
+    # Z_tot = M0^{-1/2} within kappa u, and Q is the polar factor U V^T of X
+    lam, U = mp.eigsy(M0)
+    Minv = U * mp.diag([1 / mp.sqrt(lam[i]) for i in range(k)]) * U.T
+    assert _mp_maxabs(Z - Minv) <= 100 * kappa * U64 * _mp_maxabs(Minv)
+    Us, S, Vt = mp.svd_r(X)
+    polar = Us * Vt
+    assert _mp_maxabs(Q - polar) <= 100 * kappa * U64
+
+
+def test_svqb_two_pass_one_pass_on_orthonormal_columns():
+    # orthogonal columns with power-of-two norms: both passes are exact, Z_tot = diag(1/s)
+    u = synth.hadamard_basis(64, 4, 5)
+    s = np.array([2.0, 0.25, 8.0, 1.0])
+    q, (zh, zl), rank = oracle.svqb(np.asfortranarray(u * s), passes=2)
+    assert rank == 4
+    assert np.array_equal(zh, np.diag(1 / s)) and not np.any(zl)
+    assert np.array_equal(q, u)
+
+
+# ------------------------------------------- iterated two-phase algorithm
+
+def test_orthogonalize_exact_case_takes_one_update():
+    # W and X from disjoint columns of an exact Hadamard basis, X scaled by
+    # powers of two: C = 0 exactly, M = S^2, SVQB gives Z = S^{-1} exactly,
+    # and the second iteration finds C = 0, M = I: one update, exact result.
+    full = synth.hadamard_basis(256, 9, 1401)
+    w, u = full[:, :6], np.asfortranarray(full[:, 6:])
+    s = np.array([4.0, 0.5, 2.0])
+    q, iters, rank = oracle.orthogonalize(w, u * s, eps=1e-12, max_iter=5)
+    assert iters == 1 and rank == 3
+    assert np.array_equal(q, u)
+    q0, iters0, _ = oracle.orthogonalize(w, u, eps=1e-12, max_iter=5)
+    assert iters0 == 0 and np.array_equal(q0, u)
+
+
+def test_orthogonalize_reports_no_convergence():
+    w = synth.hadamard_basis(256, 8, 1402)
+    x = synth.near_span(w, 2, 1e6, seed=1403)
+    _, iters, _ = oracle.orthogonalize(w, x, eps=0.0, max_iter=3)
+    assert iters == -3
+
+
+@pytest.mark.parametrize("k,kxw", [(1, 1e12), (3, 1e12), (4, 1e6)])
+def test_orthogonalize_invariants_and_span(k, kxw):
+    """On exit both measures are below eps (the stopping rule), and the result
+    spans the projection of X onto the complement of W:
+    ||(I - Q Q^T)(I - W W^T) X|| / ||(I - W W^T) X|| small, checked in
+    mpmath from the inputs alone."""
+    import mpmath as mp
+    mp.mp.prec = 260
+    n, kv = 256, 8
+    w = synth.hadamard_basis(n, kv, 1404 + k)
+    x = synth.near_span(w, k, kxw, seed=1405 + k, kappa=1e3)
+    q, iters, rank = oracle.orthogonalize(w, x, eps=1e-10, max_iter=8)
+    assert iters >= 1 and rank == k
+    # the stopping measures (Frobenius bounds the 2-norm), from the oracle's own measures
+    assert oracle.cross_err(w, q) <= 1e-10
+    assert oracle.orth_err(q)[1] <= 1e-10
+    W, X, Q = _mp_mat(w), _mp_mat(x), _mp_mat(q)
+    P = X - W * (W.T * X)
+    R = P - Q * (Q.T * P)
+    assert mp.mnorm(R, "f") <= 1e-12 * mp.mnorm(P, "f")
+
+
+# ------------------------------------------- the paper's CPU arithmetic
+
+def test_fp64_gram_plain_is_the_row_ordered_sum():
+    g = synth.rng(1501)
+    x = wide_range(g, 57, 3)
+    y = wide_range(g, 57, 2)
+    hi, lo = oracle.fp64_gram(x, y, mode=oracle.FP64)
+    assert not np.any(lo)
+    for i in range(3):
+        for j in range(2):
+            s = 0.0
+            for r in range(57):
+                s = s + float(x[r, i]) * float(y[r, j])
+            assert hi[i, j] == s
+
+
+@pytest.mark.parametrize("n", [10, 200, 3000])
+def test_fp64_gram_within_textbook_bounds(n):
+    g = synth.rng(1502 + n)
+    x = wide_range(g, n, 2)
+    y = wide_range(g, n, 2)
+    ex = exact_gram(x, y)
+    bound = abs_gram(x, y)
+    gam = F(n) * F(U64) / (1 - F(n) * F(U64))
+    ph, _ = oracle.fp64_gram(x, y, mode=oracle.FP64)
+    dh, dl = oracle.fp64_gram(x, y, mode=oracle.DD)
+    for i in range(2):
+        for j in range(2):
+            # plain: |s - x^T y| <= gamma_n |x|^T |y|
+            assert abs(F(float(ph[i, j])) - ex[i][j]) <= gam * F(float(bound[i, j]))
+            # Dot2 kept as a double-word: error <= gamma_n^2 |x|^T |y| (no final rounding)
+            assert abs(dd_fr(dh, dl, i, j) - ex[i][j]) <= gam * gam * F(float(bound[i, j])) + F(2.0 ** -1074)
+
+
+def test_fp64_gram_dot2_resolves_cancellation():
+    # x^T y = 2^-80 with terms of size 1: plain FP64 returns 0, Dot2 the exact value
+    x = np.array([[1.0], [2.0 ** -80], [-1.0], [3.0], [-3.0]])
+    y = np.ones((5, 1))
+    ph, _ = oracle.fp64_gram(x, y, mode=oracle.FP64)
+    dh, dl = oracle.fp64_gram(x, y, mode=oracle.DD)
+    assert ph[0, 0] == 0.0
+    assert dh[0, 0] + dl[0, 0] == 2.0 ** -80
+
+
+def test_fp64_cholqr_k1_dd_square_root():
+    # k = 1: R = ||x|| in double-double, Q = x / R rounded once
+    g = synth.rng(1503)
+    x = g.standard_normal((41, 1))
+    q, (rh, rl), info = oracle.fp64_cholqr(x, mode=oracle.DD)
+    assert info == 0
+    ss = sum((F(float(v)) ** 2 for v in x[:, 0]), F(0))
+    r = F(float(rh[0, 0])) + F(float(rl[0, 0]))
+    assert abs(r * r - ss) <= F(2.0 ** -100) * ss
+    for i in range(41):
+        ex = F(float(x[i, 0])) / r
+        assert abs(F(float(q[i, 0])) - ex) <= F(U64) * abs(ex) * F(1.0000001)
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e4, 1e6, 1e7])
+def test_fp64_cholqr_orthogonality_laws(kappa):
+    """Sec. 4.2: FP64 CholQR loses orthogonality like kappa^2 u, the DD form
+    like kappa^2 u^2 (stays at the rounding floor of the stored Q up to
+    kappa ~ 1e8); the binary128 oracle measures both."""
+    n, k = 2000, 6
+    x = synth.conditioned(n, k, kappa, 1504)
+    qp, _, ip = oracle.fp64_cholqr(x, mode=oracle.FP64)
+    qd, (rh, rl), idd = oracle.fp64_cholqr(x, mode=oracle.DD)
+    assert ip == 0 and idd == 0
+    ep = oracle.orth_err(qp)[0]
+    ed = oracle.orth_err(qd)[0]
+    assert ep <= 10 * k * kappa ** 2 * U64 + 20 * U64
+    if kappa >= 1e4:
+        assert ep >= 1e-3 * kappa ** 2 * U64  # the law is visible
+    assert ed <= 1e-14
+    if kappa >= 1e6:
+        assert ep >= 1e3 * ed
+    # the DD factorization agrees with the binary128 oracle's
+    qo, (roh, rol), _ = oracle.cholqr(x)
+    assert np.max(np.abs(qd - qo)) <= 4 * U64 + 8 * kappa ** 2 * (n + 64) * 2.0 ** -104
+    assert oracle.fact_err(x, qd, rh, rl) <= 8 * U64
+
+
+def test_fp64_cholqr_breakdown_and_two_passes():
+    x = synth.gaussian(300, 3, 1505)
+    x[:, 1] = 0.0
+    q, _, info = oracle.fp64_cholqr(x, mode=oracle.DD)
+    assert info == 2 and np.array_equal(q, x)
+    # plain FP64 CholQR2 repairs the kappa^2 u loss at kappa = 1e6
+    y = synth.conditioned(1000, 5, 1e6, 1506)
+    q2, (rh, rl), info = oracle.fp64_cholqr(y, passes=2, mode=oracle.FP64)
+    assert info == 0 and oracle.orth_err(q2)[0] <= 1e-14
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_fp64_project_against_binary128(mode):
+    n, kv, k = 3000, 8, 3
+    v = synth.orthonormal_basis(n, kv, 1507)
+    y = synth.conditioned(n, k, 1e3, 1508)
+    yt, (ch, cl), (mh, ml) = oracle.fp64_project(v, y, mode=mode)
+    yo, (cho, clo), _ = oracle.project(v, y)
+    cref = np.abs(v).T @ np.abs(y)
+    if mode == oracle.FP64:
+        assert np.all(np.abs(ch - cho) <= (n * U64 / (1 - n * U64)) * cref)
+        tol = (kv + 2) * U64 * (np.abs(y) + np.abs(v) @ np.abs(cho)) + np.abs(v) @ (n * U64 * cref)
+        assert np.all(np.abs(yt - yo) <= tol)
+    else:
+        assert np.all(np.abs((ch - cho) + (cl - clo)) <= (n * U64) ** 2 * cref + 2.0 ** -1000)
+        tol = 2 * U64 * np.abs(yo) + 2.0 ** -100 * (np.abs(y) + np.abs(v) @ np.abs(cho))
+        assert np.all(np.abs(yt - yo) <= tol)
+    mo = oracle.gram(yt)
+    assert np.all(np.abs((mh - mo[0]) + (ml - mo[1])) <= (n * U64) ** (1 + mode) * (np.abs(yt).T @ np.abs(yt)))
