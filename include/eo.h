@@ -174,10 +174,12 @@ EO_API eo_status eo_svqb(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, co
  * repeated in turn, with a rank-revealing factorization in phase II, which
  * makes the method robust; the runtime figure repeats them until both
  * measures fall below epsilon = 1e-10).  Each iteration runs phase I
- * (C = V^T Y, Y <- Y - V C) and measures max |C_ij| and max |M - I|_ij with
- * M = Y^T Y of the projected block; when both are <= eps the iteration stops
- * there, otherwise phase II applies SVQB (Z = M^{-1/2} with eigenvalue cut tol,
- * as in eo_svqb) and the next iteration follows.  Y (n-by-k, FP64) is updated
+ * (C = V^T Y, Y <- Y - V C) and measures ||C||_F and ||M - I||_F with
+ * M = Y^T Y of the projected block (the Frobenius norm bounds the 2-norm from
+ * above, so a stop certifies ||V^T Y||_2 <= eps and ||Y^T Y - I||_2 <= eps
+ * for the C and M computed); when both are <= eps the iteration stops there,
+ * otherwise phase II applies SVQB (Z = M^{-1/2} with eigenvalue cut tol, as
+ * in eo_svqb) and the next iteration follows.  Y (n-by-k, FP64) is updated
  * in place; V (n-by-kv) must be orthonormal.  All max_iter iterations
  * (1..16) are enqueued at once and skipped on the device after convergence.
  *   iters_dev: optional device int, the number of SVQB updates applied before
@@ -361,16 +363,22 @@ EO_API int eo_admission_simulate(size_t budget, int slots, size_t resident_bytes
  * fixed array of EO_NOALLOC_SCRATCH_BYTES inside the library, held on every
  * GPU that loads the library until the process exits.
  *   X, Y, G_hi, G_lo, lds: as in eo_gram (Y == NULL: Y = X); FP64 data.
- *   kx, ky must not exceed EO_NOALLOC_KMAX; larger sizes return EO_EINVAL.
+ *   kx, ky must not exceed EO_NOALLOC_KMAX, and n must not exceed
+ *   EO_NOALLOC_NMAX (152 row chunks of at most 2^22 rows: the partial sums of
+ *   more chunks would not fit the array); larger sizes return EO_EINVAL
+ *   before anything is launched.
  *   cuda_stream: the cudaStream_t to run on (NULL = default stream); the
  *   current CUDA device is used.
  * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * that device current), and so does the first call after the device's
+ * context has been re-created (e.g. by cudaDeviceReset, after which the
+ * array may sit elsewhere); make those calls before any stream capture.
  * Every call shares the one array, so calls whose work overlaps on the GPU
  * (different streams, or other host threads) race and give wrong results;
  * serialize them.  Returns EO_OK, EO_EINVAL or EO_ECUDA.
  */
 #define EO_NOALLOC_KMAX 16
+#define EO_NOALLOC_NMAX (152ll << 22)
 #define EO_NOALLOC_SCRATCH_BYTES (152u * EO_NOALLOC_KMAX * EO_NOALLOC_KMAX * 32u)
 EO_API eo_status eo_gram_dd_noalloc(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y,
                                     int64_t ldy, double* G_hi, double* G_lo, int ldg, void* cuda_stream);

@@ -517,27 +517,34 @@ __global__ void __launch_bounds__(kThreads) converge_kernel(const int* run, cons
                                                             int ldm, double eps, DevStatus* st, int iter,
                                                             int max_iter, int* iters_user, int* rank_user) {
   if (*run == 0) return;
-  __shared__ double red[kThreads];
-  double m = 0.0;
+  // Frobenius norms of C and of M - I (each bounds the 2-norm from above),
+  // as sums of squares in a fixed reduction order
+  __shared__ double red[2][kThreads];
+  double sc = 0.0, sm = 0.0;
   for (int t = threadIdx.x; t < kv * k; t += kThreads) {
     const int i = t % kv, j = t / kv;
     const double c = Ch[(size_t)j * ldc + i] + (Cl ? Cl[(size_t)j * ldc + i] : 0.0);
-    m = fmax(m, dabs(c));
+    sc += c * c;
   }
   for (int t = threadIdx.x; t < k * k; t += kThreads) {
     const int i = t % k, j = t / k;
     // (M_hi - delta) + M_lo: the subtraction of 1 is exact near 1
     const double e = (Mh[(size_t)j * ldm + i] - (i == j ? 1.0 : 0.0)) + (Ml ? Ml[(size_t)j * ldm + i] : 0.0);
-    m = fmax(m, isnan(e) ? 1e300 : dabs(e));
+    sm += e * e;
   }
-  red[threadIdx.x] = m;
+  red[0][threadIdx.x] = sc;
+  red[1][threadIdx.x] = sm;
   __syncthreads();
   for (int w = kThreads / 2; w >= 1; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    if (threadIdx.x < w) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + w];
+      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const bool conv = red[0] <= eps;
+    const double fc = sqrt(red[0][0]), fm = sqrt(red[1][0]);
+    const bool conv = fc <= eps && fm <= eps;  // false for NaN
     st->gate[kItSvqb + iter] = conv ? 0 : 1;
     if (iter + 1 < max_iter) st->gate[kItRun + iter + 1] = conv ? 0 : 1;
     if (conv) st->iters = iter;  // updates applied before convergence was seen

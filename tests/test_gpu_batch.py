@@ -271,3 +271,30 @@ def test_batch_f32_inputs_equal_single_calls(eo, ctx):
         eo.cholqr(ctx, d, passes=2, prec=eo.F32)
         assert same(host(ds[i]), host(d)), i
     b.close()
+
+
+def test_batch_two_pass_blocks_match_oracle(eo, ctx):
+    """Blocks that take the automatic second pass (kappa > 1e7) against the
+    oracle's two-pass SVQB, with the two-pass bound (4 x one pass: the first
+    pass's difference survives the second only in its skew part)."""
+    import torch
+    shapes = [(20_000, 8, 1e9), (70_016, 16, 1e10), (9_000, 32, 1e8), (4_097, 4, 1e12), (12_000, 16, 1e5)]
+    xs = blocks(shapes, seed=9)
+    ds = [dev(x) for x in xs]
+    for tune in (False, True):
+        for d, x in zip(ds, xs):
+            d.copy_(dev(x))
+        b = eo.Batch(ctx, ds, passes=0, prec=eo.DD, tune=tune, want_z=True)
+        b.run()
+        torch.cuda.synchronize()
+        passes = b.passes()
+        for i, (n, k, kappa) in enumerate(shapes):
+            assert passes[i] == (2 if kappa > 1e7 else 1), i
+            q_o, (zh_o, zl_o), rank_o = oracle.svqb(xs[i], passes=passes[i])
+            tol = (4 if passes[i] == 2 else 1) * dd_tol(n, k, kappa) + 8 * U
+            assert np.max(np.abs(host(ds[i]) - q_o)) <= tol, (i, tune)
+            z = host(b.z[i][0]) + host(b.z[i][1])
+            assert np.max(np.abs(z - (zh_o + zl_o))) <= tol * np.max(np.abs(zh_o)), (i, tune)
+            assert int(b.out[i].item()) == rank_o == k
+            assert oracle.orth_err(host(ds[i]))[0] <= 1e-14
+        b.close()

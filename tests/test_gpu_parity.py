@@ -587,6 +587,33 @@ def test_svqb_dd_matches_oracle(eo, ctx, n, k, kappa):
     assert oracle.orth_err(host(d))[0] <= 1e-14
 
 
+def svqb2_tol(n, k, kappa):
+    """|Q - Q*| after two SVQB passes: the first pass's difference Q1 - Q1* =
+    Q1* E (E k-by-k, within cholqr_tol) survives the second pass only as
+    Q1* skew(E) (the symmetric part is what the second pass removes), plus
+    the second pass's own rounding."""
+    return 4 * cholqr_tol(n, k, kappa) + 8 * U
+
+
+@pytest.mark.parametrize("n,k,kappa", [(20_000, 8, 1e8), (20_001, 16, 1e10), (9_000, 32, 1e9), (3_000, 4, 1e12)])
+def test_svqb_dd_two_passes_match_oracle(eo, ctx, n, k, kappa):
+    x = synth.conditioned(n, k, kappa, 830 + k)
+    d, da = dev(x), dev(x)
+    zh, zl, rank = eo.svqb(ctx, d, passes=2, prec=eo.DD)
+    assert int(rank.item()) == k
+    q_o, (zh_o, zl_o), rank_o = oracle.svqb(x, passes=2)
+    assert rank_o == k
+    tol = svqb2_tol(n, k, kappa)
+    q = host(d)
+    assert np.max(np.abs(q - q_o)) <= tol
+    z = host(zh) + host(zl)
+    assert np.max(np.abs(z - (zh_o + zl_o))) <= tol * np.max(np.abs(zh_o))
+    assert oracle.orth_err(q)[0] <= 1e-14
+    # the automatic pass count takes the second pass here (lambda_max / lambda_min > 1e14)
+    eo.svqb(ctx, da, passes=0, prec=eo.DD)
+    assert np.array_equal(host(da), q)
+
+
 def test_svqb_rank_deficient(eo, ctx):
     x = synth.gaussian(5000, 4, 90)
     x[:, 2] = 0.0
