@@ -365,6 +365,7 @@ def orthogonalize(ctx: Context, V, Y, eps: float = 1e-10, max_iter: int = 8, pre
 
 
 NOALLOC_KMAX = 16
+NOALLOC_NMAX = 152 << 22  # rows: 152 row chunks of at most 2^22 rows
 
 
 def gram_dd_noalloc(X, Y=None, out=None):
