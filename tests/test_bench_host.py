@@ -38,3 +38,33 @@ def test_gram_traffic_scales_reads_with_rows(bench):
     assert t1 - reads == pytest.approx(t4 - 4 * reads)  # the partials do not grow with n
     assert 0 < t1 - reads < 8e6
     assert bench.gram_traffic(1_000_000, 32, 16) is None
+
+
+def test_reference_arm_prints_one_json_line(tmp_path):
+    """`bench.py --impl reference` runs the oracle's CPU arithmetic (no GPU)
+    and prints the base contract's line with the reference keys."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--n", "20000",
+                          "--cpu-rows", "20000", "--steps", "2", "--warmup", "1"], capture_output=True, text=True,
+                         timeout=600, cwd=str(tmp_path))
+    assert out.returncode == 0, out.stderr
+    lines = [l for l in out.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    r = json.loads(lines[0])
+    assert r["impl"] == "reference" and r["unit"] == "GB/s" and r["value"] > 0
+    assert r["cpu_baseline"]["kind"] == "oracle" and r["cpu_baseline"]["cores"] >= 1
+    assert r["e2e"]["h2d_bytes_per_step"] == 0 and r["e2e"]["value"] == r["value"]
+
+
+def test_cpu_baseline_reports_dd_fp64_and_one_core(bench):
+    import numpy as np
+    import synth
+    v = synth.orthonormal_basis(3000, 8, 1)
+    y = synth.conditioned(3000, 4, 1e10, 2)
+    r = bench.cpu_baseline(v, y, 0)
+    assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] >= 1
+    assert r["orth_err"] is not None and r["orth_err"] <= 1e-14  # the DD step is accurate at kappa = 1e10
+    assert r["fp64_cholqr2"]["value"] > 0 and r["one_core_dd"]["rows"] == 3000
