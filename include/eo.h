@@ -60,14 +60,17 @@ typedef enum {
 } eo_prec;
 
 /* EO_DD accuracy: each group of values summed against another (a column of a
- * block of rows, a row of V or X, a column of C or Z) is aligned to its
- * largest exponent and held as a 104-bit integer (four 26-bit limbs; the ten
- * most significant limb products are kept) or, in Gram products with 16 or
- * more columns on one side, as a 105-bit integer of fifteen 7-bit digits
- * whose products are summed on the tensor cores (FP16 digits, exact FP32
- * sums; the 120 most significant digit pairs are kept).  Either way each
- * product carries an error below 2^-101 max|x| max|y|, the sums of the kept
- * products are exact, and every result is rounded once.  Exact sums are
+ * block of rows, a row of V or X, a column of C or Z) is aligned to an
+ * exponent at or above its largest and held as a 104-bit integer (four
+ * 26-bit limbs; the ten most significant limb products are kept) or, in Gram
+ * products with 16 or more columns on one side, as a 105-bit integer of
+ * fifteen balanced 7-bit digits whose products are summed on the tensor cores
+ * (FP16 integer digits, exact FP32 sums; the 120 most significant digit pairs
+ * are kept; a column's alignment exponent sits up to two binades above its
+ * largest, so that it rarely has to grow).  Each product then carries an
+ * error below 2^-101 max|x| max|y| (integer limbs) or 2^-96 max|x| max|y|
+ * (tensor-core digits), the sums of the kept products are exact, and every
+ * result is rounded once.  Exact sums are
  * associative: the order of the partial sums does not matter, and the same
  * inputs give bitwise the same results on every run.  A bounded wait inside
  * the tensor-core kernel that runs out (2 s) turns the affected Gram entries
@@ -104,8 +107,8 @@ EO_API uint64_t eo_kernel_launches(const eo_ctx* ctx);
  *   symmetric and both triangles are written).  FP64 data, or float data in
  *   EO_F32 mode.  G_hi (required) / G_lo: kx-by-ky with leading dimension ldg.
  * EO_DD: every G_ij is the double-double rounding of the sum of the exact
- * products (error below 2^-104 |G_ij| + n 2^-101 max|x_i| max|y_j|); results
- * are bitwise reproducible.
+ * products (error below 2^-104 |G_ij| + n 2^-96 max|x_i| max|y_j|, see the
+ * accuracy note above); results are bitwise reproducible.
  */
 EO_API eo_status eo_gram(eo_ctx* ctx, int64_t n, int kx, const void* X, int64_t ldx, int ky, const void* Y, int64_t ldy,
                   double* G_hi, double* G_lo, int ldg, eo_prec prec);

@@ -5,10 +5,13 @@
 //
 // Digits: a value x aligned to the exponent A of its group (A >= the biased
 // exponent of every member) is the integer X = floor(|x| 2^(1127 - A)) < 2^105
-// = sum_{s=0}^{14} D_s 2^(98 - 7s), D_s in [0, 127]; on the tensor cores a digit
-// is the FP16 subnormal +-D_s 2^-24 whose bit pattern is the digit with the
-// value's sign, so products of two digits are exact and FP32 sums of fewer
-// than 2^24 units of 2^-48 are exact.
+// = sum_{s=0}^{14} D_s 2^(98 - 7s).  The row kernels (umma_rowprod.cu) use
+// plain digits D_s in [0, 127], each the FP16 subnormal +-D_s 2^-24 whose bit
+// pattern is the digit with the value's sign, so products of two digits are
+// exact and FP32 sums of fewer than 2^24 units of 2^-48 are exact.  The Gram
+// kernel (umma_gram.cu) uses balanced digits (below), FP16 integers of at
+// most 64 in magnitude (128 for the top digit), whose products are smaller
+// and let its accumulators run longer between drains.
 #pragma once
 
 #include <cuda.h>
@@ -358,6 +361,71 @@ __device__ __forceinline__ void store_digits(unsigned char* dst, unsigned stride
   if constexpr (S < NS) {
     *reinterpret_cast<unsigned*>(dst + S * stride) = pair_word<S>(p, signs);
     store_digits<S + 1>(dst, stride, p, signs);
+  }
+}
+
+// Balanced digits.  With B = sum_s 64 * 2^(98 - 7s) (64 in every digit
+// place), X' = X + B has 7-bit fields f_s in [0, 127] for s >= 1 and a top
+// field f_0 = X' >> 98 in [0, 192] (X < 2^105), and
+//   X = sum_s (f_s - 64) 2^(98 - 7s),   D_s = f_s - 64,
+// so D_s is in [-64, 63] for s >= 1 and in [-64, 128] for s = 0: products
+// of two digits are at most 2^12 (2^13 with D_0, 2^14 for D_0^2) instead of
+// 127^2 for unsigned 7-bit digits.  On the tensor cores a digit is the FP16
+// integer sign(x) D_s: the field is placed in the significand of the FP16
+// 1024 (bit pattern 0x6400 | f, the value 1024 + f), and one f16x2 FMA
+// forms sign * (1024 + f) - sign * 1088 = sign (f - 64) exactly (integers
+// below 2048 are exact in FP16).
+constexpr unsigned kBias0 = 0x08102040u, kBias1 = 0x40810204u, kBias2 = 0x04081020u, kBias3 = 0x102u;
+__device__ __forceinline__ void add_bias(unsigned (&w)[4]) {
+  asm("add.cc.u32 %0, %0, %4;\n\t"
+      "addc.cc.u32 %1, %1, %5;\n\t"
+      "addc.cc.u32 %2, %2, %6;\n\t"
+      "addc.u32 %3, %3, %7;"
+      : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3])
+      : "n"(kBias0), "n"(kBias1), "n"(kBias2), "n"(kBias3));
+}
+// The FP16 exponent field of 1024 in both halves, as a register (so that
+// the digit's mask and this constant fit one three-input logic operation).
+__device__ __forceinline__ unsigned exp1024x2() {
+  unsigned r;
+  asm volatile("mov.b32 %0, 0x64006400;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned hfma2(unsigned a, unsigned b, unsigned c) {
+  unsigned d;
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+// Signs of a pair (bit 15: value a, bit 31: value b) -> the f16x2 factors
+// (+-1, +-1) and addends (-+1088, -+1088) of the digit FMA.
+struct PairSign {
+  unsigned mul, add, e1024;
+};
+__device__ __forceinline__ PairSign pair_sign(unsigned signs, unsigned e1024) {
+  return PairSign{0x3C003C00u | signs, 0xE440E440u ^ signs, e1024};
+}
+// Balanced digit word of slab S for the pair (lanes of X'): low half value a,
+// high half value b, both FP16 integers sign * D_S.
+template <int S>
+__device__ __forceinline__ unsigned bal_word(const PairLanes& p, PairSign sg) {
+  constexpr int q = 98 - 7 * S, k = q >> 4, o = q & 15;
+  constexpr unsigned m = S == 0 ? 0x00ff00ffu : 0x007f007fu;  // the top field has 8 bits
+  constexpr bool low = o <= (S == 0 ? 8 : 9);
+  constexpr int sh = low ? o : o - 8;
+  const unsigned z = low ? p.Z[k] : p.Z8[k];
+  // the shift as a high-half multiplication (the FMA pipe), then one
+  // three-input logic operation (z & m) | e1024 (the ALU)
+  unsigned zs = z, f;
+  if constexpr (sh > 0) asm("mul.hi.u32 %0, %1, %2;" : "=r"(zs) : "r"(z), "n"(1u << (32 - sh)));
+  asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(f) : "r"(zs), "n"(m), "r"(sg.e1024));
+  return hfma2(f, sg.mul, sg.add);
+}
+template <int S>
+__device__ __forceinline__ void store_bal_digits(unsigned char* dst, unsigned stride, const PairLanes& p,
+                                                 PairSign sg) {
+  if constexpr (S < NS) {
+    *reinterpret_cast<unsigned*>(dst + S * stride) = bal_word<S>(p, sg);
+    store_bal_digits<S + 1>(dst, stride, p, sg);
   }
 }
 

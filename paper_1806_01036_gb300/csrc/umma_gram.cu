@@ -5,13 +5,18 @@
 // increased precision.  The sums are exact, as in fx.cuh; the digit products
 // run on the tensor cores:
 //
-//  * each value x of a column is aligned to the column's running exponent A
-//    and held as X = floor(|x| 2^(1127 - A)) < 2^105, cut into 15 digits of
-//    7 bits, X = sum_s D_s 2^(98 - 7s);
-//  * a digit is the FP16 number +-D_s 2^-24 (bit pattern: the digit with the
-//    value's sign; an FP16 subnormal), so every product of two digits is
-//    exact on the grid 2^-48 and sums of fewer than 2^24 grid units are exact
-//    in the FP32 accumulators;
+//  * each value x of a column is aligned to the column's alignment exponent
+//    A and held as X = floor(|x| 2^(1127 - A)) < 2^105, written with 15
+//    balanced digits, X = sum_s D_s 2^(98 - 7s), D_s in [-64, 63] (D_0 in
+//    [-64, 128]; umma.cuh: the fields of X + sum_s 64 2^(98 - 7s), less 64);
+//  * a digit is the FP16 integer sign(x) D_s, so every product of two digits
+//    is an integer of at most 2^12 (2^14 for the two top digits) and FP32
+//    sums of such products are exact while they stay within 2^24;
+//  * a column's alignment exponent starts at the first panel's largest
+//    exponent plus EO_GRAM_HEADROOM binades and grows (to the new largest
+//    exponent plus the headroom) only when a value's exponent exceeds it:
+//    with the headroom, later panels rarely raise it, and each raise costs a
+//    full drain of the accumulators;
 //  * digit slabs sit in shared memory in the canonical K-major layout (8x16-
 //    byte core matrices; the K dimension is the row index of X and Y).  One
 //    MMA multiplies J consecutive X slabs (M = 128 = J x kxp TMEM lanes) by
@@ -20,19 +25,24 @@
 //    c = Jq + t of lane block j: column block c of lane block j collects the
 //    digit diagonal d = c + j, and the 120 digit pairs with d <= 14 take
 //    15 / J + 1 MMAs per 16 rows;
-//  * every R rows (R such that no accumulator can reach 2^24 units) the
-//    accumulators are read back (tcgen05.ld), converted to integers, added
-//    to 32-bit running sums per (lane, column) and set back to zero; a group
-//    of three column blocks whose blocks hold fewer digit pairs per row is
-//    drained only every 2nd, 4th or 8th time (still below 2^24 units).  The
-//    running sums are folded into a
-//    128-bit total W in the units of the integer engine (value =
-//    W 2^(Ax + Ay - 2148)) every 8192 rows, before an alignment exponent
-//    grows, and at the end.  The row-chunk partials go through the same
-//    exact, order-free reduction (fx_gram_reduce).
+//  * every R rows (R such that no accumulator can exceed 2^24 in magnitude:
+//    the largest per-row sum of digit-pair bounds that a column block
+//    collects, group_bound below) the accumulators are read back
+//    (tcgen05.ld), converted to integers, added to 32-bit running sums per
+//    (lane, column) and set back to zero; a group of three column blocks
+//    whose per-row bound is smaller is drained only every 2nd, 4th or 8th
+//    time.  The running sums are folded into a 128-bit total W in the units
+//    of the integer engine (value = W 2^(Ax + Ay - 2148)) every 8192 rows,
+//    before an alignment exponent grows, and at the end.  The row-chunk
+//    partials go through the same exact, order-free reduction
+//    (fx_gram_reduce).
 //
-// The dropped digit pairs (d >= 15) weigh less than 2^-101 max|x| max|y| per
-// row, as in the integer engine.  Pipeline per CTA (one per SM): TMA loads
+// Error per product x y: the dropped digit pairs (d >= 15) weigh less than
+// 14.2 * 2^103 units^2 (units of 2^(Ax - 1127), 2^(Ay - 1127)), and a value
+// more than 52 binades below A is truncated by less than one unit; with
+// max|x| >= 2^(104 - h) units for a headroom h, the error is below
+// 22.2 * 2^(2h - 105) max|x| max|y| (h = 2: 2^-96.5).  Pipeline per CTA (one
+// per SM): TMA loads
 // of the FP64 panels (128-byte swizzle, two panels ahead), conversion of
 // panel p into one of two digit buffers while the tensor cores run panel
 // p-1, one warp issuing the MMAs and committing them to an mbarrier per
@@ -66,6 +76,11 @@ constexpr int kMaxItems = 3;  // items (two rows of one column) per thread and p
 constexpr int kOffsetDigits = 2148;
 constexpr int kFoldRows = 8192;  // rows between folds of the 32-bit running sums
 constexpr size_t kSmemCap = 225 * 1024;
+// Binades of headroom above a column's largest exponent when its alignment
+// exponent is set (see the error bound above).
+#ifndef EO_GRAM_HEADROOM
+#define EO_GRAM_HEADROOM 2
+#endif
 
 struct UPlan {
   int kxp, kyp, J, nq;  // X tile width (J = 128 / kxp lane blocks), Y tile width, MMAs per k-step
@@ -244,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int u = 0; u < 3; ++u)
 #pragma unroll
-        for (int y = 0; y < NY; ++y) sm[u][y] += (unsigned)__float2int_rn(__uint_as_float(v[u][y]) * 0x1p48f);
+        for (int y = 0; y < NY; ++y) sm[u][y] += (unsigned)__float2int_rn(__uint_as_float(v[u][y]));
       tmem_st3<NY>(tsum + c0 * KYP, tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, sm);
       tmem_zero3<NY>(tacc + c0 * KYP, tacc + (c0 + 1) * KYP, tacc + (c0 + 2) * KYP);
     };
@@ -416,25 +431,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     // true if one of this thread's columns exceeds te[k], its nonzero
     // running exponent
     auto scan = [&](const double2 (&v)[kMaxItems], int* pmq, const int (&te)[kMaxItems]) -> bool {
-      unsigned m[kMaxItems];
-#pragma unroll
-      for (int k = 0; k < kMaxItems; ++k)
-        m[k] = max(hi32(v[k].x) & 0x7fffffffu, hi32(v[k].y) & 0x7fffffffu) |
-               min(lo32(v[k].x) | lo32(v[k].y), 1u);
       bool g = false;
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
-        if (m[k] && tid + k * kConvThreads < nitems) {
-          int e = (int)(m[k] >> 20);
-          if (e == 0) e = 1;  // subnormal
+        // the larger magnitude's bit pattern; its exponent exceeds te[k]
+        // exactly when the pattern reaches (te[k] + 1) << 20.  A panel's
+        // maxima are only ever used as max(running exponent, panel
+        // maximum), so an item within its column's running exponent changes
+        // nothing (with steady exponents, nearly all items).  Subnormals
+        // (exponent field 0) never raise a column: its alignment exponent is
+        // at least 1 anyway.  Items past the panel's end hold zeros.
+        const unsigned m = max(hi32(v[k].x) & 0x7fffffffu, hi32(v[k].y) & 0x7fffffffu);
+        if (m >= ((unsigned)te[k] + 1u) << 20) {
+          const int e = (int)(m >> 20);
           if (e == 2047) flag = 1;
-          // a panel's maxima are only ever used as max(running exponent,
-          // panel maximum): an item within its column's running exponent
-          // te[k] changes nothing (with steady exponents, nearly all items)
-          if (e > te[k]) {
-            atomicMax(&pmq[it_s[k] >> 16], e);
-            g |= te[k] != 0;
-          }
+          atomicMax(&pmq[it_s[k] >> 16], e + EO_GRAM_HEADROOM);
+          g |= te[k] != 0;
         }
       }
       return g;
@@ -475,16 +487,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (p >= 2) mbar_wait(fb0 + 8u * db, (unsigned)((p - 2) >> 1) & 1u, &bad);
       // digits of panel p
       unsigned char* dbuf = dig + (size_t)db * pl.dig_bytes;
+      const unsigned e1024 = exp1024x2();
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
         if (tid + k * kConvThreads < nitems && (!PAD || !(it_d[k] & 0x40000000u))) {
           unsigned wa[4], wb[4];
           xwords(v[k].x, A[k], wa);
           xwords(v[k].y, A[k], wb);
+          add_bias(wa);
+          add_bias(wb);
           const unsigned signs = ((hi32(v[k].x) >> 31) << 15) | (hi32(v[k].y) & 0x80000000u);
-          store_digits<0>(dbuf + (it_d[k] & (PAD ? 0x3fffffffu : 0x7fffffffu)), (it_d[k] >> 31) ? stride_b : stride_a,
-                          pair_lanes(wa, wb),
-                          signs);
+          store_bal_digits<0>(dbuf + (it_d[k] & (PAD ? 0x3fffffffu : 0x7fffffffu)),
+                              (it_d[k] >> 31) ? stride_b : stride_a, pair_lanes(wa, wb), pair_sign(signs, e1024));
         }
       }
       fence_proxy_async();
@@ -600,6 +614,24 @@ int pow2_at_least(int v) {
   return p;
 }
 
+// Largest |digit| of slab s: balanced digits are in [-64, 63] except the top
+// one, in [-64, 128].
+constexpr long long digit_bound(int s) { return s == 0 ? 128 : 64; }
+
+// Largest per-row sum of |D_s D_t| that a column block c in [c0, c1] of any
+// lane block j collects: the pairs (s, t) = (J q + j, c - J q) with J q <= c
+// and J q + j <= 14.
+long long group_bound(int c0, int c1, int J) {
+  long long worst = 0;
+  for (int c = c0; c <= c1; ++c)
+    for (int j = 0; j < J; ++j) {
+      long long b = 0;
+      for (int q = 0; J * q <= c && J * q + j <= 14; ++q) b += digit_bound(J * q + j) * digit_bound(c - J * q);
+      worst = std::max(worst, b);
+    }
+  return worst;
+}
+
 UPlan make_plan(int kx, int ky, bool sym) {
   UPlan p{};
   if (sym && kx <= 16) {
@@ -615,9 +647,10 @@ UPlan make_plan(int kx, int ky, bool sym) {
   p.ntx = (kx + p.kxp - 1) / p.kxp;
   p.nty = p.shared ? 1 : (ky + p.kyp - 1) / p.kyp;
   p.nslots = p.shared ? p.kxp : p.kxp + p.kyp;
-  // rows an accumulator may absorb: digit pairs per entry and row <= 14 / J + 1, each < 2^14
-  const int pairs = 14 / p.J + 1;
-  const int rows_cap = (int)((1u << 24) / ((unsigned)pairs * 127u * 127u));
+  // rows an accumulator may absorb: the largest sum of digit-pair bounds
+  // that one column block collects per row (below 2^24 in total)
+  const long long row_bound = group_bound(0, 14, p.J);
+  const int rows_cap = (int)((1ll << 24) / row_bound);
   int best = 16;
   for (int P = 16; P <= 128; P *= 2) {
     if (P > rows_cap || (size_t)p.nslots * P / 2 > (size_t)kMaxItems * kConvThreads) break;
@@ -629,17 +662,16 @@ UPlan make_plan(int kx, int ky, bool sym) {
   }
   p.P = best;
   p.drain_panels = std::max(1, rows_cap / p.P);
-  // a drain adds at most drain rows x pairs x 127^2 to a 32-bit running sum
-  const long long per_drain = (long long)p.drain_panels * p.P * pairs * 127 * 127;
+  // a drain adds at most drain rows x row_bound to a 32-bit running sum
+  const long long per_drain = (long long)p.drain_panels * p.P * row_bound;
   p.fold_drains = (int)std::max(1ll, std::min<long long>(kFoldRows / (p.drain_panels * p.P),
                                                           ((1ll << 31) - 1) / per_drain));
   // Column block c of a lane block collects at most c / J + 1 digit pairs
   // per row, so a group of three blocks stays exact for 2^24 / (its largest
-  // pair count x 127^2) rows: it is drained every 2^g-th drain (g <= 3).
+  // per-row bound) rows: it is drained every 2^g-th drain (g <= 3).
   p.drain_log = 0;
   for (int g = 0; g < 5; ++g) {
-    const int pg = std::min(3 * g + 2, 14) / p.J + 1;
-    const long long dmax = (1ll << 24) / ((long long)pg * 127 * 127 * p.drain_panels * p.P);
+    const long long dmax = (1ll << 24) / (group_bound(3 * g, std::min(3 * g + 2, 14), p.J) * p.drain_panels * p.P);
     int lg = 0;
     while (lg < 3 && (2ll << lg) <= dmax) ++lg;
     p.drain_log |= lg << (3 * g);

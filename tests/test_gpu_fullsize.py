@@ -40,10 +40,11 @@ def test_projection_cholqr_at_full_size(eo, ctx):
     assert int(info.item()) == 0
     q = host(yt_d)
 
-    # C = V^T Y, every entry, against the oracle (r8's bound)
+    # C = V^T Y, every entry, against the oracle: |C - C*| <= 2^-104 |C*| + n 2^-96 max|v_i| max|y_j|
+    # (the normwise bound of the compensated Gram products)
     ch_o, cl_o = oracle.gram(v, y)
     err = np.abs((host(c[0]) - ch_o) + (host(c[1]) - cl_o))
-    bound = U2 * np.abs(ch_o) + n * 2.0 ** -101 * np.outer(np.max(np.abs(v), axis=0), np.max(np.abs(y), axis=0))
+    bound = U2 * np.abs(ch_o) + n * 2.0 ** -96 * np.outer(np.max(np.abs(v), axis=0), np.max(np.abs(y), axis=0))
     assert np.all(err <= bound)
 
     # Y~ on sampled rows: the oracle's projection with its own C
@@ -83,7 +84,7 @@ def test_gram_precision_sweep_sampled_at_full_size(eo, ctx):
         absdot = float(np.abs(xi) @ np.abs(xj))
         dd = got[eo.DD][0][i, j] + got[eo.DD][1][i, j]
         assert abs((got[eo.DD][0][i, j] - rh[0, 0]) + (got[eo.DD][1][i, j] - rl[0, 0])) <= \
-            U2 * abs(ref) + n * 2.0 ** -101 * mi * mj, (i, j)
+            U2 * abs(ref) + n * 2.0 ** -96 * mi * mj, (i, j)
         assert abs(got[eo.FP64][0][i, j] - ref) <= n * U / (1 - n * U) * absdot, (i, j)
         fi, fj = X32[:, i].cpu().numpy().astype(np.float64), X32[:, j].cpu().numpy().astype(np.float64)
         rfh, rfl = oracle.gram(fi[:, None], fj[:, None])
