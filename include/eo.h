@@ -73,15 +73,15 @@ typedef enum {
  * result is rounded once.  Exact sums are
  * associative: the order of the partial sums does not matter, and the same
  * inputs give bitwise the same results on every run.  A bounded wait inside
- * the tensor-core kernel that runs out (2 s) turns the affected Gram entries
- * into NaN instead of hanging. */
+ * the tensor-core kernels that runs out (2 s) turns the affected outputs
+ * into NaN instead of hanging, and eo_device_status reports it. */
 
 typedef enum {
   EO_OK = 0,
   EO_EINVAL = 1,      /* bad argument (size, leading dimension, NULL pointer, mode) */
   EO_ENOMEM = 2,      /* scratch allocation failed                                   */
   EO_ECUDA = 3,       /* a CUDA call or kernel launch failed (see eo_last_error)     */
-  EO_ETIMEOUT = 4,    /* a bounded device-side wait expired                          */
+  EO_ETIMEOUT = 4,    /* a bounded wait expired (eo_device_status, eo_server_wait)    */
   EO_EUNSUPPORTED = 5 /* valid but not implemented combination                       */
 } eo_status;
 
@@ -98,6 +98,21 @@ EO_API const char* eo_last_error(const eo_ctx* ctx);
 EO_API int eo_version(void);
 /* Number of kernels this context has launched so far (diagnostics). */
 EO_API uint64_t eo_kernel_launches(const eo_ctx* ctx);
+/* Device-side failure record (no counterpart in the paper).  Every wait
+ * inside the tensor-core kernels (TMA arrival, MMA completion, converted
+ * digits) is bounded (2 s); a wait that runs out makes its kernel finish
+ * early with NaN outputs and records the expiry in a word on the device.
+ * eo_device_status waits for the context's stream, then returns EO_ETIMEOUT
+ * (with a message in eo_last_error) if such a record exists on the
+ * context's device, clearing it, and EO_OK otherwise.  The record is per
+ * device, shared by every context on it.
+ * eo_selftest_wait_timeout launches, on the context's stream, one kernel
+ * whose single thread waits on an mbarrier that nothing completes, bounded
+ * by `seconds` (0 < seconds <= 2): it exercises the same bounded-wait path,
+ * so the next eo_device_status reports EO_ETIMEOUT; the context stays
+ * usable. */
+EO_API eo_status eo_device_status(eo_ctx* ctx);
+EO_API eo_status eo_selftest_wait_timeout(eo_ctx* ctx, double seconds);
 
 /*
  * Gram product G = X^T Y (kx-by-ky), the matrix-matrix product that carries

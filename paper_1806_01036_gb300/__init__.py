@@ -55,6 +55,10 @@ def lib():
         L.eo_version.restype = _int
         L.eo_kernel_launches.argtypes = [_p]
         L.eo_kernel_launches.restype = C.c_uint64
+        L.eo_device_status.argtypes = [_p]
+        L.eo_device_status.restype = _int
+        L.eo_selftest_wait_timeout.argtypes = [_p, _dbl]
+        L.eo_selftest_wait_timeout.restype = _int
         L.eo_create.argtypes = [C.POINTER(_p), _int]
         L.eo_destroy.argtypes = [_p]
         L.eo_set_stream.argtypes = [_p, _p]
@@ -186,6 +190,15 @@ class Context:
         import torch
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         lib().eo_set_stream(self.h, C.c_void_p(s.cuda_stream))
+
+    def device_status(self) -> int:
+        """EO_OK, or EO_ETIMEOUT if a bounded device-side wait ran out since the
+        last call (waits for the context's stream; clears the record)."""
+        return int(lib().eo_device_status(self.h))
+
+    def selftest_wait_timeout(self, seconds: float = 0.05):
+        """Launch the one-thread kernel whose bounded wait runs out after `seconds`."""
+        self.check(lib().eo_selftest_wait_timeout(self.h, float(seconds)))
 
     def launches(self) -> int:
         """Kernels this context has launched (eo_kernel_launches)."""

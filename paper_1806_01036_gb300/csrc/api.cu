@@ -318,6 +318,31 @@ const char* eo_last_error(const eo_ctx* ctx) { return ctx ? ctx->err.c_str() : "
 
 uint64_t eo_kernel_launches(const eo_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+eo_status eo_device_status(eo_ctx* ctx) {
+  if (!ctx) return EO_EINVAL;
+  ctx->err.clear();
+  DeviceGuard g(ctx->device);
+  EO_CHECK(g.ok, EO_ECUDA, "eo_device_status: cannot select device%s", "");
+  EO_CUDA(cudaStreamSynchronize(ctx->stream), "eo_device_status (sync)");
+  unsigned a = 0, b = 0;
+  EO_CUDA(umma_gram_take_wait_record(&a), "eo_device_status (Gram record)");
+  EO_CUDA(umma_rowprod_take_wait_record(&b), "eo_device_status (row-product record)");
+  if (a || b) return fail(ctx, EO_ETIMEOUT, "a bounded device-side wait ran out%s (%lld): its outputs are NaN", "",
+                          (long long)((a ? 1 : 0) | (b ? 2 : 0)));
+  return EO_OK;
+}
+
+eo_status eo_selftest_wait_timeout(eo_ctx* ctx, double seconds) {
+  if (!ctx) return EO_EINVAL;
+  ctx->err.clear();
+  EO_CHECK(seconds > 0.0 && seconds <= 2.0, EO_EINVAL, "eo_selftest_wait_timeout: seconds must be in (0, 2]%s", "");
+  DeviceGuard g(ctx->device);
+  EO_CHECK(g.ok, EO_ECUDA, "eo_selftest_wait_timeout: cannot select device%s", "");
+  EO_CUDA(umma_wait_selftest((unsigned long long)(seconds * 1e9), ctx->stream), "eo_selftest_wait_timeout");
+  ctx->launches += 1;
+  return EO_OK;
+}
+
 eo_status eo_gram(eo_ctx* ctx, int64_t n, int kx, const void* X, int64_t ldx, int ky, const void* Y, int64_t ldy,
                   double* G_hi, double* G_lo, int ldg, eo_prec prec) {
   if (!ctx) return EO_EINVAL;

@@ -117,6 +117,12 @@ cudaError_t launch_fx_gram(int64_t n, int kx, const double* X, int64_t ldx, int 
 // kin <= 64, kout <= 16 (umma_rowprod_supported); Out may be A (in place).
 // ctas > 0 caps the CTAs of the launch (0 = one per SM).
 bool umma_rowprod_supported(int kin, int kout);
+// Bounded device-side waits that ran out (tensor-core kernels): each unit's
+// record, read and cleared (synchronous); and a one-thread kernel whose wait
+// on an mbarrier that nothing completes runs out after limit_ns.
+cudaError_t umma_gram_take_wait_record(unsigned* out);
+cudaError_t umma_rowprod_take_wait_record(unsigned* out);
+cudaError_t umma_wait_selftest(unsigned long long limit_ns, cudaStream_t st);
 cudaError_t launch_umma_rowprod(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout,
                                 const double* Bh, const double* Bl, int ldb, bool tri, const double* Yin,
                                 int64_t ldyin, double* Out, int64_t ldo, const int* gate, cudaStream_t st,

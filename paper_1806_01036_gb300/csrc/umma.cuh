@@ -52,14 +52,23 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
+// Set to 1 by a bounded wait that ran out; the host reads and clears it
+// (eo_device_status).  Every translation unit that includes this file has
+// its own copy, read through that unit's take_wait_record.
+static __device__ unsigned g_wait_expired = 0u;
+
 // Wait for the phase of the given parity to complete.  Gives up (false) once
-// *abort is set or after kWaitNs, and then sets *abort so that every other
-// wait of the CTA gives up at once.
-static __device__ __noinline__ bool mbar_wait(unsigned bar, unsigned parity, volatile int* abort) {
+// *abort is set or after limit_ns, and then sets *abort so that every other
+// wait of the CTA gives up at once; a wait that ran out records it in
+// g_wait_expired.
+static __device__ __noinline__ bool mbar_wait(unsigned bar, unsigned parity, volatile int* abort,
+                                              unsigned long long limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
   while (!mbar_try_wait(bar, parity)) {
-    if (*abort || gtimer() - t0 > kWaitNs) {
+    const bool late = gtimer() - t0 > limit_ns;
+    if (*abort || late) {
+      if (late) atomicExch(&g_wait_expired, 1u);
       *abort = 1;
       return false;
     }
@@ -72,11 +81,20 @@ static __device__ __noinline__ bool mbar_wait_final(unsigned bar, unsigned parit
   const unsigned long long t0 = gtimer();
   while (!mbar_try_wait(bar, parity)) {
     if (gtimer() - t0 > kWaitNs) {
+      atomicExch(&g_wait_expired, 1u);
       *abort = 1;
       return false;
     }
   }
   return true;
+}
+
+// Host side: copy this unit's record to *out (synchronous) and clear it.
+static inline cudaError_t take_wait_record(unsigned* out) {
+  cudaError_t e = cudaMemcpyFromSymbol(out, g_wait_expired, sizeof(unsigned), 0, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  const unsigned zero = 0u;
+  return *out ? cudaMemcpyToSymbol(g_wait_expired, &zero, sizeof(unsigned), 0, cudaMemcpyHostToDevice) : e;
 }
 __device__ __forceinline__ void mbar_arrive(unsigned bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -350,8 +368,15 @@ __device__ __forceinline__ PairLanes pair_lanes(const unsigned (&a)[4], const un
 template <int S>
 __device__ __forceinline__ unsigned pair_word(const PairLanes& p, unsigned signs) {
   constexpr int q = 98 - 7 * S, k = q >> 4, o = q & 15;
-  if constexpr (o <= 9) return ((p.Z[k] >> o) & 0x007f007fu) | signs;
-  else return ((p.Z8[k] >> (o - 8)) & 0x007f007fu) | signs;
+  constexpr bool low = o <= 9;
+  constexpr int sh = low ? o : o - 8;
+  const unsigned z = low ? p.Z[k] : p.Z8[k];
+  // the shift as a high-half multiplication (the FMA pipe), then one
+  // three-input logic operation (z & 0x007f007f) | signs (the ALU)
+  unsigned zs = z, w;
+  if constexpr (sh > 0) asm("mul.hi.u32 %0, %1, %2;" : "=r"(zs) : "r"(z), "n"(1u << (32 - sh)));
+  asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(w) : "r"(zs), "n"(0x007f007fu), "r"(signs));
+  return w;
 }
 // The 15 digit words of two consecutive rows (low half: row r, high half:
 // row r + 1) into their slabs, slab s at dst + s * stride.

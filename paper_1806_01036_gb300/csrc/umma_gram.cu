@@ -68,11 +68,14 @@ namespace {
 using namespace fx;
 using namespace umma;
 
-constexpr int kConvWarps = 16;                // staging, conversion and drains
+#ifndef EO_GRAM_CONV_WARPS
+#define EO_GRAM_CONV_WARPS 16
+#endif
+constexpr int kConvWarps = EO_GRAM_CONV_WARPS;  // staging, conversion and drains (8 or 16)
 constexpr int kConvThreads = 32 * kConvWarps;
 constexpr int kThreads = kConvThreads + 32;  // plus one MMA-issuing warp
 constexpr int kLanes = 128;   // MMA M = TMEM lanes
-constexpr int kMaxItems = 3;  // items (two rows of one column) per thread and panel
+constexpr int kMaxItems = 48 / kConvWarps;  // items (two rows of one column) per thread and panel
 constexpr int kOffsetDigits = 2148;
 constexpr int kFoldRows = 8192;  // rows between folds of the 32-bit running sums
 constexpr size_t kSmemCap = 225 * 1024;
@@ -118,7 +121,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                              const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
                              FxPart* __restrict__ parts, const int* gate) {
   if (gate && *gate == 0) return;
-  constexpr int NY = KYP / 4;  // Y columns of one converter thread in a drain
+  // Y columns of one converter thread in a drain (four warps share a TMEM
+  // lane quarter), handled NH times NY at a time
+  constexpr int NYT = KYP * 4 / kConvWarps;
+  constexpr int NY = NYT < 4 ? NYT : 4;
+  constexpr int NH = NYT / NY;
   const int kxp = pl.kxp, P = pl.P, nslots = pl.nslots;
   const int tx = blockIdx.x / pl.nty, ty = blockIdx.x % pl.nty;
   const int x0 = tx * kxp, y0 = ty * KYP;  // first X / Y column of the tile
@@ -194,10 +201,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   // the partial sums of this thread's lane: lane block jl (digit phase), X column xl
   const int Lq = (warp & 3) * 32, L = Lq + lane;
   const int jl = L >> (31 - __clz(kxp)), xl = L & (kxp - 1);
-  const int yq = (warp >> 2) * NY;  // first of this thread's NY Y columns
-  i128 W[NY];
+  const int yq = (warp >> 2) * NYT;  // first of this thread's NYT Y columns
+  i128 W[NYT];
 #pragma unroll
-  for (int y = 0; y < NY; ++y) W[y] = 0;
+  for (int y = 0; y < NYT; ++y) W[y] = 0;
 
   if (warp == kConvWarps) {
     // ---------------- MMA issuer
@@ -237,10 +244,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int y = 0; y < NY; ++y) z[u][y] = 0u;
 #pragma unroll
-      for (int c0 = 0; c0 < NS; c0 += 3) {
-        tmem_st3<NY>(tsum + c0 * KYP, tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, z);
-        tmem_st3<NY>(tacc + c0 * KYP, tacc + (c0 + 1) * KYP, tacc + (c0 + 2) * KYP, z);
-      }
+      for (int hh = 0; hh < NH; ++hh)
+#pragma unroll
+        for (int c0 = 0; c0 < NS; c0 += 3) {
+          const unsigned ts = tsum + 4u * hh, ta = tacc + 4u * hh;
+          tmem_st3<NY>(ts + c0 * KYP, ts + (c0 + 1) * KYP, ts + (c0 + 2) * KYP, z);
+          tmem_st3<NY>(ta + c0 * KYP, ta + (c0 + 1) * KYP, ta + (c0 + 2) * KYP, z);
+        }
       tmem_wait_st();
     }
 
@@ -250,9 +260,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     // power of two no shorter than that of any later group); a drained
     // group's accumulators are set back to zero.  The loads of the next group
     // are in flight while a group is added.
+    unsigned tacc_h = tacc, tsum_h = tsum;  // the NY columns being drained
     auto load = [&](int c0, unsigned (&v)[3][NY], unsigned (&sm)[3][NY]) {
-      tmem_ld3x2_nowait<NY>(tacc + c0 * KYP, tacc + (c0 + 1) * KYP, tacc + (c0 + 2) * KYP, tsum + c0 * KYP,
-                            tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, v, sm);
+      tmem_ld3x2_nowait<NY>(tacc_h + c0 * KYP, tacc_h + (c0 + 1) * KYP, tacc_h + (c0 + 2) * KYP, tsum_h + c0 * KYP,
+                            tsum_h + (c0 + 1) * KYP, tsum_h + (c0 + 2) * KYP, v, sm);
     };
     auto add_store = [&](int c0, unsigned (&v)[3][NY], unsigned (&sm)[3][NY]) {
       // (column blocks with c + jl > 14 collect no kept diagonal: the fold skips them)
@@ -260,8 +271,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int u = 0; u < 3; ++u)
 #pragma unroll
         for (int y = 0; y < NY; ++y) sm[u][y] += (unsigned)__float2int_rn(__uint_as_float(v[u][y]));
-      tmem_st3<NY>(tsum + c0 * KYP, tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, sm);
-      tmem_zero3<NY>(tacc + c0 * KYP, tacc + (c0 + 1) * KYP, tacc + (c0 + 2) * KYP);
+      tmem_st3<NY>(tsum_h + c0 * KYP, tsum_h + (c0 + 1) * KYP, tsum_h + (c0 + 2) * KYP, sm);
+      tmem_zero3<NY>(tacc_h + c0 * KYP, tacc_h + (c0 + 1) * KYP, tacc_h + (c0 + 2) * KYP);
     };
     auto drain_from = [&](auto g0) {
       constexpr int G0 = decltype(g0)::value;
@@ -292,41 +303,50 @@ __global__ void __launch_bounds__(kThreads, 1)
       tmem_wait_st();
     };
     auto drain = [&](int g0) {
-      switch (g0) {
-        case 0: drain_from(std::integral_constant<int, 0>{}); break;
-        case 1: drain_from(std::integral_constant<int, 1>{}); break;
-        case 2: drain_from(std::integral_constant<int, 2>{}); break;
-        case 3: drain_from(std::integral_constant<int, 3>{}); break;
-        case 4: drain_from(std::integral_constant<int, 4>{}); break;
-        default: break;  // no group due
+#pragma unroll
+      for (int hh = 0; hh < NH; ++hh) {
+        tacc_h = tacc + 4u * hh;
+        tsum_h = tsum + 4u * hh;
+        switch (g0) {
+          case 0: drain_from(std::integral_constant<int, 0>{}); break;
+          case 1: drain_from(std::integral_constant<int, 1>{}); break;
+          case 2: drain_from(std::integral_constant<int, 2>{}); break;
+          case 3: drain_from(std::integral_constant<int, 3>{}); break;
+          case 4: drain_from(std::integral_constant<int, 4>{}); break;
+          default: break;  // no group due
+        }
       }
     };
     auto fold = [&]() {  // running sums -> W (units 2^(Ax + Ay - 2148)), sums back to zero
-      i128 h[NY];
 #pragma unroll
-      for (int y = 0; y < NY; ++y) h[y] = 0;
+      for (int hh = 0; hh < NH; ++hh) {
+        const unsigned ts = tsum + 4u * hh;
+        i128 h[NY];
 #pragma unroll
-      for (int c0 = 0; c0 < NS; c0 += 3) {
-        unsigned sm[3][NY];
-        tmem_ld3<NY>(tsum + c0 * KYP, tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, sm);
+        for (int y = 0; y < NY; ++y) h[y] = 0;
 #pragma unroll
-        for (int u = 0; u < 3; ++u)
+        for (int c0 = 0; c0 < NS; c0 += 3) {
+          unsigned sm[3][NY];
+          tmem_ld3<NY>(ts + c0 * KYP, ts + (c0 + 1) * KYP, ts + (c0 + 2) * KYP, sm);
 #pragma unroll
-          for (int y = 0; y < NY; ++y)
-            if (c0 + u + jl <= 14) h[y] = (h[y] << 7) + (i128)(int)sm[u][y];
+          for (int u = 0; u < 3; ++u)
 #pragma unroll
-        for (int u = 0; u < 3; ++u)
+            for (int y = 0; y < NY; ++y)
+              if (c0 + u + jl <= 14) h[y] = (h[y] << 7) + (i128)(int)sm[u][y];
 #pragma unroll
-          for (int y = 0; y < NY; ++y) sm[u][y] = 0u;
-        tmem_st3<NY>(tsum + c0 * KYP, tsum + (c0 + 1) * KYP, tsum + (c0 + 2) * KYP, sm);
+          for (int u = 0; u < 3; ++u)
+#pragma unroll
+            for (int y = 0; y < NY; ++y) sm[u][y] = 0u;
+          tmem_st3<NY>(ts + c0 * KYP, ts + (c0 + 1) * KYP, ts + (c0 + 2) * KYP, sm);
+        }
+        tmem_wait_st();
+#pragma unroll
+        for (int y = 0; y < NY; ++y) W[hh * NY + y] += h[y] >> 8;
       }
-      tmem_wait_st();
-#pragma unroll
-      for (int y = 0; y < NY; ++y) W[y] += h[y] >> 8;
     };
 
     // This thread's items (two rows of one column) of every panel: i = tid +
-    // k * 512.  Within a warp, lanes l, l ^ 8, l ^ 16, l ^ 24 share a column,
+    // k * kConvThreads.  Within a warp, lanes l, l ^ 8, l ^ 16, l ^ 24 share a column,
     // the eight columns of a quarter warp read distinct 16-byte chunks of the
     // swizzled boxes, and the 32 digit words a warp stores per slab fill 128
     // contiguous bytes.  it_s: column << 16 | staging offset / 16; it_d:
@@ -532,7 +552,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (grew) {  // totals onto the new grid: divide by 2^(growth of both columns' exponents)
           const int ysb = pl.shared ? 0 : kxp;
 #pragma unroll
-          for (int y = 0; y < NY; ++y) {
+          for (int y = 0; y < NYT; ++y) {
             const int cx = xl, cy = ysb + yq + y;
             const int dx = eprev[cx] ? max(eprev[cx], pcur[cx]) - eprev[cx] : 0;
             const int dy = eprev[cy] ? max(eprev[cy], pcur[cy]) - eprev[cy] : 0;
@@ -585,7 +605,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   i128* red = reinterpret_cast<i128*>(dig);  // 128 lanes x KYP entries (the MMAs are done)
   if (warp < kConvWarps) {
 #pragma unroll
-    for (int y = 0; y < NY; ++y) red[L * KYP + yq + y] = W[y];
+    for (int y = 0; y < NYT; ++y) red[L * KYP + yq + y] = W[y];
   }
   __syncthreads();
   const int J = pl.J;
@@ -748,7 +768,27 @@ cudaError_t launch_kernel(const UPlan& plan, int chunks, int64_t n, int kx, cons
   return cudaGetLastError();
 }
 
+// One thread waits for a phase of an mbarrier that nothing completes, bounded
+// by limit_ns: the bounded-wait path of the tensor-core kernels, exercised on
+// its own (it records the expiry like any other wait that runs out).
+__global__ void wait_selftest_kernel(unsigned long long limit_ns) {
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x != 0) return;
+  abort_flag = 0;
+  mbar_init(smem_u32(&bar), 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  (void)mbar_wait(smem_u32(&bar), 0u, &abort_flag, limit_ns);
+}
+
 }  // namespace
+
+cudaError_t umma_wait_selftest(unsigned long long limit_ns, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns);
+  return cudaGetLastError();
+}
+
+cudaError_t umma_gram_take_wait_record(unsigned* out) { return take_wait_record(out); }
 
 size_t umma_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym) {
   if (sym) ky = kx;

@@ -419,14 +419,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int k = 0; k < W; ++k) v[k] = vn[k];
       }
-      // the row's exponent: max of |x| bit patterns over the four threads of the row
+      // the row's exponent: max of the |x| high words over the four threads
+      // of the row (a row of subnormals and zeros has exponent field 0 and
+      // is aligned to 1, the subnormals' own exponent)
       unsigned key = 0;
 #pragma unroll
-      for (int k = 0; k < W; ++k) key = max(key, (hi32(v[k]) & 0x7fffffffu) | min(lo32(v[k]), 1u));
+      for (int k = 0; k < W; ++k) key = max(key, hi32(v[k]) & 0x7fffffffu);
       key = max(key, __shfl_xor_sync(0xffffffffu, key, 8));
       key = max(key, __shfl_xor_sync(0xffffffffu, key, 16));
-      int e = (int)(key >> 20);
-      if (e == 0 && key) e = 1;  // subnormal
+      const int e = (int)(key >> 20);
       const int Ar = max(e, 1);
       if (cg == 0) {
         Arow[(i & 1) * kRows + r] = Ar;
@@ -508,6 +509,8 @@ cudaError_t launch_w(bool update, int64_t n, int kin, const double* A, int64_t l
 }
 
 }  // namespace
+
+cudaError_t umma_rowprod_take_wait_record(unsigned* out) { return take_wait_record(out); }
 
 bool umma_rowprod_supported(int kin, int kout) {
   const char* e = getenv("EO_DD_ROW_ENGINE");
