@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU-oracle sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-comparators", action="store_true",
+                    help="skip the FP64, DD-EFT, same-accuracy and single-block comparisons (profiling runs)")
     ap.add_argument("--workload", choices=["project", "iterated", "batched", "serve", "sweep", "single"],
                     default="project",
                     help="project: the default line; iterated: the iterated two-phase algorithm on the "
@@ -65,6 +67,10 @@ def parse():
     ap.add_argument("--budget-gb", type=float, default=150.0, help="device-memory budget of the server")
     ap.add_argument("--branches", type=int, default=0, help="graph branches of the batched workload (0 = auto)")
     return ap.parse_args()
+
+
+class _Skip(Exception):
+    """A comparison left out on request."""
 
 
 def max_over_ranks(x, device):
@@ -222,11 +228,11 @@ DIGIT_PAIRS = 120  # FP16 digit-pair products per multiply-add of the compensate
 def gram_traffic(n, kv, k):
     """DRAM bytes of one V^T Y launch of the tensor-core Gram kernel, from one
     ncu capture at n = 1e6, kv = 64, k = 16 (dram__bytes_read.sum 640.1 MB,
-    dram__bytes_write.sum 3.5 MB of row-chunk partials); reads scale with
+    dram__bytes_write.sum 3.65 MB of row-chunk partials); reads scale with
     the rows, the partials do not.  None for other shapes."""
     if (kv, k) != (64, 16):
         return None
-    return 640.127488e6 * n / 1e6 + 3.512576e6
+    return 640.143104e6 * n / 1e6 + 3.650048e6
 
 
 def peak_tensor():
@@ -386,24 +392,33 @@ def run_eo(a):
     reps = max(20, a.steps)
     # plain FP64 CholQR2 and the paper's FP64-pipe compensated kernels on the same input
     Yp = torch.empty_like(Yt.t()).t()
-    comp, eft = {}, {}
+    comp, eft, same, single = {}, {}, {}, {}
     try:
+        if a.no_comparators:
+            raise _Skip()
         ts, (_, _, infop) = timed_steps(lambda: step(prec=eo.FP64, out=Yp, passes=2), reps)
         comp = dict(summary(ts, step_bytes(n, kv, k, True)), prec="fp64 CholQR2", cholesky_info=int(infop.item()),
                     orth_err=dd_orth(Yp))
+    except _Skip:
+        comp = {"skipped": "--no-comparators"}
     except Exception as ex:  # pragma: no cover - reporting only
         comp = {"error": str(ex)}
     try:
+        if a.no_comparators:
+            raise _Skip()
         ts, (_, _, infoe) = timed_steps(lambda: step(prec=eo.DD_EFT, out=Yp, passes=0), max(5, reps // 4), warm=1)
         eft = dict(summary(ts, nbytes), prec="dd_eft (FP64-pipe TwoProd/TwoSum)", cholesky_info=int(infoe.item()),
                    orth_err=dd_orth(Yp))
+    except _Skip:
+        eft = {"skipped": "--no-comparators"}
     except Exception as ex:  # pragma: no cover - reporting only
         eft = {"error": str(ex)}
 
     # same accuracy, more blocks/s: where plain FP64 CholQR2 succeeds (kappa = 1e6) the compensated step
     # needs one CholQR pass; both are timed on the same V and a Y with kappa(Y) = 1e6
-    same = {}
     try:
+        if a.no_comparators:
+            raise _Skip()
         y6 = synth.conditioned(n, k, 1e6, synth.SEED_BASE + 2 + 1000 * rank)
         Ys6 = Y
         Y = to_dev(y6)
@@ -423,11 +438,14 @@ def run_eo(a):
                                      orth_err=orth_646)}
         same["dd_speedup_blocks_per_s"] = same["dd"]["blocks_per_s"] / same["fp64_cholqr2"]["blocks_per_s"]
         Y = Ys6
+    except _Skip:
+        same = {"skipped": "--no-comparators"}
     except Exception as ex:  # pragma: no cover - reporting only
         same = {"error": str(ex)}
     # the single-block configuration (100,000 x 8, sigma 1 .. 1e-6, L2-resident): CholQR alone
-    single = {}
     try:
+        if a.no_comparators:
+            raise _Skip()
         xs = synth.single_cholqr()
         X0s = to_dev(xs)
         Xs = torch.empty_like(X0s.t()).t()
@@ -444,6 +462,8 @@ def run_eo(a):
                          "note": "includes the device copy restoring X (0.8 MB)"}
         single = {"workload": "single CholQR, X 100,000 x 8, sigma 1 .. 1e-6 (L2-resident)", **res}
         del X0s, Xs
+    except _Skip:
+        single = {"skipped": "--no-comparators"}
     except Exception as ex:  # pragma: no cover - reporting only
         single = {"error": str(ex)}
     del Yp

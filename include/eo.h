@@ -130,13 +130,15 @@ EO_API eo_status eo_gram(eo_ctx* ctx, int64_t n, int kx, const void* X, int64_t 
 
 /*
  * Phase I projection against an orthonormal basis V (Sec. 4.2:
- * Y~ = (I - W W^T) X), with the phase-II Gram matrix of the result fused into
- * the same pass over the data (the paper fuses these two kernels).
+ * Y~ = (I - W W^T) X), optionally with the phase-II Gram matrix of the result.
  *   V: n-by-kv, Y: n-by-k (FP64).  C = V^T Y is written to C_hi/C_lo (kv-by-k,
  *   ldc; C_hi may be NULL).  Yout (n-by-k, ldyo) receives Y - V C, rounded
  *   once to FP64; Yout may equal Y (in place) but must not otherwise overlap
  *   it.  If M_hi != NULL, M = Yout^T Yout of the rounded result (k-by-k, ldm)
- *   is accumulated in the same pass.
+ *   is computed too: in EO_FP64 and EO_DD_EFT in the same pass over the data
+ *   as the projection (the paper fuses these two kernels), in EO_DD by a
+ *   second tensor-core Gram pass over Yout (the exact fused form does not fit
+ *   one SM's tensor memory next to the projection's accumulators).
  * EO_F32 is not supported (EO_EUNSUPPORTED).
  */
 EO_API eo_status eo_project(eo_ctx* ctx, int64_t n, int kv, const double* V, int64_t ldv, int k, const double* Y,
