@@ -87,6 +87,8 @@ def lib():
             L.eoq_orthogonalize.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64, _dbl, _int, _dbl, _p]
             L.eoq_orthogonalize.restype = _int
             L.eoq_set_threads.argtypes = [_int]
+            L.eoq_cholqr_piv.argtypes = [_i64, _int, _p, _i64, _dbl, _int, _p, _p, _p, _p, _int]
+            L.eoq_cholqr_piv.restype = _int
             L.eo64_gram.argtypes = [_int, _i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int]
             L.eo64_project.argtypes = [_int, _i64, _int, _p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _p, _p,
                                        _int]
@@ -319,6 +321,22 @@ def fact_err(x, q, r_hi, r_lo=None):
     r_lo = None if r_lo is None else _f64(r_lo)
     n, k = x.shape
     return float(lib().eoq_fact_err(n, k, _ptr(x), n, _ptr(q), n, _ptr(r_hi), _ptr(r_lo), k))
+
+
+def cholqr_piv(x, tol=0.0, passes=1):
+    """(Q, perm, rank, (R_hi, R_lo), info): CholQR with a diagonally pivoted
+    Cholesky stopped at the numerical rank (pivots whose remaining diagonal
+    is not above tol * max_i M_ii are dropped), Q's columns beyond the rank
+    zero, X[:, perm] ~ Q R; an unpivoted second pass on the kept columns when
+    passes = 2.  binary128."""
+    q = _f64(x).copy(order="F")
+    n, k = q.shape
+    perm = np.zeros(k, dtype=np.int32)
+    rank = C.c_int(0)
+    r_hi, r_lo = _sq(k)
+    info = lib().eoq_cholqr_piv(n, k, _ptr(q), n, float(tol), int(passes), perm.ctypes.data, C.byref(rank),
+                                _ptr(r_hi), _ptr(r_lo), k)
+    return q, perm, int(rank.value), (r_hi, r_lo), int(info)
 
 
 def orthogonalize(w, x, eps=1e-10, max_iter=8, tol=0.0):

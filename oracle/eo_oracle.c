@@ -24,6 +24,9 @@
  *                  Z = U Lambda^{-1/2} U^T = M^{-1/2}                 (Sec. 4.2, SVQB with the
  *                                                                      Frobenius-optimal Z of the
  *                                                                      Procrustes argument)
+ *   eoq_cholqr_piv CholQR with a diagonally pivoted Cholesky stopped at the
+ *                  numerical rank, then an unpivoted second pass          (Sec. 4.2, the pivoted, partial
+ *                                                                      Cholesky of phase II)
  *   eoq_orthogonalize  phase I, the measures max(||W^T Y||_F, ||Y^T Y - I||_F),
  *                  then SVQB, repeated until the measures are <= eps      (Sec. 4.2, iterated two-phase
  *                                                                      algorithm; runtime figure)
@@ -435,6 +438,114 @@ int eoq_svqb(int64_t n, int k, double* X, int64_t ldx, const double* M_hi, const
   if (Z_hi) store_dd(k, Zt, Z_hi, Z_lo, ldz);
   free(M); free(Z); free(Zt); free(T);
   return rank;
+}
+
+/* --------------------------------------- pivoted, partial Cholesky QR */
+
+/* Cholesky with diagonal pivoting, stopped early (Sec. 4.2 allows the
+ * phase-II Cholesky factorization to be pivoted and partial, which makes it
+ * rank-revealing).  On the symmetric M (k-by-k, binary128), step j takes
+ * the largest remaining diagonal entry (lowest index on ties) as pivot p,
+ * swaps rows and columns j and p, and stops with rank j when that entry is
+ * not above tol * (largest diagonal entry of M); otherwise R(j,j) =
+ * sqrt(pivot), R(j,l) = A(j,l) / R(j,j) and the trailing matrix loses the
+ * outer product of row j of R.  perm[j] is the original index of the j-th
+ * pivot; R (k-by-k, rows >= rank zero) satisfies P^T M P ~ R^T R on the
+ * leading rank columns.  Returns the rank. */
+static int q_pivchol(int k, const qreal* M, qreal tol, int* perm, qreal* R) {
+  qreal* A = qalloc((size_t)k * k);
+  memcpy(A, M, sizeof(qreal) * (size_t)k * k);
+  for (size_t t = 0; t < (size_t)k * k; ++t) R[t] = 0;
+  for (int i = 0; i < k; ++i) perm[i] = i;
+  qreal dmax = 0;
+  for (int i = 0; i < k; ++i) if (A[(size_t)i * k + i] > dmax) dmax = A[(size_t)i * k + i];
+  int rank = 0;
+  for (int j = 0; j < k; ++j) {
+    int p = j;
+    for (int i = j + 1; i < k; ++i) if (A[(size_t)i * k + i] > A[(size_t)p * k + p]) p = i;
+    const qreal d = A[(size_t)p * k + p];
+    if (!(d > 0) || !(d > tol * dmax)) break;
+    if (p != j) {  /* symmetric swap of rows and columns j and p; also the rows of R built so far */
+      for (int i = 0; i < k; ++i) {
+        qreal t = A[(size_t)j * k + i]; A[(size_t)j * k + i] = A[(size_t)p * k + i]; A[(size_t)p * k + i] = t;
+      }
+      for (int i = 0; i < k; ++i) {
+        qreal t = A[(size_t)i * k + j]; A[(size_t)i * k + j] = A[(size_t)i * k + p]; A[(size_t)i * k + p] = t;
+      }
+      for (int i = 0; i < j; ++i) {
+        qreal t = R[(size_t)j * k + i]; R[(size_t)j * k + i] = R[(size_t)p * k + i]; R[(size_t)p * k + i] = t;
+      }
+      int t = perm[j]; perm[j] = perm[p]; perm[p] = t;
+    }
+    const qreal rjj = qsqrt(A[(size_t)j * k + j]);
+    R[(size_t)j * k + j] = rjj;
+    for (int l = j + 1; l < k; ++l) R[(size_t)l * k + j] = A[(size_t)l * k + j] / rjj;
+    for (int a = j + 1; a < k; ++a)
+      for (int b = j + 1; b < k; ++b) A[(size_t)b * k + a] -= R[(size_t)a * k + j] * R[(size_t)b * k + j];
+    rank = j + 1;
+  }
+  free(A);
+  return rank;
+}
+
+/* Pivoted, partial CholQR: pass 1 factors M = X^T X with q_pivchol and sets
+ * X <- X P [R11^{-1}, 0; 0, 0] (R11 the leading rank-by-rank block), so the
+ * first rank columns of X are orthonormal and span X's numerical range and
+ * the others are zero; pass 2 (passes = 2) factors the leading rank-by-rank
+ * block of the new Gram matrix without pivoting, X <- X [R2^{-1}, 0; 0, 0],
+ * and R <- R2 R.  Every entry of X is summed in binary128 and rounded once
+ * per pass.  perm (k ints) and R (k-by-k, X P ~ Q R, rows >= rank zero) are
+ * those of the whole; *rank_out the rank.  Returns 0, or j >= 1 if the
+ * second pass breaks down at column j (X then holds the first pass). */
+int eoq_cholqr_piv(int64_t n, int k, double* X, int64_t ldx, double tol, int passes, int* perm, int* rank_out,
+                   double* R_hi, double* R_lo, int ldr) {
+  const size_t kk = (size_t)k * k;
+  qreal *M = qalloc(kk), *R = qalloc(kk), *Z = qalloc(kk), *Zs = qalloc(kk), *R2 = qalloc(kk), *T = qalloc(kk);
+  q_gram_sym(n, k, X, ldx, M);
+  const int r = q_pivchol(k, M, (qreal)tol, perm, R);
+  /* R11^{-1} (rank-by-rank upper triangular), placed at the pivots' rows */
+  for (int j = 0; j < r; ++j) {
+    Zs[(size_t)j * k + j] = 1 / R[(size_t)j * k + j];
+    for (int i = j - 1; i >= 0; --i) {
+      qreal s = 0;
+      for (int l = i + 1; l <= j; ++l) s += R[(size_t)l * k + i] * Zs[(size_t)j * k + l];
+      Zs[(size_t)j * k + i] = -s / R[(size_t)i * k + i];
+    }
+  }
+  for (int j = 0; j < r; ++j)
+    for (int i = 0; i < r; ++i) Z[(size_t)j * k + perm[i]] = Zs[(size_t)j * k + i];
+  q_update(n, k, X, ldx, Z);
+  int info = 0;
+  if (passes == 2 && r > 0) {
+    q_gram_sym(n, k, X, ldx, M);
+    qreal* Ml = qalloc((size_t)r * r);
+    for (int j = 0; j < r; ++j)
+      for (int i = 0; i < r; ++i) Ml[(size_t)j * r + i] = M[(size_t)j * k + i];
+    qreal *Rr = qalloc((size_t)r * r), *Zr = qalloc((size_t)r * r);
+    info = q_cholesky(r, Ml, Rr);
+    if (!info) {
+      q_triinv(r, Rr, Zr);
+      for (size_t t = 0; t < kk; ++t) Z[t] = 0;
+      for (int j = 0; j < r; ++j)
+        for (int i = 0; i < r; ++i) {
+          Z[(size_t)j * k + i] = Zr[(size_t)j * r + i];
+          R2[(size_t)j * k + i] = Rr[(size_t)j * r + i];
+        }
+      q_update(n, k, X, ldx, Z);
+      for (int j = 0; j < k; ++j) /* R <- R2 R (R2 upper rank-by-rank, R upper trapezoidal) */
+        for (int i = 0; i < k; ++i) {
+          qreal s = 0;
+          for (int l = 0; l < r; ++l) s += R2[(size_t)l * k + i] * R[(size_t)j * k + l];
+          T[(size_t)j * k + i] = i < r ? s : 0;
+        }
+      memcpy(R, T, sizeof(qreal) * kk);
+    }
+    free(Ml); free(Rr); free(Zr);
+  }
+  if (R_hi) store_dd(k, R, R_hi, R_lo, ldr);
+  if (rank_out) *rank_out = r;
+  free(M); free(R); free(Z); free(Zs); free(R2); free(T);
+  return info;
 }
 
 /* ------------------------------------------ iterated two-phase algorithm */

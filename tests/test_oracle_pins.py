@@ -724,3 +724,58 @@ def test_fp64_project_against_binary128(mode):
         assert np.all(np.abs(yt - yo) <= tol)
     mo = oracle.gram(yt)
     assert np.all(np.abs((mh - mo[0]) + (ml - mo[1])) <= (n * U64) ** (1 + mode) * (np.abs(yt).T @ np.abs(yt)))
+
+
+# ------------------------------------------- pivoted, partial CholQR
+
+def test_cholqr_piv_orthogonal_columns_closed_form():
+    # orthogonal columns with power-of-two norms: the pivots are the columns
+    # in decreasing norm (ties: lowest index), R = diag(sorted norms) and Q the
+    # normalized columns, all exact
+    u = synth.hadamard_basis(64, 5, 1601)
+    s = np.array([0.5, 8.0, 2.0, 8.0, 0.25])
+    q, perm, rank, (rh, rl), info = oracle.cholqr_piv(np.asfortranarray(u * s))
+    assert info == 0 and rank == 5
+    assert list(perm) == [1, 3, 2, 0, 4]
+    assert np.array_equal(rh, np.diag(s[perm])) and not np.any(rl)
+    assert np.array_equal(q, u[:, perm])
+
+
+def test_cholqr_piv_rank_deficient():
+    g = synth.rng(1602)
+    a, b = g.standard_normal((200, 1)), g.standard_normal((200, 1))
+    x = np.asfortranarray(np.hstack([a, b, a + b, 3.0 * b]))  # rank 2
+    q, perm, rank, (rh, rl), info = oracle.cholqr_piv(x, tol=1e-20)
+    assert info == 0 and rank == 2
+    assert not np.any(q[:, 2:])
+    assert oracle.orth_err(q[:, :2])[0] < 1e-15
+    # the kept columns span X: (I - Q Q^T) X = 0 to rounding
+    assert np.max(np.abs(x - q[:, :2] @ (q[:, :2].T @ x))) < 1e-13 * np.max(np.abs(x))
+    # the first pivot is the largest column (3b here or a + b)
+    norms = np.sum(x * x, axis=0)
+    assert perm[0] == int(np.argmax(norms))
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e8])
+def test_cholqr_piv_invariants(kappa):
+    n, k = 400, 7
+    x = synth.conditioned(n, k, kappa, 1603)
+    for passes in (1, 2):
+        q, perm, rank, (rh, rl), info = oracle.cholqr_piv(x, passes=passes)
+        assert info == 0 and rank == k and sorted(perm) == list(range(k))
+        r = rh + rl
+        # the pivoted diagonal does not increase
+        d = np.diag(rh)
+        assert np.all(d[1:] <= d[:-1] * (1 + 1e-12))
+        assert np.all(np.tril(rh, -1) == 0)
+        assert oracle.orth_err(q)[0] < 20 * U64 + kappa ** 2 * 2.0 ** -111
+        assert oracle.fact_err(np.asfortranarray(x[:, perm]), q, rh, rl) < 8 * U64 * np.sqrt(k)
+
+
+def test_cholqr_piv_drops_negligible_column():
+    u = synth.orthonormal_basis(300, 4, 1604)
+    x = np.asfortranarray(u * np.array([1.0, 1e-20, 2.0, 0.5]))
+    q, perm, rank, _, info = oracle.cholqr_piv(x, tol=1e-30)
+    assert rank == 3 and perm[3] == 1 and not np.any(q[:, 3])
+    q2, _, rank2, _, _ = oracle.cholqr_piv(x, tol=1e-50)
+    assert rank2 == 4  # below the cut it is kept
