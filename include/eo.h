@@ -174,6 +174,30 @@ EO_API eo_status eo_cholqr(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, 
                     int ldm, double* R_hi, double* R_lo, int ldr, int passes, eo_prec prec, int* info_dev);
 
 /*
+ * Pivoted, partial CholQR (Sec. 4.2: the Cholesky factorization of phase II
+ * may be pivoted and partial, which makes it rank-revealing): X <- Q in
+ * place.  Pass 1 factors M = X^T X with diagonal pivoting -- each step takes
+ * the largest remaining diagonal entry (lowest index on ties) -- and stops
+ * at the numerical rank r, when that entry is not above tol times the
+ * largest diagonal entry of M (tol < 0 selects k * 2^-104 in EO_DD,
+ * k * 2^-52 in EO_FP64 and EO_DD_EFT); then X <- X P [R11^{-1}, 0; 0, 0]:
+ * Q's first r columns are orthonormal and span X's numerical range, the
+ * others are zero.  Pass 2 (passes = 2, or passes = 0 and the pivoted
+ * diagonal ratio R_11 / R_rr above 1e7 in EO_DD, 1e4 otherwise) repeats the
+ * Cholesky on the leading r columns without pivoting.
+ *   X: n-by-k FP64, ldx.  R_hi/R_lo: optional k-by-k outputs (ldr): upper
+ *   trapezoidal, rows >= r zero, X(:, perm) = Q R up to rounding.
+ *   perm_dev: optional device int[k], the pivot order (X's column perm[j]
+ *   was factored at step j).  rank_dev: optional device int, r (-1 if M had
+ *   a NaN or Inf).  info_dev: optional device int, 0, -1 (NaN or Inf: X is
+ *   left as it was) or j >= 1 if the second pass broke down at column j (X
+ *   keeps the first pass).  EO_F32 is not supported.
+ */
+EO_API eo_status eo_cholqr_piv(eo_ctx* ctx, int64_t n, int k, double* X, int64_t ldx, double* R_hi, double* R_lo,
+                               int ldr, double tol, int passes, eo_prec prec, int* perm_dev, int* rank_dev,
+                               int* info_dev);
+
+/*
  * SVQB (Sec. 4.2: M = U Lambda U^T, Y = Y~ Z): X <- X Z in place with the
  * symmetric Z = U Lambda^{-1/2} U^T = M^{-1/2}, the solution of
  * min ||Z - I||_F subject to Z^T M Z = I (the Procrustes argument of the same

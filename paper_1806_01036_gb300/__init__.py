@@ -71,6 +71,7 @@ def lib():
         L.eo_orthogonalize.argtypes = [_p, _i64, _int, _p, _i64, _int, _p, _i64, _dbl, _int, _dbl, _int, _p, _p]
         L.eo_cholqr.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _int, _int, _p]
         L.eo_svqb.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _dbl, _int, _int, _p]
+        L.eo_cholqr_piv.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _dbl, _int, _int, _p, _p, _p]
         L.eo_gram_dd_noalloc.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int, _p]
         L.eo_cholqr_b.argtypes = [_p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _int, _int, _p]
         L.eo_svqb_b.argtypes = [_p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _dbl, _int, _int, _p]
@@ -100,7 +101,7 @@ def lib():
         L.eo_batch_branches.argtypes = [_p]
         L.eo_batch_branches.restype = _int
         for f in ("eo_create", "eo_destroy", "eo_set_stream", "eo_gram", "eo_project", "eo_project_apply",
-                  "eo_cholqr", "eo_svqb", "eo_orthogonalize", "eo_gram_dd_noalloc", "eo_tune_cache",
+                  "eo_cholqr", "eo_svqb", "eo_cholqr_piv", "eo_orthogonalize", "eo_gram_dd_noalloc", "eo_tune_cache",
                   "eo_cholqr_b", "eo_svqb_b", "eo_project_b",
                   "eo_batch_create", "eo_batch_run", "eo_batch_destroy", "eo_batch_tile", "eo_batch_passes", "eo_batch_sweeps",
                   "eo_server_create", "eo_server_destroy", "eo_server_add_basis", "eo_server_submit",
@@ -305,6 +306,22 @@ def svqb(ctx: Context, X, passes: int = 1, prec: int = DD, tol: float = -1.0, M=
                             None if ml is None else ml.data_ptr(), ldm, zh.data_ptr(), zl.data_ptr(), _ld(zh),
                             float(tol), int(passes), prec, rank.data_ptr()))
     return zh, zl, rank
+
+
+def cholqr_piv(ctx: Context, X, passes: int = 1, prec: int = DD, tol: float = -1.0):
+    """Pivoted, partial CholQR of X (in place): X <- Q with its first `rank`
+    columns orthonormal and the rest zero, X_in[:, perm] ~ Q R.  Returns
+    (R_hi, R_lo, perm, rank, info) as device tensors."""
+    import torch
+    X, n, k, ldx = _mat(X, "X", torch.float64)
+    rh, rl = _small(k, k, X.device)
+    perm = torch.zeros(k, dtype=torch.int32, device=X.device)
+    rank = torch.zeros(1, dtype=torch.int32, device=X.device)
+    info = torch.zeros(1, dtype=torch.int32, device=X.device)
+    ctx.set_stream()
+    ctx.check(lib().eo_cholqr_piv(ctx.h, n, k, X.data_ptr(), ldx, rh.data_ptr(), rl.data_ptr(), _ld(rh),
+                                  float(tol), int(passes), prec, perm.data_ptr(), rank.data_ptr(), info.data_ptr()))
+    return rh, rl, perm, rank, info
 
 
 def cholqr_b(ctx: Context, X, BX, passes: int = 1, prec: int = DD, info=None):

@@ -449,6 +449,59 @@ eo_status eo_svqb(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, const dou
                             rank_dev);
 }
 
+eo_status eo_cholqr_piv(eo_ctx* ctx, int64_t n, int k, double* X, int64_t ldx, double* R_hi, double* R_lo, int ldr,
+                        double tol, int passes, eo_prec prec, int* perm_dev, int* rank_dev, int* info_dev) {
+  if (!ctx) return EO_EINVAL;
+  ctx->err.clear();
+  EO_CHECK(valid_prec(prec), EO_EINVAL, "eo_cholqr_piv: bad precision mode%s %lld", "", (long long)prec);
+  EO_CHECK(prec != EO_F32, EO_EUNSUPPORTED, "eo_cholqr_piv: FP32 inputs are not supported%s", "");
+  EO_CHECK(n >= 0 && k >= 1 && k <= KMAX, EO_EINVAL, "eo_cholqr_piv: bad sizes%s (n=%lld)", "", (long long)n);
+  EO_CHECK(X != nullptr || n == 0, EO_EINVAL, "eo_cholqr_piv: null X%s", "");
+  EO_CHECK(ldx >= std::max<int64_t>(1, n), EO_EINVAL, "eo_cholqr_piv: ldx too small%s %lld", "", (long long)ldx);
+  EO_CHECK(!(R_hi || R_lo) || ldr >= k, EO_EINVAL, "eo_cholqr_piv: ldr too small%s %lld", "", (long long)ldr);
+  EO_CHECK(passes >= 0 && passes <= 2, EO_EINVAL, "eo_cholqr_piv: passes must be 0, 1 or 2%s (%lld)", "",
+           (long long)passes);
+  DeviceGuard g(ctx->device);
+  EO_CHECK(g.ok, EO_ECUDA, "eo_cholqr_piv: cannot select device%s", "");
+  eo_status s = ensure_scratch(ctx, orth_scratch(n, k, prec, false));
+  if (s != EO_OK) return s;
+  const bool fx = prec == EO_DD;
+  const Mode mode = pipe_mode(prec);
+  const Mode small_mode = mode == MODE_DD ? MODE_DD : MODE_FP64;
+  if (tol < 0.0) tol = k * (small_mode == MODE_DD ? 0x1p-104 : 0x1p-52);
+  DevStatus* st = status_of(ctx);
+  SmallWs* ws = ws_of(ctx);
+  const size_t parts_bytes = ctx->scratch_bytes - kOffParts;
+  EO_CUDA(launch_status_init(st, k, ctx->stream), "eo_cholqr_piv (status)");
+  ctx->launches += 1;
+  const int npass = passes == 1 ? 1 : 2;
+  for (int p = 0; p < npass; ++p) {
+    const int* run = &st->gate[2 * p];
+    if (fx)
+      EO_CUDA(launch_dd_gram(n, k, X, ldx, k, X, ldx, true, parts_of(ctx), ws->Mh, ws->Ml, KMAX, run, ctx->stream),
+              "eo_cholqr_piv (Gram)");
+    else
+      EO_CUDA(launch_gram(mode, n, k, X, ldx, k, X, ldx, true, parts_of(ctx), ws->Mh, ws->Ml, KMAX, run,
+                          ctx->stream),
+              "eo_cholqr_piv (Gram)");
+    const SmallGates gates{run, &st->gate[2 * p + 1], p + 1 < npass ? &st->gate[2 * p + 2] : nullptr};
+    EO_CUDA(launch_pivchol_small(small_mode, k, ws->Mh, ws->Ml, KMAX, ws, R_hi, R_lo, ldr, tol, st, gates, p, passes,
+                                 info_dev, rank_dev, perm_dev, ctx->stream),
+            "eo_cholqr_piv (factorization)");
+    // pass 0: Z = P [R11^{-1}, 0; 0, 0] is a full matrix; pass 1: upper triangular
+    const bool tri = p == 1;
+    if (fx)
+      EO_CUDA(launch_fx_update(n, k, X, ldx, ws->Zh, ws->Zl, tri, &st->gate[2 * p + 1], ctx->stream, 0, parts_of(ctx),
+                               parts_bytes),
+              "eo_cholqr_piv (update)");
+    else
+      EO_CUDA(launch_update(mode, n, k, X, ldx, ws->Zh, ws->Zl, tri, &st->gate[2 * p + 1], ctx->stream),
+              "eo_cholqr_piv (update)");
+    ctx->launches += kGramLaunches + 1 + (fx ? fx_update_launches(n, k, parts_bytes) : 1);
+  }
+  return EO_OK;
+}
+
 eo_status eo_cholqr_b(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, void* BX, int64_t ldbx, double* R_hi,
                       double* R_lo, int ldr, int passes, eo_prec prec, int* info_dev) {
   if (!ctx) return EO_EINVAL;

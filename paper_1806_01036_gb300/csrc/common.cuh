@@ -41,6 +41,7 @@ struct DevStatus {
   int iters;
   int sweeps;  // Jacobi sweeps of the last SVQB eigensolve (0: none ran)
   int gate[64];
+  int perm[64];  // pivot order of a pivoted Cholesky (eo_cholqr_piv)
 };
 
 // Gate layout of eo_orthogonalize (iteration i < kMaxIter): the projection,
@@ -168,6 +169,17 @@ cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* 
 cudaError_t launch_svqb_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
                               double* Z_hi, double* Z_lo, int ldz, double tol, DevStatus* s, SmallGates g, int pass,
                               int passes, int* rank_user, cudaStream_t st);
+// Pivoted, partial Cholesky of the pass's Gram matrix (one CTA): pass 0
+// pivots on the largest remaining diagonal entry and stops at the numerical
+// rank (remaining diagonal not above tol * the largest diagonal of M),
+// Z = P [R11^{-1}, 0; 0, 0] (ws->Z) and R (ws->T); pass 1 factors the
+// leading rank-by-rank block without pivoting, Z = [R2^{-1}, 0; 0, 0],
+// R <- R2 R.  Rank and pivots go to the status (and the optional user
+// outputs); info = -1 for a NaN or Inf, j >= 1 for a breakdown of pass 1.
+cudaError_t launch_pivchol_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
+                                 double* R_hi, double* R_lo, int ldr, double tol, DevStatus* s, SmallGates g,
+                                 int pass, int passes, int* info_user, int* rank_user, int* perm_user,
+                                 cudaStream_t st);
 // Many independent factorizations in one launch (one CTA per job): the
 // Gram matrix of job j is in jobs[j].ws->Mh/Ml (leading dimension KMAX) and
 // its gates in jobs[j].st (pass p as in the single launches); tol < 0 is

@@ -246,6 +246,179 @@ __device__ __forceinline__ void chol_small_body(int k, const double* Mh, const d
   }
 }
 
+// ----------------------------------------- pivoted, partial Cholesky
+
+// One CTA.  A, R and the inverse of R11 in shared memory (double-double in
+// EO_DD, FP64 otherwise); see launch_pivchol_small.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads)
+    pivchol_small_kernel(int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws, double* Rh_u,
+                         double* Rl_u, int ldr, double tol, DevStatus* st, SmallGates g, int pass, int passes,
+                         double thr, int* info_user, int* rank_user, int* perm_user) {
+  using A_ = Ar<MODE>;
+  if (*g.run == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  dd* A = reinterpret_cast<dd*>(smem_raw);  // A(i,j) = A[j*k+i], the trailing matrix
+  dd* R = A + k * k;                        // R(i,j) = R[j*k+i]
+  dd* Zs = R + k * k;                       // R11^{-1}
+  __shared__ int flag, piv, stop, perm_s[KMAX];
+  __shared__ dd rinv;
+  const int tid = threadIdx.x;
+  const int lim = pass == 0 ? k : st->rank;  // columns that may be factored
+  if (tid == 0) {
+    flag = 0;
+    stop = lim;
+  }
+  for (int i = tid; i < k; i += kThreads) perm_s[i] = pass == 0 ? i : st->perm[i];
+  __syncthreads();
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    const int a = min(i, j), b = max(i, j);
+    dd v = dd{Mh[(size_t)b * ldm + a], Ml ? Ml[(size_t)b * ldm + a] : 0.0};
+    if (MODE != MODE_DD) v.lo = 0.0;
+    if (!dd_finite(v)) atomicExch(&flag, -1);
+    A[t] = v;
+    R[t] = dd{0.0, 0.0};
+    Zs[t] = dd{0.0, 0.0};
+  }
+  __syncthreads();
+  double dmax = 0.0;
+  for (int i = 0; i < k; ++i) dmax = fmax(dmax, A[i * k + i].hi);
+  const double cut = tol * dmax;
+  int r = 0;
+  if (flag == 0) {
+    for (int j = 0; j < lim; ++j) {
+      if (tid == 0) {
+        int p = j;
+        if (pass == 0)  // the largest remaining diagonal entry, lowest index on ties
+          for (int i = j + 1; i < k; ++i) {
+            const dd a = A[i * k + i], b = A[p * k + p];
+            if (a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo)) p = i;
+          }
+        const dd d = A[p * k + p];
+        if (pass == 0 ? !(d.hi > 0.0 && d.hi > cut) : !(d.hi > 0.0)) {
+          stop = j;
+          if (pass != 0) flag = j + 1;  // the second pass breaks down
+        } else {
+          piv = p;
+        }
+      }
+      __syncthreads();
+      if (stop == j) break;
+      const int p = piv;
+      if (p != j) {  // symmetric swap of rows and columns j and p; the rows of R built so far
+        for (int i = tid; i < k; i += kThreads) {
+          const dd t = A[j * k + i];
+          A[j * k + i] = A[p * k + i];
+          A[p * k + i] = t;
+        }
+        __syncthreads();
+        for (int i = tid; i < k; i += kThreads) {
+          const dd t = A[i * k + j];
+          A[i * k + j] = A[i * k + p];
+          A[i * k + p] = t;
+          if (i < j) {
+            const dd u = R[j * k + i];
+            R[j * k + i] = R[p * k + i];
+            R[p * k + i] = u;
+          }
+        }
+        if (tid == 0) {
+          const int t = perm_s[j];
+          perm_s[j] = perm_s[p];
+          perm_s[p] = t;
+        }
+        __syncthreads();
+      }
+      if (tid == 0) {
+        const dd rjj = A_::sqrt(A[j * k + j]);
+        R[j * k + j] = rjj;
+        rinv = A_::recip(rjj);
+      }
+      __syncthreads();
+      for (int l = j + 1 + tid; l < lim; l += kThreads) R[l * k + j] = A_::mul(A[l * k + j], rinv);
+      __syncthreads();
+      const int m = lim - j - 1;
+      for (int t = tid; t < m * m; t += kThreads) {
+        const int a = j + 1 + t % m, b = j + 1 + t / m;
+        A[b * k + a] = A_::sub(A[b * k + a], A_::mul(R[a * k + j], R[b * k + j]));
+      }
+      __syncthreads();
+      r = j + 1;
+    }
+  }
+  if (flag != 0) {  // NaN / Inf, or a breakdown of the second pass: X stays as it is
+    if (tid == 0) {
+      st->info = flag;
+      if (flag < 0) st->rank = -1;
+      finish_gates(g, 0, 0);
+      if (info_user) *info_user = flag;
+      if (rank_user) *rank_user = st->rank;
+    }
+    return;
+  }
+  // R11^{-1}: column c by one thread, back substitution
+  for (int c = tid; c < r; c += kThreads) {
+    Zs[c * k + c] = A_::recip(R[c * k + c]);
+    for (int i = c - 1; i >= 0; --i) {
+      dd s2 = dd{0.0, 0.0};
+      for (int l = i + 1; l <= c; ++l) s2 = A_::fma(R[l * k + i], Zs[c * k + l], s2);
+      Zs[c * k + i] = A_::mul(dd_neg(s2), Zs[i * k + i]);
+    }
+  }
+  __syncthreads();
+  // Z: the pivots' rows of R11^{-1} (pass 0), R2^{-1} itself (pass 1); zero beyond the rank
+  for (int t = tid; t < KMAX * k; t += kThreads) {
+    const int i = t % KMAX, c = t / KMAX;
+    if (i < k) {
+      ws->Zh[c * KMAX + i] = 0.0;
+      ws->Zl[c * KMAX + i] = 0.0;
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < r * r; t += kThreads) {
+    const int i = t % r, c = t / r;
+    const int row = pass == 0 ? perm_s[i] : i;
+    ws->Zh[c * KMAX + row] = Zs[c * k + i].hi;
+    ws->Zl[c * KMAX + row] = Zs[c * k + i].lo;
+  }
+  // R of the whole: R (pass 0) or R2 R_old (pass 1), rows beyond the rank zero
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    dd v = dd{0.0, 0.0};
+    if (i < r) {
+      if (pass == 0) {
+        v = R[j * k + i];
+      } else {
+        for (int l = i; l < r; ++l) v = A_::fma(R[l * k + i], dd{ws->Th[j * KMAX + l], ws->Tl[j * KMAX + l]}, v);
+      }
+    }
+    Zs[t] = v;
+  }
+  __syncthreads();
+  for (int t = tid; t < k * k; t += kThreads) {
+    const int i = t % k, j = t / k;
+    ws->Th[j * KMAX + i] = Zs[t].hi;
+    ws->Tl[j * KMAX + i] = Zs[t].lo;
+    if (Rh_u) Rh_u[(size_t)j * ldr + i] = Zs[t].hi;
+    if (Rl_u) Rl_u[(size_t)j * ldr + i] = Zs[t].lo;
+  }
+  if (pass == 0)
+    for (int i = tid; i < k; i += kThreads) {
+      st->perm[i] = perm_s[i];
+      if (perm_user) perm_user[i] = perm_s[i];
+    }
+  if (tid == 0) {
+    if (pass == 0) st->rank = r;
+    int next = 0;
+    if (pass == 0 && r > 0)
+      next = passes == 2 ? 1 : (passes == 0 ? (R[0].hi > thr * R[(r - 1) * k + (r - 1)].hi) : 0);
+    finish_gates(g, 1, next);
+    if (info_user) *info_user = st->info;
+    if (rank_user) *rank_user = st->rank;
+  }
+}
+
 // --------------------------------------------------------------- SVQB
 
 template <int MODE>
@@ -589,6 +762,26 @@ cudaError_t launch_status_init(DevStatus* s, int k, cudaStream_t st) {
 }
 
 size_t chol_smem(int k) { return 3 * (size_t)k * k * sizeof(dd); }
+
+cudaError_t launch_pivchol_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
+                                 double* R_hi, double* R_lo, int ldr, double tol, DevStatus* s, SmallGates g,
+                                 int pass, int passes, int* info_user, int* rank_user, int* perm_user,
+                                 cudaStream_t st) {
+  const size_t smem = chol_smem(k);
+  cudaError_t e;
+  if (mode == MODE_DD) {
+    e = set_dyn_smem(pivchol_small_kernel<MODE_DD>, smem);
+    if (e != cudaSuccess) return e;
+    pivchol_small_kernel<MODE_DD><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, R_hi, R_lo, ldr, tol, s, g, pass,
+                                                              passes, 1e7, info_user, rank_user, perm_user);
+  } else {
+    e = set_dyn_smem(pivchol_small_kernel<MODE_FP64>, smem);
+    if (e != cudaSuccess) return e;
+    pivchol_small_kernel<MODE_FP64><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, R_hi, R_lo, ldr, tol, s, g,
+                                                                pass, passes, 1e4, info_user, rank_user, perm_user);
+  }
+  return cudaGetLastError();
+}
 size_t svqb_smem(int k) {
   return 3 * (size_t)k * k * sizeof(dd) + 2 * (size_t)(k / 2 + 1) * sizeof(dd) + 2 * (size_t)(k / 2 + 1) * sizeof(int);
 }

@@ -648,6 +648,71 @@ def test_svqb_dd_two_passes_match_oracle(eo, ctx, n, k, kappa):
     assert np.array_equal(host(da), q)
 
 
+# ------------------------------------------------- pivoted, partial CholQR
+
+@pytest.mark.parametrize("n,k,kappa,passes", [(20_000, 8, 1e4, 1), (20_001, 16, 1e8, 2), (5_000, 5, 1.0, 1),
+                                              (9_000, 32, 1e6, 2)])
+def test_cholqr_piv_matches_oracle(eo, ctx, n, k, kappa, passes):
+    x = synth.conditioned(n, k, kappa, 840 + k)
+    d = dev(x)
+    rh, rl, perm, rank, info = eo.cholqr_piv(ctx, d, passes=passes, prec=eo.DD)
+    q_o, perm_o, rank_o, (rh_o, rl_o), info_o = oracle.cholqr_piv(x, tol=k * U2, passes=passes)
+    assert int(info.item()) == 0 == info_o
+    assert int(rank.item()) == rank_o == k
+    assert list(perm.cpu().numpy()) == list(perm_o)
+    tol = (4 if passes == 2 else 1) * cholqr_tol(n, k, kappa)
+    q = host(d)
+    assert np.max(np.abs(q - q_o)) <= tol
+    r = host(rh) + host(rl)
+    assert np.max(np.abs(r - (rh_o + rl_o))) <= tol * np.max(np.abs(rh_o))
+    assert oracle.orth_err(q)[0] <= 1e-14
+    assert oracle.fact_err(np.asfortranarray(x[:, perm_o]), q, host(rh), host(rl)) <= 1e-14
+
+
+def test_cholqr_piv_ties_rank_and_special_inputs(eo, ctx):
+    # orthogonal columns with equal norms: exact ties, broken by the lowest index as in the oracle
+    u = synth.hadamard_basis(4096, 5, 841)
+    s = np.array([0.5, 8.0, 2.0, 8.0, 0.25])
+    d = dev(np.asfortranarray(u * s))
+    rh, rl, perm, rank, info = eo.cholqr_piv(ctx, d, prec=eo.DD)
+    assert list(perm.cpu().numpy()) == [1, 3, 2, 0, 4] and int(rank.item()) == 5
+    assert np.array_equal(host(rh), np.diag(s[[1, 3, 2, 0, 4]])) and np.array_equal(host(d), u[:, [1, 3, 2, 0, 4]])
+    # rank deficiency: the dependent columns are cut and their columns of Q are zero
+    g = synth.rng(842)
+    a, b = g.standard_normal((30_000, 1)), g.standard_normal((30_000, 1))
+    x = np.asfortranarray(np.hstack([a, b, a + b, 3.0 * b, g.standard_normal((30_000, 1))]))
+    d = dev(x)
+    _, _, perm, rank, info = eo.cholqr_piv(ctx, d, prec=eo.DD, tol=1e-20)
+    q_o, perm_o, rank_o, _, _ = oracle.cholqr_piv(x, tol=1e-20)
+    assert int(rank.item()) == rank_o == 3 and list(perm.cpu().numpy()) == list(perm_o)
+    q = host(d)
+    assert not np.any(q[:, 3:])
+    assert np.max(np.abs(q - q_o)) <= cholqr_tol(30_000, 3, 10.0)
+    # NaN: info -1, X unchanged; the automatic pass count matches passes = 2 at kappa = 1e9
+    y = synth.gaussian(1000, 3, 843)
+    y[5, 1] = np.nan
+    d = dev(y)
+    _, _, _, rank, info = eo.cholqr_piv(ctx, d, prec=eo.DD)
+    assert int(info.item()) == -1 and int(rank.item()) == -1
+    assert np.array_equal(host(d), y, equal_nan=True)
+    x = synth.conditioned(8000, 6, 1e9, 844)
+    d2, da = dev(x), dev(x)
+    eo.cholqr_piv(ctx, d2, passes=2, prec=eo.DD)
+    eo.cholqr_piv(ctx, da, passes=0, prec=eo.DD)
+    assert np.array_equal(host(d2), host(da))
+
+
+def test_cholqr_piv_fp64(eo, ctx):
+    n, k = 20_000, 6
+    x = synth.conditioned(n, k, 10.0, 845)
+    d = dev(x)
+    rh, _, perm, rank, info = eo.cholqr_piv(ctx, d, prec=eo.FP64)
+    q_o, perm_o, rank_o, (rh_o, _), _ = oracle.cholqr_piv(x, tol=k * U)
+    assert list(perm.cpu().numpy()) == list(perm_o) and int(rank.item()) == rank_o == k
+    tol = 8 * 100 * (gamma(n) + gamma(k + 1))
+    assert np.max(np.abs(host(d) - q_o)) <= tol
+
+
 def test_svqb_rank_deficient(eo, ctx):
     x = synth.gaussian(5000, 4, 90)
     x[:, 2] = 0.0
