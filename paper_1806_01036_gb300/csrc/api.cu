@@ -130,8 +130,38 @@ int dd_gram_ctas(int64_t n, int kx, int ky, bool sym, int ctas) {
   return use_umma_gram(kx, sym ? kx : ky) ? umma_gram_ctas(n, kx, ky, sym, ctas) : fx_gram_ctas(n, kx, ky, sym, ctas);
 }
 
+// EO_F32 Gram products with 16 or more columns on one side run on the
+// tensor-core digit engine (exact sums of the FP32 products, rounded once:
+// at least as accurate as FP64 accumulation, and faster than summing on the
+// FP64 pipe); narrower ones, and operands it cannot copy, sum their exact
+// products in FP64.  The low parts are written as zero either way.
+static bool f32_on_digits(const void* X, const void* Y, int kx, int ky, bool sym) {
+  const char* e = getenv("EO_F32_GRAM_ENGINE");
+  if (e && e[0] == 'f') return false;  // "fp64": the FP64-pipe sums
+  return std::max(kx, sym ? kx : ky) >= 16 &&
+         umma_gram_f32_supported(static_cast<const float*>(X), static_cast<const float*>(Y), kx, ky, sym);
+}
+
+size_t f32_gram_scratch(int64_t n, int kx, int ky, bool sym) {
+  return std::max(gram_scratch_bytes(n, kx, ky, sym), umma_gram_scratch_bytes(n, kx, ky, sym));
+}
+
+cudaError_t launch_f32_gram(int64_t n, int kx, const void* X, int64_t ldx, int ky, const void* Y, int64_t ldy,
+                            bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
+                            cudaStream_t st) {
+  if (!f32_on_digits(X, Y, kx, ky, sym))
+    return launch_gram(MODE_F32, n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st);
+  cudaError_t e = launch_umma_gram_f32(n, kx, static_cast<const float*>(X), ldx, ky, static_cast<const float*>(Y),
+                                       ldy, sym, scratch, G_hi, nullptr, ldg, gate, st);
+  if (e == cudaSuccess && G_lo)
+    e = cudaMemset2DAsync(G_lo, (size_t)ldg * sizeof(double), 0, (size_t)kx * sizeof(double), (size_t)(sym ? kx : ky),
+                          st);
+  return e;
+}
+
 size_t orth_scratch(int64_t n, int k, eo_prec prec, bool b_inner) {
-  size_t s = prec == EO_DD ? dd_gram_scratch(n, k, k, true) : gram_scratch_bytes(n, k, k, true);
+  size_t s = prec == EO_DD ? dd_gram_scratch(n, k, k, true)
+                           : (prec == EO_F32 ? f32_gram_scratch(n, k, k, true) : gram_scratch_bytes(n, k, k, true));
   if (b_inner) s = std::max(s, prec == EO_DD ? dd_gram_scratch(n, k, k, false) : gram_scratch_bytes(n, k, k, false));
   if (prec == EO_DD) s = std::max(s, fx_update_tmp_bytes(n, k));  // the partials are consumed before the update
   return s;
@@ -154,6 +184,9 @@ cudaError_t enqueue_orth_step(const OrthArgs& a, const OrthRes& r, int p, OrthSt
       if (fx) {
         e = launch_dd_gram(a.n, a.k, static_cast<const double*>(a.X), a.ldx, a.k, static_cast<const double*>(Y), ldy,
                            !b, r.parts, ws->Mh, ws->Ml, KMAX, &st->gate[2 * p], r.stream, r.tile.gram);
+      } else if (a.prec == EO_F32) {
+        e = launch_f32_gram(a.n, a.k, a.X, a.ldx, a.k, Y, ldy, !b, r.parts, ws->Mh, ws->Ml, KMAX, &st->gate[2 * p],
+                            r.stream);
       } else {
         e = launch_gram(mode, a.n, a.k, a.X, a.ldx, a.k, Y, ldy, !b, r.parts, ws->Mh, ws->Ml, KMAX, &st->gate[2 * p],
                         r.stream);
@@ -365,6 +398,12 @@ eo_status eo_gram(eo_ctx* ctx, int64_t n, int kx, const void* X, int64_t ldx, in
     if (s != EO_OK) return s;
     EO_CUDA(launch_dd_gram(n, kx, static_cast<const double*>(X), ldx, ky, static_cast<const double*>(sym ? X : Y),
                            ldy, sym, parts_of(ctx), G_hi, G_lo, ldg, nullptr, ctx->stream),
+            "eo_gram");
+  } else if (prec == EO_F32) {
+    eo_status s = ensure_scratch(ctx, f32_gram_scratch(n, kx, ky, sym));
+    if (s != EO_OK) return s;
+    EO_CUDA(launch_f32_gram(n, kx, X, ldx, ky, sym ? X : Y, ldy, sym, parts_of(ctx), G_hi, G_lo, ldg, nullptr,
+                            ctx->stream),
             "eo_gram");
   } else {
     eo_status s = ensure_scratch(ctx, gram_scratch_bytes(n, kx, ky, sym));

@@ -108,6 +108,12 @@ cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, in
 size_t fx_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym);
 // CTAs of the partial-sum launch of each engine under a cap (0 = none).
 int umma_gram_ctas(int64_t n, int kx, int ky, bool sym, int ctas);
+// The same exact sums for FP32 operands (the EO_F32 mode), each value
+// widened to FP64 exactly: G_hi = the sum rounded once (G_lo its low part).
+bool umma_gram_f32_supported(const float* X, const float* Y, int kx, int ky, bool sym);
+cudaError_t launch_umma_gram_f32(int64_t n, int kx, const float* X, int64_t ldx, int ky, const float* Y,
+                                 int64_t ldy, bool sym, void* scratch, double* G_hi, double* G_lo, int ldg,
+                                 const int* gate, cudaStream_t st);
 int fx_gram_ctas(int64_t n, int kx, int ky, bool sym, int ctas);
 cudaError_t launch_fx_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
                            bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,

@@ -346,6 +346,10 @@ __device__ __forceinline__ void xwords(double x, int A, unsigned (&w)[4]) {
 __device__ __forceinline__ void cp_async8z(unsigned dst, const void* src, unsigned src_bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
+// 4-byte asynchronous copy global -> shared; src_bytes 0 writes zeros.
+__device__ __forceinline__ void cp_async4z(unsigned dst, const void* src, unsigned src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 // A pair of values (a, b) interleaved in 16-bit lanes: Z[k] holds bits

@@ -112,21 +112,37 @@ struct UPlan {
 // matrix) and reads them back at panel p; the rest is the same.
 constexpr unsigned kDirectStageBytes = 2u * kMaxItems * kConvThreads * 16u;
 
+// An FP32 value widened to FP64 exactly in integer arithmetic (the FP64
+// conversion unit is slow on this GPU); zeros, subnormals, infinities and
+// NaNs (the exponent field 0 or 255) take the conversion instruction.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 255u) return (double)f;
+  return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)), (int)(b << 29));
+}
+
 // PAD: the tile has padded columns (beyond kx or ky, e.g. kx = 40 in a
 // 64-column plan): their digits are zeroed once and never converted.
-template <int KYP, bool DIRECT, bool PAD>
+// T: the element type of X and Y; FP32 (the EO_F32 mode) only with DIRECT
+// loads, every value widened to FP64 exactly as it is read.  KXPC, PC: the
+// plan's X tile width and panel rows when known at compile time (the hot
+// plans: slab strides become immediate store offsets), 0 = from the plan.
+template <int KYP, bool DIRECT, bool PAD, typename T = double, int KXPC = 0, int PC = 0>
 __global__ void __launch_bounds__(kThreads, 1)
-    umma_gram_partial_kernel(int64_t n, int kx, const double* __restrict__ X, int64_t ldx, int ky,
-                             const double* __restrict__ Y, int64_t ldy, UPlan pl, int64_t rows_per_chunk,
+    umma_gram_partial_kernel(int64_t n, int kx, const T* __restrict__ X, int64_t ldx, int ky,
+                             const T* __restrict__ Y, int64_t ldy, UPlan pl, int64_t rows_per_chunk,
                              const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
                              FxPart* __restrict__ parts, const int* gate) {
+  static_assert(sizeof(T) == 8 || DIRECT, "FP32 operands are copied by the converter threads");
   if (gate && *gate == 0) return;
   // Y columns of one converter thread in a drain (four warps share a TMEM
   // lane quarter), handled NH times NY at a time
   constexpr int NYT = KYP * 4 / kConvWarps;
   constexpr int NY = NYT < 4 ? NYT : 4;
   constexpr int NH = NYT / NY;
-  const int kxp = pl.kxp, P = pl.P, nslots = pl.nslots;
+  const int kxp = KXPC ? KXPC : pl.kxp, P = PC ? PC : pl.P;
+  const int nslots = KXPC ? (pl.shared ? KXPC : KXPC + KYP) : pl.nslots;
   const int tx = blockIdx.x / pl.nty, ty = blockIdx.x % pl.nty;
   const int x0 = tx * kxp, y0 = ty * KYP;  // first X / Y column of the tile
   const unsigned SBO = (unsigned)P * 16;   // bytes per 8-row group of a slab (P / 8 core matrices)
@@ -386,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     // DIRECT: each item's column (null: zeros) and row offset in the panel
-    const double* gcol[kMaxItems];
+    const T* gcol[kMaxItems];
     int irow[kMaxItems];
     const unsigned slot0 = smem_u32(stage) + (unsigned)tid * 16u;
     auto prefetch = [&](int pp) {  // this thread's items of panel pp into slot buffer pp & 1
@@ -396,8 +412,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!gcol[k]) continue;
         const int64_t row = base + irow[k];
         const unsigned d = slot0 + (unsigned)(((pp & 1) * kMaxItems + k) * kConvThreads) * 16u;
-        cp_async8z(d, row < r1 ? gcol[k] + row : gcol[k], row < r1 ? 8u : 0u);
-        cp_async8z(d + 8u, row + 1 < r1 ? gcol[k] + row + 1 : gcol[k], row + 1 < r1 ? 8u : 0u);
+        if constexpr (sizeof(T) == 8) {
+          cp_async8z(d, row < r1 ? gcol[k] + row : gcol[k], row < r1 ? 8u : 0u);
+          cp_async8z(d + 8u, row + 1 < r1 ? gcol[k] + row + 1 : gcol[k], row + 1 < r1 ? 8u : 0u);
+        } else {
+          cp_async4z(d, row < r1 ? gcol[k] + row : gcol[k], row < r1 ? 4u : 0u);
+          cp_async4z(d + 4u, row + 1 < r1 ? gcol[k] + row + 1 : gcol[k], row + 1 < r1 ? 4u : 0u);
+        }
       }
       cp_async_commit_group();
     };
@@ -429,10 +450,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       if constexpr (DIRECT) {
         asm volatile("cp.async.wait_group 1;" ::: "memory");  // panel q's copies (q + 1's may be in flight)
 #pragma unroll
-        for (int k = 0; k < kMaxItems; ++k)
-          v[k] = gcol[k] ? *reinterpret_cast<const double2*>(stage + ((size_t)((q & 1) * kMaxItems + k) * kConvThreads +
-                                                                      tid) * 16u)
-                         : make_double2(0.0, 0.0);
+        for (int k = 0; k < kMaxItems; ++k) {
+          const unsigned char* slot = stage + ((size_t)((q & 1) * kMaxItems + k) * kConvThreads + tid) * 16u;
+          if constexpr (sizeof(T) == 8) {
+            v[k] = gcol[k] ? *reinterpret_cast<const double2*>(slot) : make_double2(0.0, 0.0);
+          } else {
+            const float2 f = gcol[k] ? *reinterpret_cast<const float2*>(slot) : make_float2(0.0f, 0.0f);
+            v[k] = make_double2(widen(f.x), widen(f.y));
+          }
+        }
         prefetch(q + 2);  // into the slots just read (zeros past the chunk)
       } else {
         mbar_wait(sb0 + 8u * (unsigned)(q & 1), (unsigned)(q >> 1) & 1u, &bad);  // panel q staged
@@ -517,8 +543,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           add_bias(wa);
           add_bias(wb);
           const unsigned signs = ((hi32(v[k].x) >> 31) << 15) | (hi32(v[k].y) & 0x80000000u);
-          store_bal_digits<0>(dbuf + (it_d[k] & (PAD ? 0x3fffffffu : 0x7fffffffu)),
-                              (it_d[k] >> 31) ? stride_b : stride_a, pair_lanes(wa, wb), pair_sign(signs, e1024));
+          // operand A or B (warp-uniform): two copies of the stores, so that
+          // with a compile-time plan the slab stride is an immediate offset
+          unsigned char* dst = dbuf + (it_d[k] & (PAD ? 0x3fffffffu : 0x7fffffffu));
+          if (it_d[k] >> 31)
+            store_bal_digits<0>(dst, stride_b, pair_lanes(wa, wb), pair_sign(signs, e1024));
+          else
+            store_bal_digits<0>(dst, stride_a, pair_lanes(wa, wb), pair_sign(signs, e1024));
         }
       }
       fence_proxy_async();
@@ -755,15 +786,15 @@ size_t plan_smem_direct(const UPlan& p) {
   return plan_smem(p) - 2 * (size_t)p.stage_bytes + std::max<size_t>(2 * (size_t)p.stage_bytes, kDirectStageBytes);
 }
 
-template <int KYP, bool DIRECT, bool PAD>
-cudaError_t launch_kernel(const UPlan& plan, int chunks, int64_t n, int kx, const double* X, int64_t ldx, int ky,
-                          const double* Y, int64_t ldy, int64_t rpc, const CUtensorMap& tmx, const CUtensorMap& tmy,
+template <int KYP, bool DIRECT, bool PAD, typename T = double, int KXPC = 0, int PC = 0>
+cudaError_t launch_kernel(const UPlan& plan, int chunks, int64_t n, int kx, const T* X, int64_t ldx, int ky,
+                          const T* Y, int64_t ldy, int64_t rpc, const CUtensorMap& tmx, const CUtensorMap& tmy,
                           FxPart* parts, const int* gate, cudaStream_t st) {
   const size_t smem = DIRECT ? plan_smem_direct(plan) : plan_smem(plan);
-  cudaError_t e = set_dyn_smem(umma_gram_partial_kernel<KYP, DIRECT, PAD>, smem);
+  cudaError_t e = set_dyn_smem(umma_gram_partial_kernel<KYP, DIRECT, PAD, T, KXPC, PC>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(plan.ntx * plan.nty, chunks);
-  umma_gram_partial_kernel<KYP, DIRECT, PAD>
+  umma_gram_partial_kernel<KYP, DIRECT, PAD, T, KXPC, PC>
       <<<grid, kThreads, smem, st>>>(n, kx, X, ldx, ky, Y, ldy, plan, rpc, tmx, tmy, parts, gate);
   return cudaGetLastError();
 }
@@ -831,13 +862,59 @@ cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, in
   cudaError_t e;
 #define EO_UMMA_LAUNCH(K, D, PD) \
   launch_kernel<K, D, PD>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts, gate, st)
-  if (plan.kyp == 16)
+  // the two plans of the projection step: V^T Y (64 + 16 columns, 32-row
+  // panels) and a symmetric 16-column Gram (128-row panels)
+  const bool hot_vty = !direct && !pad && plan.kyp == 16 && !plan.shared && plan.kxp == 64 && plan.P == 32;
+  const bool hot_sym = !direct && !pad && plan.kyp == 16 && plan.shared && plan.kxp == 16 && plan.P == 128;
+  if (hot_vty)
+    e = launch_kernel<16, false, false, double, 64, 32>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy, parts,
+                                                        gate, st);
+  else if (hot_sym)
+    e = launch_kernel<16, false, false, double, 16, 128>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tmx, tmy,
+                                                         parts, gate, st);
+  else if (plan.kyp == 16)
     e = direct ? (pad ? EO_UMMA_LAUNCH(16, true, true) : EO_UMMA_LAUNCH(16, true, false))
                : (pad ? EO_UMMA_LAUNCH(16, false, true) : EO_UMMA_LAUNCH(16, false, false));
   else
     e = direct ? (pad ? EO_UMMA_LAUNCH(8, true, true) : EO_UMMA_LAUNCH(8, true, false))
                : (pad ? EO_UMMA_LAUNCH(8, false, true) : EO_UMMA_LAUNCH(8, false, false));
 #undef EO_UMMA_LAUNCH
+  if (e != cudaSuccess) return e;
+  return launch_fx_reduce(kx, ky, sym, chunks, parts, G_hi, G_lo, ldg, gate, st);
+}
+
+bool umma_gram_f32_supported(const float* X, const float* Y, int kx, int ky, bool sym) {
+  if (sym) {
+    Y = X;
+    ky = kx;
+  }
+  return (uintptr_t)X % 4 == 0 && (uintptr_t)Y % 4 == 0 && plan_smem_direct(make_plan(kx, ky, sym)) <= kSmemCap;
+}
+
+cudaError_t launch_umma_gram_f32(int64_t n, int kx, const float* X, int64_t ldx, int ky, const float* Y,
+                                 int64_t ldy, bool sym, void* scratch, double* G_hi, double* G_lo, int ldg,
+                                 const int* gate, cudaStream_t st) {
+  if (sym) {
+    Y = X;
+    ldy = ldx;
+    ky = kx;
+  }
+  const UPlan plan = make_plan(kx, ky, sym);
+  alignas(64) CUtensorMap tm{};  // unused: FP32 operands are copied by the converter threads
+  const int chunks = capped_chunks(n, plan, 0);
+  int64_t rpc = (n + chunks - 1) / chunks;
+  rpc = std::max<int64_t>(plan.P, (rpc + plan.P - 1) / plan.P * plan.P);
+  FxPart* parts = static_cast<FxPart*>(scratch);
+  const bool pad = plan.ntx * plan.kxp > kx || (!plan.shared && plan.nty * plan.kyp > ky);
+  cudaError_t e;
+  if (plan.kyp == 16)
+    e = pad ? launch_kernel<16, true, true, float>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tm, tm, parts, gate, st)
+            : launch_kernel<16, true, false, float>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tm, tm, parts, gate,
+                                                    st);
+  else
+    e = pad ? launch_kernel<8, true, true, float>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tm, tm, parts, gate, st)
+            : launch_kernel<8, true, false, float>(plan, chunks, n, kx, X, ldx, ky, Y, ldy, rpc, tm, tm, parts, gate,
+                                                   st);
   if (e != cudaSuccess) return e;
   return launch_fx_reduce(kx, ky, sym, chunks, parts, G_hi, G_lo, ldg, gate, st);
 }

@@ -114,6 +114,51 @@ def test_gram_fp64_and_f32_within_textbook_bound(eo, ctx, prec, n, k):
     assert not np.any(host(gl))
 
 
+@pytest.mark.parametrize("n,kx,ky,sym", [(50_000, 16, 16, True), (20_001, 32, 32, True), (30_000, 64, 16, False),
+                                         (7_777, 5, 19, False), (4_097, 64, 64, True), (1, 16, 16, True)])
+def test_gram_f32_on_the_digit_engine(eo, ctx, monkeypatch, n, kx, ky, sym):
+    """EO_F32 with 16 or more columns on one side: the FP32 products summed
+    exactly by the tensor-core engine (values widened to FP64 exactly, by
+    integer arithmetic), the sum rounded once -- within u |G*| plus the
+    engine's own n 2^-96 max|x_i| max|y_j| of the binary128 value, i.e. at
+    least as accurate as FP64 accumulation; the low parts are zero.  Edge
+    values (subnormal, zero, negative zero, powers of two) go through the
+    widening's conversion path.  The FP64-pipe sums (EO_F32_GRAM_ENGINE=fp64)
+    agree within the textbook bound."""
+    g = synth.rng(310 + kx)
+    x = g.standard_normal((n, kx)).astype(np.float32)
+    y = x if sym else g.standard_normal((n, ky)).astype(np.float32)
+    if n > 8:
+        x[3, 0] = np.float32(1e-40)  # subnormal
+        x[4, 0] = np.float32(-0.0)
+        x[5, min(1, kx - 1)] = np.float32(2.0 ** -20)
+    dx = dev(x)
+    dy = None if sym else dev(y)
+    gh, gl = eo.gram(ctx, dx, dy, prec=eo.F32)
+    rh, rl = oracle.gram_f32(x, None if sym else y)
+    yy = x if sym else y
+    ax, ay = np.abs(x.astype(np.float64)), np.abs(yy.astype(np.float64))
+    err = np.abs(host(gh) - (rh + rl))
+    bound = U * np.abs(rh) + n * 2.0 ** -96 * np.outer(ax.max(axis=0), ay.max(axis=0))
+    assert np.all(err <= bound), float(np.max(err / bound))
+    assert not np.any(host(gl))
+    monkeypatch.setenv("EO_F32_GRAM_ENGINE", "fp64")
+    ph, _ = eo.gram(ctx, dx, dy, prec=eo.F32)
+    assert np.all(np.abs(host(ph) - (rh + rl)) <= gamma(n) * (ax.T @ ay) + U * np.abs(rh))
+
+
+def test_cholqr_f32_wide_block(eo, ctx):
+    n, k = 40_000, 24  # the Gram of the CholQR passes on the digit engine
+    x = synth.conditioned(n, k, 1e2, 81).astype(np.float32)
+    d = dev(x)
+    rh, _, info = eo.cholqr(ctx, d, prec=eo.F32)
+    assert int(info.item()) == 0
+    q = host(d).astype(np.float64)
+    assert oracle.orth_err(q)[0] <= 1e-5  # FP32 storage of Q
+    q_o, (rh_o, _), _ = oracle.cholqr(x.astype(np.float64))
+    np.testing.assert_allclose(host(rh), rh_o, rtol=0, atol=1e-12 * np.max(np.abs(rh_o)))
+
+
 @pytest.mark.parametrize("engine", ["int", "umma"])
 @pytest.mark.parametrize("n,kx,ky,sym", [(1, 1, 1, True), (33, 3, 3, True), (1000, 8, 8, False), (4099, 13, 5, False),
                                          (100_003, 16, 16, True), (20_000, 64, 64, True), (20_001, 64, 16, False),
