@@ -460,6 +460,21 @@ def run_eo(a):
             res[name] = {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
                          "blocks_per_s": 1e3 / float(np.percentile(ts, 50)), "orth_err": dd_orth(Xs),
                          "note": "includes the device copy restoring X (0.8 MB)"}
+            # the same call captured once in a CUDA graph and replayed: one launch per block
+            one(prec, passes)
+            torch.cuda.synchronize()
+            gr = torch.cuda.CUDAGraph()
+            cap = torch.cuda.Stream(dev)
+            cap.wait_stream(stream)
+            with torch.cuda.stream(cap):
+                with torch.cuda.graph(gr, stream=cap):
+                    one(prec, passes)  # the binding runs the call on the capturing stream
+            torch.cuda.synchronize()
+            tsg, _ = timed_steps(gr.replay, max(50, reps))
+            res[name + "_graph"] = {"p50_ms": float(np.percentile(tsg, 50)), "p99_ms": float(np.percentile(tsg, 99)),
+                                    "blocks_per_s": 1e3 / float(np.percentile(tsg, 50)), "orth_err": dd_orth(Xs),
+                                    "note": "one CUDA-graph replay of the copy restoring X and the call"}
+            del gr
         single = {"workload": "single CholQR, X 100,000 x 8, sigma 1 .. 1e-6 (L2-resident)", **res}
         del X0s, Xs
     except _Skip:
@@ -1044,6 +1059,28 @@ def run_single(a):
         orth = float(np.linalg.norm((gh.cpu().numpy() - np.eye(8)) + gl.cpu().numpy(), 2))
         res[name] = {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
                      "blocks_per_s": 1e3 / float(np.percentile(ts, 50)), "orth_err": orth}
+        # the copy and the call captured once in a CUDA graph, replayed per block
+        gr = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(dev)
+        cap.wait_stream(stream)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(gr, stream=cap):
+                X.copy_(X0)
+                eo.cholqr(ctx, X, passes=passes, prec=prec)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            gr.replay()
+        ts = []
+        for _ in range(max(50, a.steps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gr.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        res[name + "_graph"] = {"p50_ms": float(np.percentile(ts, 50)), "p99_ms": float(np.percentile(ts, 99)),
+                                "blocks_per_s": 1e3 / float(np.percentile(ts, 50))}
     out = {"metric": SINGLE_METRIC, "n_gpus": ws, "dtype": "f64", "data": "synthetic (synth.single_cholqr)",
            "config": {"workload": "single CholQR, X 100,000 x 8, sigma 1 .. 1e-6", "l2": "L2-warm (6.4 MB)"},
            "results": res}
