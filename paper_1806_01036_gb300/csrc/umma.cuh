@@ -61,9 +61,8 @@ static __device__ unsigned g_wait_expired = 0u;
 // *abort is set or after limit_ns, and then sets *abort so that every other
 // wait of the CTA gives up at once; a wait that ran out records it in
 // g_wait_expired.
-static __device__ __noinline__ bool mbar_wait(unsigned bar, unsigned parity, volatile int* abort,
-                                              unsigned long long limit_ns = kWaitNs) {
-  if (mbar_try_wait(bar, parity)) return true;
+static __device__ __noinline__ bool mbar_wait_slow(unsigned bar, unsigned parity, volatile int* abort,
+                                                   unsigned long long limit_ns) {
   const unsigned long long t0 = gtimer();
   while (!mbar_try_wait(bar, parity)) {
     const bool late = gtimer() - t0 > limit_ns;
@@ -74,6 +73,11 @@ static __device__ __noinline__ bool mbar_wait(unsigned bar, unsigned parity, vol
     }
   }
   return true;
+}
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, volatile int* abort,
+                                          unsigned long long limit_ns = kWaitNs) {
+  if (mbar_try_wait(bar, parity)) return true;  // the common case: no call
+  return mbar_wait_slow(bar, parity, abort, limit_ns);
 }
 // The same, but only the time limit ends it (waits for MMAs already issued).
 static __device__ __noinline__ bool mbar_wait_final(unsigned bar, unsigned parity, volatile int* abort) {
@@ -340,6 +344,24 @@ __device__ __forceinline__ void xwords(double x, int A, unsigned (&w)[4]) {
     w[2] = 0u;
     w[3] = 0u;
   }
+}
+
+// X for a value within 20 binades of A (t = 52 - A + e >= 32): the
+// significand shifted by t - 32 lands in words 1..3 and word 0 is zero.
+__device__ __forceinline__ void xwords_near(double x, int A, unsigned (&w)[4]) {
+  const unsigned hi = hi32(x), lo = lo32(x);
+  const int e = (hi >> 20) & 0x7ff;  // >= 1 here: A - e <= 20 and A >= 1... e may still be 0 for zeros
+  const unsigned mh = (hi & 0xfffffu) | (e ? 0x100000u : 0u);
+  const int bo = (52 - A + max(e, 1)) & 31;
+  w[0] = 0u;
+  w[1] = lo << bo;
+  w[2] = __funnelshift_l(lo, mh, bo);
+  w[3] = __funnelshift_l(mh, 0u, bo);
+}
+// t >= 32 for x aligned to A (zero counts as near: all its words are zero)
+__device__ __forceinline__ bool near_exp(double x, int A) {
+  const int e = (hi32(x) >> 20) & 0x7ff;
+  return e == 0 ? (hi32(x) & 0x7fffffffu) == 0u && lo32(x) == 0u : A - e <= 20;
 }
 
 // 8-byte asynchronous copy global -> shared; src_bytes 0 writes zeros.

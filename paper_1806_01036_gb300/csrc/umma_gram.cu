@@ -536,10 +536,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       const unsigned e1024 = exp1024x2();
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
-        if (tid + k * kConvThreads < nitems && (!PAD || !(it_d[k] & 0x40000000u))) {
+        const bool valid = tid + k * kConvThreads < nitems && (!PAD || !(it_d[k] & 0x40000000u));
+        // every value of the warp's items within 20 binades of its alignment
+        // exponent (nearly always): the words without selects
+        const bool near = __all_sync(0xffffffffu, !valid || (near_exp(v[k].x, A[k]) && near_exp(v[k].y, A[k])));
+        if (valid) {
           unsigned wa[4], wb[4];
-          xwords(v[k].x, A[k], wa);
-          xwords(v[k].y, A[k], wb);
+          if (near) {
+            xwords_near(v[k].x, A[k], wa);
+            xwords_near(v[k].y, A[k], wb);
+          } else {
+            xwords(v[k].x, A[k], wa);
+            xwords(v[k].y, A[k], wb);
+          }
           add_bias(wa);
           add_bias(wb);
           const unsigned signs = ((hi32(v[k].x) >> 31) << 15) | (hi32(v[k].y) & 0x80000000u);

@@ -435,11 +435,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       PairLanes P[W / 2];  // the W values as interleaved pairs
       unsigned sg[W / 2];
+      // every value of the warp within 20 binades of its row's exponent
+      // (nearly always): the aligned words without selects (for W >= 8; with
+      // four values a thread the vote costs more than it saves: measured)
+      bool near_all = W >= 8;
+#pragma unroll
+      for (int k = 0; k < W; ++k) near_all = near_all && near_exp(v[k], Ar);
+      const bool near = W >= 8 && __all_sync(0xffffffffu, near_all);
 #pragma unroll
       for (int m = 0; m < W / 2; ++m) {
         unsigned xa[4], xb[4];
-        xwords(v[2 * m], Ar, xa);
-        xwords(v[2 * m + 1], Ar, xb);
+        if (near) {
+          xwords_near(v[2 * m], Ar, xa);
+          xwords_near(v[2 * m + 1], Ar, xb);
+        } else {
+          xwords(v[2 * m], Ar, xa);
+          xwords(v[2 * m + 1], Ar, xb);
+        }
         P[m] = pair_lanes(xa, xb);
         sg[m] = ((hi32(v[2 * m]) >> 31) << 15) | (hi32(v[2 * m + 1]) & 0x80000000u);
       }
