@@ -765,6 +765,12 @@ def run_batched(a):
         e = (gh.cpu().numpy() - np.eye(int(k))) + gl.cpu().numpy()
         orth = max(orth, float(np.linalg.norm(e, 2)))
     ranks = bt.out.cpu().numpy()
+    sweeps = bt.sweeps()  # Jacobi sweeps of each block's last eigensolve
+    sweep_stats = {}
+    for kk in (4, 8, 16, 32):
+        sel = [sw for sw, kb, pb in zip(sweeps, ks, passes) if int(kb) == kk]
+        if sel:
+            sweep_stats[f"k{kk}"] = {"blocks": len(sel), "mean": float(np.mean(sel)), "max": int(np.max(sel))}
 
     torch.cuda.synchronize()
     l0 = ctx.launches()
@@ -819,7 +825,7 @@ def run_batched(a):
         "gpu_launches": launches, "graph_kernels": bt.kernels(), "create_s": create_s,
         "comparators": {"untuned_ms": untuned, "sequential_calls_ms": seq, "fp64_graph_ms": fp64,
                         "fp64_orth_err_max": orth_fp64},
-        "tiles": tiles, "clocks": clk.summary(),
+        "tiles": tiles, "clocks": clk.summary(), "last_pass_jacobi_sweeps": sweep_stats,
     }
     bt.close()
     if rank == 0:

@@ -844,7 +844,14 @@ cudaError_t launch_small_batched(bool chol, Mode mode, int njobs, int kmax, cons
     if (e != cudaSuccess) return e;
     kern<<<njobs, kThreads, smem, st>>>(jobs, pass, passes, ddm ? 1e7 : 1e4);
   } else {
-    const size_t smem = svqb_smem(kmax);
+    // A DD Jacobi eigensolve of 16 or more columns keeps one SM's FP64 pipe
+    // busy on its own (a k = 32 one takes 7-11 ms alone): when several share
+    // an SM they all slow down and the launch ends with the last of them.
+    // Asking for more than half of an SM's shared memory keeps one such CTA
+    // per SM (the jobs are ordered widest first, so the first wave spreads
+    // the widest over the SMs).
+    size_t smem = svqb_smem(kmax);
+    if (kmax >= 16) smem = std::max<size_t>(smem, 116 * 1024);
     auto kern = ddm ? svqb_small_batched_kernel<MODE_DD> : svqb_small_batched_kernel<MODE_FP64>;
     e = set_dyn_smem(kern, smem);
     if (e != cudaSuccess) return e;
