@@ -435,6 +435,16 @@ __device__ __forceinline__ void add_bias(unsigned (&w)[4]) {
       : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3])
       : "n"(kBias0), "n"(kBias1), "n"(kBias2), "n"(kBias3));
 }
+// add_bias for X with its low word zero (a value within 20 binades of A):
+// the low word becomes the bias's own and carries nothing.
+__device__ __forceinline__ void add_bias_near(unsigned (&w)[4]) {
+  w[0] = kBias0;
+  asm("add.cc.u32 %0, %0, %3;\n\t"
+      "addc.cc.u32 %1, %1, %4;\n\t"
+      "addc.u32 %2, %2, %5;"
+      : "+r"(w[1]), "+r"(w[2]), "+r"(w[3])
+      : "n"(kBias1), "n"(kBias2), "n"(kBias3));
+}
 // The FP16 exponent field of 1024 in both halves, as a register (so that
 // the digit's mask and this constant fit one three-input logic operation).
 __device__ __forceinline__ unsigned exp1024x2() {
@@ -477,6 +487,17 @@ __device__ __forceinline__ void store_bal_digits(unsigned char* dst, unsigned st
   if constexpr (S < NS) {
     *reinterpret_cast<unsigned*>(dst + S * stride) = bal_word<S>(p, sg);
     store_bal_digits<S + 1>(dst, stride, p, sg);
+  }
+}
+// The same for a pair whose X have their low 32 bits zero (add_bias_near):
+// the fields of slabs 11..14 (bits 0..27) are then the bias's, so those
+// digits are zero.
+template <int S>
+__device__ __forceinline__ void store_bal_digits_near(unsigned char* dst, unsigned stride, const PairLanes& p,
+                                                      PairSign sg) {
+  if constexpr (S < NS) {
+    *reinterpret_cast<unsigned*>(dst + S * stride) = S >= 11 ? 0u : bal_word<S>(p, sg);
+    store_bal_digits_near<S + 1>(dst, stride, p, sg);
   }
 }
 

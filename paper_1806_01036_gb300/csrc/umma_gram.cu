@@ -542,23 +542,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool near = __all_sync(0xffffffffu, !valid || (near_exp(v[k].x, A[k]) && near_exp(v[k].y, A[k])));
         if (valid) {
           unsigned wa[4], wb[4];
-          if (near) {
-            xwords_near(v[k].x, A[k], wa);
-            xwords_near(v[k].y, A[k], wb);
-          } else {
-            xwords(v[k].x, A[k], wa);
-            xwords(v[k].y, A[k], wb);
-          }
-          add_bias(wa);
-          add_bias(wb);
           const unsigned signs = ((hi32(v[k].x) >> 31) << 15) | (hi32(v[k].y) & 0x80000000u);
           // operand A or B (warp-uniform): two copies of the stores, so that
           // with a compile-time plan the slab stride is an immediate offset
           unsigned char* dst = dbuf + (it_d[k] & (PAD ? 0x3fffffffu : 0x7fffffffu));
-          if (it_d[k] >> 31)
-            store_bal_digits<0>(dst, stride_b, pair_lanes(wa, wb), pair_sign(signs, e1024));
-          else
-            store_bal_digits<0>(dst, stride_a, pair_lanes(wa, wb), pair_sign(signs, e1024));
+          if (near) {
+            xwords_near(v[k].x, A[k], wa);
+            xwords_near(v[k].y, A[k], wb);
+            add_bias_near(wa);
+            add_bias_near(wb);
+            if (it_d[k] >> 31)
+              store_bal_digits_near<0>(dst, stride_b, pair_lanes(wa, wb), pair_sign(signs, e1024));
+            else
+              store_bal_digits_near<0>(dst, stride_a, pair_lanes(wa, wb), pair_sign(signs, e1024));
+          } else {
+            xwords(v[k].x, A[k], wa);
+            xwords(v[k].y, A[k], wb);
+            add_bias(wa);
+            add_bias(wb);
+            if (it_d[k] >> 31)
+              store_bal_digits<0>(dst, stride_b, pair_lanes(wa, wb), pair_sign(signs, e1024));
+            else
+              store_bal_digits<0>(dst, stride_a, pair_lanes(wa, wb), pair_sign(signs, e1024));
+          }
         }
       }
       fence_proxy_async();

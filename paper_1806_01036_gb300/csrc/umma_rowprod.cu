@@ -116,11 +116,20 @@ __device__ __forceinline__ void tmem_ld3x4(unsigned a0, unsigned a1, unsigned a2
 // Digit words of slab S for W values of one row (two values per word, low
 // half first), stored at dst (W = 16: two 16-byte chunks 128 bytes apart;
 // W = 8: one chunk; W = 4: half a chunk).
+// near: every value of the warp had its X's low 32 bits zero (within 20
+// binades of its row's exponent), so the digits of slabs 11..14 (bits
+// 0..27) are zero and are stored as such without being extracted.
 template <int S, int W>
-__device__ __forceinline__ void store_slab(unsigned dst, const PairLanes (&P)[W / 2], const unsigned (&sg)[W / 2]) {
+__device__ __forceinline__ void store_slab(unsigned dst, const PairLanes (&P)[W / 2], const unsigned (&sg)[W / 2],
+                                           bool near) {
   unsigned w[W / 2];
+  if (S >= 11 && near) {
 #pragma unroll
-  for (int m = 0; m < W / 2; ++m) w[m] = pair_word<S>(P[m], sg[m]);
+    for (int m = 0; m < W / 2; ++m) w[m] = 0u;
+  } else {
+#pragma unroll
+    for (int m = 0; m < W / 2; ++m) w[m] = pair_word<S>(P[m], sg[m]);
+  }
   if constexpr (W == 16) {
     st_shared_v4(dst, w[0], w[1], w[2], w[3]);
     st_shared_v4(dst + 128u, w[4], w[5], w[6], w[7]);
@@ -133,23 +142,23 @@ __device__ __forceinline__ void store_slab(unsigned dst, const PairLanes (&P)[W 
 
 template <int G, int W, int J = 0>
 __device__ __forceinline__ void store_group(unsigned dst, unsigned slab_bytes, const PairLanes (&P)[W / 2],
-                                            const unsigned (&sg)[W / 2]) {
+                                            const unsigned (&sg)[W / 2], bool near) {
   if constexpr (J < kGroupSlabs<W>) {
-    store_slab<G * kGroupSlabs<W> + J, W>(dst + J * slab_bytes, P, sg);
-    store_group<G, W, J + 1>(dst, slab_bytes, P, sg);
+    store_slab<G * kGroupSlabs<W> + J, W>(dst + J * slab_bytes, P, sg, near);
+    store_group<G, W, J + 1>(dst, slab_bytes, P, sg, near);
   }
 }
 
 // store_group for a group index known at run time
 template <int W>
 __device__ __forceinline__ void store_group_rt(int g, unsigned dst, unsigned slab_bytes, const PairLanes (&P)[W / 2],
-                                               const unsigned (&sg)[W / 2]) {
+                                               const unsigned (&sg)[W / 2], bool near) {
   switch (g) {
-    case 0: store_group<0, W>(dst, slab_bytes, P, sg); break;
-    case 1: store_group<1, W>(dst, slab_bytes, P, sg); break;
-    case 2: store_group<2, W>(dst, slab_bytes, P, sg); break;
-    case 3: if constexpr (kGroups<W> > 3) store_group<3, W>(dst, slab_bytes, P, sg); break;
-    default: if constexpr (kGroups<W> > 4) store_group<4, W>(dst, slab_bytes, P, sg); break;
+    case 0: store_group<0, W>(dst, slab_bytes, P, sg, near); break;
+    case 1: store_group<1, W>(dst, slab_bytes, P, sg, near); break;
+    case 2: store_group<2, W>(dst, slab_bytes, P, sg, near); break;
+    case 3: if constexpr (kGroups<W> > 3) store_group<3, W>(dst, slab_bytes, P, sg, near); break;
+    default: if constexpr (kGroups<W> > 4) store_group<4, W>(dst, slab_bytes, P, sg, near); break;
   }
 }
 
@@ -461,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int g = 0; g < NG; ++g, ++G) {
         const int b = G & 1;
         if (G >= 2) mbar_wait(fb0 + 8u * b, (unsigned)((G - 2) >> 1) & 1u, &bad);  // MMAs of group G - 2 done
-        store_group_rt<W>(g, adig_s + (unsigned)b * GS * SLAB_A + dofs, SLAB_A, P, sg);
+        store_group_rt<W>(g, adig_s + (unsigned)b * GS * SLAB_A + dofs, SLAB_A, P, sg, near);
         fence_proxy_async();
         mbar_arrive(rb0 + 8u * b);
       }
