@@ -346,23 +346,25 @@ __device__ __forceinline__ void xwords(double x, int A, unsigned (&w)[4]) {
   }
 }
 
-// X for a value within 20 binades of A (t = 52 - A + e >= 32): the
-// significand shifted by t - 32 lands in words 1..3 and word 0 is zero.
-__device__ __forceinline__ void xwords_near(double x, int A, unsigned (&w)[4]) {
+// X for a normal value within 20 binades of A (its exponent e >= A - 20,
+// so t = 52 - A + e is in [32, 52]): the significand shifted by t - 32
+// lands in words 1..3 and word 0 is zero.  cA = 52 - A.  The shift amount
+// is taken from the low five bits of (hi >> 20) + cA: the sign bit above
+// the exponent field adds a multiple of 32, and the funnel shifts use the
+// amount modulo 32.
+__device__ __forceinline__ void xwords_near(double x, int cA, unsigned (&w)[4]) {
   const unsigned hi = hi32(x), lo = lo32(x);
-  const int e = (hi >> 20) & 0x7ff;  // >= 1 here: A - e <= 20 and A >= 1... e may still be 0 for zeros
-  const unsigned mh = (hi & 0xfffffu) | (e ? 0x100000u : 0u);
-  const int bo = (52 - A + max(e, 1)) & 31;
+  const unsigned bo = (hi >> 20) + (unsigned)cA;
+  const unsigned mh = (hi & 0xfffffu) | 0x100000u;
   w[0] = 0u;
-  w[1] = lo << bo;
+  w[1] = __funnelshift_l(0u, lo, bo);
   w[2] = __funnelshift_l(lo, mh, bo);
   w[3] = __funnelshift_l(mh, 0u, bo);
 }
-// t >= 32 for x aligned to A (zero counts as near: all its words are zero)
-__device__ __forceinline__ bool near_exp(double x, int A) {
-  const int e = (hi32(x) >> 20) & 0x7ff;
-  return e == 0 ? (hi32(x) & 0x7fffffffu) == 0u && lo32(x) == 0u : A - e <= 20;
-}
+// Smallest |x| high word that xwords_near accepts for alignment exponent A:
+// exponent at least max(A - 20, 1) (zeros and subnormals take xwords).
+__device__ __forceinline__ unsigned near_floor(int A) { return (unsigned)max(A - 20, 1) << 20; }
+__device__ __forceinline__ unsigned abs_hi(double x) { return hi32(x) & 0x7fffffffu; }
 
 // 8-byte asynchronous copy global -> shared; src_bytes 0 writes zeros.
 __device__ __forceinline__ void cp_async8z(unsigned dst, const void* src, unsigned src_bytes) {

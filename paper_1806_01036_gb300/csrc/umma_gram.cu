@@ -135,6 +135,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                              const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmy,
                              FxPart* __restrict__ parts, const int* gate) {
   static_assert(sizeof(T) == 8 || DIRECT, "FP32 operands are copied by the converter threads");
+  // The compile-time plans: (KXPC, PC) = (64, 32) with separate X and Y
+  // (V^T Y, 64 + 16 columns) and (16, 128) with X = Y (symmetric, 16
+  // columns); TMA loads, no padded columns.  Their A items fill the first KA
+  // item slots of every thread exactly, the B items (if any) the next slot of
+  // the first KYP * PC / 2 threads.
+  constexpr bool kHot = KXPC > 0;
+  constexpr bool kHotShared = KXPC == 16;
+  constexpr int KA = kHot ? KXPC * PC / 2 / kConvThreads : 0;
+  constexpr bool kSplit = kHot && !kHotShared;
+  static_assert(!kHot || ((KXPC == 64 && PC == 32) || (KXPC == 16 && PC == 128)), "compile-time plans");
+  static_assert(!kHot || (!DIRECT && !PAD && KYP == 16), "compile-time plans load by TMA");
+  static_assert(!kHot || (KA * kConvThreads == KXPC * PC / 2 && KA + (kHotShared ? 0 : 1) <= kMaxItems &&
+                          (kHotShared || KYP * PC / 2 <= kConvThreads)),
+                "compile-time plans fill whole item slots");
   if (gate && *gate == 0) return;
   // Y columns of one converter thread in a drain (four warps share a TMEM
   // lane quarter), handled NH times NY at a time
@@ -234,8 +248,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const unsigned bbase = pl.shared ? abase : abase + pl.a_bytes;
         for (int ks = 0; ks < P / 16; ++ks) {
           for (int q = 0; q < pl.nq; ++q) {
-            const int T = NS - pl.J * q;
-            const int Tp = KYP == 16 ? T : (T + 1) & ~1;  // N a multiple of 16
+            const int nt = NS - pl.J * q;
+            const int Tp = KYP == 16 ? nt : (nt + 1) & ~1;  // N a multiple of 16
             const unsigned long long ad =
                 sdesc(abase + (unsigned)(pl.J * q * kxp / 8) * SBO + (unsigned)ks * 256u, 128u, SBO);
             const unsigned long long bd = sdesc(bbase + (unsigned)ks * 256u, 128u, SBO);
@@ -367,14 +381,32 @@ __global__ void __launch_bounds__(kThreads, 1)
     // swizzled boxes, and the 32 digit words a warp stores per slab fill 128
     // contiguous bytes.  it_s: column << 16 | staging offset / 16; it_d:
     // digit offset | B operand << 31.
+    // In the hot plans the A items come first (k < KA, all threads) and the
+    // B items after them (k >= KA, threads below KYP * P / 2), so that an
+    // item's operand, and whether it exists, are known per k at compile
+    // time.
     const int half = P >> 1, ncg = nslots >> 3;
     const int nitems = nslots * half;
     unsigned it_s[kMaxItems], it_d[kMaxItems];
 #pragma unroll
     for (int k = 0; k < kMaxItems; ++k) {
-      const int i = tid + k * kConvThreads;
-      const int cl = i & 7, rl = (i >> 3) & 3, rest = i >> 5;
-      const int c = (rest % ncg) * 8 + cl, rh = rest / ncg, r = (rh * 4 + rl) * 2;
+      int c, rh, cl, rl;
+      if constexpr (kSplit) {
+        const bool kb = k >= KA;
+        const int i = kb ? tid + (k - KA) * kConvThreads : tid + k * kConvThreads;
+        const int g = kb ? KYP / 8 : KXPC / 8;  // column groups of the operand
+        cl = i & 7;
+        rl = (i >> 3) & 3;
+        c = ((i >> 5) % g) * 8 + cl + (kb ? KXPC : 0);
+        rh = (i >> 5) / g;
+      } else {
+        const int i = tid + k * kConvThreads;
+        cl = i & 7;
+        rl = (i >> 3) & 3;
+        c = ((i >> 5) % ncg) * 8 + cl;
+        rh = (i >> 5) / ncg;
+      }
+      const int r = (rh * 4 + rl) * 2;
       const bool isb = !pl.shared && c >= kxp;
       const int lc = isb ? c - kxp : c;
       const unsigned so = (isb ? (unsigned)(P / 16) * xbox : 0u) + (unsigned)(r >> 4) * (isb ? ybox : xbox) +
@@ -384,9 +416,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                  (unsigned)(lc & 7) * 16u + (unsigned)rl * 4u) |
                 ((unsigned)isb << 31);
       if constexpr (PAD) {  // bit 30: a padded column, whose digits stay zero
-        if (i < nitems && !(isb ? y0 + lc < ky : x0 + lc < kx)) it_d[k] |= 1u << 30;
+        if (tid + k * kConvThreads < nitems && !(isb ? y0 + lc < ky : x0 + lc < kx)) it_d[k] |= 1u << 30;
       }
     }
+    // item k exists for this thread; it belongs to the B operand
+    auto item_valid = [&](int k) -> bool {
+      if constexpr (kHot) return k < KA || (!kHotShared && k == KA && tid < KYP * PC / 2);
+      else return tid + k * kConvThreads < nitems;
+    };
+    auto item_b = [&](int k) -> bool {
+      if constexpr (kHot) return !kHotShared && k >= KA;
+      else return (it_d[k] >> 31) != 0u;
+    };
     const unsigned stride_a = (unsigned)kxp / 8u * SBO, stride_b = (unsigned)KYP / 8u * SBO;
     if constexpr (PAD) {  // the digit words of padded columns: zero once, in both buffers
 #pragma unroll
@@ -465,8 +506,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const unsigned char* st = stage + (size_t)(q & 1) * pl.stage_bytes;
 #pragma unroll
         for (int k = 0; k < kMaxItems; ++k)
-          v[k] = tid + k * kConvThreads < nitems ? *reinterpret_cast<const double2*>(st + ((it_s[k] & 0xffffu) << 4))
-                                                 : make_double2(0.0, 0.0);
+          v[k] = item_valid(k) ? *reinterpret_cast<const double2*>(st + ((it_s[k] & 0xffffu) << 4))
+                               : make_double2(0.0, 0.0);
       }
     };
     // largest exponent of each column of a panel into pmq (the exponent
@@ -536,22 +577,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       const unsigned e1024 = exp1024x2();
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
-        const bool valid = tid + k * kConvThreads < nitems && (!PAD || !(it_d[k] & 0x40000000u));
-        // every value of the warp's items within 20 binades of its alignment
-        // exponent (nearly always): the words without selects
-        const bool near = __all_sync(0xffffffffu, !valid || (near_exp(v[k].x, A[k]) && near_exp(v[k].y, A[k])));
+        const bool valid = item_valid(k) && (!PAD || !(it_d[k] & 0x40000000u));
+        // every value of the warp's items normal and within 20 binades of its
+        // alignment exponent (nearly always): the words without selects
+        const bool near =
+            __all_sync(0xffffffffu, !valid || min(abs_hi(v[k].x), abs_hi(v[k].y)) >= near_floor(A[k]));
         if (valid) {
           unsigned wa[4], wb[4];
           const unsigned signs = ((hi32(v[k].x) >> 31) << 15) | (hi32(v[k].y) & 0x80000000u);
-          // operand A or B (warp-uniform): two copies of the stores, so that
-          // with a compile-time plan the slab stride is an immediate offset
+          // operand A or B (warp-uniform; known at compile time in the hot
+          // plans): two copies of the stores, so that with a compile-time
+          // plan the slab stride is an immediate offset
           unsigned char* dst = dbuf + (it_d[k] & (PAD ? 0x3fffffffu : 0x7fffffffu));
           if (near) {
-            xwords_near(v[k].x, A[k], wa);
-            xwords_near(v[k].y, A[k], wb);
+            xwords_near(v[k].x, 52 - A[k], wa);
+            xwords_near(v[k].y, 52 - A[k], wb);
             add_bias_near(wa);
             add_bias_near(wb);
-            if (it_d[k] >> 31)
+            if (item_b(k))
               store_bal_digits_near<0>(dst, stride_b, pair_lanes(wa, wb), pair_sign(signs, e1024));
             else
               store_bal_digits_near<0>(dst, stride_a, pair_lanes(wa, wb), pair_sign(signs, e1024));
@@ -560,7 +603,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             xwords(v[k].y, A[k], wb);
             add_bias(wa);
             add_bias(wb);
-            if (it_d[k] >> 31)
+            if (item_b(k))
               store_bal_digits<0>(dst, stride_b, pair_lanes(wa, wb), pair_sign(signs, e1024));
             else
               store_bal_digits<0>(dst, stride_a, pair_lanes(wa, wb), pair_sign(signs, e1024));

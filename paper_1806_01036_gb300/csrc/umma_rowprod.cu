@@ -76,6 +76,9 @@ constexpr size_t kMinSmem = 120 * 1024;      // keeps one CTA per SM (TMEM: 512 
 // previous tile's epilogue.
 template <int W>
 constexpr bool kStageValues = W <= 8;
+#ifndef EO_ROW_NEAR
+#define EO_ROW_NEAR(W) ((W) >= 8)
+#endif
 
 // Diagonal d of a tile sums (d + 1) kin <= (d + 1) 4 W digit products of
 // magnitude <= 127^2.  Diagonals d <= kRoundDiag stay below 2^22 units, so
@@ -431,9 +434,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       // the row's exponent: max of the |x| high words over the four threads
       // of the row (a row of subnormals and zeros has exponent field 0 and
       // is aligned to 1, the subnormals' own exponent)
-      unsigned key = 0;
+      unsigned key = 0, low = 0xffffffffu;  // largest and smallest |x| high word
 #pragma unroll
-      for (int k = 0; k < W; ++k) key = max(key, hi32(v[k]) & 0x7fffffffu);
+      for (int k = 0; k < W; ++k) {
+        key = max(key, abs_hi(v[k]));
+        low = min(low, abs_hi(v[k]));
+      }
       key = max(key, __shfl_xor_sync(0xffffffffu, key, 8));
       key = max(key, __shfl_xor_sync(0xffffffffu, key, 16));
       const int e = (int)(key >> 20);
@@ -444,19 +450,15 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       PairLanes P[W / 2];  // the W values as interleaved pairs
       unsigned sg[W / 2];
-      // every value of the warp within 20 binades of its row's exponent
-      // (nearly always): the aligned words without selects (for W >= 8; with
-      // four values a thread the vote costs more than it saves: measured)
-      bool near_all = W >= 8;
-#pragma unroll
-      for (int k = 0; k < W; ++k) near_all = near_all && near_exp(v[k], Ar);
-      const bool near = W >= 8 && __all_sync(0xffffffffu, near_all);
+      // every value of the warp normal and within 20 binades of its row's
+      // exponent (nearly always): the aligned words without selects
+      const bool near = EO_ROW_NEAR(W) && __all_sync(0xffffffffu, low >= near_floor(Ar));
 #pragma unroll
       for (int m = 0; m < W / 2; ++m) {
         unsigned xa[4], xb[4];
         if (near) {
-          xwords_near(v[2 * m], Ar, xa);
-          xwords_near(v[2 * m + 1], Ar, xb);
+          xwords_near(v[2 * m], 52 - Ar, xa);
+          xwords_near(v[2 * m + 1], 52 - Ar, xb);
         } else {
           xwords(v[2 * m], Ar, xa);
           xwords(v[2 * m + 1], Ar, xb);
