@@ -68,14 +68,19 @@ namespace {
 using namespace fx;
 using namespace umma;
 
+// 19 converter warps and the MMA warp: five warps per SM sub-partition, so
+// that each may hold 96 registers (a sixth warp on one of them caps every
+// thread at 80, and the kernel spills).
 #ifndef EO_GRAM_CONV_WARPS
-#define EO_GRAM_CONV_WARPS 16
+#define EO_GRAM_CONV_WARPS 19
 #endif
-constexpr int kConvWarps = EO_GRAM_CONV_WARPS;  // staging, conversion and drains (8 or 16)
+constexpr int kConvWarps = EO_GRAM_CONV_WARPS;  // staging and conversion (16 to 19)
+constexpr int kDrainWarps = 16;  // the first 16 also drain TMEM: 4 per lane quarter
 constexpr int kConvThreads = 32 * kConvWarps;
 constexpr int kThreads = kConvThreads + 32;  // plus one MMA-issuing warp
+static_assert(kConvWarps >= kDrainWarps, "every drain warp converts");
 constexpr int kLanes = 128;   // MMA M = TMEM lanes
-constexpr int kMaxItems = 48 / kConvWarps;  // items (two rows of one column) per thread and panel
+constexpr int kMaxItems = 3;  // items (two rows of one column) per thread and panel
 constexpr int kOffsetDigits = 2148;
 constexpr int kFoldRows = 8192;  // rows between folds of the 32-bit running sums
 constexpr size_t kSmemCap = 225 * 1024;
@@ -100,8 +105,9 @@ struct UPlan {
 };
 
 // ------------------------------------------------------------ kernel
-// Warps 0..15 stage, scan, convert and drain (named barrier 1); warp 16
-// issues the MMAs: per panel p it waits for ready[p & 1] (512 arrivals: the
+// Warps 0..kConvWarps-1 stage, scan and convert (named barrier 1), the
+// first 16 of them also drain TMEM; warp kConvWarps issues the MMAs: per
+// panel p it waits for ready[p & 1] (one arrival per converter thread: the
 // digits of p are in buffer p & 1 and TMEM is drained if due), issues the
 // MMAs and commits them to full[p & 1], which the converters wait on before
 // they reuse the buffer (panel p + 2) or read TMEM.
@@ -137,22 +143,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   static_assert(sizeof(T) == 8 || DIRECT, "FP32 operands are copied by the converter threads");
   // The compile-time plans: (KXPC, PC) = (64, 32) with separate X and Y
   // (V^T Y, 64 + 16 columns) and (16, 128) with X = Y (symmetric, 16
-  // columns); TMA loads, no padded columns.  Their A items fill the first KA
-  // item slots of every thread exactly, the B items (if any) the next slot of
-  // the first KYP * PC / 2 threads.
+  // columns); TMA loads, no padded columns.  Their items are numbered A
+  // items first (kNA of them), then B items (kNB), so that whether an item
+  // exists and which operand it belongs to is known per item slot at compile
+  // time or is uniform over a warp.
   constexpr bool kHot = KXPC > 0;
   constexpr bool kHotShared = KXPC == 16;
-  constexpr int KA = kHot ? KXPC * PC / 2 / kConvThreads : 0;
-  constexpr bool kSplit = kHot && !kHotShared;
+  constexpr int kNA = kHot ? KXPC * PC / 2 : 0, kNB = kHot && !kHotShared ? KYP * PC / 2 : 0;
   static_assert(!kHot || ((KXPC == 64 && PC == 32) || (KXPC == 16 && PC == 128)), "compile-time plans");
   static_assert(!kHot || (!DIRECT && !PAD && KYP == 16), "compile-time plans load by TMA");
-  static_assert(!kHot || (KA * kConvThreads == KXPC * PC / 2 && KA + (kHotShared ? 0 : 1) <= kMaxItems &&
-                          (kHotShared || KYP * PC / 2 <= kConvThreads)),
-                "compile-time plans fill whole item slots");
+  static_assert(!kHot || (kNA + kNB <= kMaxItems * kConvThreads && kNA % 32 == 0 && kNB % 32 == 0),
+                "compile-time plans: whole warps of items");
   if (gate && *gate == 0) return;
   // Y columns of one converter thread in a drain (four warps share a TMEM
   // lane quarter), handled NH times NY at a time
-  constexpr int NYT = KYP * 4 / kConvWarps;
+  constexpr int NYT = KYP * 4 / kDrainWarps;
   constexpr int NY = NYT < 4 ? NYT : 4;
   constexpr int NH = NYT / NY;
   const int kxp = KXPC ? KXPC : pl.kxp, P = PC ? PC : pl.P;
@@ -231,7 +236,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   // the partial sums of this thread's lane: lane block jl (digit phase), X column xl
   const int Lq = (warp & 3) * 32, L = Lq + lane;
   const int jl = L >> (31 - __clz(kxp)), xl = L & (kxp - 1);
-  const int yq = (warp >> 2) * NYT;  // first of this thread's NYT Y columns
+  const int yq = (warp >> 2) * NYT;  // first of this thread's NYT Y columns (drain warps)
+  const bool drainer = warp < kDrainWarps;
   i128 W[NYT];
 #pragma unroll
   for (int y = 0; y < NYT; ++y) W[y] = 0;
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- converters: staging, exponents, digits, drains
     const unsigned tacc = taddr + ((unsigned)Lq << 16) + (unsigned)yq;
     const unsigned tsum = tacc + 256u;
-    {
+    if (drainer) {
       unsigned z[3][NY];
 #pragma unroll
       for (int u = 0; u < 3; ++u)
@@ -381,19 +387,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     // swizzled boxes, and the 32 digit words a warp stores per slab fill 128
     // contiguous bytes.  it_s: column << 16 | staging offset / 16; it_d:
     // digit offset | B operand << 31.
-    // In the hot plans the A items come first (k < KA, all threads) and the
-    // B items after them (k >= KA, threads below KYP * P / 2), so that an
-    // item's operand, and whether it exists, are known per k at compile
-    // time.
+    // In the hot plans the kNA items of the A operand come first and the kNB
+    // items of the B operand after them (item_valid, item_b below).
     const int half = P >> 1, ncg = nslots >> 3;
     const int nitems = nslots * half;
     unsigned it_s[kMaxItems], it_d[kMaxItems];
 #pragma unroll
     for (int k = 0; k < kMaxItems; ++k) {
       int c, rh, cl, rl;
-      if constexpr (kSplit) {
-        const bool kb = k >= KA;
-        const int i = kb ? tid + (k - KA) * kConvThreads : tid + k * kConvThreads;
+      if constexpr (kHot) {
+        // an empty slot (past the kNA + kNB items) takes item 0's column, so
+        // that every column index stays below nslots
+        const int i0 = tid + k * kConvThreads;
+        const bool live = i0 < kNA + kNB;
+        const bool kb = live && i0 >= kNA;
+        const int i = kb ? i0 - kNA : (live ? i0 : 0);
         const int g = kb ? KYP / 8 : KXPC / 8;  // column groups of the operand
         cl = i & 7;
         rl = (i >> 3) & 3;
@@ -421,12 +429,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     // item k exists for this thread; it belongs to the B operand
     auto item_valid = [&](int k) -> bool {
-      if constexpr (kHot) return k < KA || (!kHotShared && k == KA && tid < KYP * PC / 2);
-      else return tid + k * kConvThreads < nitems;
+      if constexpr (kHot) {
+        if (k * kConvThreads >= kNA + kNB) return false;
+        if ((k + 1) * kConvThreads <= kNA + kNB) return true;
+        return tid + k * kConvThreads < kNA + kNB;
+      } else {
+        return tid + k * kConvThreads < nitems;
+      }
     };
     auto item_b = [&](int k) -> bool {
-      if constexpr (kHot) return !kHotShared && k >= KA;
-      else return (it_d[k] >> 31) != 0u;
+      if constexpr (kHot) {
+        if (kNB == 0 || (k + 1) * kConvThreads <= kNA) return false;
+        if (k * kConvThreads >= kNA) return true;
+        return tid + k * kConvThreads >= kNA;
+      } else {
+        return (it_d[k] >> 31) != 0u;
+      }
     };
     const unsigned stride_a = (unsigned)kxp / 8u * SBO, stride_b = (unsigned)KYP / 8u * SBO;
     if constexpr (PAD) {  // the digit words of padded columns: zero once, in both buffers
@@ -521,6 +539,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool g = false;
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
+        if (!item_valid(k)) continue;  // an empty slot
         // the larger magnitude's bit pattern; its exponent exceeds te[k]
         // exactly when the pattern reaches (te[k] + 1) << 20.  A panel's
         // maxima are only ever used as max(running exponent, panel
@@ -615,9 +634,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       // this thread's accumulators (its own TMEM lanes and columns) are drained
       // before it marks panel p ready
       if ((grew || undrained >= pl.drain_panels) && undrained > 0) {
-        // all MMAs so far (the last commit is panel p-1's) are done before TMEM is read
-        mbar_wait(fb0 + 8u * ((p - 1) & 1), (unsigned)((p - 1) >> 1) & 1u, &bad);
-        tc_fence_after();
         // a full drain before a fold or a growth; otherwise the groups whose
         // period ends here
         const bool full = grew || drains + 1 == pl.fold_drains;
@@ -630,15 +646,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (g0 == g + 1 && ((ev + 1) & (per - 1)) == 0) g0 = g;
           }
         }
-        drain(g0);
+        if (drainer) {
+          // all MMAs so far (the last commit is panel p-1's) are done before TMEM is read
+          mbar_wait(fb0 + 8u * ((p - 1) & 1), (unsigned)((p - 1) >> 1) & 1u, &bad);
+          tc_fence_after();
+          drain(g0);
+          if (full) fold();
+        }
         ++drains;
         ++ev;
         if (full) {
-          fold();
           drains = 0;
           ev = 0;
         }
-        if (grew) {  // totals onto the new grid: divide by 2^(growth of both columns' exponents)
+        if (grew && drainer) {  // totals onto the new grid: divide by 2^(growth of both columns' exponents)
           const int ysb = pl.shared ? 0 : kxp;
 #pragma unroll
           for (int y = 0; y < NYT; ++y) {
@@ -675,7 +696,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if constexpr (DIRECT) asm volatile("cp.async.wait_all;" ::: "memory");  // the last (empty) copies
     // last drain and fold
-    if (npan > 0) {
+    if (npan > 0 && drainer) {
       mbar_wait(fb0 + 8u * ((npan - 1) & 1), (unsigned)((npan - 1) >> 1) & 1u, &bad);
       tc_fence_after();
       drain(0);
@@ -692,7 +713,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   // sum the lane blocks (digit phase j) of every output and write the partials
   i128* red = reinterpret_cast<i128*>(dig);  // 128 lanes x KYP entries (the MMAs are done)
-  if (warp < kConvWarps) {
+  if (warp < kDrainWarps) {
 #pragma unroll
     for (int y = 0; y < NYT; ++y) red[L * KYP + yq + y] = W[y];
   }
