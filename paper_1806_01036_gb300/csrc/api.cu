@@ -114,6 +114,13 @@ static bool use_umma_gram(int kx, int ky) {
   return std::max(kx, ky) >= 16;
 }
 
+// Kernels one launch_dd_gram call launches.
+static uint64_t dd_gram_launches(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y,
+                                 int64_t ldy, bool sym) {
+  return use_umma_gram(kx, sym ? kx : ky) ? (uint64_t)umma_gram_launches(n, kx, X, ldx, ky, Y, ldy, sym)
+                                          : kGramLaunches;
+}
+
 size_t dd_gram_scratch(int64_t n, int kx, int ky, bool sym) {
   return std::max(fx_gram_scratch_bytes(n, kx, ky, sym), umma_gram_scratch_bytes(n, kx, ky, sym));
 }
@@ -191,7 +198,9 @@ cudaError_t enqueue_orth_step(const OrthArgs& a, const OrthRes& r, int p, OrthSt
         e = launch_gram(mode, a.n, a.k, a.X, a.ldx, a.k, Y, ldy, !b, r.parts, ws->Mh, ws->Ml, KMAX, &st->gate[2 * p],
                         r.stream);
       }
-      *launches += kGramLaunches;
+      *launches += fx ? dd_gram_launches(a.n, a.k, static_cast<const double*>(a.X), a.ldx, a.k,
+                                         static_cast<const double*>(Y), ldy, !b)
+                      : kGramLaunches;
       if (e == cudaSuccess && b) {
         e = launch_symmetrize(a.k, ws->Mh, ws->Ml, KMAX, &st->gate[2 * p], r.stream);
         *launches += 1;
@@ -261,7 +270,7 @@ eo_status apply_projection(eo_ctx* ctx, int64_t n, int kv, const double* V, int6
       EO_CUDA(launch_dd_gram(n, k, Yout, ldyo, k, Yout, ldyo, true, parts_of(ctx), M_hi, M_lo, ldm, gate,
                              ctx->stream),
               "eo_project (Gram)");
-      ctx->launches += kGramLaunches;
+      ctx->launches += dd_gram_launches(n, k, Yout, ldyo, k, Yout, ldyo, true);
     }
   } else {
     const Mode mode = pipe_mode(prec);
@@ -399,6 +408,9 @@ eo_status eo_gram(eo_ctx* ctx, int64_t n, int kx, const void* X, int64_t ldx, in
     EO_CUDA(launch_dd_gram(n, kx, static_cast<const double*>(X), ldx, ky, static_cast<const double*>(sym ? X : Y),
                            ldy, sym, parts_of(ctx), G_hi, G_lo, ldg, nullptr, ctx->stream),
             "eo_gram");
+    ctx->launches += dd_gram_launches(n, kx, static_cast<const double*>(X), ldx, ky,
+                                      static_cast<const double*>(sym ? X : Y), ldy, sym);
+    return EO_OK;
   } else if (prec == EO_F32) {
     eo_status s = ensure_scratch(ctx, f32_gram_scratch(n, kx, ky, sym));
     if (s != EO_OK) return s;
@@ -536,7 +548,8 @@ eo_status eo_cholqr_piv(eo_ctx* ctx, int64_t n, int k, double* X, int64_t ldx, d
     else
       EO_CUDA(launch_update(mode, n, k, X, ldx, ws->Zh, ws->Zl, tri, &st->gate[2 * p + 1], ctx->stream),
               "eo_cholqr_piv (update)");
-    ctx->launches += kGramLaunches + 1 + (fx ? fx_update_launches(n, k, parts_bytes) : 1);
+    ctx->launches += (fx ? dd_gram_launches(n, k, X, ldx, k, X, ldx, true) : kGramLaunches) + 1 +
+                     (fx ? fx_update_launches(n, k, parts_bytes) : 1);
   }
   return EO_OK;
 }

@@ -93,10 +93,12 @@ struct __align__(16) FxPart {
   int s, flag;
   long long pad;
 };
-// Sum the row-chunk partials of every entry exactly and round once:
-// G_hi/G_lo (kx-by-ky, ldg; the upper triangle mirrored when sym).
+// Sum the row-chunk partials of every entry exactly and round once: entry
+// (i, j) of the kx-by-ky product into G(i, jo + j) (G_hi/G_lo, ldg).  sym:
+// the product is columns jo .. jo + ky - 1 of a symmetric G; only entries
+// with i <= jo + j are summed, each also written to G(jo + j, i).
 cudaError_t launch_fx_reduce(int kx, int ky, bool sym, int nchunks, const FxPart* parts, double* G_hi, double* G_lo,
-                             int ldg, const int* gate, cudaStream_t st);
+                             int ldg, const int* gate, cudaStream_t st, int jo = 0);
 // The same product on the tcgen05 tensor cores (umma_gram.cu); same partial format.
 // ctas > 0 caps the CTAs of the partial-sum launch (a launch shape picked by
 // the batch autotuner); 0 = one CTA per SM.  The scratch sizes below hold for
@@ -106,8 +108,14 @@ cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, in
                              bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
                              cudaStream_t st, int ctas = 0);
 size_t fx_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym);
-// CTAs of the partial-sum launch of each engine under a cap (0 = none).
+// CTAs of the partial-sum launch of each engine under a cap (0 = none; the
+// largest launch of a product run as column strips).
 int umma_gram_ctas(int64_t n, int kx, int ky, bool sym, int ctas);
+// Kernels launch_umma_gram launches for these operands: 2 (partial sums and
+// their reduction) per launch, 2 per column strip of a symmetric product
+// with more than 16 columns.
+int umma_gram_launches(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
+                       bool sym);
 // The same exact sums for FP32 operands (the EO_F32 mode), each value
 // widened to FP64 exactly: G_hi = the sum rounded once (G_lo its low part).
 bool umma_gram_f32_supported(const float* X, const float* Y, int kx, int ky, bool sym);

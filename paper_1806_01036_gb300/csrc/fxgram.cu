@@ -338,13 +338,14 @@ constexpr int kRedThreads = 256;
 
 __global__ void __launch_bounds__(kRedThreads) fx_gram_reduce_kernel(int kx, int ky, int sym, int nchunks,
                                                                      const FxPart* __restrict__ parts, double* G_hi,
-                                                                     double* G_lo, int ldg, const int* gate) {
+                                                                     double* G_lo, int ldg, const int* gate,
+                                                                     int jo) {
   if (gate && *gate == 0) return;
   const int e = (blockIdx.x * kRedThreads + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int E = kx * ky;
   if (e >= E) return;
   const int i = e % kx, j = e / kx;
-  if (sym && i > j) return;
+  if (sym && i > jo + j) return;  // X = Y: the upper triangle of G, mirrored below
   int smax = -1 << 30, fl = 0;
   for (int c = lane; c < nchunks; c += 32) {
     const FxPart& p = parts[(size_t)c * E + e];
@@ -370,11 +371,12 @@ __global__ void __launch_bounds__(kRedThreads) fx_gram_reduce_kernel(int kx, int
       const i128 w = acc.narrow(extra);
       w_to_dd(w, smax + extra, hi, lo);
     }
-    G_hi[(size_t)j * ldg + i] = hi;
-    if (G_lo) G_lo[(size_t)j * ldg + i] = lo;
-    if (sym && i != j) {
-      G_hi[(size_t)i * ldg + j] = hi;
-      if (G_lo) G_lo[(size_t)i * ldg + j] = lo;
+    // entry (i, jo + j) of G; with X = Y its mirror (jo + j, i) too
+    G_hi[(size_t)(jo + j) * ldg + i] = hi;
+    if (G_lo) G_lo[(size_t)(jo + j) * ldg + i] = lo;
+    if (sym && i != jo + j) {
+      G_hi[(size_t)i * ldg + jo + j] = hi;
+      if (G_lo) G_lo[(size_t)i * ldg + jo + j] = lo;
     }
   }
 }
@@ -442,10 +444,10 @@ int num_chunks(int64_t n, const GramPlan& p, int ctas = 0) {
 }  // namespace
 
 cudaError_t launch_fx_reduce(int kx, int ky, bool sym, int nchunks, const FxPart* parts, double* G_hi, double* G_lo,
-                             int ldg, const int* gate, cudaStream_t st) {
+                             int ldg, const int* gate, cudaStream_t st, int jo) {
   const int E = kx * ky;
   fx_gram_reduce_kernel<<<(E * 32 + kRedThreads - 1) / kRedThreads, kRedThreads, 0, st>>>(
-      kx, ky, sym ? 1 : 0, nchunks, parts, G_hi, G_lo, ldg, gate);
+      kx, ky, sym ? 1 : 0, nchunks, parts, G_hi, G_lo, ldg, gate, jo);
   return cudaGetLastError();
 }
 
@@ -480,7 +482,7 @@ cudaError_t launch_fx_gram(int64_t n, int kx, const double* X, int64_t ldx, int 
   fx_gram_partial_kernel<<<grid, kThreads, smem, st>>>(n, kx, X, ldx, ky, Y, ldy, plan, rpc, parts, gate);
   const int E = kx * ky;
   fx_gram_reduce_kernel<<<(E * 32 + kRedThreads - 1) / kRedThreads, kRedThreads, 0, st>>>(
-      kx, ky, sym ? 1 : 0, chunks, parts, G_hi, G_lo, ldg, gate);
+      kx, ky, sym ? 1 : 0, chunks, parts, G_hi, G_lo, ldg, gate, 0);
   return cudaGetLastError();
 }
 

@@ -900,39 +900,55 @@ cudaError_t umma_wait_selftest(unsigned long long limit_ns, cudaStream_t st) {
 
 cudaError_t umma_gram_take_wait_record(unsigned* out) { return take_wait_record(out); }
 
-size_t umma_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym) {
-  if (sym) ky = kx;
-  return (size_t)num_chunks(n, make_plan(kx, ky, sym)) * (size_t)kx * ky * sizeof(FxPart);
-}
+namespace {
 
-int umma_gram_ctas(int64_t n, int kx, int ky, bool sym, int ctas) {
-  if (sym) ky = kx;
-  const UPlan plan = make_plan(kx, ky, sym);
-  return plan.ntx * plan.nty * capped_chunks(n, plan, ctas);
-}
-
-cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
-                             bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
-                             cudaStream_t st, int ctas) {
-  if (sym) {
-    Y = X;
-    ldy = ldx;
-    ky = kx;
-  }
-  const UPlan plan = make_plan(kx, ky, sym);
+// How one product reaches its operands: by TMA (tensor maps) or by the
+// converter threads' own copies (direct); neither: the integer limbs.
+struct Route {
+  UPlan plan;
+  bool tma_ok, direct;
+  CUtensorMap tmx, tmy;
+};
+void route(Route& r, int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
+           bool sym) {
+  r.plan = make_plan(kx, ky, sym);
+  r.tmx = CUtensorMap{};
+  r.tmy = CUtensorMap{};
   // TMA addresses 16-byte aligned bases and leading dimensions of whole 16-byte units
-  alignas(64) CUtensorMap tmx{}, tmy{};
-  const bool tma_ok = (uintptr_t)X % 16 == 0 && (uintptr_t)Y % 16 == 0 && ldx % 2 == 0 && ldy % 2 == 0 &&
-                      n < (1ll << 31) && make_map(&tmx, X, n, kx, ldx, plan.kxp) &&
-                      make_map(&tmy, Y, n, ky, ldy, plan.kyp);
-  // without TMA: the converters copy their own items (when the slots fit), else the integer limbs.
+  r.tma_ok = (uintptr_t)X % 16 == 0 && (uintptr_t)Y % 16 == 0 && ldx % 2 == 0 && ldy % 2 == 0 && n < (1ll << 31) &&
+             make_map(&r.tmx, X, n, kx, ldx, r.plan.kxp) && make_map(&r.tmy, Y, n, ky, ldy, r.plan.kyp);
   // EO_DD_GRAM_LOADS=direct uses the copies for TMA-addressable operands too.
   const char* lm = getenv("EO_DD_GRAM_LOADS");
   const bool force_direct = lm && lm[0] == 'd';
-  const bool direct = (!tma_ok || force_direct) && (uintptr_t)X % 8 == 0 && (uintptr_t)Y % 8 == 0 &&
-                      plan_smem_direct(plan) <= kSmemCap;
-  if (!tma_ok && !direct)
-    return launch_fx_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st, ctas);
+  r.direct = (!r.tma_ok || force_direct) && (uintptr_t)X % 8 == 0 && (uintptr_t)Y % 8 == 0 &&
+             plan_smem_direct(r.plan) <= kSmemCap;
+}
+
+// A symmetric product with more than 16 columns runs as column strips of 16:
+// strip c0 .. c1 - 1 is X[:, 0:c1]^T X[:, c0:c1] (the first one the symmetric
+// 16-column product), of which the reduction keeps the entries on and above
+// the diagonal of G and mirrors them (so G is exactly symmetric).  Each
+// value is converted once per strip that reads it, where the one-tile plans
+// of X^T Y over all columns convert it once per 16-column Y tile and once
+// more as the Y operand.
+bool use_strips(int64_t n, int kx, const double* X, int64_t ldx, bool sym) {
+  if (!sym || kx <= 16) return false;
+  for (int c0 = 0; c0 < kx; c0 += 16) {
+    const int c1 = std::min(kx, c0 + 16);
+    Route r;
+    route(r, n, c1, X, ldx, c1 - c0, X + (size_t)c0 * ldx, ldx, c0 == 0);
+    if (!r.tma_ok && !r.direct) return false;
+  }
+  return true;
+}
+
+cudaError_t launch_one(const Route& r, int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y,
+                       int64_t ldy, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
+                       cudaStream_t st, int ctas, bool sym, int jo) {
+  const UPlan& plan = r.plan;
+  const bool direct = r.direct;
+  const CUtensorMap& tmx = r.tmx;
+  const CUtensorMap& tmy = r.tmy;
   const int chunks = capped_chunks(n, plan, ctas);
   int64_t rpc = (n + chunks - 1) / chunks;
   rpc = std::max<int64_t>(plan.P, (rpc + plan.P - 1) / plan.P * plan.P);
@@ -959,7 +975,72 @@ cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, in
                : (pad ? EO_UMMA_LAUNCH(8, false, true) : EO_UMMA_LAUNCH(8, false, false));
 #undef EO_UMMA_LAUNCH
   if (e != cudaSuccess) return e;
-  return launch_fx_reduce(kx, ky, sym, chunks, parts, G_hi, G_lo, ldg, gate, st);
+  return launch_fx_reduce(kx, ky, sym, chunks, parts, G_hi, G_lo, ldg, gate, st, jo);
+}
+
+}  // namespace
+
+size_t umma_gram_scratch_bytes(int64_t n, int kx, int ky, bool sym) {
+  if (sym) ky = kx;
+  size_t b = (size_t)num_chunks(n, make_plan(kx, ky, sym)) * (size_t)kx * ky * sizeof(FxPart);
+  if (sym && kx > 16) {  // the column strips (one after another: the largest)
+    for (int c0 = 0; c0 < kx; c0 += 16) {
+      const int c1 = std::min(kx, c0 + 16);
+      b = std::max(b, (size_t)num_chunks(n, make_plan(c1, c1 - c0, c0 == 0)) * (size_t)c1 * (c1 - c0) *
+                          sizeof(FxPart));
+    }
+  }
+  return b;
+}
+
+int umma_gram_ctas(int64_t n, int kx, int ky, bool sym, int ctas) {
+  if (sym) ky = kx;
+  const UPlan plan = make_plan(kx, ky, sym);
+  int c = plan.ntx * plan.nty * capped_chunks(n, plan, ctas);
+  if (sym && kx > 16) {
+    for (int c0 = 0; c0 < kx; c0 += 16) {
+      const int c1 = std::min(kx, c0 + 16);
+      const UPlan ps = make_plan(c1, c1 - c0, c0 == 0);
+      c = std::max(c, ps.ntx * ps.nty * capped_chunks(n, ps, ctas));
+    }
+  }
+  return c;
+}
+
+int umma_gram_launches(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
+                       bool sym) {
+  (void)ky;
+  (void)Y;
+  (void)ldy;
+  return use_strips(n, kx, X, ldx, sym) ? 2 * ((kx + 15) / 16) : 2;
+}
+
+cudaError_t launch_umma_gram(int64_t n, int kx, const double* X, int64_t ldx, int ky, const double* Y, int64_t ldy,
+                             bool sym, void* scratch, double* G_hi, double* G_lo, int ldg, const int* gate,
+                             cudaStream_t st, int ctas) {
+  if (sym) {
+    Y = X;
+    ldy = ldx;
+    ky = kx;
+  }
+  if (use_strips(n, kx, X, ldx, sym)) {
+    for (int c0 = 0; c0 < kx; c0 += 16) {
+      const int c1 = std::min(kx, c0 + 16);
+      const double* Xs = X + (size_t)c0 * ldx;
+      Route r;
+      route(r, n, c1, X, ldx, c1 - c0, Xs, ldx, c0 == 0);
+      cudaError_t e =
+          launch_one(r, n, c1, X, ldx, c1 - c0, Xs, ldx, scratch, G_hi, G_lo, ldg, gate, st, ctas, true, c0);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  Route r;
+  route(r, n, kx, X, ldx, ky, Y, ldy, sym);
+  // without TMA: the converters copy their own items (when the slots fit), else the integer limbs
+  if (!r.tma_ok && !r.direct)
+    return launch_fx_gram(n, kx, X, ldx, ky, Y, ldy, sym, scratch, G_hi, G_lo, ldg, gate, st, ctas);
+  return launch_one(r, n, kx, X, ldx, ky, Y, ldy, scratch, G_hi, G_lo, ldg, gate, st, ctas, sym, 0);
 }
 
 bool umma_gram_f32_supported(const float* X, const float* Y, int kx, int ky, bool sym) {

@@ -163,9 +163,13 @@ def test_cholqr_f32_wide_block(eo, ctx):
 @pytest.mark.parametrize("n,kx,ky,sym", [(1, 1, 1, True), (33, 3, 3, True), (1000, 8, 8, False), (4099, 13, 5, False),
                                          (100_003, 16, 16, True), (20_000, 64, 64, True), (20_001, 64, 16, False),
                                          (70_001, 2, 7, False), (50_000, 40, 24, False), (30_017, 33, 33, True),
-                                         (131, 17, 9, False), (9_000, 64, 12, False), (5_003, 48, 16, False)])
+                                         (131, 17, 9, False), (9_000, 64, 12, False), (5_003, 48, 16, False),
+                                         (9_000, 24, 24, True), (20_001, 48, 48, True)])
 def test_gram_dd_both_engines(eo, ctx, monkeypatch, engine, n, kx, ky, sym):
-    """The integer-limb and the tcgen05 digit engines of EO_DD against the oracle."""
+    """The integer-limb and the tcgen05 digit engines of EO_DD against the
+    oracle.  A symmetric product with more than 16 columns runs on the tensor
+    cores as column strips of 16 (a partial last strip at k = 24, 33; odd n:
+    operands copied by the converter threads); it is exactly symmetric."""
     monkeypatch.setenv("EO_DD_GRAM_ENGINE", engine)
     x = synth.gaussian(n, kx, 400 + kx)
     y = x if sym else synth.gaussian(n, ky, 500 + ky)
@@ -175,7 +179,7 @@ def test_gram_dd_both_engines(eo, ctx, monkeypatch, engine, n, kx, ky, sym):
     tol = dd_gram_tol(x, y, rh, 1)
     assert np.all(err <= tol), float(np.max(err / tol))
     if sym:
-        assert np.array_equal(host(gh), host(gh).T)
+        assert np.array_equal(host(gh), host(gh).T) and np.array_equal(host(gl), host(gl).T)
 
 
 @pytest.mark.parametrize("engine", ["int", "umma"])
