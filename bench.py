@@ -227,12 +227,24 @@ DIGIT_PAIRS = 120  # FP16 digit-pair products per multiply-add of the compensate
 
 def gram_traffic(n, kv, k):
     """DRAM bytes of one V^T Y launch of the tensor-core Gram kernel, from one
-    ncu capture at n = 1e6, kv = 64, k = 16 (dram__bytes_read.sum 640.1 MB,
-    dram__bytes_write.sum 3.65 MB of row-chunk partials); reads scale with
-    the rows, the partials do not.  None for other shapes."""
+    ncu capture of the full-size launch (4e6 rows, kv = 64, k = 16:
+    dram__bytes_read.sum 2,560.22 MB, dram__bytes_write.sum 3.04 MB of
+    row-chunk partials); reads scale with the rows, the partials do not.
+    None for other shapes."""
     if (kv, k) != (64, 16):
         return None
-    return 640.143104e6 * n / 1e6 + 3.650048e6
+    return 2560.219904e6 * n / 4e6 + 3.041024e6
+
+
+def apply_traffic(n, kv, k):
+    """DRAM bytes of one projection launch (umma_rowprod_kernel<16>) at
+    kv = 64, k = 16, from one ncu capture of the full-size launch (4e6 rows:
+    dram__bytes_read.sum 2,560.17 MB, dram__bytes_write.sum 497.52 MB; the
+    rest of the 512 MB of Y~ was still in L2 when the kernel ended); None for
+    other shapes."""
+    if (n, kv, k) != (4_000_000, 64, 16):
+        return None
+    return 2560.165376e6 + 497.521408e6
 
 
 def peak_tensor():
@@ -333,36 +345,39 @@ def run_eo(a):
     ms = total_ms / a.steps
     value = weak_scaling_value(ws, nbytes, ms)
 
-    # roofline of the dominant kernel, umma_gram_partial_kernel<16> (the
-    # compensated Gram products V^T Y, M and Q^T Q; measured on its V^T Y
-    # launch): the path streams its operands from HBM, so the bound is the
+    # roofline of the dominant kernel: the projection umma_rowprod_kernel<16>
+    # (compensated Y - V C; the largest launch of the step, ahead of the
+    # V^T Y Gram umma_gram_partial_kernel<16>, whose roofline is kept beside
+    # it).  The path streams its operands from HBM, so the bound is the
     # measured copy bandwidth and `achieved` counts the algorithmic bytes
-    # (V and Y read once) over the launch's CUDA-event time.  The
-    # tensor-core view (algorithmic flops against the FP16 dense peak / 120
-    # digit pairs per multiply-add) is kept beside it.
+    # (V and Y read once, Y~ written once; V^T Y: V and Y read once) over the
+    # launch's CUDA-event time.  The tensor-core view of the Gram
+    # (algorithmic flops against the FP16 dense peak / 120 digit pairs per
+    # multiply-add) is kept beside it.
     hbm_peak, peak_kind = peak_hbm()
     tc_peak, tc_kind = peak_tensor()
     gram_bytes = 8 * n * (kv + k)
     apply_bytes = 8 * n * (kv + 2 * k)
     gram_flops = 2.0 * n * kv * k
-    achieved = gram_bytes / (gram_ms * 1e-3) / 1e9
+    gram_gbs = gram_bytes / (gram_ms * 1e-3) / 1e9
+    apply_gbs = apply_bytes / (apply_ms * 1e-3) / 1e9
     tc_achieved = gram_flops / (gram_ms * 1e-3) / 1e12
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": gram_traffic(n, kv, k),
-            "kernel": f"umma_gram_partial_kernel<16> (compensated V^T Y, {n:,} x {kv} x {k})",
+    roof = {"bound": "hbm", "achieved": apply_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": apply_gbs / hbm_peak,
+            "traffic": apply_traffic(n, kv, k),
+            "kernel": f"umma_rowprod_kernel<16> (compensated Y - V C, {n:,} x {kv} x {k})",
             "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-            "algorithmic_bytes_per_launch": gram_bytes, "launch_ms": gram_ms,
-            "tensor_digit_pairs": {"achieved_tflops": tc_achieved, "peak_tflops": tc_peak / DIGIT_PAIRS,
-                                   "frac": tc_achieved / (tc_peak / DIGIT_PAIRS),
-                                   "peak_source": f"{tc_kind} FP16/BF16 dense sustained {tc_peak:.1f} TFLOP/s / "
-                                                  f"{DIGIT_PAIRS} digit pairs per multiply-add"},
+            "algorithmic_bytes_per_launch": apply_bytes, "launch_ms": apply_ms,
+            "gram_vty": {"kernel": f"umma_gram_partial_kernel<16> (compensated V^T Y, {n:,} x {kv} x {k})",
+                         "ms": gram_ms, "algorithmic_bytes_per_launch": gram_bytes, "achieved": gram_gbs,
+                         "frac": gram_gbs / hbm_peak, "traffic": gram_traffic(n, kv, k),
+                         "tensor_digit_pairs": {"achieved_tflops": tc_achieved, "peak_tflops": tc_peak / DIGIT_PAIRS,
+                                                "frac": tc_achieved / (tc_peak / DIGIT_PAIRS),
+                                                "peak_source": f"{tc_kind} FP16/BF16 dense sustained {tc_peak:.1f} "
+                                                               f"TFLOP/s / {DIGIT_PAIRS} digit pairs per multiply-add"}},
             "phases_ms": {"gram_vty": gram_ms, "apply": apply_ms, "gram_m": gram_m_ms, "cholqr": chol_ms},
-            "phases_gbs": {"gram_vty": achieved, "apply": apply_bytes / (apply_ms * 1e-3) / 1e9,
+            "phases_gbs": {"gram_vty": gram_gbs, "apply": apply_gbs,
                            "gram_m": 8 * n * k / (gram_m_ms * 1e-3) / 1e9,
-                           "cholqr": (nbytes - gram_bytes - apply_bytes) / (chol_ms * 1e-3) / 1e9},
-            "apply": {"kernel": "umma_rowprod_kernel<16> (compensated Y - V C, tcgen05)", "ms": apply_ms,
-                      "hbm_gbs": apply_bytes / (apply_ms * 1e-3) / 1e9,
-                      "frac": apply_bytes / (apply_ms * 1e-3) / 1e9 / hbm_peak}}
+                           "cholqr": (nbytes - gram_bytes - apply_bytes) / (chol_ms * 1e-3) / 1e9}}
 
     def timed_steps(fn, reps, warm=3):
         """Warm-up, then `reps` CUDA-event timings of fn(); returns (times, last result)."""

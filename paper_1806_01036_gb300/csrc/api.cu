@@ -103,15 +103,16 @@ __global__ void copy_small_kernel(int rows, int cols, const double* sh, const do
 }  // namespace
 
 // Engine of a compensated Gram product: the tcgen05 digit engine
-// (umma_gram.cu) once one side has 16 columns or more (its 128-lane tensor-
-// memory tiles are then reasonably filled), the integer limbs (fxgram.cu)
-// otherwise.  EO_DD_GRAM_ENGINE=int|umma overrides the choice (both engines
-// give results within the same bound).
+// (umma_gram.cu) once one side has more than 8 columns, the integer limbs
+// (fxgram.cu) below (measured, symmetric, 4e6 rows: k = 4 0.26 ms on the
+// limbs vs 0.51 ms on the tensor cores, k = 8 0.53 vs 0.51, k = 12 0.91 vs
+// 0.55).  EO_DD_GRAM_ENGINE=int|umma overrides the choice (both engines give
+// results within the same bound).
 static bool use_umma_gram(int kx, int ky) {
   const char* e = getenv("EO_DD_GRAM_ENGINE");
   if (e && e[0] == 'u') return true;
   if (e && e[0] == 'i') return false;
-  return std::max(kx, ky) >= 16;
+  return std::max(kx, ky) > 8;
 }
 
 // Kernels one launch_dd_gram call launches.
