@@ -247,6 +247,33 @@ def test_gram_dd_integer_inputs_are_exact(eo, ctx):
     assert np.array_equal(host(gh), ref.astype(np.float64)) and not np.any(host(gl))
 
 
+def _straddling_integers(g, n, k):
+    """Integers sign * m * 2^j (m odd below 128, some zeros): in the first
+    half of the rows j in [14, 25), so whole warps lie within 20 binades of
+    their column's largest value; in the second half j in [0, 25), so most
+    warps do not.  Products and sums stay exact in binary128."""
+    m = 2 * g.integers(0, 64, size=(n, k)) + 1
+    j = np.where(np.arange(n)[:, None] < n // 2, g.integers(14, 25, size=(n, k)), g.integers(0, 25, size=(n, k)))
+    x = np.ldexp(m.astype(np.float64), j) * np.where(g.random((n, k)) < 0.5, -1.0, 1.0)
+    x[g.random((n, k)) < 0.002] = 0.0
+    return np.asfortranarray(x)
+
+
+@pytest.mark.parametrize("n,kx,ky,sym", [(40_000, 64, 16, False), (40_000, 16, 16, True), (20_001, 24, 8, False),
+                                         (30_000, 40, 40, True)])
+def test_gram_dd_near_path_boundary_is_exact(eo, ctx, n, kx, ky, sym):
+    """Integer values straddling the 20-binade window of the tensor-core
+    Gram's near path (both paths in one product, panels of each kind): no
+    digit pair is dropped for them, so G_hi + G_lo is the exact sum rounded
+    to a double-double, bit for bit the oracle's (binary128 is exact here)."""
+    g = synth.rng(83 + kx)
+    x = _straddling_integers(g, n, kx)
+    y = x if sym else _straddling_integers(g, n, ky)
+    gh, gl = eo.gram(ctx, dev(x), None if sym else dev(y), prec=eo.DD)
+    rh, rl = oracle.gram(x, None if sym else y)
+    assert np.array_equal(host(gh), rh) and np.array_equal(host(gl), rl)
+
+
 def test_gram_dd_growing_exponents_rescale(eo, ctx):
     # the first rows are tiny, later rows large: the running alignment exponent of
     # every column grows many times and the accumulators are shifted each time
@@ -384,6 +411,27 @@ def test_project_apply_integer_inputs_are_exact(eo, ctx, monkeypatch, engine, n,
     c_lo = torch.zeros_like(c_hi)
     out, _ = eo.project_apply(ctx, dev(vi.astype(np.float64)), dev(yi.astype(np.float64)), (c_hi, c_lo),
                               prec=eo.DD, want_m=False)
+    exact = yi - vi @ ci  # |.| < 2^53: exact in int64 and in FP64
+    assert np.array_equal(host(out), exact.astype(np.float64))
+
+
+@pytest.mark.parametrize("n,kv", [(20_000, 64), (9_001, 32)])
+def test_project_apply_near_path_boundary_is_exact(eo, ctx, n, kv):
+    """Rows of V whose integer values straddle the 20-binade window of the
+    row kernels' near path (kv > 16), in the first half of the rows within
+    it, in the second half mostly not: Y - V C is exact in FP64 and must
+    come back bit for bit."""
+    torch = torch_mod()
+    g = synth.rng(91 + kv)
+    m = 2 * g.integers(0, 64, size=(n, kv)) + 1
+    j = np.where(np.arange(n)[:, None] < n // 2, g.integers(7, 13, size=(n, kv)), g.integers(0, 18, size=(n, kv)))
+    vi = (m << j) * np.where(g.random((n, kv)) < 0.5, -1, 1)
+    vi[g.random((n, kv)) < 0.002] = 0
+    ci = g.integers(-1000, 1001, size=(kv, 16))
+    yi = g.integers(-2 ** 40, 2 ** 40, size=(n, 16))
+    c_hi = dev(ci.astype(np.float64))
+    out, _ = eo.project_apply(ctx, dev(vi.astype(np.float64)), dev(yi.astype(np.float64)),
+                              (c_hi, torch.zeros_like(c_hi)), prec=eo.DD, want_m=False)
     exact = yi - vi @ ci  # |.| < 2^53: exact in int64 and in FP64
     assert np.array_equal(host(out), exact.astype(np.float64))
 
