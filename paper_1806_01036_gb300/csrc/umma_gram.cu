@@ -387,8 +387,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     // swizzled boxes, and the 32 digit words a warp stores per slab fill 128
     // contiguous bytes.  it_s: column << 16 | staging offset / 16; it_d:
     // digit offset | B operand << 31.
-    // In the hot plans the kNA items of the A operand come first and the kNB
-    // items of the B operand after them (item_valid, item_b below).
+    // Item i of a panel goes to thread slot i % kConvThreads, slot k = i /
+    // kConvThreads; thread tid holds slot titem, rotated so that the slots
+    // past the last whole round of items (the third item of some threads)
+    // fall to the converter warps that do not drain TMEM.  In the hot plans
+    // the kNA items of the A operand come first and the kNB items of the B
+    // operand after them (item_valid, item_b below).
+    const int titem = (tid + 32 * (kConvWarps - kDrainWarps)) % kConvThreads;
     const int half = P >> 1, ncg = nslots >> 3;
     const int nitems = nslots * half;
     unsigned it_s[kMaxItems], it_d[kMaxItems];
@@ -398,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if constexpr (kHot) {
         // an empty slot (past the kNA + kNB items) takes item 0's column, so
         // that every column index stays below nslots
-        const int i0 = tid + k * kConvThreads;
+        const int i0 = titem + k * kConvThreads;
         const bool live = i0 < kNA + kNB;
         const bool kb = live && i0 >= kNA;
         const int i = kb ? i0 - kNA : (live ? i0 : 0);
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         c = ((i >> 5) % g) * 8 + cl + (kb ? KXPC : 0);
         rh = (i >> 5) / g;
       } else {
-        const int i = tid + k * kConvThreads;
+        const int i = titem + k * kConvThreads;
         cl = i & 7;
         rl = (i >> 3) & 3;
         c = ((i >> 5) % ncg) * 8 + cl;
@@ -424,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                  (unsigned)(lc & 7) * 16u + (unsigned)rl * 4u) |
                 ((unsigned)isb << 31);
       if constexpr (PAD) {  // bit 30: a padded column, whose digits stay zero
-        if (tid + k * kConvThreads < nitems && !(isb ? y0 + lc < ky : x0 + lc < kx)) it_d[k] |= 1u << 30;
+        if (titem + k * kConvThreads < nitems && !(isb ? y0 + lc < ky : x0 + lc < kx)) it_d[k] |= 1u << 30;
       }
     }
     // item k exists for this thread; it belongs to the B operand
@@ -432,16 +437,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       if constexpr (kHot) {
         if (k * kConvThreads >= kNA + kNB) return false;
         if ((k + 1) * kConvThreads <= kNA + kNB) return true;
-        return tid + k * kConvThreads < kNA + kNB;
+        return titem + k * kConvThreads < kNA + kNB;
       } else {
-        return tid + k * kConvThreads < nitems;
+        return titem + k * kConvThreads < nitems;
       }
     };
     auto item_b = [&](int k) -> bool {
       if constexpr (kHot) {
         if (kNB == 0 || (k + 1) * kConvThreads <= kNA) return false;
         if (k * kConvThreads >= kNA) return true;
-        return tid + k * kConvThreads >= kNA;
+        return titem + k * kConvThreads >= kNA;
       } else {
         return (it_d[k] >> 31) != 0u;
       }
@@ -484,7 +489,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if constexpr (DIRECT) {
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
-        const int i = tid + k * kConvThreads;
+        const int i = titem + k * kConvThreads;
         const int cl = i & 7, rl = (i >> 3) & 3, rest = i >> 5;
         const int c = (rest % ncg) * 8 + cl, rh = rest / ncg;
         const bool isb = !pl.shared && c >= kxp;
