@@ -469,6 +469,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const T* gcol[kMaxItems];
     int irow[kMaxItems];
     const unsigned slot0 = smem_u32(stage) + (unsigned)tid * 16u;
+    // a copy of no bytes (a row past the chunk: the slot is zero-filled) names
+    // the partials array as its source, an address that is always valid
+    const T* zsrc = reinterpret_cast<const T*>(parts);
     auto prefetch = [&](int pp) {  // this thread's items of panel pp into slot buffer pp & 1
       const int64_t base = r0 + (int64_t)pp * P;
 #pragma unroll
@@ -477,11 +480,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t row = base + irow[k];
         const unsigned d = slot0 + (unsigned)(((pp & 1) * kMaxItems + k) * kConvThreads) * 16u;
         if constexpr (sizeof(T) == 8) {
-          cp_async8z(d, row < r1 ? gcol[k] + row : gcol[k], row < r1 ? 8u : 0u);
-          cp_async8z(d + 8u, row + 1 < r1 ? gcol[k] + row + 1 : gcol[k], row + 1 < r1 ? 8u : 0u);
+          cp_async8z(d, row < r1 ? gcol[k] + row : zsrc, row < r1 ? 8u : 0u);
+          cp_async8z(d + 8u, row + 1 < r1 ? gcol[k] + row + 1 : zsrc, row + 1 < r1 ? 8u : 0u);
         } else {
-          cp_async4z(d, row < r1 ? gcol[k] + row : gcol[k], row < r1 ? 4u : 0u);
-          cp_async4z(d + 4u, row + 1 < r1 ? gcol[k] + row + 1 : gcol[k], row + 1 < r1 ? 4u : 0u);
+          cp_async4z(d, row < r1 ? gcol[k] + row : zsrc, row < r1 ? 4u : 0u);
+          cp_async4z(d + 4u, row + 1 < r1 ? gcol[k] + row + 1 : zsrc, row + 1 < r1 ? 4u : 0u);
         }
       }
       cp_async_commit_group();

@@ -328,8 +328,10 @@ def test_gram_dd_nonfinite_input_gives_nan(eo, ctx):
     assert np.isnan(host(gh)[1, 1]) and np.isnan(host(gh)[0, 1])
 
 
-def test_gram_ld_padding_is_not_read(eo, ctx):
-    n, k, ld = 1001, 4, 1040
+@pytest.mark.parametrize("n,k,ld", [(1001, 4, 1040), (5003, 40, 5010)])
+def test_gram_ld_padding_is_not_read(eo, ctx, n, k, ld):
+    """NaN in the padding rows between columns (ld > n) must not reach G; k =
+    40 runs on the tensor cores as column strips, each at its own offset."""
     x = synth.gaussian(n, k, 5)
     buf = synth.with_ld(x, ld, fill=np.nan)
     torch = torch_mod()
@@ -341,12 +343,15 @@ def test_gram_ld_padding_is_not_read(eo, ctx):
     assert np.all(dd_err(host(gh), host(gl), rh, rl) <= U2 * np.abs(rh) + (n + 64) * 2.0 ** -105 * (np.abs(x).T @ np.abs(x)))
 
 
-def test_gram_empty_rows_give_zero(eo, ctx):
+@pytest.mark.parametrize("k", [3, 12, 40])
+def test_gram_empty_rows_give_zero(eo, ctx, k):
+    """No rows: G = 0 for every engine (k = 3 integer limbs, 12 the tensor
+    cores, 40 the tensor cores as column strips)."""
     torch = torch_mod()
-    x = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    x = torch.zeros((0, k), dtype=torch.float64, device="cuda")
     x = x.t().contiguous().t()
-    hi = torch.full((3, 3), 7.0, dtype=torch.float64, device="cuda").t()
-    lo = torch.full((3, 3), 7.0, dtype=torch.float64, device="cuda").t()
+    hi = torch.full((k, k), 7.0, dtype=torch.float64, device="cuda").t()
+    lo = torch.full((k, k), 7.0, dtype=torch.float64, device="cuda").t()
     gh, gl = eo.gram(ctx, x, prec=eo.DD, out=(hi, lo))
     assert not torch.any(gh) and not torch.any(gl)
 
