@@ -235,23 +235,23 @@ DIGIT_PAIRS = 120  # FP16 digit-pair products per multiply-add of the compensate
 def gram_traffic(n, kv, k):
     """DRAM bytes of one V^T Y launch of the tensor-core Gram kernel, from one
     ncu capture of the full-size launch (4e6 rows, kv = 64, k = 16:
-    dram__bytes_read.sum 2,560.22 MB, dram__bytes_write.sum 3.04 MB of
+    dram__bytes_read.sum 2,560.29 MB, dram__bytes_write.sum 3.18 MB of
     row-chunk partials); reads scale with the rows, the partials do not.
     None for other shapes."""
     if (kv, k) != (64, 16):
         return None
-    return 2560.219904e6 * n / 4e6 + 3.041024e6
+    return 2560.294656e6 * n / 4e6 + 3.181824e6
 
 
 def apply_traffic(n, kv, k):
     """DRAM bytes of one projection launch (umma_rowprod_kernel<16>) at
     kv = 64, k = 16, from one ncu capture of the full-size launch (4e6 rows:
-    dram__bytes_read.sum 2,560.17 MB, dram__bytes_write.sum 497.52 MB; the
+    dram__bytes_read.sum 2,560.16 MB, dram__bytes_write.sum 497.44 MB; the
     rest of the 512 MB of Y~ was still in L2 when the kernel ended); None for
     other shapes."""
     if (n, kv, k) != (4_000_000, 64, 16):
         return None
-    return 2560.165376e6 + 497.521408e6
+    return 2560.161024e6 + 497.438464e6
 
 
 def peak_tensor():
