@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cpu-rows", type=int, default=0, help="rows of the CPU-oracle sample (0 = auto)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip the runs of the other workloads that the default line summarises")
     ap.add_argument("--no-comparators", action="store_true",
                     help="skip the FP64, DD-EFT, same-accuracy and single-block comparisons (profiling runs)")
     ap.add_argument("--workload", choices=["project", "iterated", "batched", "serve", "sweep", "single"],
@@ -585,6 +587,9 @@ def run_eo(a):
     cpu = None
     if rank == 0 and not a.no_cpu:
         cpu = cpu_baseline(v_np, y_np, a.cpu_rows)
+    others = None
+    if rank == 0 and ws == 1 and not a.no_comparators and not a.no_other_configs:
+        others = other_configs()
 
     out = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
@@ -598,12 +603,74 @@ def run_eo(a):
         "orth_err": orth, "cross_err": cross_err, "cholesky_info": info0,
         "bytes_per_step": nbytes, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "clocks": clk.summary(), "gpu_launches": launches, "fp64_comparator": comp, "dd_eft_comparator": eft,
-        "same_accuracy": same, "single_block": single,
+        "same_accuracy": same, "single_block": single, "other_configs": others,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def other_configs():
+    """The other workloads, each in its own process after the step's
+    measurements (outside its timed region), summarised: the precision sweep,
+    the batched SVQB graph, serving at 2,000 requests/s offered and at 0.8x
+    the capacity that run measured, and the iterated two-phase algorithm.
+    A workload that fails or runs out of time is reported as such."""
+    def run(args, timeout=420):
+        t0 = time.time()
+        try:
+            r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, capture_output=True,
+                               text=True, timeout=timeout, cwd=ROOT)
+            lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+            if r.returncode != 0 or not lines:
+                return None, {"error": f"exit {r.returncode}", "stderr_tail": r.stderr[-300:]}
+            return json.loads(lines[-1]), {"seconds": round(time.time() - t0, 1)}
+        except Exception as e:  # reported, never fatal to the main line
+            return None, {"error": repr(e)[:300]}
+
+    out = {}
+    d, info = run(["--workload", "sweep"])
+    if d:
+        res = {}
+        for r in d["results"]:
+            res.setdefault(str(r["k"]), {})[r["mode"]] = [round(r["xtx_gbs"], 1), round(r["xty_gbs"], 1)]
+        info.update({"command": "python bench.py --workload sweep", "unit": "GB/s [X^T X, X^T Y]",
+                     "config": d["config"]["workload"], "results": res})
+    out["sweep"] = info
+    d, info = run(["--workload", "batched", "--steps", "5", "--warmup", "3"])
+    if d:
+        info.update({"command": "python bench.py --workload batched --steps 5 --warmup 3",
+                     "config": d["config"]["workload"], "ms_per_step": d["ms_per_step"],
+                     "blocks_per_s": d["blocks_per_s"], "gbs": d["value"], "p50_ms": d["p50_ms"],
+                     "p99_ms": d["p99_ms"], "orth_err_max": d["orth_err_max"], "hbm_frac": d["roofline"]["frac"],
+                     "fp64_graph_ms": d["comparators"]["fp64_graph_ms"], "clocks": d["clocks"]})
+    out["batched"] = info
+    d, info = run(["--workload", "serve"])
+    cap = None
+    if d:
+        cap = d["value"]
+        info.update({"command": "python bench.py --workload serve", "config": d["config"]["workload"],
+                     "requests_per_s": d["value"], "gbs": d["gbs"], "p50_ms": d["p50_ms"], "p99_ms": d["p99_ms"],
+                     "queue_p50_ms": d["queue_p50_ms"], "queue_p99_ms": d["queue_p99_ms"],
+                     "orth_err_max": d["orth_err_max"], "cross_err_max": d["cross_err_max"]})
+    out["serve_offered_2000"] = info
+    if cap:
+        rate = round(0.8 * cap, 1)
+        d, info = run(["--workload", "serve", "--rate", str(rate), "--requests", "1500"])
+        if d:
+            info.update({"command": f"python bench.py --workload serve --rate {rate} --requests 1500",
+                         "offered_per_s": rate, "requests_per_s": d["value"], "p50_ms": d["p50_ms"],
+                         "p99_ms": d["p99_ms"], "queue_p99_ms": d["queue_p99_ms"]})
+        out["serve_at_0.8_capacity"] = info
+    d, info = run(["--workload", "iterated"])
+    if d:
+        info.update({"command": "python bench.py --workload iterated", "config": d["config"]["workload"],
+                     "ms_per_block [kv, k, fp64, dd, dd iterations]": [
+                         [r["kv"], r["k"], round(r["fp64"]["ms"], 2), round(r["dd"]["ms"], 2), r["dd"]["iterations"]]
+                         for r in d["results"]]})
+    out["iterated"] = info
+    return out
 
 
 # --------------------------------------------------------- reference arm
