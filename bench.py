@@ -629,46 +629,59 @@ def other_configs():
         except Exception as e:  # reported, never fatal to the main line
             return None, {"error": repr(e)[:300]}
 
+    def summarise(info, f):
+        try:
+            info.update(f())
+        except Exception as e:  # a workload whose line lacks a field: reported, never fatal
+            info["error"] = "summary: " + repr(e)[:200]
+        return info
+
     out = {}
     d, info = run(["--workload", "sweep"])
     if d:
-        res = {}
-        for r in d["results"]:
-            res.setdefault(str(r["k"]), {})[r["mode"]] = [round(r["xtx_gbs"], 1), round(r["xty_gbs"], 1)]
-        info.update({"command": "python bench.py --workload sweep", "unit": "GB/s [X^T X, X^T Y]",
-                     "config": d["config"]["workload"], "results": res})
+        def sweep():
+            res = {}
+            for r in d["results"]:
+                res.setdefault(str(r["k"]), {})[r["mode"]] = [round(r["xtx_gbs"], 1), round(r["xty_gbs"], 1)]
+            return {"command": "python bench.py --workload sweep", "unit": "GB/s [X^T X, X^T Y]",
+                    "config": d["config"]["workload"], "results": res}
+        summarise(info, sweep)
     out["sweep"] = info
     d, info = run(["--workload", "batched", "--steps", "5", "--warmup", "3"])
     if d:
-        info.update({"command": "python bench.py --workload batched --steps 5 --warmup 3",
-                     "config": d["config"]["workload"], "ms_per_step": d["ms_per_step"],
-                     "blocks_per_s": d["blocks_per_s"], "gbs": d["value"], "p50_ms": d["p50_ms"],
-                     "p99_ms": d["p99_ms"], "orth_err_max": d["orth_err_max"], "hbm_frac": d["roofline"]["frac"],
-                     "fp64_graph_ms": d["comparators"]["fp64_graph_ms"], "clocks": d["clocks"]})
+        summarise(info, lambda: {
+            "command": "python bench.py --workload batched --steps 5 --warmup 3", "config": d["config"]["workload"],
+            "ms_per_step": d["ms_per_step"], "blocks_per_s": d["blocks_per_s"], "gbs": d["value"],
+            "p50_ms": d["p50_ms"], "p99_ms": d["p99_ms"], "orth_err_max": d["orth_err_max"],
+            "hbm_frac": d["roofline"]["frac"], "fp64_graph_ms": d["comparators"]["fp64_graph_ms"],
+            "clocks": d["clocks"]})
     out["batched"] = info
     d, info = run(["--workload", "serve"])
     cap = None
     if d:
-        cap = d["value"]
-        info.update({"command": "python bench.py --workload serve", "config": d["config"]["workload"],
-                     "requests_per_s": d["value"], "gbs": d["gbs"], "p50_ms": d["p50_ms"], "p99_ms": d["p99_ms"],
-                     "queue_p50_ms": d["queue_p50_ms"], "queue_p99_ms": d["queue_p99_ms"],
-                     "orth_err_max": d["orth_err_max"], "cross_err_max": d["cross_err_max"]})
+        summarise(info, lambda: {
+            "command": "python bench.py --workload serve", "config": d["config"]["workload"],
+            "requests_per_s": d["value"], "gbs": d["gbs"], "p50_ms": d["p50_ms"], "p99_ms": d["p99_ms"],
+            "queue_p50_ms": d["queue_p50_ms"], "queue_p99_ms": d["queue_p99_ms"],
+            "orth_err_max": d["orth_err_max"], "cross_err_max": d["cross_err_max"]})
+        cap = d.get("value")
     out["serve_offered_2000"] = info
     if cap:
         rate = round(0.8 * cap, 1)
         d, info = run(["--workload", "serve", "--rate", str(rate), "--requests", "1500"])
         if d:
-            info.update({"command": f"python bench.py --workload serve --rate {rate} --requests 1500",
-                         "offered_per_s": rate, "requests_per_s": d["value"], "p50_ms": d["p50_ms"],
-                         "p99_ms": d["p99_ms"], "queue_p99_ms": d["queue_p99_ms"]})
+            summarise(info, lambda: {
+                "command": f"python bench.py --workload serve --rate {rate} --requests 1500",
+                "offered_per_s": rate, "requests_per_s": d["value"], "p50_ms": d["p50_ms"], "p99_ms": d["p99_ms"],
+                "queue_p99_ms": d["queue_p99_ms"]})
         out["serve_at_0.8_capacity"] = info
     d, info = run(["--workload", "iterated"])
     if d:
-        info.update({"command": "python bench.py --workload iterated", "config": d["config"]["workload"],
-                     "ms_per_block [kv, k, fp64, dd, dd iterations]": [
-                         [r["kv"], r["k"], round(r["fp64"]["ms"], 2), round(r["dd"]["ms"], 2), r["dd"]["iterations"]]
-                         for r in d["results"]]})
+        summarise(info, lambda: {
+            "command": "python bench.py --workload iterated", "config": d["config"]["workload"],
+            "ms_per_block [kv, k, fp64, dd, dd iterations]": [
+                [r["kv"], r["k"], round(r["fp64"]["ms"], 2), round(r["dd"]["ms"], 2), r["dd"]["iterations"]]
+                for r in d["results"]]})
     out["iterated"] = info
     return out
 

@@ -68,3 +68,47 @@ def test_cpu_baseline_reports_dd_fp64_and_one_core(bench):
     assert r["kind"] == "oracle" and r["value"] > 0 and r["cores"] >= 1
     assert r["orth_err"] is not None and r["orth_err"] <= 1e-14  # the DD step is accurate at kappa = 1e10
     assert r["fp64_cholqr2"]["value"] > 0 and r["one_core_dd"]["rows"] == 3000
+
+
+def test_other_configs_summarises_each_workload(bench, monkeypatch):
+    """The default line's summary of the other workloads, from canned lines
+    (no GPU): every field is taken from its workload's own line, serving at
+    0.8x is offered 0.8x the capacity that run measured, and a workload that
+    fails or lacks a field is reported without stopping the others."""
+    import json
+    import subprocess
+
+    lines = {
+        "sweep": {"config": {"workload": "sweep"}, "results": [
+            {"k": 16, "mode": "dd", "xtx_gbs": 1200.04, "xty_gbs": 1300.06}]},
+        "batched": {"config": {"workload": "batched"}, "ms_per_step": 150.0, "blocks_per_s": 3400.0, "value": 700.0,
+                    "p50_ms": 150.0, "p99_ms": 151.0, "orth_err_max": 1e-16, "roofline": {"frac": 0.1},
+                    "comparators": {"fp64_graph_ms": 330.0}, "clocks": {"sm_mhz": 2070.0}},
+        "serve": {"config": {"workload": "serve"}, "value": 500.0, "gbs": 900.0, "p50_ms": 9.0, "p99_ms": 40.0,
+                  "queue_p50_ms": 0.01, "queue_p99_ms": 10.0, "orth_err_max": 1e-18, "cross_err_max": 1e-18},
+        "iterated": {"config": {"workload": "iterated"}},  # no results: a summary error
+    }
+    seen = []
+
+    class Done:
+        def __init__(self, out, rc=0):
+            self.stdout, self.stderr, self.returncode = out, "", rc
+
+    def fake_run(cmd, **kw):
+        args = cmd[2:]
+        seen.append(args)
+        w = args[args.index("--workload") + 1]
+        return Done("noise\n" + json.dumps(lines[w]) + "\n")
+
+    monkeypatch.setattr(subprocess, "run", fake_run)
+    out = bench.other_configs()
+    assert out["sweep"]["results"] == {"16": {"dd": [1200.0, 1300.1]}}
+    assert out["batched"]["blocks_per_s"] == 3400.0 and out["batched"]["hbm_frac"] == 0.1
+    assert out["serve_offered_2000"]["requests_per_s"] == 500.0
+    assert ["--workload", "serve", "--rate", "400.0", "--requests", "1500"] in seen
+    assert out["serve_at_0.8_capacity"]["offered_per_s"] == 400.0
+    assert "error" in out["iterated"]
+
+    monkeypatch.setattr(subprocess, "run", lambda cmd, **kw: Done("", rc=1))
+    out = bench.other_configs()
+    assert all("error" in v for v in out.values()) and "serve_at_0.8_capacity" not in out
