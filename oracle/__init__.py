@@ -72,6 +72,8 @@ def lib():
             L.eoq_cholqr.restype = _int
             L.eoq_svqb.argtypes = [_i64, _int, _p, _i64, _p, _p, _int, _dbl, _int, _p, _p, _int]
             L.eoq_svqb.restype = _int
+            L.eoq_svqb_rot.argtypes = [_i64, _int, _p, _i64, _p, _p, _int, _dbl, _p, _p, _int]
+            L.eoq_svqb_rot.restype = _int
             L.eoq_orth_err.argtypes = [_i64, _int, _p, _i64, _p]
             L.eoq_orth_err_diag.argtypes = [_i64, _int, _p, _i64, _p, _p]
             L.eoq_cholqr_b.argtypes = [_i64, _int, _p, _i64, _p, _i64, _int, _p, _p, _int]
@@ -244,6 +246,18 @@ def svqb(x, passes=1, tol=0.0, m=None):
     mh, ml = (None, None) if m is None else (_f64(m[0]), None if m[1] is None else _f64(m[1]))
     rank = lib().eoq_svqb(n, k, _ptr(q), n, _ptr(mh), _ptr(ml), k, float(tol), int(passes),
                           _ptr(z_hi), _ptr(z_lo), k)
+    return q, (z_hi, z_lo), int(rank)
+
+
+def svqb_rotated(x, tol=0.0, m=None):
+    """(Q, (Z_hi, Z_lo), rank): one SVQB pass with Z = D U Lambda^{-1/2}
+    (D = diag(M)^{-1/2}, D M D = U Lambda U^T, eigenvalues ascending, each
+    eigenvector's largest entry positive), binary128."""
+    q = _f64(x).copy(order="F")
+    n, k = q.shape
+    z_hi, z_lo = _sq(k)
+    mh, ml = (None, None) if m is None else (_f64(m[0]), None if m[1] is None else _f64(m[1]))
+    rank = lib().eoq_svqb_rot(n, k, _ptr(q), n, _ptr(mh), _ptr(ml), k, float(tol), _ptr(z_hi), _ptr(z_lo), k)
     return q, (z_hi, z_lo), int(rank)
 
 

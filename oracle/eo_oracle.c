@@ -24,6 +24,12 @@
  *                  Z = U Lambda^{-1/2} U^T = M^{-1/2}                 (Sec. 4.2, SVQB with the
  *                                                                      Frobenius-optimal Z of the
  *                                                                      Procrustes argument)
+ *   eoq_svqb_rot   one pass of SVQB with the transform as the section first
+ *                  writes it, Z = D U Lambda^{-1/2} (D = diag(M)^{-1/2},
+ *                  D M D = U Lambda U^T; eigenvalues ascending, each
+ *                  eigenvector's largest entry positive)              (Sec. 4.2, SVQB, Z = U Lambda^{-1/2}
+ *                                                                      with the diagonal scaling of
+ *                                                                      Stathopoulos and Wu)
  *   eoq_cholqr_piv CholQR with a diagonally pivoted Cholesky stopped at the
  *                  numerical rank, then an unpivoted second pass          (Sec. 4.2, the pivoted, partial
  *                                                                      Cholesky of phase II)
@@ -349,6 +355,46 @@ int eoq_svqb_z(int k, const double* M_hi, const double* M_lo, int ldm, double to
   return rank;
 }
 
+/* The rotated SVQB transform: with d_i = M_ii^{-1/2} (0 for a column with
+ * no positive diagonal entry) and D M D = U Lambda U^T, Z = D U Lambda^{+1/2}
+ * with the eigenpairs in ascending order of eigenvalue (equal ones by index)
+ * and each eigenvector's largest-magnitude entry made positive (the first
+ * one on a tie).  Eigenvalues not above tol * lambda_max give zero columns.
+ * Returns the number kept. */
+static int q_svqb_rot_z(int k, const qreal* M, qreal tol, qreal* Z) {
+  qreal *A = qalloc((size_t)k * k), *U = qalloc((size_t)k * k), *lam = qalloc(k), *d = qalloc(k);
+  int* order = (int*)malloc(sizeof(int) * (size_t)k);
+  for (int i = 0; i < k; ++i) d[i] = M[(size_t)i * k + i] > 0 ? 1 / qsqrt(M[(size_t)i * k + i]) : 0;
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i < k; ++i) A[(size_t)j * k + i] = d[i] * M[(size_t)j * k + i] * d[j];
+  q_jacobi(k, A, U, lam);
+  for (int a = 0; a < k; ++a) order[a] = a;
+  for (int a = 1; a < k; ++a) {  /* insertion sort, ascending, stable */
+    int v = order[a], b = a - 1;
+    while (b >= 0 && lam[order[b]] > lam[v]) { order[b + 1] = order[b]; --b; }
+    order[b + 1] = v;
+  }
+  for (int a = 0; a < k; ++a) {  /* sign: the largest |U(m, a)| positive */
+    int mbest = 0;
+    for (int m = 1; m < k; ++m)
+      if (qabs(U[(size_t)a * k + m]) > qabs(U[(size_t)a * k + mbest])) mbest = m;
+    if (U[(size_t)a * k + mbest] < 0)
+      for (int m = 0; m < k; ++m) U[(size_t)a * k + m] = -U[(size_t)a * k + m];
+  }
+  qreal lmax = 0;
+  for (int i = 0; i < k; ++i) if (lam[i] > lmax) lmax = lam[i];
+  int rank = 0;
+  for (int j = 0; j < k; ++j) {
+    const int a = order[j];
+    const int keep = lmax > 0 && lam[a] > tol * lmax;
+    const qreal w = keep ? 1 / qsqrt(lam[a]) : 0;
+    rank += keep;
+    for (int i = 0; i < k; ++i) Z[(size_t)j * k + i] = d[i] * U[(size_t)a * k + i] * w;
+  }
+  free(A); free(U); free(lam); free(d); free(order);
+  return rank;
+}
+
 /* Q = X Z with every entry summed in binary128 and rounded once; Q may alias X. */
 static void q_update(int64_t n, int k, double* X, int64_t ldx, const qreal* Z) {
 #pragma omp parallel
@@ -416,6 +462,11 @@ int eoq_cholqr(int64_t n, int k, double* X, int64_t ldx, const double* M_hi, con
 /* SVQB: per pass, M = X^T X, Z = M^{-1/2} (pseudo-inverse square root with
  * relative eigenvalue cut tol), X <- X Z.  Z_out gets the product of the
  * passes' transforms (Z_1 Z_2 ...).  Returns the rank of the last pass. */
+/* Rotated SVQB, one pass: M = X^T X (or the given one), Z from
+ * q_svqb_rot_z, X <- X Z.  Returns the number of kept directions. */
+int eoq_svqb_rot(int64_t n, int k, double* X, int64_t ldx, const double* M_hi, const double* M_lo, int ldm,
+                 double tol, double* Z_hi, double* Z_lo, int ldz);
+
 int eoq_svqb(int64_t n, int k, double* X, int64_t ldx, const double* M_hi, const double* M_lo, int ldm,
              double tol, int passes, double* Z_hi, double* Z_lo, int ldz) {
   size_t kk = (size_t)k * k;
@@ -437,6 +488,19 @@ int eoq_svqb(int64_t n, int k, double* X, int64_t ldx, const double* M_hi, const
   }
   if (Z_hi) store_dd(k, Zt, Z_hi, Z_lo, ldz);
   free(M); free(Z); free(Zt); free(T);
+  return rank;
+}
+
+int eoq_svqb_rot(int64_t n, int k, double* X, int64_t ldx, const double* M_hi, const double* M_lo, int ldm,
+                 double tol, double* Z_hi, double* Z_lo, int ldz) {
+  size_t kk = (size_t)k * k;
+  qreal *M = qalloc(kk), *Z = qalloc(kk);
+  if (M_hi) load_sym(k, M_hi, M_lo, ldm, M);
+  else q_gram_sym(n, k, X, ldx, M);
+  int rank = q_svqb_rot_z(k, M, (qreal)tol, Z);
+  q_update(n, k, X, ldx, Z);
+  if (Z_hi) store_dd(k, Z, Z_hi, Z_lo, ldz);
+  free(M); free(Z);
   return rank;
 }
 

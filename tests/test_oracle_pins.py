@@ -779,3 +779,82 @@ def test_cholqr_piv_drops_negligible_column():
     assert rank == 3 and perm[3] == 1 and not np.any(q[:, 3])
     q2, _, rank2, _, _ = oracle.cholqr_piv(x, tol=1e-50)
     assert rank2 == 4  # below the cut it is kept
+
+
+# ------------------------------------------------- rotated SVQB (Z = D U Lambda^{-1/2})
+
+def _rot_parts(m, z):
+    """V = D^{-1} Z (its columns u_j lambda_j^{-1/2}) and S = D M D, in mpmath."""
+    import mpmath as mp
+    mp.mp.prec = 120
+    k = m.shape[0]
+    M = mp.matrix([[mp.mpf(float(m[i, j])) for j in range(k)] for i in range(k)])
+    d = [1 / mp.sqrt(M[i, i]) for i in range(k)]
+    S = mp.matrix(k, k)
+    for i in range(k):
+        for j in range(k):
+            S[i, j] = d[i] * M[i, j] * d[j]
+    return M, d, S
+
+
+def test_svqb_rotated_invariants_in_mpmath():
+    """Z^T M Z = I; the columns of V = D^{-1} Z are eigenvectors of D M D
+    with eigenvalue 1 / |v_j|^2, ascending; each one's largest entry is
+    positive."""
+    import mpmath as mp
+    x = synth.conditioned(2000, 5, 1e3, 707)
+    m = x.T @ x
+    _, (zh, zl), rank = oracle.svqb_rotated(x, m=(m, None))
+    assert rank == 5
+    M, d, S = _rot_parts(m, zh)
+    k = 5
+    Z = mp.matrix([[mp.mpf(float(zh[i, j])) + mp.mpf(float(zl[i, j])) for j in range(k)] for i in range(k)])
+    G = Z.T * M * Z
+    assert max(abs(G[i, j] - (1 if i == j else 0)) for i in range(k) for j in range(k)) < 1e-28
+    lams = []
+    for j in range(k):
+        v = mp.matrix([Z[i, j] / d[i] for i in range(k)])
+        lam = 1 / sum(v[i] ** 2 for i in range(k))
+        r = S * v - lam * v
+        assert max(abs(r[i]) for i in range(k)) < 1e-28 * max(abs(v[i]) for i in range(k))
+        big = max(range(k), key=lambda i: abs(v[i]))
+        assert v[big] > 0
+        lams.append(lam)
+    assert all(lams[j] <= lams[j + 1] for j in range(k - 1))
+
+
+def test_svqb_rotated_matches_numpy_eigh_on_a_separated_spectrum():
+    """A well-conditioned case with distinct eigenvalues: Z equals
+    D U Lambda^{-1/2} built from numpy's eigh (ascending; signs fixed by the
+    largest entry) to FP64 accuracy."""
+    g = synth.rng(708)
+    x = np.asfortranarray(g.standard_normal((400, 6)) * np.array([1.0, 2.0, 0.5, 3.0, 1.5, 0.7]))
+    q, (zh, zl), rank = oracle.svqb_rotated(x)
+    m = x.T @ x
+    d = 1 / np.sqrt(np.diag(m))
+    lam, u = np.linalg.eigh(d[:, None] * m * d[None, :])
+    assert np.min(np.diff(lam)) > 1e-3
+    for a in range(6):
+        u[:, a] *= np.sign(u[np.argmax(np.abs(u[:, a])), a])
+    z = d[:, None] * u / np.sqrt(lam)[None, :]
+    assert rank == 6 and np.max(np.abs((zh + zl) - z)) <= 1e-12 * np.max(np.abs(z))
+    assert np.max(np.abs(q - x @ z)) <= 1e-12 * np.max(np.abs(q))
+
+
+def test_svqb_rotated_orthogonal_columns_and_rank():
+    """Orthogonal columns: D M D = I, no rotation, the eigenpairs keep their
+    index order, so Z = D and Q = the normalized columns, exactly; a zero
+    column gives eigenvalue 0, a zero first column of Z and rank k - 1."""
+    h = synth.hadamard_basis(256, 4, 709)  # exactly orthonormal columns
+    scale = np.array([2.0, 0.25, 8.0, 1.0])
+    x = np.asfortranarray(h * scale)
+    q, (zh, zl), rank = oracle.svqb_rotated(x)
+    assert rank == 4
+    assert np.array_equal(zh, np.diag(1 / scale)) and not np.any(zl)
+    assert np.array_equal(q, h)
+    x0 = x.copy(order="F")
+    x0[:, 2] = 0.0
+    q0, (zh0, zl0), rank0 = oracle.svqb_rotated(x0)
+    assert rank0 == 3
+    assert not np.any(zh0[:, 0]) and not np.any(q0[:, 0])
+    assert oracle.orth_err(q0[:, 1:])[0] < 1e-15
