@@ -214,6 +214,23 @@ EO_API eo_status eo_svqb(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, co
                   int ldm, double* Z_hi, double* Z_lo, int ldz, double tol, int passes, eo_prec prec, int* rank_dev);
 
 /*
+ * SVQB in its rotated form (Sec. 4.2 with the scaling of the SVQB of
+ * Stathopoulos and Wu, 2002): one pass of X <- X Z with
+ * Z = D U Lambda^{-1/2}, where D = diag(M)^{-1/2} (d_i = 0 where M_ii <= 0)
+ * and D M D = U Lambda U^T.  The columns of Z follow the eigenvalues in
+ * ascending order (equal ones by index), each eigenvector's largest-magnitude
+ * entry (lowest row on ties) is positive, and the columns of eigenvalues at
+ * or below tol * lambda_max (of D M D) are zero.  Z^T M Z is the identity on
+ * the kept columns; unlike eo_svqb's Z, this one is not symmetric and is not
+ * the Frobenius-nearest to I, and Q spans the same space with its columns
+ * rotated.  Arguments, tol < 0, layout, modes and rank_dev as in eo_svqb;
+ * Z_hi/Z_lo (optional, ldz) receive Z.
+ */
+EO_API eo_status eo_svqb_rotated(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, const double* M_hi,
+                                 const double* M_lo, int ldm, double* Z_hi, double* Z_lo, int ldz, double tol,
+                                 eo_prec prec, int* rank_dev);
+
+/*
  * Iterated two-phase orthogonalization (Sec. 4.2: the two phases are
  * repeated in turn, with a rank-revealing factorization in phase II, which
  * makes the method robust; the runtime figure repeats them until both

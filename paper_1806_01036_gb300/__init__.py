@@ -71,6 +71,7 @@ def lib():
         L.eo_orthogonalize.argtypes = [_p, _i64, _int, _p, _i64, _int, _p, _i64, _dbl, _int, _dbl, _int, _p, _p]
         L.eo_cholqr.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _int, _int, _p]
         L.eo_svqb.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _dbl, _int, _int, _p]
+        L.eo_svqb_rotated.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _p, _p, _int, _dbl, _int, _p]
         L.eo_cholqr_piv.argtypes = [_p, _i64, _int, _p, _i64, _p, _p, _int, _dbl, _int, _int, _p, _p, _p]
         L.eo_gram_dd_noalloc.argtypes = [_i64, _int, _p, _i64, _int, _p, _i64, _p, _p, _int, _p]
         L.eo_cholqr_b.argtypes = [_p, _i64, _int, _p, _i64, _p, _i64, _p, _p, _int, _int, _int, _p]
@@ -101,7 +102,7 @@ def lib():
         L.eo_batch_branches.argtypes = [_p]
         L.eo_batch_branches.restype = _int
         for f in ("eo_create", "eo_destroy", "eo_set_stream", "eo_gram", "eo_project", "eo_project_apply",
-                  "eo_cholqr", "eo_svqb", "eo_cholqr_piv", "eo_orthogonalize", "eo_gram_dd_noalloc", "eo_tune_cache",
+                  "eo_cholqr", "eo_svqb", "eo_svqb_rotated", "eo_cholqr_piv", "eo_orthogonalize", "eo_gram_dd_noalloc", "eo_tune_cache",
                   "eo_cholqr_b", "eo_svqb_b", "eo_project_b",
                   "eo_batch_create", "eo_batch_run", "eo_batch_destroy", "eo_batch_tile", "eo_batch_passes", "eo_batch_sweeps",
                   "eo_server_create", "eo_server_destroy", "eo_server_add_basis", "eo_server_submit",
@@ -305,6 +306,25 @@ def svqb(ctx: Context, X, passes: int = 1, prec: int = DD, tol: float = -1.0, M=
     ctx.check(lib().eo_svqb(ctx.h, n, k, X.data_ptr(), ldx, None if mh is None else mh.data_ptr(),
                             None if ml is None else ml.data_ptr(), ldm, zh.data_ptr(), zl.data_ptr(), _ld(zh),
                             float(tol), int(passes), prec, rank.data_ptr()))
+    return zh, zl, rank
+
+
+def svqb_rotated(ctx: Context, X, prec: int = DD, tol: float = -1.0, M=None, rank=None):
+    """One pass of X <- X Z with Z = D U Lambda^{-1/2} (D = diag(M)^{-1/2},
+    eigenvalues ascending, each eigenvector's largest entry positive).
+    Returns (Z_hi, Z_lo, rank) with rank a device int32 tensor."""
+    import torch
+    X, n, k, ldx = _mat(X, "X", _dtype(prec))
+    zh, zl = _small(k, k, X.device)
+    if rank is None:
+        rank = torch.zeros(1, dtype=torch.int32, device=X.device)
+    mh, ml, ldm = None, None, k
+    if M is not None:
+        mh, ml, ldm = _dd_pair(M, k, k, "M", True)
+    ctx.set_stream()
+    ctx.check(lib().eo_svqb_rotated(ctx.h, n, k, X.data_ptr(), ldx, None if mh is None else mh.data_ptr(),
+                                    None if ml is None else ml.data_ptr(), ldm, zh.data_ptr(), zl.data_ptr(),
+                                    _ld(zh), float(tol), prec, rank.data_ptr()))
     return zh, zl, rank
 
 

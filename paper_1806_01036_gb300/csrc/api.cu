@@ -217,7 +217,7 @@ cudaError_t enqueue_orth_step(const OrthArgs& a, const OrthRes& r, int p, OrthSt
       e = a.chol ? launch_chol_small(small_mode, a.k, mh, ml, ld, ws, a.O_hi, a.O_lo, a.ldo, st, gates, p, a.passes,
                                      a.out_dev, r.stream)
                  : launch_svqb_small(small_mode, a.k, mh, ml, ld, ws, a.O_hi, a.O_lo, a.ldo, a.tol, st, gates, p,
-                                     a.passes, a.out_dev, r.stream);
+                                     a.passes, a.out_dev, r.stream, a.rotated);
       *launches += 1;
       return e;
     }
@@ -290,7 +290,7 @@ size_t apply_scratch(int64_t n, int kv, int k, eo_prec prec) {
 template <bool CHOL>
 eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, int64_t ldx, const double* M_hi,
                       const double* M_lo, int ldm, double* O_hi, double* O_lo, int ldo, double tol, int passes,
-                      eo_prec prec, int* out_dev, void* P = nullptr, int64_t ldp = 0) {
+                      eo_prec prec, int* out_dev, void* P = nullptr, int64_t ldp = 0, bool rotated = false) {
   if (!ctx) return EO_EINVAL;
   ctx->err.clear();
   EO_CHECK(valid_prec(prec), EO_EINVAL, "%s: bad precision mode %lld", name, (long long)prec);
@@ -307,6 +307,7 @@ eo_status orth_common(eo_ctx* ctx, const char* name, int64_t n, int k, void* X, 
   OrthArgs a{CHOL, n, k, X, ldx, M_hi, M_lo, ldm, O_hi, O_lo, ldo, tol, passes, prec, out_dev};
   a.P = P;
   a.ldp = ldp;
+  a.rotated = rotated;
   OrthRes r{status_of(ctx), ws_of(ctx), parts_of(ctx), ctx->stream, Tile{}};
   r.parts_bytes = ctx->scratch_bytes - kOffParts;
   const char* where = "";
@@ -499,6 +500,12 @@ eo_status eo_svqb(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, const dou
                   int ldm, double* Z_hi, double* Z_lo, int ldz, double tol, int passes, eo_prec prec, int* rank_dev) {
   return orth_common<false>(ctx, "eo_svqb", n, k, X, ldx, M_hi, M_lo, ldm, Z_hi, Z_lo, ldz, tol, passes, prec,
                             rank_dev);
+}
+
+eo_status eo_svqb_rotated(eo_ctx* ctx, int64_t n, int k, void* X, int64_t ldx, const double* M_hi, const double* M_lo,
+                          int ldm, double* Z_hi, double* Z_lo, int ldz, double tol, eo_prec prec, int* rank_dev) {
+  return orth_common<false>(ctx, "eo_svqb_rotated", n, k, X, ldx, M_hi, M_lo, ldm, Z_hi, Z_lo, ldz, tol, 1, prec,
+                            rank_dev, nullptr, 0, true);
 }
 
 eo_status eo_cholqr_piv(eo_ctx* ctx, int64_t n, int k, double* X, int64_t ldx, double* R_hi, double* R_lo, int ldr,

@@ -182,7 +182,7 @@ cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* 
                               int* info_user, cudaStream_t st);
 cudaError_t launch_svqb_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
                               double* Z_hi, double* Z_lo, int ldz, double tol, DevStatus* s, SmallGates g, int pass,
-                              int passes, int* rank_user, cudaStream_t st);
+                              int passes, int* rank_user, cudaStream_t st, bool rotated = false);
 // Pivoted, partial Cholesky of the pass's Gram matrix (one CTA): pass 0
 // pivots on the largest remaining diagonal entry and stops at the numerical
 // rank (remaining diagonal not above tol * the largest diagonal of M),

@@ -93,6 +93,8 @@ struct OrthArgs {
   // Gram matrix is the symmetric part of X^T P, and P is updated with X.
   void* P = nullptr;
   int64_t ldp = 0;
+  // SVQB only: Z = D U Lambda^{-1/2} (D = diag(M)^{-1/2}) instead of M^{-1/2}
+  bool rotated = false;
 };
 struct OrthRes {
   DevStatus* st;

@@ -11,6 +11,10 @@
 //                (round-robin) ordering, Z = U Lambda^{+1/2} U^T = M^{-1/2}
 //                (Frobenius-nearest to I among Z with Z^T M Z = I, by the
 //                Procrustes argument of the same section), T <- T Z.
+//                Rotated form (one pass): the Jacobi runs on D M D with
+//                D = diag(M)^{-1/2} and Z = D U Lambda^{+1/2}, columns in
+//                ascending eigenvalue order, each eigenvector's largest
+//                entry positive (the SVQB of Stathopoulos and Wu, 2002).
 // In EO_DD the arithmetic is DD throughout (divisions, reciprocals and
 // square roots by Newton-Raphson); otherwise it is FP64.
 #include <algorithm>
@@ -425,7 +429,7 @@ template <int MODE>
 __device__ __forceinline__ void svqb_small_body(int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
                                                 double* Zh_u, double* Zl_u, int ldz, double tol, DevStatus* st,
                                                 SmallGates g, int pass, int passes, double thr, double eps,
-                                                int* rank_user) {
+                                                int* rank_user, bool rotated) {
   using A_ = Ar<MODE>;
   if (*g.run == 0) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -433,7 +437,9 @@ __device__ __forceinline__ void svqb_small_body(int k, const double* Mh, const d
   dd* A2 = A + k * k;                        // k*k: the next A
   dd* U = A2 + k * k;                        // k*k
   dd* cs = U + k * k;                        // 2 * (k/2 + 1): c, s per pair
-  int* pr = reinterpret_cast<int*>(cs + 2 * (k / 2 + 1));  // 2 * (k/2 + 1): p, q per pair
+  dd* dv = cs + 2 * (k / 2 + 1);             // k: D = diag(M)^{-1/2} (rotated form)
+  int* pr = reinterpret_cast<int*>(dv + k);  // 2 * (k/2 + 1): p, q per pair
+  int* perm = pr + 2 * (k / 2 + 1);          // k: eigenpair of column j (rotated form)
   __shared__ int flag, rot_count;
   const int tid = threadIdx.x;
   const int kk = k + (k & 1);  // even number of players; index k is a dummy
@@ -457,6 +463,16 @@ __device__ __forceinline__ void svqb_small_body(int k, const double* Mh, const d
       if (rank_user) *rank_user = -1;
     }
     return;
+  }
+  if (rotated) {  // the Jacobi runs on D M D (unit diagonal; a zero diagonal gives d_i = 0)
+    for (int i = tid; i < k; i += kThreads) {
+      const dd m = A[i * k + i];
+      dv[i] = m.hi > 0.0 ? A_::div(dd{1.0, 0.0}, A_::sqrt(m)) : dd{0.0, 0.0};
+      perm[i] = i;
+    }
+    __syncthreads();
+    for (int t = tid; t < k * k; t += kThreads) A[t] = A_::mul(A_::mul(dv[t % k], A[t]), dv[t / k]);
+    __syncthreads();
   }
   // Sweeps of the parallel (round-robin) ordering.  Per step: (1) each pair's
   // rotation: the angle in FP64 from the hi parts (t = tan(phi)), then
@@ -555,6 +571,30 @@ __device__ __forceinline__ void svqb_small_body(int k, const double* Mh, const d
     if (i > j) A[t] = A[i * k + j];
   }
   __syncthreads();
+  if (rotated) {
+    // Column a of U: its largest-magnitude entry (lowest row on ties) made
+    // positive; its place in the ascending order of the eigenvalues (ties by
+    // index) gives the column of Z it lands in.  Normalized double-doubles
+    // compare exactly as (hi, lo) pairs.
+    auto lt = [](dd x, dd y) { return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo); };
+    auto mag = [](dd x) { return x.hi < 0.0 ? dd_neg(x) : x; };
+    for (int a = tid; a < k; a += kThreads) {
+      dd* u = U + a * k;
+      int mb = 0;
+      for (int m = 1; m < k; ++m)
+        if (lt(mag(u[mb]), mag(u[m]))) mb = m;
+      if (u[mb].hi < 0.0)
+        for (int m = 0; m < k; ++m) u[m] = dd_neg(u[m]);
+      const dd la = A[a * k + a];
+      int pos = 0;
+      for (int b = 0; b < k; ++b) {
+        const dd lb = A[b * k + b];
+        pos += lt(lb, la) || (!lt(la, lb) && b < a);
+      }
+      perm[pos] = a;  // pos < k; with a NaN eigenvalue two columns may collide, the rest keep the identity
+    }
+    __syncthreads();
+  }
   // w_l = lambda_l^{-1/2} for kept eigenvalues; Z = U diag(w) U^T into A's storage.
   __shared__ double lmax_s, lmin_s;
   __shared__ int rank_s;
@@ -579,20 +619,27 @@ __device__ __forceinline__ void svqb_small_body(int k, const double* Mh, const d
     rank_s = rank;
   }
   __syncthreads();
-  // one triangle, mirrored, so that Z is exactly symmetric
-  for (int t = tid; t < k * k; t += kThreads) {
-    const int i = t % k, j = t / k;
-    if (i > j) continue;
-    dd v = dd{0.0, 0.0};
-    for (int l = 0; l < k; ++l) v = A_::fma(A_::mul(U[l * k + i], w[l]), U[l * k + j], v);
-    A[t] = v;
+  if (rotated) {  // Z(:, j) = D u_a w_a with a = perm[j]
+    for (int t = tid; t < k * k; t += kThreads) {
+      const int i = t % k, a = perm[t / k];
+      A[t] = A_::mul(A_::mul(dv[i], U[a * k + i]), w[a]);
+    }
+    __syncthreads();
+  } else {  // one triangle, mirrored, so that Z is exactly symmetric
+    for (int t = tid; t < k * k; t += kThreads) {
+      const int i = t % k, j = t / k;
+      if (i > j) continue;
+      dd v = dd{0.0, 0.0};
+      for (int l = 0; l < k; ++l) v = A_::fma(A_::mul(U[l * k + i], w[l]), U[l * k + j], v);
+      A[t] = v;
+    }
+    __syncthreads();
+    for (int t = tid; t < k * k; t += kThreads) {
+      const int i = t % k, j = t / k;
+      if (i > j) A[t] = A[i * k + j];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int t = tid; t < k * k; t += kThreads) {
-    const int i = t % k, j = t / k;
-    if (i > j) A[t] = A[i * k + j];
-  }
-  __syncthreads();
   for (int t = tid; t < k * k; t += kThreads) {
     const int i = t % k, j = t / k;
     ws->Zh[j * KMAX + i] = A[t].hi;
@@ -641,8 +688,9 @@ template <int MODE>
 __global__ void __launch_bounds__(kThreads) svqb_small_kernel(int k, const double* Mh, const double* Ml, int ldm,
                                                               SmallWs* ws, double* Zh_u, double* Zl_u, int ldz,
                                                               double tol, DevStatus* st, SmallGates g, int pass,
-                                                              int passes, double thr, double eps, int* rank_user) {
-  svqb_small_body<MODE>(k, Mh, Ml, ldm, ws, Zh_u, Zl_u, ldz, tol, st, g, pass, passes, thr, eps, rank_user);
+                                                              int passes, double thr, double eps, int* rank_user,
+                                                              bool rotated) {
+  svqb_small_body<MODE>(k, Mh, Ml, ldm, ws, Zh_u, Zl_u, ldz, tol, st, g, pass, passes, thr, eps, rank_user, rotated);
 }
 
 // One CTA per job: the factorization of pass `pass` of many independent
@@ -667,7 +715,7 @@ __global__ void __launch_bounds__(kThreads) svqb_small_batched_kernel(const Smal
   const SmallJob j = jobs[blockIdx.x];
   const int npass = passes == 1 ? 1 : 2;
   svqb_small_body<MODE>(j.k, j.ws->Mh, j.ws->Ml, KMAX, j.ws, j.Oh, j.Ol, j.ldo, j.tol, j.st,
-                        job_gates(j, pass, npass), pass, passes, thr, eps, j.out);
+                        job_gates(j, pass, npass), pass, passes, thr, eps, j.out, false);
 }
 
 __global__ void status_init_batched_kernel(const SmallJob* jobs, int njobs) {
@@ -783,7 +831,8 @@ cudaError_t launch_pivchol_small(Mode mode, int k, const double* Mh, const doubl
   return cudaGetLastError();
 }
 size_t svqb_smem(int k) {
-  return 3 * (size_t)k * k * sizeof(dd) + 2 * (size_t)(k / 2 + 1) * sizeof(dd) + 2 * (size_t)(k / 2 + 1) * sizeof(int);
+  return 3 * (size_t)k * k * sizeof(dd) + (2 * (size_t)(k / 2 + 1) + k) * sizeof(dd) +
+         (2 * (size_t)(k / 2 + 1) + k) * sizeof(int);
 }
 
 cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
@@ -807,21 +856,22 @@ cudaError_t launch_chol_small(Mode mode, int k, const double* Mh, const double* 
 
 cudaError_t launch_svqb_small(Mode mode, int k, const double* Mh, const double* Ml, int ldm, SmallWs* ws,
                               double* Z_hi, double* Z_lo, int ldz, double tol, DevStatus* s, SmallGates g, int pass,
-                              int passes, int* rank_user, cudaStream_t st) {
+                              int passes, int* rank_user, cudaStream_t st, bool rotated) {
   const size_t smem = svqb_smem(k);
+  if (rotated) passes = 1;
   cudaError_t e;
   if (mode == MODE_DD) {
     if (tol < 0) tol = k * 0x1p-104;
     e = set_dyn_smem(svqb_small_kernel<MODE_DD>, smem);
     if (e != cudaSuccess) return e;
     svqb_small_kernel<MODE_DD><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, Z_hi, Z_lo, ldz, tol, s, g, pass,
-                                                         passes, 1e7, kJacobiEpsDD, rank_user);
+                                                         passes, 1e7, kJacobiEpsDD, rank_user, rotated);
   } else {
     if (tol < 0) tol = k * 0x1p-52;
     e = set_dyn_smem(svqb_small_kernel<MODE_FP64>, smem);
     if (e != cudaSuccess) return e;
     svqb_small_kernel<MODE_FP64><<<1, kThreads, smem, st>>>(k, Mh, Ml, ldm, ws, Z_hi, Z_lo, ldz, tol, s, g, pass,
-                                                           passes, 1e4, kJacobiEpsFP64, rank_user);
+                                                           passes, 1e4, kJacobiEpsFP64, rank_user, rotated);
   }
   return cudaGetLastError();
 }

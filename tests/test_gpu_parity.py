@@ -837,6 +837,101 @@ def test_svqb_orthonormal_input_is_fixed(eo, ctx):
     assert np.max(np.abs(host(d) - u)) <= du + 8 * U
 
 
+# ------------------------------------------- rotated SVQB (Z = D U Lambda^{-1/2})
+
+def _rot_separated(x):
+    """True when D M D has well-separated eigenvalues and every eigenvector a
+    clear largest entry, so that the order and signs are fixed far above the
+    rounding of either side."""
+    m = x.T @ x
+    d = 1 / np.sqrt(np.diag(m))
+    lam, u = np.linalg.eigh(d[:, None] * m * d[None, :])
+    au = np.sort(np.abs(u), axis=0)
+    return np.min(np.diff(lam) / lam[1:]) > 1e-3 and np.min((au[-1] - au[-2]) / au[-1]) > 1e-4
+
+
+@pytest.mark.parametrize("n,k,kappa", [(20_000, 8, 1e2), (10_001, 16, 1e5), (4_097, 40, 1e3), (9_000, 64, 1e4),
+                                       (20_000, 8, 1e7)])
+def test_svqb_rotated_dd_matches_oracle(eo, ctx, n, k, kappa):
+    x = synth.conditioned(n, k, kappa, 900 + k)
+    assert _rot_separated(x)
+    d = dev(x)
+    zh, zl, rank = eo.svqb_rotated(ctx, d, prec=eo.DD)
+    assert int(rank.item()) == k
+    q_o, (zh_o, zl_o), rank_o = oracle.svqb_rotated(x)
+    assert rank_o == k
+    tol = cholqr_tol(n, k, kappa)
+    q = host(d)
+    assert np.max(np.abs(q - q_o)) <= tol
+    z = host(zh) + host(zl)
+    assert np.max(np.abs(z - (zh_o + zl_o))) <= tol * np.max(np.abs(zh_o))
+    assert oracle.orth_err(q)[0] <= 1e-14
+
+
+def test_svqb_rotated_given_m_and_fp64(eo, ctx):
+    n, k = 20_000, 12
+    x = synth.conditioned(n, k, 1e3, 950)
+    assert _rot_separated(x)
+    mh, ml = oracle.gram(x)
+    q_o, (zh_o, zl_o), _ = oracle.svqb_rotated(x, m=(mh, ml))
+    d = dev(x)
+    zh, zl, rank = eo.svqb_rotated(ctx, d, prec=eo.DD, M=(dev(mh), dev(ml)))
+    assert int(rank.item()) == k
+    assert np.max(np.abs(host(d) - q_o)) <= cholqr_tol(n, k, 1e3)
+    # FP64: Gram, Jacobi and update in FP64 (M to n u |X|^2, the eigenvectors to u / relgap)
+    d = dev(x)
+    zh, _, rank = eo.svqb_rotated(ctx, d, prec=eo.FP64)
+    assert int(rank.item()) == k
+    assert np.max(np.abs(host(d) - q_o)) <= 1e-9
+    assert oracle.orth_err(host(d))[0] <= 1e-9
+
+
+def test_svqb_rotated_degenerate_and_special_inputs(eo, ctx):
+    # exactly orthogonal columns (Hadamard, power-of-two scales): D M D = I with
+    # no rotation, ties kept in index order, so Z = D and Q the unit columns exactly
+    h = synth.hadamard_basis(4096, 4, 951)
+    s = np.array([2.0, 0.25, 8.0, 1.0])
+    x = np.asfortranarray(h * s)
+    q_o, (zh_o, zl_o), _ = oracle.svqb_rotated(x)
+    d = dev(x)
+    zh, zl, rank = eo.svqb_rotated(ctx, d, prec=eo.DD)
+    assert int(rank.item()) == 4
+    assert np.array_equal(host(zh), zh_o) and np.array_equal(host(zl), zl_o)
+    assert np.array_equal(host(d), h) and np.array_equal(q_o, h)
+    # a zero column: eigenvalue 0 first in the order, its column of Z and Q zero
+    x0 = x.copy(order="F")
+    x0[:, 2] = 0.0
+    d = dev(x0)
+    zh, zl, rank = eo.svqb_rotated(ctx, d, prec=eo.DD)
+    q_o, _, rank_o = oracle.svqb_rotated(x0)
+    assert int(rank.item()) == rank_o == 3
+    assert np.array_equal(host(d), q_o) and not np.any(host(zh)[:, 0])
+    # a dependent column: its eigenvalue (at the rounding level) is cut
+    g = synth.rng(952)
+    a, b = g.standard_normal((30_000, 1)), g.standard_normal((30_000, 1))
+    x = np.asfortranarray(np.hstack([a, b, a - 2.0 * b, g.standard_normal((30_000, 2))]))
+    d = dev(x)
+    _, _, rank = eo.svqb_rotated(ctx, d, prec=eo.DD, tol=1e-20)
+    assert int(rank.item()) == 4
+    q = host(d)
+    assert not np.any(q[:, 0]) and oracle.orth_err(np.asfortranarray(q[:, 1:]))[0] <= 1e-14
+    # nearly orthonormal input: D M D = I + O(u), order and vectors set by
+    # rounding, so only what is unique is compared: the span and Z^T M Z = I
+    x = synth.conditioned(777, 3, 1.0, 953)
+    d = dev(x)
+    zh, zl, rank = eo.svqb_rotated(ctx, d, prec=eo.DD)
+    q = host(d)
+    assert int(rank.item()) == 3 and oracle.orth_err(q)[0] <= 1e-14
+    assert np.max(np.abs(q @ q.T - x @ x.T)) <= 1e-14
+    # NaN: rank -1 and X left as it was
+    y = synth.gaussian(1000, 3, 954)
+    y[7, 2] = np.nan
+    d = dev(y)
+    _, _, rank = eo.svqb_rotated(ctx, d, prec=eo.DD)
+    assert int(rank.item()) == -1
+    assert np.array_equal(host(d), y, equal_nan=True)
+
+
 # ------------------------------------------------------------ arguments
 
 def test_invalid_arguments_are_rejected(eo, ctx):
