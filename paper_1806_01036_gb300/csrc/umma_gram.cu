@@ -178,6 +178,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) unsigned long long full_bar[2], ready_bar[2], stage_bar[2];
   __shared__ unsigned tmem_base;
   __shared__ int flag, bad;
+  // far[b]: the last panel in digit buffer b with an item off the near path
+  // (its digit slabs 11..14 may be nonzero); written by the converters before
+  // they mark the panel ready, read by the MMA warp after that
+  __shared__ int far[2];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -193,6 +197,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     flag = 0;
     bad = 0;
+    far[0] = far[1] = -1;
   }
   for (int c = tid; c < 5 * nslots; c += kThreads) Erun[c] = 0;  // Erun and pmax
   {  // slab 15 of every operand stays zero
@@ -252,9 +257,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const unsigned abase = dig_s + (unsigned)db * pl.dig_bytes;
         const unsigned bbase = pl.shared ? abase : abase + pl.a_bytes;
+        // every item of the panel on the near path: digit slabs 11..14 of
+        // both operands are zero, and the MMAs that would only multiply them
+        // are left out (exactly the same sums)
+        const int ns = *reinterpret_cast<volatile int*>(&far[db]) == p ? NS : 11;
         for (int ks = 0; ks < P / 16; ++ks) {
           for (int q = 0; q < pl.nq; ++q) {
-            const int nt = NS - pl.J * q;
+            if (pl.J * q >= ns) break;  // all of this MMA's X slabs are zero
+            const int nt = min(NS - pl.J * q, ns);
             const int Tp = KYP == 16 ? nt : (nt + 1) & ~1;  // N a multiple of 16
             const unsigned long long ad =
                 sdesc(abase + (unsigned)(pl.J * q * kxp / 8) * SBO + (unsigned)ks * 256u, 128u, SBO);
@@ -609,6 +619,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // alignment exponent (nearly always): the words without selects
         const bool near =
             __all_sync(0xffffffffu, !valid || min(abs_hi(v[k].x), abs_hi(v[k].y)) >= near_floor(A[k]));
+        if (!near && lane == 0) far[db] = p;
         if (valid) {
           unsigned wa[4], wb[4];
           const unsigned signs = ((hi32(v[k].x) >> 31) << 15) | (hi32(v[k].y) & 0x80000000u);
