@@ -612,6 +612,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // digits of panel p
       unsigned char* dbuf = dig + (size_t)db * pl.dig_bytes;
       const unsigned e1024 = exp1024x2();
+      bool off_near = false;  // an item of this warp took the general path
 #pragma unroll
       for (int k = 0; k < kMaxItems; ++k) {
         const bool valid = item_valid(k) && (!PAD || !(it_d[k] & 0x40000000u));
@@ -619,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // alignment exponent (nearly always): the words without selects
         const bool near =
             __all_sync(0xffffffffu, !valid || min(abs_hi(v[k].x), abs_hi(v[k].y)) >= near_floor(A[k]));
-        if (!near && lane == 0) far[db] = p;
+        off_near |= !near;
         if (valid) {
           unsigned wa[4], wb[4];
           const unsigned signs = ((hi32(v[k].x) >> 31) << 15) | (hi32(v[k].y) & 0x80000000u);
@@ -648,6 +649,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      if (off_near && lane == 0) far[db] = p;
       fence_proxy_async();
 
       // this thread's accumulators (its own TMEM lanes and columns) are drained
