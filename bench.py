@@ -248,12 +248,12 @@ def gram_traffic(n, kv, k):
 def apply_traffic(n, kv, k):
     """DRAM bytes of one projection launch (umma_rowprod_kernel<16>) at
     kv = 64, k = 16, from one ncu capture of the full-size launch (4e6 rows:
-    dram__bytes_read.sum 2,560.16 MB, dram__bytes_write.sum 497.44 MB; the
+    dram__bytes_read.sum 2,560.24 MB, dram__bytes_write.sum 497.86 MB; the
     rest of the 512 MB of Y~ was still in L2 when the kernel ended); None for
     other shapes."""
     if (n, kv, k) != (4_000_000, 64, 16):
         return None
-    return 2560.161024e6 + 497.438464e6
+    return 2560.240384e6 + 497.863680e6
 
 
 def peak_tensor():
@@ -557,7 +557,9 @@ def run_eo(a):
                 Rh[b].copy_(Rd[b].t(), non_blocking=True)
                 ev_back[b].record(down)
 
-        def run_steps(count):
+        done = []  # per step: its read-back finished (timing events on the copy-back stream)
+
+        def run_steps(count, mark=False):
             upload(0)
             for i in range(count):
                 b = i & 1
@@ -565,6 +567,9 @@ def run_eo(a):
                     upload(b ^ 1)
                 compute(b)
                 download(b)
+                if mark:
+                    done.append(torch.cuda.Event(enable_timing=True))
+                    done[-1].record(down)
             stream.wait_stream(down)
 
         run_steps(2)
@@ -573,10 +578,11 @@ def run_eo(a):
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         s0.record(stream)
-        run_steps(ke)
+        run_steps(ke, mark=True)
         s1.record(stream)
         torch.cuda.synchronize()
         ems = max_over_ranks(s0.elapsed_time(s1) / ke, dev)
+        gaps = [s0.elapsed_time(done[0])] + [done[i - 1].elapsed_time(done[i]) for i in range(1, len(done))]
         q_ok = bool(np.array_equal(Qh[(ke - 1) & 1].numpy()[:, :1024], Yt.t()[:, :1024].cpu().numpy()))
         # the copies of one step alone, both directions at once (after the
         # timed region): the least time a step can take on this host link,
@@ -601,7 +607,9 @@ def run_eo(a):
         e2e = {"value": weak_scaling_value(ws, nbytes, ems), "unit": "GB/s", "ms_per_step": ems,
                "h2d_bytes_per_step": 8 * n * (kv + k), "d2h_bytes_per_step": 8 * n * k + 8 * k * k,
                "steps": ke, "overlap": "inputs of step i+1 uploaded and Q of step i-1 read back while step i runs",
-               "copy_floor_ms": float(np.median(fl)), "result_matches_device_run": q_ok}
+               "copy_floor_ms": float(np.median(fl)),
+               "step_gaps_ms": [round(g, 3) for g in gaps],  # start -> first read-back done, then between read-backs
+               "result_matches_device_run": q_ok}
         del Vd, Yd, Qd
 
     cpu = None

@@ -360,6 +360,49 @@ FX_HD double sub_round(double y, i128 w, int S) {
   return w_to_double(ym - w, T);
 }
 
+// Branch-free forms of w_to_double and sub_round for the common case, so
+// that a thread can interleave the roundings of several outputs: the same
+// bits as those functions whenever ok is set; ok is cleared when the
+// result is not a normal double, and (sub_round) when y is not a normal
+// double or has bits below the grid 2^S, and the caller then takes the
+// general function.
+FX_HD double w_to_double_fast(i128 w, int S, bool& ok) {
+  const bool neg = w < 0;
+  const u128 u = neg ? (u128)(-w) : (u128)w;
+  const unsigned long long uh = (unsigned long long)(u >> 64), ul = (unsigned long long)u;
+  const int lz = uh ? clz64(uh) : 64 + clz64(ul);
+  const u128 v = u << (lz & 127);  // top bit at 127 (u == 0: result replaced below)
+  const unsigned long long t = (unsigned long long)(v >> 64);
+  const bool sticky = (unsigned long long)v != 0ull;
+  unsigned long long m = t >> 11;
+  const unsigned long long rb = t & 0x7ffull;
+  m += (unsigned long long)(rb > 0x400ull || (rb == 0x400ull && (sticky || (m & 1ull))));
+  const int carry = (int)(m >> 53);
+  m >>= carry;
+  const int be = S + 1150 - lz + carry;  // e2 + 52 + 1023 with e2 = S + (127 - lz) - 52 + carry
+  ok = u == 0 || (be >= 1 && be <= 2046);
+  const unsigned long long bits =
+      ((unsigned long long)neg << 63) | ((unsigned long long)(be & 0x7ff) << 52) | (m & ((1ull << 52) - 1));
+  return u == 0 ? 0.0 : from_bits(bits);
+}
+
+FX_HD double sub_round_fast(double y, i128 w, int S, bool& ok) {
+  const unsigned hi = hi32(y), lo = lo32(y);
+  const int be = (int)((hi >> 20) & 0x7ffu);
+  const unsigned long long m = ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo;
+  const int d = be - 1075 - S;  // y = +-m 2^(S + d)
+  // y dominating by more than 2^72: the product's grid coarsened to
+  // 2^(S + d - 72), w truncated onto it (as sub_round does)
+  const int sh = d > 72 ? d - 72 : 0;
+  const i128 wc = sh >= 127 ? (i128)0 : (w >> sh);
+  const u128 ym = (u128)m << (d < 0 ? 0 : (d > 72 ? 72 : d));
+  const i128 r = ((hi >> 31) ? -(i128)ym : (i128)ym) - wc;
+  bool okr;
+  const double o = w_to_double_fast(r, S + sh, okr);
+  ok = okr && be >= 1 && be <= 2046 && d >= 0;
+  return o;
+}
+
 // 256-bit signed accumulator for sums of 128-bit terms.
 struct Acc256 {
   u128 lo;

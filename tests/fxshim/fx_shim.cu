@@ -49,6 +49,20 @@ double fxs_w_to_double(long long wlo, long long whi, int S) { return w_to_double
 
 double fxs_sub_round(double y, long long wlo, long long whi, int S) { return sub_round(y, mk(wlo, whi), S); }
 
+double fxs_w_to_double_fast(long long wlo, long long whi, int S, int* ok) {
+  bool o = false;
+  const double r = w_to_double_fast(mk(wlo, whi), S, o);
+  *ok = o;
+  return r;
+}
+
+double fxs_sub_round_fast(double y, long long wlo, long long whi, int S, int* ok) {
+  bool o = false;
+  const double r = sub_round_fast(y, mk(wlo, whi), S, o);
+  *ok = o;
+  return r;
+}
+
 // Sum of m 128-bit terms in the 256-bit accumulator, narrowed back to 128 bits
 // (w_out, extra shift).
 void fxs_acc256(int m, const long long* lo, const long long* hi, long long* wlo, long long* whi, int* extra) {

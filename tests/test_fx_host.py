@@ -36,6 +36,10 @@ def fx(tmp_path_factory):
     L.fxs_w_to_double.restype = d
     L.fxs_sub_round.argtypes = [d, ll, ll, i]
     L.fxs_sub_round.restype = d
+    L.fxs_w_to_double_fast.argtypes = [ll, ll, i, p]
+    L.fxs_w_to_double_fast.restype = d
+    L.fxs_sub_round_fast.argtypes = [d, ll, ll, i, p]
+    L.fxs_sub_round_fast.restype = d
     L.fxs_acc256.argtypes = [i, p, p, p, p, p]
     L.fxs_scale_offset.restype = i
     return L
@@ -221,6 +225,71 @@ def test_sub_round_is_correctly_rounded(fx):
             assert got == rn(exact), (y, w, S)
         else:  # w truncated to the coarser grid first: absolute error below two grid units
             assert abs(F(got) - exact) <= abs(exact) * F(2) ** -53 + 2 * unit
+
+
+def _bits(x):
+    return np.float64(x).view(np.uint64).item()
+
+
+def test_fast_roundings_match_the_general_ones_bitwise(fx):
+    """w_to_double_fast / sub_round_fast (the row kernels' branch-free
+    epilogue forms): wherever they report ok, the same bits as w_to_double /
+    sub_round; ok on every normal-range case of the kernels' kind (y normal,
+    the product grid at or below y's, a normal result)."""
+    g = np.random.default_rng(17)
+    ok = C.c_int(0)
+    n_ok = n_typ = 0
+    for _ in range(6000):
+        bits = int(g.integers(0, 127))
+        w = (int(g.integers(0, 2 ** 62)) << 64 | int(g.integers(0, 2 ** 62)) << 2 | int(g.integers(0, 4)))
+        w %= (1 << bits) if bits else 1
+        if g.random() < 0.2 and bits > 60:  # a tie
+            top = bits - 53
+            w = (w >> top << top) | (1 << (top - 1))
+        if g.random() < 0.5:
+            w = -w
+        S = int(g.integers(-1300, 1000)) if g.random() < 0.15 else int(g.integers(-300, 100))
+        lo_, hi_ = split_w(w)
+        got = fx.fxs_w_to_double_fast(lo_, hi_, S, C.byref(ok))
+        if ok.value:
+            n_ok += 1
+            assert _bits(got) == _bits(fx.fxs_w_to_double(lo_, hi_, S)), (w, S)
+        exact = abs(F(w)) * F(2) ** S
+        if w == 0 or F(2) ** -1022 <= exact < F(2) ** 1023:
+            n_typ += 1
+            assert ok.value, (w, S)
+    assert n_ok >= n_typ > 4000
+    n_typ = 0
+    for _ in range(8000):
+        y = float(np.ldexp(g.standard_normal(), int(g.integers(-80, 80))))
+        mode = int(g.integers(0, 4))
+        S = int(g.integers(-300, -30))
+        if mode == 0:  # cancellation: w 2^S close to y
+            w = int(F(y) / F(2) ** S) + int(g.integers(-10 ** 6, 10 ** 6))
+        elif mode == 1:  # y dominating by 0 .. 120 binades (the coarsened grid beyond 72)
+            e = int(np.frexp(abs(y))[1]) - S - int(g.integers(0, 120))
+            w = int(g.integers(-2 ** 60, 2 ** 60)) << max(e - 60, 0) if e > 0 else int(g.integers(-4, 4))
+        elif mode == 2:
+            w = int(g.integers(-2 ** 62, 2 ** 62)) << int(g.integers(0, 60))
+        else:
+            w = 0
+        if not -(1 << 126) < w < (1 << 126):
+            continue
+        lo_, hi_ = split_w(w)
+        got = fx.fxs_sub_round_fast(y, lo_, hi_, S, C.byref(ok))
+        want = fx.fxs_sub_round(y, lo_, hi_, S)
+        ey = int(np.frexp(abs(y))[1]) - 53
+        if ok.value:
+            assert _bits(got) == _bits(want), (y, w, S)
+        if ey >= S and (want == 0.0 or 2.0 ** -1022 <= abs(want) < 2.0 ** 1023):
+            n_typ += 1
+            assert ok.value, (y, w, S)
+    assert n_typ > 3000
+    # the rare cases fall back: subnormal y, y below the grid, a result past the range
+    assert not (fx.fxs_sub_round_fast(5e-324, *split_w(1), -1074, C.byref(ok)), ok.value)[1]
+    assert not (fx.fxs_sub_round_fast(1.0, *split_w(3), -40, C.byref(ok)), ok.value)[1]
+    assert not (fx.fxs_w_to_double_fast(*split_w(1), -1080, C.byref(ok)), ok.value)[1]
+    assert not (fx.fxs_w_to_double_fast(*split_w(1 << 100), 950, C.byref(ok)), ok.value)[1]
 
 
 def test_acc256_sums_exactly(fx):
