@@ -124,6 +124,107 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
+// The general exact rounding (the rare inputs the branch-free forms leave),
+// out of line.
+__device__ __noinline__ double fx_round_general(int update, double y, i128 w, int S) {
+  return update ? w_to_double(w, S) : sub_round(y, w, S);
+}
+
+// Narrow row products (kin <= KIN <= 8): a thread holds its row's values in
+// registers, loaded one row ahead, and forms up to four outputs of it; the
+// threads of a row's output groups are adjacent lanes of one warp, so the
+// row's exponent needs no shared memory and the kernel no block barrier
+// after the small matrix's limbs are set up.  The sums, their order and the
+// rounding are those of fx_rowprod_kernel (bitwise the same outputs).  In
+// place (update): every lane's loads of a row precede the warp's stores to
+// it (the __syncwarp at the end of each step).
+template <int MODE_UPDATE, int KIN>
+__global__ void __launch_bounds__(kThreads, 2)
+    fx_rowreg_kernel(int64_t n, int kin, const double* A, int64_t lda, int kout, const double* Bh, const double* Bl,
+                     int ldb, int tri, const double* Yin, int64_t ldyin, double* Out, int64_t ldo, int lgng,
+                     const int* gate) {
+  if (gate && *gate == 0) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int4* Blimb = reinterpret_cast<int4*>(smem_raw);                 // kout * kin
+  int* Eb = reinterpret_cast<int*>(Blimb + (size_t)kout * kin);    // kout
+  load_small_limbs(kin, kout, Bh, Bl, ldb, Blimb, Eb);
+
+  const int lane = threadIdx.x & 31;
+  const int g = lane & ((1 << lgng) - 1);     // output group of this lane: outputs 4g .. 4g + 3
+  const int rpw = 32 >> lgng;                 // rows per warp and step
+  const int64_t warp = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+  const int64_t slots = (int64_t)gridDim.x * (kThreads / 32) * rpw;  // rows per step of the grid
+  const int j0 = JG * g;
+  const bool active = j0 < kout;
+  const int iend = tri ? min(kin, j0 + JG) : kin;  // Z is upper triangular for CholQR
+  auto load_row = [&](int64_t r, double (&v)[KIN]) {
+#pragma unroll
+    for (int i = 0; i < KIN; ++i) v[i] = (i < kin && r < n) ? A[(size_t)i * lda + r] : 0.0;
+  };
+  int64_t w0 = warp * rpw;  // first row of this warp's step (uniform over the warp)
+  double v[KIN];
+  load_row(w0 + (lane >> lgng), v);
+  for (; w0 < n; w0 += slots) {
+    const int64_t r = w0 + (lane >> lgng);
+    double vn[KIN];
+    load_row(r + slots, vn);  // the row of the next step, in flight during this one
+    int e = 0;
+#pragma unroll
+    for (int i = 0; i < KIN; ++i) e = max(e, align_exp(v[i]));
+    const int Er = max(e, 1);
+    if (active && r < n) {
+      long long acc[JG][4];
+#pragma unroll
+      for (int q = 0; q < JG; ++q)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) acc[q][d] = 0;
+#pragma unroll
+      for (int i = 0; i < KIN; ++i) {
+        if (i < iend) {
+          const Limbs L = to_limbs(v[i], Er);
+          const int4 a = make_int4(L.v[0], L.v[1], L.v[2], L.v[3]);
+#pragma unroll
+          for (int q = 0; q < JG; ++q) mac4(acc[q], a, Blimb[(size_t)min(j0 + q, kout - 1) * kin + i]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < JG; ++q) {
+        const int j = j0 + q;
+        if (j < kout) {
+          const i128 w = acc_to_w(acc[q]);
+          const int S = Er + Eb[j] - kScaleOffset;
+          const double y = MODE_UPDATE ? 0.0 : Yin[(size_t)j * ldyin + r];
+          bool ok;
+          double out = MODE_UPDATE ? w_to_double_fast(w, S, ok) : sub_round_fast(y, w, S, ok);
+          if (!ok) out = fx_round_general(MODE_UPDATE, y, w, S);
+          if (e >= 2047 || Eb[j] >= 2048) out = __longlong_as_double(0x7ff8000000000000ll);  // Inf/NaN input
+          Out[(size_t)j * ldo + r] = out;
+        }
+      }
+    }
+    __syncwarp();  // every lane's loads of this step's rows precede the next step's stores
+#pragma unroll
+    for (int i = 0; i < KIN; ++i) v[i] = vn[i];
+  }
+}
+
+constexpr int kRegKin = 8;  // widest kin of fx_rowreg_kernel
+
+int reg_groups_log2(int kout) {
+  const int ng = (kout + JG - 1) / JG;
+  int lg = 0;
+  while ((1 << lg) < ng) ++lg;
+  return lg;
+}
+
+bool use_rowreg(int kin, int kout) { return kin <= kRegKin && reg_groups_log2(kout) <= 3; }
+
+int grid_reg(int64_t n, int kout, int ctas) {
+  const int64_t rows_per_block = (int64_t)(kThreads / 32) * (32 >> reg_groups_log2(kout));
+  const int64_t need = (n + rows_per_block - 1) / rows_per_block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, ctas > 0 ? ctas : 152 * 4));
+}
+
 constexpr size_t kSmemBudget = 110 * 1024;  // two CTAs per SM
 
 int rows_per_panel(int kin, int kout) {
@@ -150,6 +251,16 @@ int grid_of(int64_t n, int P, int ctas) {
 cudaError_t launch_rowprod(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout, const double* Bh,
                            const double* Bl, int ldb, bool tri, const double* Yin, int64_t ldyin, double* Out,
                            int64_t ldo, const int* gate, cudaStream_t st, int ctas = 0) {
+  if (use_rowreg(kin, kout)) {
+    const int lgng = reg_groups_log2(kout);
+    const size_t smem = sizeof(int4) * (size_t)kout * kin + sizeof(int) * kout;
+    const int blocks = grid_reg(n, kout, ctas);
+    auto kern = update ? (kin <= 4 ? fx_rowreg_kernel<1, 4> : fx_rowreg_kernel<1, 8>)
+                       : (kin <= 4 ? fx_rowreg_kernel<0, 4> : fx_rowreg_kernel<0, 8>);
+    kern<<<blocks, kThreads, smem, st>>>(n, kin, A, lda, kout, Bh, Bl, ldb, tri ? 1 : 0, update ? nullptr : Yin,
+                                         update ? 0 : ldyin, Out, ldo, lgng, gate);
+    return cudaGetLastError();
+  }
   const int P = rows_per_panel(kin, kout);
   int lgP = 0;
   while ((1 << lgP) < P) ++lgP;
@@ -209,6 +320,7 @@ int fx_update_ctas(int64_t n, int k, int ctas) {
     const int64_t ntiles = (n + 127) / 128;  // 128-row tiles of the tensor-core engine
     return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, ctas > 0 ? ctas : 152));
   }
+  if (use_rowreg(k, k)) return grid_reg(n, k, ctas);
   return grid_of(n, rows_per_panel(k, k), ctas);
 }
 
