@@ -298,7 +298,7 @@ __global__ void copy_cols_kernel(int64_t n, int cols, const double* __restrict__
 }
 
 size_t fx_update_tmp_bytes(int64_t n, int k) {
-  if (k <= 16 || !umma_rowprod_supported(k, 16)) return 0;
+  if (k <= 16 || umma_rowprod_supported(k, k) || !umma_rowprod_supported(k, 16)) return 0;
   return (size_t)n * 16 * ((k + 15) / 16 - 1) * sizeof(double);
 }
 

@@ -192,8 +192,15 @@ __device__ __noinline__ double round_general(int update, double y, i128 h, int S
 }
 
 // KP = 4 W: the K dimension (kin padded to 16, 32 or 64; padded columns
-// are converted as zeros).
-template <int W>
+// are converted as zeros).  KO: blocks of 16 output columns (1, or 2 for
+// kout up to 32 with kin <= 32).  With one block, TMEM holds two
+// accumulators and the epilogue of tile i - 1 overlaps the MMAs of tile i;
+// with two, the 480 columns of the two blocks leave one accumulator each:
+// the converters store groups 0 and 1 of tile i, read tile i - 1's
+// accumulators, release them (tfree) and then store group 2, and the MMAs of
+// tile i wait for that release, so the inputs are converted once for all 32
+// outputs.
+template <int W, int KO = 1>
 __global__ void __launch_bounds__(kThreads, 1)
     umma_rowprod_kernel(int update, int64_t n, int kin, const double* A, int64_t lda, int kout,
                         const double* __restrict__ Bh, const double* __restrict__ Bl, int ldb, int tri,
@@ -203,18 +210,20 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int KC = KP / 16;             // MMAs (K = 16) per slab
   constexpr unsigned SBO = 16u * KP;      // bytes between 8-row groups of an operand
   constexpr unsigned SLAB_A = 16u * SBO;  // one digit slab of the tile (128 rows)
-  constexpr unsigned B_BYTES = 32u * SBO; // 16 slabs x 16 columns
+  constexpr unsigned B_BYTES = 32u * SBO; // 16 slabs x 16 columns (one block of outputs)
+  constexpr int NOUT = kOut * KO;
+  static_assert(KO == 1 || (KO == 2 && W <= 8), "two output blocks only for kin <= 32");
 
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* bdig = smem;                                  // the small matrix's digits
-  unsigned char* adig = smem + B_BYTES;                        // two group buffers of 5 slabs
+  unsigned char* adig = smem + KO * B_BYTES;                   // two group buffers of 5 slabs
   constexpr int GS = kGroupSlabs<W>, NG = kGroups<W>;
   int* Arow = reinterpret_cast<int*>(adig + 2 * GS * SLAB_A);  // [2][128] row exponents
   int* Rbad = Arow + 2 * kRows;                                // [2][128] non-finite rows
-  int* Bexp = Rbad + 2 * kRows;                                // [16] column exponents
-  int* Bbad = Bexp + kOut;                                     // [16] non-finite columns
-  double* stg = reinterpret_cast<double*>(Bbad + kOut);        // [W][512] staged values (kin <= 32)
-  __shared__ __align__(8) unsigned long long full_bar[2], ready_bar[2];
+  int* Bexp = Rbad + 2 * kRows;                                // [NOUT] column exponents
+  int* Bbad = Bexp + NOUT;                                     // [NOUT] non-finite columns
+  double* stg = reinterpret_cast<double*>(Bbad + NOUT);        // [W][512] staged values (kin <= 32)
+  __shared__ __align__(8) unsigned long long full_bar[2], ready_bar[2], tfree_bar;
   __shared__ unsigned tmem_base;
   __shared__ int bad;
 
@@ -228,10 +237,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(smem_u32(&full_bar[b]), 1);
       mbar_init(smem_u32(&ready_bar[b]), kConvThreads);
     }
+    mbar_init(smem_u32(&tfree_bar), kConvThreads);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     bad = 0;
   }
-  if (tid < kOut) {
+  if (tid < NOUT) {
     const int j = tid;
     int e = 0, nf = 0;
     if (j < kout) {
@@ -246,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     Bbad[j] = nf;
   }
   __syncthreads();
-  for (int e = tid; e < kOut * KP; e += kThreads) {  // B row R = t * 16 + j (slab t), K index i
+  for (int e = tid; e < NOUT * KP; e += kThreads) {  // block j / 16: B row R = t * 16 + j % 16 (slab t), K index i
     const int j = e / KP, i = e % KP;
     i128 x = 0;
     if (j < kout && i < kin && !(tri && i > j) && !Bbad[j]) {
@@ -257,8 +267,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const u128 U = x < 0 ? (u128)(-x) : (u128)x;  // < 2^104
     for (int t = 0; t < 16; ++t) {
       const unsigned dgt = t < NS ? ((unsigned)(U >> (98 - 7 * t)) & 127u) | sign : 0u;
-      const int R = t * kOut + j;
-      *reinterpret_cast<unsigned short*>(bdig + (R >> 3) * SBO + (i >> 3) * 128 + (R & 7) * 16 + (i & 7) * 2) =
+      const int R = t * kOut + j % kOut;
+      *reinterpret_cast<unsigned short*>(bdig + (j / kOut) * B_BYTES + (R >> 3) * SBO + (i >> 3) * 128 +
+                                         (R & 7) * 16 + (i & 7) * 2) =
           (unsigned short)dgt;
     }
   }
@@ -267,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const unsigned taddr = tmem_base;
-  const unsigned fb0 = smem_u32(&full_bar[0]), rb0 = smem_u32(&ready_bar[0]);
+  const unsigned fb0 = smem_u32(&full_bar[0]), rb0 = smem_u32(&ready_bar[0]), tfb = smem_u32(&tfree_bar);
   const unsigned adig_s = smem_u32(adig), bdig_s = smem_u32(bdig);
 
   if (warp == kConvWarps) {
@@ -276,7 +287,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       int G = 0;  // groups issued
       bool ok = true;
       for (int64_t T = blockIdx.x, i = 0; T < ntiles && ok; T += gridDim.x, ++i) {
-        const unsigned acc = taddr + (unsigned)(i & 1) * kAccCols;
+        const unsigned acc = taddr + (KO > 1 ? 0u : (unsigned)(i & 1) * kAccCols);
+        if constexpr (KO > 1) {
+          if (i > 0) {  // tile i - 1's accumulators read by its epilogue
+            if (!mbar_wait(tfb, (unsigned)(i - 1) & 1u, &bad)) break;
+            tc_fence_after();
+          }
+        }
 #pragma unroll 1
         for (int g = 0; g < NG; ++g, ++G) {
           const int b = G & 1;
@@ -290,11 +307,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int s = g * GS + sg;
             const unsigned idesc = idesc_f16(kRows, kOut * (NS - s));
 #pragma unroll
-            for (int kc = 0; kc < KC; ++kc) {
-              const unsigned long long ad = sdesc(abuf + (unsigned)sg * SLAB_A + (unsigned)kc * 256u, 128u, SBO);
-              const unsigned long long bd = sdesc(bdig_s + (unsigned)kc * 256u, 128u, SBO);
-              mma_f16(acc + (unsigned)(kOut * s), ad, bd, idesc, (s == 0 && kc == 0) ? 0u : 1u);
-            }
+            for (int h = 0; h < KO; ++h)
+#pragma unroll
+              for (int kc = 0; kc < KC; ++kc) {
+                const unsigned long long ad = sdesc(abuf + (unsigned)sg * SLAB_A + (unsigned)kc * 256u, 128u, SBO);
+                const unsigned long long bd = sdesc(bdig_s + (unsigned)h * B_BYTES + (unsigned)kc * 256u, 128u, SBO);
+                mma_f16(acc + (unsigned)h * kAccCols + (unsigned)(kOut * s), ad, bd, idesc,
+                        (s == 0 && kc == 0) ? 0u : 1u);
+              }
           }
           mma_commit(fb0 + 8u * b);
         }
@@ -331,15 +351,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     };
     if constexpr (kStageValues<W>) prefetch(blockIdx.x);
 
-    auto epilogue = [&](int64_t T, int64_t i) {
-      if (ep * 4 >= kout) return;  // all four outputs of this warp are padding (warp-uniform)
-      const unsigned tb = tq + (unsigned)(i & 1) * kAccCols;
+    // outputs 16 ob + 4 ep .. + 3 (output block ob) of tile T (the index is
+    // written out at each use: a variable for it costs a register at the
+    // 96-register limit of the kin = 64 kernel, and it spills)
+    auto epilogue_block = [&](int64_t T, int64_t i, int ob) {
+      if (ob * kOut + ep * 4 >= kout) return;  // all four outputs of this warp are padding (warp-uniform)
+      const unsigned tb = tq + (unsigned)(KO > 1 ? ob : (int)(i & 1)) * kAccCols;
       double yv[4];
       {
         const int64_t grow = T * kRows + L;
 #pragma unroll
         for (int y = 0; y < 4; ++y)
-          yv[y] = (!update && ep * 4 + y < kout && grow < n) ? Yin[(size_t)(ep * 4 + y) * ldyin + grow] : 0.0;
+          yv[y] = (!update && ob * kOut + ep * 4 + y < kout && grow < n)
+                      ? Yin[(size_t)(ob * kOut + ep * 4 + y) * ldyin + grow]
+                      : 0.0;
       }
       i128 h[4];
       if constexpr (kRoundDiag<W> >= NS - 1) {
@@ -415,15 +440,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (update) {
 #pragma unroll
           for (int u = 0; u < kRoundPair<W>; ++u)
-            o[u] = w_to_double_fast(h[y0 + u], Ar + Bexp[ep * 4 + y0 + u] - kScaleProd, ok[u]);
+            o[u] = w_to_double_fast(h[y0 + u], Ar + Bexp[ob * kOut + ep * 4 + y0 + u] - kScaleProd, ok[u]);
         } else {
 #pragma unroll
           for (int u = 0; u < kRoundPair<W>; ++u)
-            o[u] = sub_round_fast(yv[y0 + u], h[y0 + u], Ar + Bexp[ep * 4 + y0 + u] - kScaleProd, ok[u]);
+            o[u] = sub_round_fast(yv[y0 + u], h[y0 + u], Ar + Bexp[ob * kOut + ep * 4 + y0 + u] - kScaleProd, ok[u]);
         }
 #pragma unroll
         for (int u = 0; u < kRoundPair<W>; ++u) {
-          const int y = y0 + u, j = ep * 4 + y;
+          const int y = y0 + u, j = ob * kOut + ep * 4 + y;
           if (j < kout && grow < n) {
             if (!ok[u]) o[u] = round_general(update, yv[y], h[y], Ar + Bexp[j] - kScaleProd);
             if (rbad || Bbad[j] || bad) o[u] = __longlong_as_double(0x7ff8000000000000ll);
@@ -498,6 +523,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int g = 0; g < NG; ++g, ++G) {
         const int b = G & 1;
+        if constexpr (KO > 1) {
+          if (g == NG - 1 && Tprev >= 0) {
+            // one accumulator per output block: the previous tile's MMAs are
+            // done (its last group was waited for before group 1 of this tile
+            // was stored), so its epilogue reads them here and releases them
+            // to this tile's MMAs
+            tc_fence_after();
+#pragma unroll 1
+            for (int ob = 0; ob < KO; ++ob) epilogue_block(Tprev, iprev, ob);
+            tc_fence_before();
+            mbar_arrive(tfb);
+          }
+        }
         if (G >= 2) mbar_wait(fb0 + 8u * b, (unsigned)((G - 2) >> 1) & 1u, &bad);  // MMAs of group G - 2 done
         store_group_rt<W>(g, adig_s + (unsigned)b * GS * SLAB_A + dofs, SLAB_A, P, sg, near);
         fence_proxy_async();
@@ -510,10 +548,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       // the previous tile's MMAs completed (its last group was waited for before
       // this tile's second group was written): its epilogue overlaps this tile's MMAs
-      if (Tprev >= 0) {
-        tc_fence_after();
-        epilogue(Tprev, iprev);
-        tc_fence_before();
+      if constexpr (KO == 1) {
+        if (Tprev >= 0) {
+          tc_fence_after();
+          epilogue_block(Tprev, iprev, 0);
+          tc_fence_before();
+        }
       }
       bar_conv<kConvThreads>();  // row exponents of buffer (i - 1) & 1 are free again
       Tprev = T;
@@ -522,7 +562,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (Tprev >= 0) {  // the last tile
       mbar_wait(fb0 + 8u * ((G - 1) & 1), (unsigned)((G - 1) >> 1) & 1u, &bad);
       tc_fence_after();
-      epilogue(Tprev, iprev);
+      if constexpr (KO == 1) {
+        epilogue_block(Tprev, iprev, 0);
+      } else {
+#pragma unroll 1
+        for (int ob = 0; ob < KO; ++ob) epilogue_block(Tprev, iprev, ob);
+      }
       tc_fence_before();
     }
     if constexpr (kStageValues<W>) asm volatile("cp.async.wait_all;" ::: "memory");  // the last (empty) prefetch
@@ -535,26 +580,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int W>
+template <int W, int KO>
 size_t smem_bytes() {
   constexpr int KP = 4 * W;
   const size_t sbo = 16u * KP;
-  const size_t b = 32 * sbo, a = 2 * kGroupSlabs<W> * 16 * sbo, small = (4 * kRows + 2 * kOut) * sizeof(int);
+  const size_t b = KO * 32 * sbo, a = 2 * kGroupSlabs<W> * 16 * sbo, small = (4 * kRows + 2 * kOut * KO) * sizeof(int);
   const size_t stage = kStageValues<W> ? (size_t)W * kConvThreads * sizeof(double) : 0;
   return std::max(b + a + small + stage, kMinSmem);
 }
 
-template <int W>
+template <int W, int KO = 1>
 cudaError_t launch_w(bool update, int64_t n, int kin, const double* A, int64_t lda, int kout, const double* Bh,
                      const double* Bl, int ldb, bool tri, const double* Yin, int64_t ldyin, double* Out, int64_t ldo,
                      const int* gate, cudaStream_t st, int ctas) {
-  const size_t smem = smem_bytes<W>();
-  cudaError_t e = set_dyn_smem(umma_rowprod_kernel<W>, smem);
+  const size_t smem = smem_bytes<W, KO>();
+  cudaError_t e = set_dyn_smem(umma_rowprod_kernel<W, KO>, smem);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = (n + kRows - 1) / kRows;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, ctas > 0 ? ctas : 152));
-  umma_rowprod_kernel<W><<<grid, kThreads, smem, st>>>(update ? 1 : 0, n, kin, A, lda, kout, Bh, Bl, ldb,
-                                                            tri ? 1 : 0, Yin, ldyin, Out, ldo, gate);
+  umma_rowprod_kernel<W, KO><<<grid, kThreads, smem, st>>>(update ? 1 : 0, n, kin, A, lda, kout, Bh, Bl, ldb,
+                                                                tri ? 1 : 0, Yin, ldyin, Out, ldo, gate);
   return cudaGetLastError();
 }
 
@@ -565,7 +610,7 @@ cudaError_t umma_rowprod_take_wait_record(unsigned* out) { return take_wait_reco
 bool umma_rowprod_supported(int kin, int kout) {
   const char* e = getenv("EO_DD_ROW_ENGINE");
   if (e && e[0] == 'i') return false;
-  if (kin < 1 || kin > 64 || kout < 1 || kout > kOut) return false;
+  if (kin < 1 || kin > 64 || kout < 1 || kout > 2 * kOut || (kout > kOut && kin > 32)) return false;
   // Small products run faster on the integer limbs: a tile's fixed cost
   // (15 digit slabs, 16 padded outputs) dominates below kin max(kout, 4) =
   // 128 (measured on 4e6 rows: kin = kout = 4 0.38 vs 1.29 ms, kin = 10,
@@ -580,6 +625,8 @@ cudaError_t launch_umma_rowprod(bool update, int64_t n, int kin, const double* A
                                 int64_t ldyin, double* Out, int64_t ldo, const int* gate, cudaStream_t st,
                                 int ctas) {
   if (n <= 0) return cudaSuccess;
+  if (kout > kOut)  // two blocks of output columns (kin <= 32): the inputs converted once
+    return launch_w<8, 2>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
   if (kin <= 16)
     return launch_w<4>(update, n, kin, A, lda, kout, Bh, Bl, ldb, tri, Yin, ldyin, Out, ldo, gate, st, ctas);
   if (kin <= 32)
