@@ -544,8 +544,9 @@ def test_project_apply_nonfinite_and_padding(eo, ctx, monkeypatch, engine):
 
 @pytest.mark.parametrize("n,k", [(60_000, 16), (30_001, 33), (20_000, 64), (9_000, 17)])
 def test_cholqr_update_engines_agree(eo, ctx, monkeypatch, n, k):
-    """One DD CholQR pass with either row engine for Q = X R^-1 (k > 16: the
-    tensor cores in groups of 16 output columns through a scratch copy)."""
+    """One DD CholQR pass with either row engine for Q = X R^-1 (17 <= k <= 32:
+    the tensor cores in one pass over two 16-column output blocks; k > 32: in
+    groups of 16 output columns through a scratch copy)."""
     x = synth.conditioned(n, k, 1e6, 81)
     qs = {}
     for engine in ("int", "umma"):
@@ -955,7 +956,8 @@ def test_invalid_arguments_are_rejected(eo, ctx):
 
 @pytest.mark.parametrize("k", [24, 32, 64])
 def test_svqb_update_engines_agree(eo, ctx, monkeypatch, k):
-    """SVQB's full Z with k > 16: grouped tensor-core update vs integer limbs, both against the oracle."""
+    """SVQB's full Z with k > 16 (24 and 32: one tensor-core pass over two output
+    blocks; 64: groups of 16 output columns) vs integer limbs, both against the oracle."""
     n, kappa = 12_000, 1e4
     x = synth.conditioned(n, k, kappa, 83 + k)
     qs = {}
