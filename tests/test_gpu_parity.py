@@ -491,12 +491,13 @@ def _random_dd(g, rows, cols):
 @pytest.mark.parametrize("engine", ["int", "umma"])
 @pytest.mark.parametrize("n,kv,k", [(1, 64, 16), (127, 16, 1), (129, 17, 7), (255, 32, 16), (1000, 33, 2),
                                     (4097, 48, 16), (2049, 1, 16), (3333, 64, 5), (1000, 64, 33), (5000, 16, 64),
-                                    (257, 8, 17), (4099, 32, 32), (600, 20, 24)])
+                                    (257, 8, 17), (4099, 32, 32), (600, 20, 24), (3001, 4, 20), (1025, 3, 32)])
 def test_project_apply_shapes_against_oracle(eo, ctx, monkeypatch, engine, n, kv, k):
     """Row tails, every tile width of the tensor-core row engine (kv <= 16, 32,
     64), one and two blocks of 16 output columns (k <= 32 with kv <= 32: the
-    inputs converted once) and odd output counts, with a genuine
-    double-double C."""
+    inputs converted once), the integer limbs' register kernel with one to
+    eight output groups per row (kv <= 8; 20 outputs leave three of eight
+    groups idle) and odd output counts, with a genuine double-double C."""
     monkeypatch.setenv("EO_DD_ROW_ENGINE", engine)
     torch = torch_mod()
     g = synth.rng(90 + kv + k)
