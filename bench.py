@@ -55,12 +55,14 @@ def parse():
                     help="skip the runs of the other workloads that the default line summarises")
     ap.add_argument("--no-comparators", action="store_true",
                     help="skip the FP64, DD-EFT, same-accuracy and single-block comparisons (profiling runs)")
-    ap.add_argument("--workload", choices=["project", "iterated", "batched", "serve", "sweep", "single"],
+    ap.add_argument("--workload", choices=["project", "iterated", "batched", "serve", "sweep", "single", "update"],
                     default="project",
                     help="project: the default line; iterated: the iterated two-phase algorithm on the "
                          "runtime-figure shapes (n = 8e6 unless --n is given); batched: many SVQB blocks of "
                          "uneven n and k in one graph launch; serve: the request server under Poisson arrivals; "
-                         "sweep: the Gram precision sweep (n = 32e6, k 1..64); single: one 100,000 x 8 CholQR")
+                         "sweep: the Gram precision sweep (n = 32e6, k 1..64); single: one 100,000 x 8 CholQR; "
+                         "update: the compensated update Q = X R^-1 alone (one CholQR pass, M given) for --ks")
+    ap.add_argument("--ks", default="4,8,16,32", help="column counts of the update workload")
     ap.add_argument("--blocks", type=int, default=512, help="blocks of the batched workload")
     ap.add_argument("--clients", type=int, default=256, help="resident bases of the serving workload")
     ap.add_argument("--requests", type=int, default=2000, help="requests of the serving trace")
@@ -1224,6 +1226,50 @@ def run_single(a):
         print(json.dumps(out), flush=True)
 
 
+UPDATE_METRIC = "compensated update Q = X R^-1 (one CholQR pass with M given): HBM GB/s per k; p50/p99"
+
+
+def run_update(a):
+    """The row engines alone: one compensated CholQR pass of X (n x k, seeded
+    Gaussian on the device) with its Gram matrix given, i.e. the k x k
+    factorization and the update Q = X R^-1, which reads and writes X once
+    (16 n k algorithmic bytes), restored from a device copy before each
+    call (outside the timed region)."""
+    import torch
+    import paper_1806_01036_gb300 as eo
+
+    ws, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    ctx = eo.Context(local)
+    stream = torch.cuda.current_stream(dev)
+    n = a.n
+    res = {}
+    for k in [int(t) for t in a.ks.split(",") if t]:
+        g = torch.Generator(device=dev).manual_seed(20180604 + 31 * k + rank)
+        X0 = torch.randn((k, n), device=dev, dtype=torch.float64, generator=g).t()
+        X = torch.empty_like(X0.t()).t()
+        mh, ml = eo.gram(ctx, X0, prec=eo.DD)
+        ts = []
+        for it in range(max(1, a.warmup) + max(3, a.steps)):
+            X.copy_(X0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, info = eo.cholqr(ctx, X, passes=1, prec=eo.DD, M=(mh, ml))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if it >= max(1, a.warmup):
+                ts.append(e0.elapsed_time(e1))
+        p50 = float(np.percentile(ts, 50))
+        res[str(k)] = {"p50_ms": p50, "p99_ms": float(np.percentile(ts, 99)), "gbs": 16 * n * k / p50 / 1e6,
+                       "cholesky_info": int(info.item())}
+        del X0, X
+    out = {"metric": UPDATE_METRIC, "n_gpus": ws, "dtype": "f64", "data": "synthetic (seeded Gaussian on the GPU)",
+           "config": {"workload": f"compensated update alone: X {n:,} x k, k in {a.ks}", "n": n},
+           "results": res}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -1238,6 +1284,8 @@ def main():
         run_sweep(a)
     elif a.workload == "single":
         run_single(a)
+    elif a.workload == "update":
+        run_update(a)
     else:
         run_eo(a)
 
