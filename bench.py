@@ -645,8 +645,9 @@ def other_configs():
     """The other workloads, each in its own process after the step's
     measurements (outside its timed region), summarised: the precision sweep,
     the batched SVQB graph, serving at 2,000 requests/s offered and at 0.8x
-    the capacity that run measured, and the iterated two-phase algorithm.
-    A workload that fails or runs out of time is reported as such."""
+    the capacity that run measured, the iterated two-phase algorithm and the
+    compensated update alone per k.  A workload that fails or runs out of
+    time is reported as such."""
     def run(args, timeout=420):
         t0 = time.time()
         try:
@@ -713,6 +714,12 @@ def other_configs():
                 [r["kv"], r["k"], round(r["fp64"]["ms"], 2), round(r["dd"]["ms"], 2), r["dd"]["iterations"]]
                 for r in d["results"]]})
     out["iterated"] = info
+    d, info = run(["--workload", "update"])
+    if d:
+        summarise(info, lambda: {
+            "command": "python bench.py --workload update", "config": d["config"]["workload"],
+            "p50_ms_and_gbs_per_k": {k: [round(r["p50_ms"], 3), round(r["gbs"], 1)] for k, r in d["results"].items()}})
+    out["update"] = info
     return out
 
 

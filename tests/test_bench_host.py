@@ -87,6 +87,7 @@ def test_other_configs_summarises_each_workload(bench, monkeypatch):
         "serve": {"config": {"workload": "serve"}, "value": 500.0, "gbs": 900.0, "p50_ms": 9.0, "p99_ms": 40.0,
                   "queue_p50_ms": 0.01, "queue_p99_ms": 10.0, "orth_err_max": 1e-18, "cross_err_max": 1e-18},
         "iterated": {"config": {"workload": "iterated"}},  # no results: a summary error
+        "update": {"config": {"workload": "update"}, "results": {"16": {"p50_ms": 0.9054, "gbs": 1130.04}}},
     }
     seen = []
 
@@ -108,6 +109,7 @@ def test_other_configs_summarises_each_workload(bench, monkeypatch):
     assert ["--workload", "serve", "--rate", "400.0", "--requests", "1500"] in seen
     assert out["serve_at_0.8_capacity"]["offered_per_s"] == 400.0
     assert "error" in out["iterated"]
+    assert out["update"]["p50_ms_and_gbs_per_k"] == {"16": [0.905, 1130.0]}
 
     monkeypatch.setattr(subprocess, "run", lambda cmd, **kw: Done("", rc=1))
     out = bench.other_configs()
