@@ -32,7 +32,8 @@
 // alternating shared-memory buffers; one warp issues the group's MMAs and
 // commits them to an mbarrier per buffer; TMEM holds two accumulators, so
 // the epilogue of tile i - 1 (tcgen05.ld, exact rounding, stores) runs
-// while the tensor cores work on tile i.  The projection's Y of a tile is
+// while the tensor cores work on tile i (with two blocks of 16 output
+// columns, one accumulator each: see the kernel).  The projection's Y of a tile is
 // prefetched into L2 a tile ahead and loaded before its epilogue reads
 // TMEM.  Every wait is bounded (the outputs of a CTA whose wait ran out are
 // NaN).  Each tile's loads precede its own stores, and no tile is written
