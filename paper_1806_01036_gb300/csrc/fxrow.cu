@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   int64_t w0 = warp * rpw;  // first row of this warp's step (uniform over the warp)
   double v[KIN];
   load_row(w0 + (lane >> lgng), v);
+  __syncwarp();  // every lane's loads of the first step's rows precede its stores
   for (; w0 < n; w0 += slots) {
     const int64_t r = w0 + (lane >> lgng);
     double vn[KIN];
