@@ -858,3 +858,29 @@ def test_svqb_rotated_orthogonal_columns_and_rank():
     assert rank0 == 3
     assert not np.any(zh0[:, 0]) and not np.any(q0[:, 0])
     assert oracle.orth_err(q0[:, 1:])[0] < 1e-15
+
+
+@pytest.mark.parametrize("a", [0.5, -0.25, 0.9])
+def test_svqb_rotated_2x2_closed_form(a):
+    """M = D^-1 [[1, a], [a, 1]] D^-1 with D = diag(1/2, 4): D M D has
+    eigenvalues 1 - a and 1 + a with eigenvectors (1, -1)/sqrt 2 and
+    (1, 1)/sqrt 2, so |Z| = |D U Lambda^-1/2| is known in closed form, the
+    columns follow the eigenvalues in ascending order, the column of
+    (1, -1) has entries of opposite sign and the column of (1, 1) two
+    positive ones (its largest entry is positive).  (Which entry of (1, -1)
+    is positive is a tie that rounding decides.)"""
+    import mpmath as mp
+    mp.mp.prec = 120
+    d = np.array([0.5, 4.0])
+    m = np.asfortranarray(np.array([[1.0, a], [a, 1.0]]) / d[:, None] / d[None, :])  # exact: powers of two
+    x = np.asfortranarray(np.linalg.cholesky(m).T)  # any X: M is passed explicitly
+    _, (zh, zl), rank = oracle.svqb_rotated(x, m=(m, None))
+    assert rank == 2
+    lam = sorted([1 - mp.mpf(a), 1 + mp.mpf(a)])
+    for j in range(2):
+        want = [mp.mpf(d[i]) / mp.sqrt(2) / mp.sqrt(lam[j]) for i in range(2)]
+        got = [mp.mpf(float(zh[i, j])) + mp.mpf(float(zl[i, j])) for i in range(2)]
+        assert max(abs(abs(got[i]) - want[i]) for i in range(2)) < mp.mpf(2) ** -100 * max(want)
+    j_anti = 0 if a > 0 else 1  # the eigenvalue 1 - a of (1, -1) is the smaller when a > 0
+    assert zh[0, j_anti] * zh[1, j_anti] < 0
+    assert zh[0, 1 - j_anti] > 0 and zh[1, 1 - j_anti] > 0
